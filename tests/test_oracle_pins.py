@@ -1,0 +1,359 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle itself:
+closed forms, library routines for special cases, invariants of the kinetic
+model, exact fixed points and the two limits of plane Couette flow.
+
+Each test names the passage of arXiv 1709.01819 it checks.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import integrate, special
+
+from oracle import oracle as O
+from paper_1709_01819_gb300 import inputs as I
+
+
+# ---------------------------------------------------------------------------
+# velocity quadrature (Section 2.2, closing paragraph)
+# ---------------------------------------------------------------------------
+
+def test_trapezoid_and_simpson_rules_match_library():
+    f = lambda x: np.exp(-0.7 * x * x) * (1 + 0.3 * x + 0.1 * x ** 3)
+    for n in (9, 32, 89):
+        x, w = O.quadrature(I.NC_TRAP, n, -4.0, 4.0)
+        assert np.allclose(x, np.linspace(-4, 4, n), rtol=0, atol=1e-14)
+        assert abs(np.dot(w, f(x)) - np.trapezoid(f(x), x)) < 1e-13
+    for n in (9, 89):
+        x, w = O.quadrature(I.NC_SIMPSON, n, -15.0, 15.0)
+        assert abs(np.dot(w, f(x)) - integrate.simpson(f(x), x=x)) < 1e-12
+        # Simpson is exact on cubics
+        p = lambda x: 1 + 2 * x - 0.5 * x ** 2 + 0.25 * x ** 3
+        exact = 30 + (-0.5) * (2 * 15 ** 3 / 3)
+        assert abs(np.dot(w, p(x)) - exact) < 1e-9 * abs(exact)
+    with pytest.raises(ValueError):
+        O.quadrature(I.NC_SIMPSON, 32, -4, 4)
+
+
+@pytest.mark.parametrize("n", [1, 2, 8, 28, 60, 90])
+def test_gauss_hermite_matches_numpy_hermgauss(n):
+    x, w = O.quadrature(I.GAUSS_HERMITE, n, 0.0, 1.0)
+    xr, wr = np.polynomial.hermite.hermgauss(n)
+    assert np.allclose(x, xr, rtol=0, atol=1e-12 * max(1, abs(xr).max()))
+    # the oracle returns plain-integration weights w = W e^{x^2}
+    assert np.allclose(w * np.exp(-x * x), wr, rtol=1e-10, atol=1e-300)
+
+
+@pytest.mark.parametrize("n", [5, 28])
+def test_gauss_hermite_exact_on_even_moments(n):
+    x, w = O.quadrature(I.GAUSS_HERMITE, n, 0.0, 1.0)
+    W = w * np.exp(-x * x)
+    for m in range(n):
+        exact = special.gamma(m + 0.5)
+        assert abs(np.dot(W, x ** (2 * m)) - exact) <= 1e-12 * exact * (1 + m)
+
+
+# ---------------------------------------------------------------------------
+# kinetic model: Eq. (2), (4), (5), (20)
+# ---------------------------------------------------------------------------
+
+def _small_problem(**kw):
+    base = dict(ncell=4, U=0.0, Kn=0.1, nv=kw.pop("nv", 48), vmax=kw.pop("vmax", 8.0))
+    p = I.couette(**base)
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def test_maxwellian_discrete_moments_match_closed_forms():
+    """Eq. (4): moments of the reduced Maxwellian give rho, rho U, rho V, rho E."""
+    o = O.Oracle(_small_problem(nv=64, vmax=8.0))
+    ux, uy, w = o.velocity_grid()
+    rho, U, V, RT = 1.3, 0.12, -0.07, 0.61
+    G, H = o.equilibrium(rho, U, V, RT)
+    K = 1
+    assert abs(np.dot(w, G) - rho) < 1e-12
+    assert abs(np.dot(w, ux * G) - rho * U) < 1e-12
+    assert abs(np.dot(w, uy * G) - rho * V) < 1e-12
+    E = 0.5 * np.dot(w, (ux ** 2 + uy ** 2) * G + H)
+    assert abs(E - 0.5 * rho * (U * U + V * V + (K + 2) * RT)) < 1e-12
+
+
+@pytest.mark.parametrize("K", [1, 3])
+def test_reduced_H_equals_internal_energy_integral(K):
+    """Eq. (5): H = int xi^2 f dxi over K internal dimensions of Eq. (2)."""
+    p = _small_problem(nv=16, vmax=4.0)
+    p.K = K
+    o = O.Oracle(p)
+    ux, uy, _ = o.velocity_grid()
+    rho, U, V, RT = 0.9, 0.2, 0.1, 0.45
+    G, H = o.equilibrium(rho, U, V, RT)
+    lam = 1 / (2 * RT)
+    k = 37
+    c2 = (ux[k] - U) ** 2 + (uy[k] - V) ** 2
+    pref = rho * (lam / math.pi) ** ((K + 2) / 2) * math.exp(-lam * c2)
+    # integrate over the K-dimensional internal space in spherical shells
+    area = 2 * math.pi ** (K / 2) / special.gamma(K / 2)
+    g_int, _ = integrate.quad(lambda r: area * r ** (K - 1) * math.exp(-lam * r * r), 0, 50)
+    h_int, _ = integrate.quad(lambda r: area * r ** (K + 1) * math.exp(-lam * r * r), 0, 50)
+    assert abs(G[k] - pref * g_int) < 1e-12 * G[k]
+    assert abs(H[k] - pref * h_int) < 1e-12 * H[k]
+
+
+def test_shakhov_correction_invariants():
+    """Eq. (20) (reading: derived from the full Shakhov model for D=2+K):
+    the correction carries no mass, momentum or energy and its heat flux is
+    (1-Pr) q; Pr = 1 gives back the Maxwellian."""
+    p = _small_problem(nv=161, vmax=10.0)
+    p.shakhov, p.Pr = 1, 2.0 / 3.0
+    o = O.Oracle(p)
+    ux, uy, w = o.velocity_grid()
+    rho, U, V, RT, qx, qy = 1.2, 0.1, -0.05, 0.6, 0.02, -0.013
+    Gs, Hs = o.equilibrium(rho, U, V, RT, qx, qy)
+    G0, H0 = o.equilibrium(rho, U, V, RT, 0.0, 0.0)
+    dG, dH = Gs - G0, Hs - H0
+    assert abs(np.dot(w, dG)) < 1e-13
+    assert abs(np.dot(w, ux * dG)) < 1e-13
+    assert abs(np.dot(w, uy * dG)) < 1e-13
+    assert abs(0.5 * np.dot(w, (ux ** 2 + uy ** 2) * dG + dH)) < 1e-13
+    cx, cy = ux - U, uy - V
+    e = (cx ** 2 + cy ** 2) * Gs + Hs
+    assert abs(0.5 * np.dot(w, cx * e) - (1 - p.Pr) * qx) < 1e-12
+    assert abs(0.5 * np.dot(w, cy * e) - (1 - p.Pr) * qy) < 1e-12
+    p.Pr = 1.0
+    o1 = O.Oracle(p)
+    G1, H1 = o1.equilibrium(rho, U, V, RT, qx, qy)
+    assert np.array_equal(G1, G0) and np.array_equal(H1, H0)
+
+
+def test_vhs_reference_viscosity():
+    """Eq. (36) with Bird's VHS mean free path: mu_ref = 15 sqrt(2 pi RT) Kn / (2(5-2w)(7-2w));
+    checked through tau = mu/p of a uniform state at T_ref."""
+    for omega, coef in ((0.5, 0.553892), (0.81, 0.731033)):
+        p = _small_problem(nv=8, vmax=4.0)
+        p.omega, p.Kn = omega, 0.3
+        o = O.Oracle(p)
+        o.init_uniform(1.0, 0.0, 0.0, 1.0)
+        _, _, _, tau = o.cell_prep()
+        mu = tau[0] * 1.0 * 0.5
+        assert abs(mu - coef * 0.3) < 2e-6 * 0.3
+
+
+def test_transform_coefficients_by_composition():
+    """Eq. (10) inverted then Eq. (12): fb+ from f~ through f."""
+    p = I.cavity(4, Kn=0.05, U=0.1, nv=12)
+    o = O.Oracle(p)
+    G, H, W = I.random_state(p, seed=3)
+    o.set_state(G, H, W)
+    fbG, fbH, q, tau = o.cell_prep()
+    dt = o.dt
+    h = dt / 2
+    for c in (0, 5, 15):
+        rho = W[c, 0]
+        U, V = W[c, 1] / rho, W[c, 2] / rho
+        RT = (2 * W[c, 3] / rho - U * U - V * V) / 3
+        Ge, He = o.equilibrium(rho, U, V, RT, q[c, 0], q[c, 1])
+        t = tau[c]
+        f_G = (2 * t * G[c] + dt * Ge) / (2 * t + dt)          # Eq. (10) first line, solved for f
+        f_H = (2 * t * H[c] + dt * He) / (2 * t + dt)
+        ref_G = f_G + (h / 2) * (Ge - f_G) / t                 # Eq. (12), second line
+        ref_H = f_H + (h / 2) * (He - f_H) / t
+        assert np.allclose(fbG[c], ref_G, rtol=1e-13, atol=1e-15)
+        assert np.allclose(fbH[c], ref_H, rtol=1e-13, atol=1e-15)
+
+
+def test_cell_heat_flux_from_transformed_distribution():
+    """f~ = f - (dt/2) Omega with the Shakhov heat-flux relaxation rate Pr/tau gives
+    q = 2 tau q~/(2 tau + dt Pr): rebuild q~ from q and compare with the moment of f~."""
+    p = I.cavity(4, Kn=0.05, U=0.1, nv=24, vmax=6.0)
+    o = O.Oracle(p)
+    G, H, W = I.random_state(p, seed=5)
+    o.set_state(G, H, W)
+    _, _, q, tau = o.cell_prep()
+    ux, uy, w = o.velocity_grid()
+    c = 7
+    rho = W[c, 0]
+    U, V = W[c, 1] / rho, W[c, 2] / rho
+    cx, cy = ux - U, uy - V
+    e = (cx ** 2 + cy ** 2) * G[c] + H[c]
+    qt = np.array([0.5 * np.dot(w, cx * e), 0.5 * np.dot(w, cy * e)])
+    # q~ = q - (dt/2)(-Pr q / tau)
+    assert np.allclose(q[c] * (1 + o.dt * p.Pr / (2 * tau[c])), qt, rtol=1e-12, atol=1e-16)
+
+
+# ---------------------------------------------------------------------------
+# reconstruction: Eq. (14)-(17)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("mesh", ["tanh", "ogrid"])
+def test_least_squares_gradient_exact_on_linear_fields(mesh):
+    if mesh == "tanh":
+        p = I.cavity(12, stretch_beta=1.5, nv=4)
+    else:
+        p = I.cylinder(ntheta=24, nr=10, nv=5, vmax=4.0)
+    o = O.Oracle(p)
+    cx, cy, _ = o.geometry()
+    a, b, c = 0.37, -1.2, 0.8
+    g = o.ls_gradient(a + b * cx + c * cy)
+    assert np.allclose(g[:, 0], b, atol=1e-10)
+    assert np.allclose(g[:, 1], c, atol=1e-10)
+
+
+def test_venkatakrishnan_theta():
+    th = O.venkat_theta
+    assert th(0.0) == 0.0
+    assert abs(th(1.0) - 0.75) < 1e-16
+    assert abs(th(1e8) - 1.0) < 1e-7
+    assert abs(th(2.0) - 1.0) < 1e-16
+    xs = np.linspace(0, 2, 200)
+    vals = [th(x) for x in xs]
+    assert all(np.diff(vals) > 0)  # monotone up to x = 2, where it reaches 1
+    assert max(th(x) for x in np.linspace(2, 50, 500)) < 1.1  # mild overshoot, no cap in Eq. (17)
+
+
+def test_geometry_of_ogrid_is_closed_and_positive():
+    p = I.cylinder(ntheta=40, nr=12, nv=5, vmax=4.0)
+    o = O.Oracle(p)
+    _, _, area = o.geometry()
+    assert (area > 0).all()
+    r0, r1 = 1.0, 15.0
+    ring = 0.5 * 40 * (math.sin(2 * math.pi / 40)) * (r1 ** 2 - r0 ** 2)  # polygon annulus
+    assert abs(area.sum() - ring) < 1e-9 * ring
+
+
+# ---------------------------------------------------------------------------
+# whole-iteration pins
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("case", ["cavity", "couette", "cylinder"])
+def test_uniform_maxwellian_is_a_fixed_point(case):
+    """A gas at rest in equilibrium with resting walls at its own temperature stays put."""
+    if case == "cavity":
+        p = I.cavity(8, Kn=0.075, U=0.0, nv=16)
+    elif case == "couette":
+        p = I.couette(8, U=0.0, Kn=0.1, nv=16)
+    else:
+        p = I.cylinder(ntheta=16, nr=6, nv=9, vmax=6.0, Ma=0.0)
+        p.init = (1.0, 0.0, 0.0, 1.0)
+    o = O.Oracle(p)
+    o.init_uniform()
+    G0, H0, W0 = o.get_state()
+    o.iterate(30)
+    G, H, W = o.get_state()
+    assert np.abs(G - G0).max() <= 1e-14 * np.abs(G0).max()
+    assert np.abs(H - H0).max() <= 1e-14 * np.abs(H0).max()
+    assert np.abs(W - W0).max() <= 1e-14
+
+
+def test_explicit_dugks_conserves_mass_in_a_periodic_box():
+    """Eq. (21): fluxes telescope; with a discrete-mass-normalised equilibrium the
+    BGK collision of Eq. (10) conserves mass exactly."""
+    X, Y = I.uniform_nodes(6, 5)
+    bc = [(I.BC_PERIODIC, 0, 0, 0, 0)] * 4
+    p = I.Problem(X, Y, bc, I.NC_TRAP, 12, 12, (-4, 4, -4, 4), K=1, Pr=1.0, Kn=0.05,
+                  shakhov=0, flags=1)
+    o = O.Oracle(p)
+    G, H, W = I.random_state(p, seed=11)
+    o.set_state(G, H, W)
+    _, _, area = o.geometry()
+    _, _, w = o.velocity_grid()
+    m0 = np.dot(area, G @ w)
+    o.explicit(40)
+    G1, _, _ = o.get_state()
+    m1 = np.dot(area, G1 @ w)
+    assert abs(m1 - m0) <= 1e-13 * m0
+    assert np.abs(G1 - G).max() > 1e-4  # the state did evolve
+
+
+def test_macroscopic_residual_mass_telescopes_in_a_closed_cavity():
+    """Eq. (27): interior face fluxes cancel pairwise and the walls are impermeable."""
+    p = I.cavity(10, Kn=0.075, U=0.15, nv=16)
+    o = O.Oracle(p)
+    o.init_uniform()
+    o.iterate(5)
+    rw = o.rw()
+    assert abs(rw[:, 0].sum()) <= 1e-14 * np.abs(rw[:, 0]).sum() + 1e-18
+    assert np.abs(rw[:, 0]).sum() > 0
+
+
+def test_couette_continuum_limit_navier_stokes():
+    """Small Kn: linear velocity profile, antisymmetric about the mid-plane, and the
+    Navier-Stokes viscous-heating parabola T = T_w + a y(1-y) with
+    a = Pr (du/dy)^2 / ((D+2) RT_ref), D = 2 + K (temperature in T_ref units)."""
+    p = I.couette(16, U=0.1, Kn=2e-3, nv=16, vmax=4.0, cfl_imp=1000.0)
+    o = O.Oracle(p)
+    o.init_uniform()
+    res = o.iterate(6000)
+    assert res[-1] < 1e-8 * res[0]
+    m = o.moments()
+    u, T = m[:, 1], m[:, 3]
+    y = (np.arange(16) + 0.5) / 16
+    assert np.abs(u + u[::-1]).max() < 1e-6  # limited by the slow diffusive mode's convergence
+    assert np.abs(T - T[::-1]).max() < 1e-6
+    slope = np.polyfit(y, u, 1)[0]
+    assert abs(slope - 0.2) < 0.01 * 0.2            # velocity slip is O(Kn)
+    assert np.abs(np.diff(u, 2)).max() < 1e-4 * 0.1  # linear
+    # Eq. (2001) L2 error against the no-slip analytic profile
+    ue = 0.1 * (2 * y - 1)
+    assert np.sqrt(np.sum((u - ue) ** 2) / np.sum(ue ** 2)) < 1e-2
+    D = 3
+    a_ns = p.Pr * slope ** 2 / ((D + 2) * 0.5)
+    a_fit = -np.polyfit(y, T, 2)[0]
+    assert abs(a_fit - a_ns) < 0.02 * a_ns
+
+
+def test_couette_free_molecular_shear_matches_closed_form():
+    """Very large Kn: each half-range is the Maxwellian of the wall it came from,
+    so the shear stress is the discrete half-range closed form, and close to the
+    continuous value -rho U / sqrt(pi)."""
+    U = 0.1
+    p = I.couette(8, U=U, Kn=1e6, nv=32, vmax=4.0, cfl_imp=1000.0)
+    o = O.Oracle(p)
+    o.init_uniform()
+    res = o.iterate(150)
+    # W couples to f~ only through the vanishing collision term here, so the
+    # macroscopic residual stalls near 1e-7 while f~ itself has converged
+    assert res[-1] < 1e-6 * res[0]
+    ux, uy, w = o.velocity_grid()
+    lam = 1.0
+    M = lambda Uw: (lam / math.pi) * np.exp(-lam * ((ux - Uw) ** 2 + uy ** 2))
+    up, dn = uy > 0, uy < 0
+    num = np.sum((w * ux * uy * M(-U))[up]) + np.sum((w * ux * uy * M(U))[dn])
+    den = np.sum((w * M(-U))[up]) + np.sum((w * M(U))[dn])
+    closed = num / den
+    G, _, _ = o.get_state()
+    rho_cells = G @ w
+    phi = o.face_phi()
+    f = o.faces()
+    inner = (f["L"] >= 0) & (f["R"] >= 0) & (np.abs(f["ny"]) > 0.5)
+    pxy = phi[inner, 1] / f["S"][inner]
+    assert np.allclose(pxy, pxy[0], rtol=1e-8)
+    assert abs(pxy[0] / rho_cells.mean() - closed) < 1e-6 * abs(closed)
+    assert abs(closed + U / math.sqrt(math.pi)) < 0.01 * U / math.sqrt(math.pi)
+
+
+def test_explicit_and_implicit_reach_the_same_steady_state():
+    """Eq. (21) marched in time and the implicit iteration of Eq. (22)-(32) share the
+    same fixed point up to the quadrature error in the discrete equilibrium."""
+    # 24 points on [-6, 6]: the quadrature error of the discrete equilibrium is ~1e-13
+    kw = dict(ncell=12, U=0.1, Kn=0.1, nv=24, vmax=6.0, cfl_imp=1000.0)
+    pi = I.couette(**kw)
+    pi.flags = 1
+    oi = O.Oracle(pi)
+    oi.init_uniform()
+    res = oi.iterate(500)
+    assert res[-1] < 1e-13 * res[0]
+    mi = oi.moments()
+    Gi, _, _ = oi.get_state()
+    _, _, w = oi.velocity_grid()
+    mass = (Gi @ w).mean()
+    pe = I.couette(**kw)
+    pe.flags = 1
+    oe = O.Oracle(pe)
+    oe.init_uniform(rho=mass)
+    oe.explicit(9000)
+    me = oe.moments()
+    u_i, u_e = mi[:, 1], me[:, 1]
+    T_i, T_e = mi[:, 3], me[:, 3]
+    assert np.linalg.norm(u_i - u_e) / np.linalg.norm(u_i) < 1e-9
+    assert np.linalg.norm(T_i - T_e) / np.linalg.norm(T_i) < 1e-9
