@@ -1,0 +1,341 @@
+"""Benchmark of one IDUGKS iteration (the whole hot path) on one GB300.
+
+Workload (N=1): the 64 x 64 lid-driven cavity (Shakhov Pr=2/3, Kn=0.075, lid
+0.15, 32 x 32 trapezoid velocities on [-4,4]^2, CFL 1000), mixed precision
+(f in float32; moments, predictor, residual in float64).  A step is one
+iteration: cell prep, interior and boundary faces, macroscopic LU-SGS
+predictor, micro LU-SGS forward and backward sweeps.  The f state (33.6 MB)
+fits in L2, so L2 is flushed (a 256 MB write) between timed steps.
+
+Prints one JSON line (metric: cell-velocity updates per second).
+--impl reference times the FP64 CPU oracle on the host cores instead.
+Under torchrun (N > 1) every rank solves its own copy of the cavity (the
+method has no data-parallel exchange: replicas only) and rank 0 reports the
+aggregate over ranks with the max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_1709_01819_gb300 import inputs as I  # noqa: E402
+
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+KERNELS = ["k_cell_prep", "k_face_interior", "k_face_boundary", "k_macro", "k_sweep_fwd", "k_sweep_bwd"]
+
+
+def workload(name: str) -> I.Problem:
+    if name == "cavity64":
+        return I.cavity_c2()
+    if name == "couette64":
+        return I.couette_c1()
+    if name == "cavity128":
+        return I.cavity_c3()
+    if name == "cylinder":
+        return I.cylinder_c5()
+    raise SystemExit(f"unknown workload {name}")
+
+
+def algorithmic_bytes(prob: I.Problem, s: int, nf: int):
+    """Bytes each kernel must move per launch (s = bytes per scalar of f).
+    k_cell_prep: read f~, write fb+ (2 scalars each per cell-velocity);
+    k_face_interior: read fb+ once, write the face flux (2 per face-velocity);
+    k_sweep_fwd: read the face fluxes once, read f~, write Delta*;
+    k_sweep_bwd: read Delta* and f~, write Delta and f~."""
+    N, Nv = prob.ncells, prob.nvel
+    return {
+        "k_cell_prep": 4 * s * N * Nv,
+        "k_face_interior": 2 * s * N * Nv + 2 * s * nf * Nv,
+        "k_sweep_fwd": 2 * s * nf * Nv + 4 * s * N * Nv,
+        "k_sweep_bwd": 8 * s * N * Nv,
+    }
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args, prob):
+    """The FP64 oracle on the host cores: each step is one IDUGKS iteration of
+    the same cavity."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    o = O.Oracle(prob)
+    o.init_uniform()
+    o.iterate(args.warmup)
+    t0 = time.perf_counter()
+    o.iterate(args.steps)
+    dt = time.perf_counter() - t0
+    ups = prob.ncells * prob.nvel * args.steps / dt
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {
+        "impl": "reference", "metric": "cell-velocity updates/s", "value": ups,
+        "unit": "cell-velocity updates/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": prob.name, "cells": prob.ncells, "velocities": prob.nvel,
+                   "precision": "fp64-oracle"},
+        "cpu_baseline": {"value": ups, "unit": "cell-velocity updates/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} full IDUGKS iterations of {prob.name} after {args.warmup} warm-up"},
+        "e2e": {"value": ups, "unit": "cell-velocity updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(prob, budget_s=15.0):
+    """Time the oracle as it stands on a bounded sample: whole IDUGKS iterations
+    of the same cavity until about budget_s seconds have passed."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    p = ctx.Process(target=_cpu_worker, args=(prob.name, budget_s, q))
+    p.start()
+    p.join(timeout=budget_s * 6 + 120)
+    if p.is_alive():
+        p.kill()
+        return None
+    return q.get() if not q.empty() else None
+
+
+def _cpu_worker(name, budget_s, q):
+    sys.path.insert(0, ROOT)
+    from oracle import oracle as O
+    prob = workload_by_name(name)
+    o = O.Oracle(prob)
+    o.init_uniform()
+    o.iterate(1)
+    n, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < budget_s or n < 2:
+        o.iterate(1)
+        n += 1
+    dt = time.perf_counter() - t0
+    q.put({"value": prob.ncells * prob.nvel * n / dt, "unit": "cell-velocity updates/s",
+           "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)), "kind": "oracle",
+           "sample": f"{n} full FP64 IDUGKS iterations of {name} ({dt:.1f} s)"})
+
+
+def workload_by_name(name):
+    for w in ("cavity64", "couette64", "cavity128", "cylinder"):
+        p = workload(w)
+        if p.name == name:
+            return p
+    raise KeyError(name)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cavity64")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ttr", action="store_true", help="skip the time-to-residual runs")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    prob = workload(args.workload)
+    if args.impl == "reference":
+        run_reference(args, prob)
+        return
+
+    ws, rank, local = dist_env()
+    # the CPU baseline runs first, in a spawned process, before any GPU work
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(prob)
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1709_01819_gb300 import build
+    from paper_1709_01819_gb300.solver import Solver
+    build.build()
+
+    s = Solver(prob, args.precision, device=local)
+    s.init_uniform()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{local}")
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        s.iterate(1)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    # timed region: K iterations, each bracketed by CUDA events on the launching
+    # stream, with an L2 flush (outside the events) between them
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        for q in range(args.steps):
+            flush.fill_(q & 0xff)
+            starts[q].record(stream)
+            s.iterate(1)
+            ends[q].record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device=f"cuda:{local}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ups = prob.ncells * prob.nvel * args.steps * ws / (total_ms * 1e-3)
+
+    # per-kernel device time (events between launches) for the roofline
+    kms = np.zeros(6)
+    nprof = 10
+    for _ in range(nprof):
+        flush.fill_(1)
+        kms += s.iterate_profiled()
+    kms /= nprof
+    sbytes = 8 if args.precision == "fp64" else 4
+    alg = algorithmic_bytes(prob, sbytes, s.nf)
+    dom = max((k for k in alg), key=lambda k: kms[KERNELS.index(k)])
+    dom_ms = kms[KERNELS.index(dom)]
+    peaks = {}
+    if os.path.exists(PEAKS_FILE):
+        peaks = json.load(open(PEAKS_FILE))
+    peak = peaks.get("hbm_gbs", 6800.0)
+    achieved = alg[dom] / (dom_ms * 1e-3) / 1e9
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tfile):
+        tr = json.load(open(tfile)).get(f"{args.workload}:{args.precision}:{dom}")
+        traffic = tr
+
+    # end to end through the C ABI with host buffers: per step upload the state
+    # from pinned host memory (set_state), iterate once, read the moments back
+    G, H, W = s.get_state()
+    Gp = torch.from_numpy(G).pin_memory().numpy()
+    Hp = torch.from_numpy(H).pin_memory().numpy()
+    Wp = torch.from_numpy(W).pin_memory().numpy()
+    e2e_steps = min(args.steps, 10)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        s.set_state(Gp, Hp, Wp)
+        s.iterate(1)
+        m = s.moments()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": prob.ncells * prob.nvel * e2e_steps / e2e_s, "unit": "cell-velocity updates/s",
+           "h2d_bytes_per_step": int(G.nbytes + H.nbytes + W.nbytes), "d2h_bytes_per_step": int(m.nbytes),
+           "steps": e2e_steps}
+
+    # time to residual 1e-6 from the uniform start, mixed and FP64
+    ttr = None
+    if rank == 0 and not args.no_ttr:
+        ttr = {}
+        for prec in ("mixed", "fp64"):
+            s2 = Solver(prob, prec, device=local)
+            s2.init_uniform()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ok, n, r = s2.iterate(20000, 1e-6)
+            torch.cuda.synchronize()
+            ttr[prec] = {"seconds": time.perf_counter() - t0, "iterations": n, "residual": r, "converged": ok}
+            del s2
+
+    if rank == 0:
+        line = {
+            "metric": "cell-velocity updates/s", "value": ups, "unit": "cell-velocity updates/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision == "mixed" else "f64", "data": "synthetic",
+            "config": {"workload": prob.name, "cells": prob.ncells, "velocities": prob.nvel,
+                       "precision": args.precision, "l2": "flushed between timed steps (256 MB write)",
+                       "parallelism": "replicas" if ws > 1 else "single"},
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_source": "measured" if peaks else "fallback",
+                         "algorithmic_bytes": alg[dom], "kernel_ms": dom_ms},
+            "kernel_ms": {k: float(v) for k, v in zip(KERNELS, kms)},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "time_to_residual_1e-6": ttr,
+            "clocks": clk.summary(),
+            "gpu_launches": 6 * args.steps if s.nf else 5 * args.steps,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

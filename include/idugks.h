@@ -1,0 +1,165 @@
+/*
+ * idugks.h -- C ABI of libidugks, a GB300 (sm_103a) implementation of one
+ * iteration of the implicit discrete unified gas-kinetic scheme (IDUGKS) of
+ * Pan, Zhong & Zhuo, "An Implicit Discrete Unified Gas-Kinetic Scheme for
+ * Simulations of Steady Flow in All Flow Regimes", arXiv 1709.01819.
+ *
+ * The problem statement follows Section 2 of the paper: a 2-D BGK or
+ * BGK-Shakhov gas (Eq. 1-7, 20) on a structured quadrilateral block, discrete
+ * velocities from a Gauss-Hermite or Newton-Cotes rule (Section 2.2, last
+ * paragraph), diffuse walls and far-field ghosts (Section 2.3, Eq. 34-35).
+ * One call to idg_iterate performs, per iteration: the DUGKS interface flux
+ * (Eq. 10-19), the macroscopic LU-SGS predictor (Eq. 27-31) and the
+ * matrix-free LU-SGS sweeps for the distribution (Eq. 22-26), then the update
+ * of Eq. (32).
+ *
+ * Conventions
+ *  - Units: reference density 1, reference length 1, velocity unit
+ *    sqrt(2 R T_ref).  Temperatures are in units of T_ref; RT_ref is set by
+ *    idg_set_gas (1/2 in this unit system).
+ *  - Every function returns an idg_status.  On failure idg_last_error(ctx)
+ *    gives a one-line reason.  No function traps or aborts; device-side
+ *    problems surface as IDG_ERR_NONFINITE or IDG_ERR_CUDA.
+ *  - Host arrays are owned by the caller and copied during the call.
+ *  - Device memory comes from one caller-owned workspace (idg_workspace_size,
+ *    idg_bind_workspace); the library allocates no device memory itself.
+ *    The workspace must stay valid until idg_destroy or the next bind.
+ *  - All device work is ordered on the caller's CUDA stream (cudaStream_t
+ *    passed as void*; NULL is the legacy default stream).  Functions that
+ *    return host data synchronise that stream.
+ *  - Setters are accepted until idg_bind_workspace; afterwards they return
+ *    IDG_ERR_STATE.
+ *  - Layouts: cell index c = j*ni + i; mesh node index j*(ni+1) + i; discrete
+ *    velocity index k = ky*nvx + kx; per-(cell, velocity) host arrays are
+ *    [cell][velocity] row-major float64.
+ */
+#ifndef IDUGKS_H
+#define IDUGKS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct idg_ctx idg_ctx;
+
+typedef enum {
+    IDG_OK = 0,
+    IDG_ERR_ARG = 1,           /* invalid argument (size, range, NULL)                 */
+    IDG_ERR_STATE = 2,         /* call not allowed in the context's current state      */
+    IDG_ERR_CUDA = 3,          /* a CUDA runtime call failed                           */
+    IDG_ERR_OOM = 4,           /* workspace smaller than idg_workspace_size            */
+    IDG_ERR_NONFINITE = 5,     /* the residual became NaN or Inf                       */
+    IDG_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up                   */
+    IDG_ERR_NOT_CONVERGED = 7  /* idg_iterate reached max_iter above tol               */
+} idg_status;
+
+enum { IDG_FP64 = 0, IDG_MIXED = 1 };              /* storage/compute precision of f   */
+enum { IDG_BC_PERIODIC = 0, IDG_BC_WALL = 1, IDG_BC_FARFIELD = 2 };
+enum { IDG_NC_TRAP = 0, IDG_NC_SIMPSON = 1, IDG_GAUSS_HERMITE = 2 };
+enum { IDG_IMIN = 0, IDG_IMAX = 1, IDG_JMIN = 2, IDG_JMAX = 3 };
+enum { IDG_BGK = 0, IDG_SHAKHOV = 1 };
+
+/* Create a context.  precision: IDG_FP64 (f stored and processed in float64)
+ * or IDG_MIXED (f in float32; moments, macroscopic predictor and residual in
+ * float64).  device: CUDA ordinal used by later calls.  No GPU work happens
+ * here.  *out receives a context owned by the caller (free with idg_destroy). */
+idg_status idg_create(idg_ctx **out, int precision, int device);
+void idg_destroy(idg_ctx *ctx);
+const char *idg_last_error(const idg_ctx *ctx);
+
+/* Structured quadrilateral block of ni x nj cells (Fig. 1 and Section 2.3).
+ * nodes_x/nodes_y: (ni+1)*(nj+1) host float64, node (i,j) at j*(ni+1)+i, cells
+ * counter-clockwise (positive area).  A periodic direction is declared with
+ * idg_set_boundary(kind = IDG_BC_PERIODIC) on both of its sides; the last node
+ * column/row then equals the first up to a constant translation. */
+idg_status idg_set_mesh_structured(idg_ctx *ctx, int ni, int nj, const double *nodes_x,
+                                   const double *nodes_y);
+
+/* Tensor-product discrete velocity grid (Section 2.2, closing paragraph).
+ * IDG_NC_TRAP: composite trapezoid (closed 2-point Newton-Cotes) on
+ * [xmin,xmax] x [ymin,ymax], any n >= 2.  IDG_NC_SIMPSON: composite Simpson,
+ * odd n >= 3.  IDG_GAUSS_HERMITE: nodes scaled by sqrt(2 RT_ref), ranges
+ * ignored.  At most 16384 velocities in total. */
+idg_status idg_set_velocity_grid(idg_ctx *ctx, int rule, int nx, int ny, double xmin,
+                                 double xmax, double ymin, double ymax);
+
+/* Gas (Eq. 1-7, 20, 36): K internal degrees of freedom, Prandtl number (used
+ * by IDG_SHAKHOV), viscosity exponent omega (mu ~ T^omega), Knudsen number
+ * defining mu_ref by the VHS mean free path, RT_ref, model IDG_BGK/IDG_SHAKHOV. */
+idg_status idg_set_gas(idg_ctx *ctx, int K, double Pr, double omega, double Kn, double RT_ref,
+                       int model);
+
+/* Boundary of one side (Section 2.3).  IDG_BC_WALL: diffuse wall with velocity
+ * (u, v) and temperature T (Eq. 34-35); rho ignored.  IDG_BC_FARFIELD: incoming
+ * particles from the Maxwellian (rho, u, v, T).  IDG_BC_PERIODIC: set on both
+ * sides of a direction. */
+idg_status idg_set_boundary(idg_ctx *ctx, int side, int kind, double rho, double u, double v,
+                            double T);
+
+/* Numerics: cfl_imp sets the per-cell pseudo time step dt_imp = cfl_imp h_i /
+ * xi_max of Eq. (26) and (30); cfl_phys the physical DUGKS step dt = cfl_phys
+ * h_min / xi_max of Eq. (8); limiter 0 (phi = 1) or 1 (Eq. 16-17);
+ * lusgs_omega the relaxation of the macroscopic LU-SGS (2 reproduces Eq. 30);
+ * flags must be 0. */
+idg_status idg_set_numerics(idg_ctx *ctx, double cfl_imp, double cfl_phys, int limiter,
+                            double lusgs_omega, int flags);
+
+/* Bytes of device workspace the configured problem needs (>= 0; host only). */
+idg_status idg_workspace_size(idg_ctx *ctx, size_t *bytes);
+
+/* Bind a caller-owned device buffer of at least idg_workspace_size bytes,
+ * 256-byte aligned, on the context's device.  Uploads geometry and velocity
+ * tables (synchronous).  Ends the setter phase. */
+idg_status idg_bind_workspace(idg_ctx *ctx, void *dev_ptr, size_t bytes);
+
+/* Uniform Maxwellian start (Section 3): W = exact moments of (rho, u, v, T),
+ * f~ = discrete equilibrium.  Also fixes the reference Maxwellian the storage
+ * is taken relative to.  Resets the iteration count and residual history. */
+idg_status idg_init_uniform(idg_ctx *ctx, double rho, double u, double v, double T,
+                            void *stream);
+
+/* Replace / read the state.  G, H: host [ncell][nvel] float64 of f~ (Eq. 10),
+ * W: host [ncell][4] float64 conservative variables (Eq. 4).  Any pointer may
+ * be NULL in idg_get_state. */
+idg_status idg_set_state(idg_ctx *ctx, const double *G, const double *H, const double *W,
+                         void *stream);
+idg_status idg_get_state(idg_ctx *ctx, double *G, double *H, double *W, void *stream);
+
+/* Run IDUGKS iterations (Section 2.2) until the residual ||R_W/Omega||_2
+ * divided by that of the first iteration after the last (re)start is <= tol,
+ * or max_iter iterations ran.  tol <= 0 runs exactly max_iter iterations.
+ * iters_done and residual (relative) may be NULL.  Returns
+ * IDG_ERR_NOT_CONVERGED when tol > 0 was not reached. */
+idg_status idg_iterate(idg_ctx *ctx, int max_iter, double tol, void *stream, int *iters_done,
+                       double *residual);
+
+/* Per cell: rho, u, v, T/T_ref from W and the heat flux qx, qy of f from f~
+ * (host [ncell][6] float64). */
+idg_status idg_get_moments(idg_ctx *ctx, double *out6, void *stream);
+
+/* Absolute residuals ||R_W/Omega||_2 of the iterations since the last
+ * (re)start, oldest first; *n receives the count copied (<= cap). */
+idg_status idg_get_residual_history(idg_ctx *ctx, double *out, int cap, int *n);
+
+/* Face moment fluxes Phi_f = sum_k w_k psi_k F_k (Eq. 27) of the last
+ * iteration, host [nface][4] float64, faces numbered i-faces row by row then
+ * j-faces row by row; normal from the lower to the higher cell index side. */
+idg_status idg_get_face_flux_moments(idg_ctx *ctx, double *phi4, void *stream);
+
+/* One iteration with a CUDA event recorded between its kernel launches on
+ * the caller's stream (synchronises it).  kernel_ms[0..5] receives the
+ * device time of: cell prep, interior faces, boundary faces, macroscopic
+ * predictor, forward sweep, backward sweep (0 for a kernel not launched). */
+idg_status idg_iterate_profiled(idg_ctx *ctx, void *stream, double *kernel_ms);
+
+/* Sizes and host-side tables (valid after the corresponding setters). */
+idg_status idg_get_sizes(const idg_ctx *ctx, int *ncell, int *nvel, int *nface);
+idg_status idg_get_dt(const idg_ctx *ctx, double *dt);
+idg_status idg_velocity_grid(const idg_ctx *ctx, double *ux, double *uy, double *w);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

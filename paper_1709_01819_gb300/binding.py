@@ -1,0 +1,205 @@
+"""Thin ctypes binding of libidugks (include/idugks.h): same names, argument
+marshalling only.  Every step of the scheme runs in the CUDA library; there is
+no Python or CPU fallback.  Importing this module fails loudly when the library
+has not been built (run paper_1709_01819_gb300.build.build()).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from .build import LIB
+
+IDG_OK, IDG_ERR_ARG, IDG_ERR_STATE, IDG_ERR_CUDA, IDG_ERR_OOM = 0, 1, 2, 3, 4
+IDG_ERR_NONFINITE, IDG_ERR_TIMEOUT, IDG_ERR_NOT_CONVERGED = 5, 6, 7
+IDG_FP64, IDG_MIXED = 0, 1
+IDG_BC_PERIODIC, IDG_BC_WALL, IDG_BC_FARFIELD = 0, 1, 2
+IDG_NC_TRAP, IDG_NC_SIMPSON, IDG_GAUSS_HERMITE = 0, 1, 2
+IDG_IMIN, IDG_IMAX, IDG_JMIN, IDG_JMAX = 0, 1, 2, 3
+IDG_BGK, IDG_SHAKHOV = 0, 1
+
+_STATUS = {0: "IDG_OK", 1: "IDG_ERR_ARG", 2: "IDG_ERR_STATE", 3: "IDG_ERR_CUDA", 4: "IDG_ERR_OOM",
+           5: "IDG_ERR_NONFINITE", 6: "IDG_ERR_TIMEOUT", 7: "IDG_ERR_NOT_CONVERGED"}
+
+# (name, restype, argtypes)
+_d, _i, _vp, _sz = C.c_double, C.c_int, C.c_void_p, C.c_size_t
+_P = C.POINTER
+SIGNATURES = [
+    ("idg_create", _i, [_P(_vp), _i, _i]),
+    ("idg_destroy", None, [_vp]),
+    ("idg_last_error", C.c_char_p, [_vp]),
+    ("idg_set_mesh_structured", _i, [_vp, _i, _i, _P(_d), _P(_d)]),
+    ("idg_set_velocity_grid", _i, [_vp, _i, _i, _i, _d, _d, _d, _d]),
+    ("idg_set_gas", _i, [_vp, _i, _d, _d, _d, _d, _i]),
+    ("idg_set_boundary", _i, [_vp, _i, _i, _d, _d, _d, _d]),
+    ("idg_set_numerics", _i, [_vp, _d, _d, _i, _d, _i]),
+    ("idg_workspace_size", _i, [_vp, _P(_sz)]),
+    ("idg_bind_workspace", _i, [_vp, _vp, _sz]),
+    ("idg_init_uniform", _i, [_vp, _d, _d, _d, _d, _vp]),
+    ("idg_set_state", _i, [_vp, _P(_d), _P(_d), _P(_d), _vp]),
+    ("idg_get_state", _i, [_vp, _P(_d), _P(_d), _P(_d), _vp]),
+    ("idg_iterate", _i, [_vp, _i, _d, _vp, _P(_i), _P(_d)]),
+    ("idg_iterate_profiled", _i, [_vp, _vp, _P(_d)]),
+    ("idg_get_moments", _i, [_vp, _P(_d), _vp]),
+    ("idg_get_residual_history", _i, [_vp, _P(_d), _i, _P(_i)]),
+    ("idg_get_face_flux_moments", _i, [_vp, _P(_d), _vp]),
+    ("idg_get_sizes", _i, [_vp, _P(_i), _P(_i), _P(_i)]),
+    ("idg_get_dt", _i, [_vp, _P(_d)]),
+    ("idg_velocity_grid", _i, [_vp, _P(_d), _P(_d), _P(_d)]),
+]
+
+_lib = None
+
+
+def lib():
+    """Load libidugks.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise ImportError(f"libidugks.so not built at {LIB}; call paper_1709_01819_gb300.build.build()")
+        L = C.CDLL(LIB)
+        for name, res, args in SIGNATURES:
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+class IdgError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def dptr(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def check(ctx, status: int, allow=()):
+    if status != IDG_OK and status not in allow:
+        msg = lib().idg_last_error(ctx)
+        raise IdgError(status, msg.decode() if msg else "")
+    return status
+
+
+# ---- one Python function per C entry point (argument marshalling only) ----
+
+def idg_create(precision: int, device: int):
+    h = C.c_void_p()
+    check(None, lib().idg_create(C.byref(h), precision, device))
+    return h
+
+
+def idg_destroy(ctx):
+    lib().idg_destroy(ctx)
+
+
+def idg_last_error(ctx) -> str:
+    m = lib().idg_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def idg_set_mesh_structured(ctx, nodes_x: np.ndarray, nodes_y: np.ndarray):
+    X = np.ascontiguousarray(nodes_x, dtype=np.float64)
+    Y = np.ascontiguousarray(nodes_y, dtype=np.float64)
+    nj, ni = X.shape[0] - 1, X.shape[1] - 1
+    return check(ctx, lib().idg_set_mesh_structured(ctx, ni, nj, dptr(X), dptr(Y)))
+
+
+def idg_set_velocity_grid(ctx, rule, nx, ny, xmin, xmax, ymin, ymax):
+    return check(ctx, lib().idg_set_velocity_grid(ctx, rule, nx, ny, xmin, xmax, ymin, ymax))
+
+
+def idg_set_gas(ctx, K, Pr, omega, Kn, RT_ref, model):
+    return check(ctx, lib().idg_set_gas(ctx, K, Pr, omega, Kn, RT_ref, model))
+
+
+def idg_set_boundary(ctx, side, kind, rho, u, v, T):
+    return check(ctx, lib().idg_set_boundary(ctx, side, kind, rho, u, v, T))
+
+
+def idg_set_numerics(ctx, cfl_imp, cfl_phys, limiter, lusgs_omega, flags=0):
+    return check(ctx, lib().idg_set_numerics(ctx, cfl_imp, cfl_phys, limiter, lusgs_omega, flags))
+
+
+def idg_workspace_size(ctx) -> int:
+    n = C.c_size_t()
+    check(ctx, lib().idg_workspace_size(ctx, C.byref(n)))
+    return n.value
+
+
+def idg_bind_workspace(ctx, dev_ptr: int, nbytes: int):
+    return check(ctx, lib().idg_bind_workspace(ctx, C.c_void_p(dev_ptr), nbytes))
+
+
+def idg_init_uniform(ctx, rho, u, v, T, stream=None):
+    return check(ctx, lib().idg_init_uniform(ctx, rho, u, v, T, stream))
+
+
+def idg_set_state(ctx, G, H, W, stream=None):
+    G = np.ascontiguousarray(G, dtype=np.float64)
+    H = np.ascontiguousarray(H, dtype=np.float64)
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    return check(ctx, lib().idg_set_state(ctx, dptr(G), dptr(H), dptr(W), stream))
+
+
+def idg_get_state(ctx, N, Nv, stream=None):
+    G = np.zeros((N, Nv))
+    H = np.zeros((N, Nv))
+    W = np.zeros((N, 4))
+    check(ctx, lib().idg_get_state(ctx, dptr(G), dptr(H), dptr(W), stream))
+    return G, H, W
+
+
+def idg_iterate(ctx, max_iter, tol, stream=None):
+    n = C.c_int()
+    r = C.c_double()
+    st = check(ctx, lib().idg_iterate(ctx, max_iter, tol, stream, C.byref(n), C.byref(r)),
+               allow=(IDG_ERR_NOT_CONVERGED,))
+    return st, n.value, r.value
+
+
+def idg_iterate_profiled(ctx, stream=None):
+    ms = np.zeros(6)
+    check(ctx, lib().idg_iterate_profiled(ctx, stream, dptr(ms)))
+    return ms
+
+
+def idg_get_moments(ctx, N, stream=None):
+    out = np.zeros((N, 6))
+    check(ctx, lib().idg_get_moments(ctx, dptr(out), stream))
+    return out
+
+
+def idg_get_residual_history(ctx, cap):
+    out = np.zeros(max(cap, 1))
+    n = C.c_int()
+    check(ctx, lib().idg_get_residual_history(ctx, dptr(out), cap, C.byref(n)))
+    return out[: n.value]
+
+
+def idg_get_face_flux_moments(ctx, nf, stream=None):
+    out = np.zeros((nf, 4))
+    check(ctx, lib().idg_get_face_flux_moments(ctx, dptr(out), stream))
+    return out
+
+
+def idg_get_sizes(ctx):
+    a, b, c = C.c_int(), C.c_int(), C.c_int()
+    check(ctx, lib().idg_get_sizes(ctx, C.byref(a), C.byref(b), C.byref(c)))
+    return a.value, b.value, c.value
+
+
+def idg_get_dt(ctx) -> float:
+    d = C.c_double()
+    check(ctx, lib().idg_get_dt(ctx, C.byref(d)))
+    return d.value
+
+
+def idg_velocity_grid(ctx, Nv):
+    ux, uy, w = np.zeros(Nv), np.zeros(Nv), np.zeros(Nv)
+    check(ctx, lib().idg_velocity_grid(ctx, dptr(ux), dptr(uy), dptr(w)))
+    return ux, uy, w

@@ -1,0 +1,897 @@
+// idugks_host.cpp -- host side of libidugks: the C ABI of include/idugks.h,
+// problem validation, structured-mesh geometry, discrete velocity quadrature,
+// workspace layout, state transfer and the iteration driver.
+#include "idugks.h"
+#include "idugks_internal.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using idg::KParams;
+
+struct idg_ctx {
+    int precision = IDG_FP64;
+    int device = 0;
+    std::string err;
+    // problem description
+    int ni = 0, nj = 0;
+    std::vector<double> nodes_x, nodes_y;
+    int vrule = -1, nvx = 0, nvy = 0;
+    double vx0 = 0, vx1 = 0, vy0 = 0, vy1 = 0;
+    bool gas_set = false;
+    int K = 1, model = IDG_BGK;
+    double Pr = 1.0, omega = 0.5, Kn = 0.1, RT_ref = 0.5;
+    int bc_kind[4] = {-1, -1, -1, -1};
+    double bc_rho[4] = {0, 0, 0, 0}, bc_u[4] = {0, 0, 0, 0}, bc_v[4] = {0, 0, 0, 0},
+           bc_T[4] = {0, 0, 0, 0};
+    double cfl_imp = 100.0, cfl_phys = 0.5, lusgs_omega = 2.0;
+    int limiter = 0, flags = 0;
+    // derived on the host
+    bool built = false;
+    int N = 0, Nv = 0, nf = 0;
+    std::vector<double> area, cxc, cyc, hcell, dtimp, cr, clsg, fgeo;
+    std::vector<int> cface, cnb, csign, fL, fR, fbc, fside, ilist, blist;
+    std::vector<double> ux, uy, w;
+    double xi_max = 0, dt = 0, mu_ref = 0;
+    // reference Maxwellian of the storage
+    double ref_rho = 1.0, ref_u = 0.0, ref_v = 0.0, ref_T = 1.0;
+    // device
+    bool bound = false;
+    char *ws = nullptr;
+    size_t ws_bytes = 0;
+    KParams kp{};
+    double *moments_dev = nullptr;
+    double *stage = nullptr;  // staging for host<->device state copies (aliases F)
+    size_t stage_bytes = 0;
+    // iteration bookkeeping
+    long long host_iter = 0;   // iterations launched since bind
+    long long start_iter = 0;  // iteration index of the last (re)start
+    std::vector<double> hist;  // absolute residuals since the last (re)start
+};
+
+namespace {
+
+idg_status fail(idg_ctx *c, idg_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return s;
+}
+
+idg_status cuda_fail(idg_ctx *c, cudaError_t e, const char *where)
+{
+    return fail(c, IDG_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+// -------------------------------------------------------------------------
+// discrete velocity quadrature (Section 2.2, closing paragraph)
+// -------------------------------------------------------------------------
+
+// Gauss-Hermite rule for the weight exp(-x^2) by the Golub-Welsch idea: the
+// nodes are the eigenvalues of the symmetric Jacobi matrix of the Hermite
+// recurrence (off-diagonal sqrt(k/2)).  The eigenvalues come from cyclic
+// Jacobi rotations, then one or two Newton steps on the orthonormal
+// recurrence polish them; the weights use W_i = 1 / (n p_{n-1}(x_i)^2).
+bool gauss_hermite(int n, std::vector<double> &x, std::vector<double> &wt)
+{
+    if (n < 1 || n > 512) return false;
+    std::vector<double> A((size_t)n * n, 0.0);
+    for (int k = 1; k < n; ++k) A[(size_t)(k - 1) * n + k] = A[(size_t)k * n + k - 1] = std::sqrt(0.5 * k);
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) off += A[(size_t)p * n + q] * A[(size_t)p * n + q];
+        if (off < 1e-300) break;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                double apq = A[(size_t)p * n + q];
+                if (std::fabs(apq) < 1e-300) continue;
+                double app = A[(size_t)p * n + p], aqq = A[(size_t)q * n + q];
+                double theta = (aqq - app) / (2.0 * apq);
+                double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                double cs = 1.0 / std::sqrt(t * t + 1.0), sn = t * cs;
+                for (int r = 0; r < n; ++r) {
+                    double arp = A[(size_t)r * n + p], arq = A[(size_t)r * n + q];
+                    A[(size_t)r * n + p] = cs * arp - sn * arq;
+                    A[(size_t)r * n + q] = sn * arp + cs * arq;
+                }
+                for (int r = 0; r < n; ++r) {
+                    double apr = A[(size_t)p * n + r], aqr = A[(size_t)q * n + r];
+                    A[(size_t)p * n + r] = cs * apr - sn * aqr;
+                    A[(size_t)q * n + r] = sn * apr + cs * aqr;
+                }
+            }
+    }
+    x.resize(n);
+    wt.resize(n);
+    for (int i = 0; i < n; ++i) x[i] = A[(size_t)i * n + i];
+    std::sort(x.begin(), x.end());
+    auto orth = [n](double xv, double &pn, double &pn1) {
+        double p0 = std::pow(M_PI, -0.25), p1 = std::sqrt(2.0) * xv * p0;
+        if (n == 1) { pn = p1; pn1 = p0; return; }
+        for (int k = 1; k < n; ++k) {
+            double p2 = std::sqrt(2.0 / (k + 1)) * xv * p1 - std::sqrt((double)k / (k + 1)) * p0;
+            p0 = p1;
+            p1 = p2;
+        }
+        pn = p1;
+        pn1 = p0;
+    };
+    for (int i = 0; i < n; ++i) {
+        for (int it = 0; it < 3; ++it) {
+            double pn, pn1;
+            orth(x[i], pn, pn1);
+            double d = std::sqrt(2.0 * n) * pn1;  // p_n' = sqrt(2n) p_{n-1}
+            if (d == 0.0) break;
+            x[i] -= pn / d;
+        }
+    }
+    for (int i = 0; i < n / 2; ++i) {  // exact symmetry
+        double a = 0.5 * (x[n - 1 - i] - x[i]);
+        x[i] = -a;
+        x[n - 1 - i] = a;
+    }
+    if (n % 2) x[n / 2] = 0.0;
+    for (int i = 0; i < n; ++i) {
+        double pn, pn1;
+        orth(x[i], pn, pn1);
+        wt[i] = 1.0 / (n * pn1 * pn1);
+    }
+    for (int i = 0; i < n / 2; ++i) {
+        double a = 0.5 * (wt[i] + wt[n - 1 - i]);
+        wt[i] = wt[n - 1 - i] = a;
+    }
+    return true;
+}
+
+bool rule_1d(int rule, int n, double a, double b, double unit, std::vector<double> &x,
+             std::vector<double> &w)
+{
+    x.assign(n, 0.0);
+    w.assign(n, 0.0);
+    if (rule == IDG_NC_TRAP || rule == IDG_NC_SIMPSON) {
+        if (n < 2 || !(b > a)) return false;
+        if (rule == IDG_NC_SIMPSON && (n < 3 || n % 2 == 0)) return false;
+        double step = (b - a) / (n - 1), mid = 0.5 * (a + b);
+        for (int i = 0; i < n; ++i) {
+            // symmetric about the midpoint by construction
+            int m = i - (n - 1) / 2;
+            double off = (n % 2) ? m * step : (i - 0.5 * (n - 1)) * step;
+            x[i] = mid + off;
+            if (rule == IDG_NC_TRAP) w[i] = (i == 0 || i == n - 1) ? 0.5 * step : step;
+            else w[i] = (i == 0 || i == n - 1) ? step / 3.0 : ((i % 2) ? 4.0 : 2.0) * step / 3.0;
+        }
+        return true;
+    }
+    if (rule == IDG_GAUSS_HERMITE) {
+        std::vector<double> gx, gw;
+        if (!gauss_hermite(n, gx, gw)) return false;
+        for (int i = 0; i < n; ++i) {
+            x[i] = unit * gx[i];
+            w[i] = unit * gw[i] * std::exp(gx[i] * gx[i]);
+        }
+        return true;
+    }
+    return false;
+}
+
+// -------------------------------------------------------------------------
+// structured block geometry (Fig. 1, Section 2.3)
+// -------------------------------------------------------------------------
+idg_status build(idg_ctx *c)
+{
+    if (c->built) return IDG_OK;
+    if (c->ni < 1 || c->nj < 1) return fail(c, IDG_ERR_STATE, "mesh not set");
+    if (c->vrule < 0) return fail(c, IDG_ERR_STATE, "velocity grid not set");
+    if (!c->gas_set) return fail(c, IDG_ERR_STATE, "gas not set");
+    for (int s = 0; s < 4; ++s)
+        if (c->bc_kind[s] < 0) return fail(c, IDG_ERR_STATE, "boundary of side %d not set", s);
+    const bool per_i = c->bc_kind[IDG_IMIN] == IDG_BC_PERIODIC;
+    const bool per_j = c->bc_kind[IDG_JMIN] == IDG_BC_PERIODIC;
+    if (per_i != (c->bc_kind[IDG_IMAX] == IDG_BC_PERIODIC) || per_j != (c->bc_kind[IDG_JMAX] == IDG_BC_PERIODIC))
+        return fail(c, IDG_ERR_ARG, "a periodic direction needs IDG_BC_PERIODIC on both sides");
+    const int ni = c->ni, nj = c->nj;
+    c->N = ni * nj;
+    // velocities
+    std::vector<double> x1, w1, y1, v1;
+    double unit = std::sqrt(2.0 * c->RT_ref);
+    if (!rule_1d(c->vrule, c->nvx, c->vx0, c->vx1, unit, x1, w1) ||
+        !rule_1d(c->vrule, c->nvy, c->vy0, c->vy1, unit, y1, v1))
+        return fail(c, IDG_ERR_ARG, "invalid velocity quadrature (rule %d, %d x %d)", c->vrule, c->nvx, c->nvy);
+    c->Nv = c->nvx * c->nvy;
+    c->ux.resize(c->Nv);
+    c->uy.resize(c->Nv);
+    c->w.resize(c->Nv);
+    c->xi_max = 0;
+    for (int ky = 0; ky < c->nvy; ++ky)
+        for (int kx = 0; kx < c->nvx; ++kx) {
+            int k = ky * c->nvx + kx;
+            c->ux[k] = x1[kx];
+            c->uy[k] = y1[ky];
+            c->w[k] = w1[kx] * v1[ky];
+            c->xi_max = std::max(c->xi_max, std::sqrt(x1[kx] * x1[kx] + y1[ky] * y1[ky]));
+        }
+    auto X = [&](int i, int j) { return c->nodes_x[(size_t)j * (ni + 1) + i]; };
+    auto Y = [&](int i, int j) { return c->nodes_y[(size_t)j * (ni + 1) + i]; };
+    // cells: shoelace area and polygon centroid
+    c->area.assign(c->N, 0);
+    c->cxc.assign(c->N, 0);
+    c->cyc.assign(c->N, 0);
+    for (int j = 0; j < nj; ++j)
+        for (int i = 0; i < ni; ++i) {
+            double px[4] = {X(i, j), X(i + 1, j), X(i + 1, j + 1), X(i, j + 1)};
+            double py[4] = {Y(i, j), Y(i + 1, j), Y(i + 1, j + 1), Y(i, j + 1)};
+            double a2 = 0, sx = 0, sy = 0;
+            for (int m = 0; m < 4; ++m) {
+                int n2 = (m + 1) & 3;
+                double cr = px[m] * py[n2] - px[n2] * py[m];
+                a2 += cr;
+                sx += (px[m] + px[n2]) * cr;
+                sy += (py[m] + py[n2]) * cr;
+            }
+            int cc = j * ni + i;
+            if (!(a2 > 0)) return fail(c, IDG_ERR_ARG, "cell (%d,%d) has non-positive area", i, j);
+            c->area[cc] = 0.5 * a2;
+            c->cxc[cc] = sx / (3.0 * a2);
+            c->cyc[cc] = sy / (3.0 * a2);
+        }
+    // faces: i-faces row by row, then j-faces row by row
+    const int nfi_row = per_i ? ni : ni + 1;
+    const int nfj_rows = per_j ? nj : nj + 1;
+    c->nf = nfi_row * nj + nfj_rows * ni;
+    c->fL.assign(c->nf, -1);
+    c->fR.assign(c->nf, -1);
+    c->fbc.assign(c->nf, -1);
+    c->fside.assign(c->nf, -1);
+    c->fgeo.assign((size_t)7 * c->nf, 0.0);
+    auto set_face = [&](int f, double x0, double y0, double x1_, double y1_, bool ifc, int L, int R,
+                        double mLx, double mLy, double mRx, double mRy, int side) {
+        double tx = x1_ - x0, ty = y1_ - y0, S = std::sqrt(tx * tx + ty * ty);
+        double *g = &c->fgeo[(size_t)7 * f];
+        g[0] = ifc ? ty / S : -ty / S;
+        g[1] = ifc ? -tx / S : tx / S;
+        g[2] = S;
+        c->fL[f] = L;
+        c->fR[f] = R;
+        if (L >= 0) { g[3] = mLx - c->cxc[L]; g[4] = mLy - c->cyc[L]; }
+        if (R >= 0) { g[5] = mRx - c->cxc[R]; g[6] = mRy - c->cyc[R]; }
+        if (side >= 0) { c->fside[f] = side; c->fbc[f] = c->bc_kind[side]; }
+    };
+    int f = 0;
+    for (int j = 0; j < nj; ++j)
+        for (int i = 0; i < nfi_row; ++i, ++f) {
+            double x0 = X(i, j), y0 = Y(i, j), x1_ = X(i, j + 1), y1_ = Y(i, j + 1);
+            double mx = 0.5 * (x0 + x1_), my = 0.5 * (y0 + y1_);
+            if (per_i) {
+                int L = j * ni + (i + ni - 1) % ni, R = j * ni + i;
+                double mLx = mx, mLy = my;
+                if (i == 0) { mLx = 0.5 * (X(ni, j) + X(ni, j + 1)); mLy = 0.5 * (Y(ni, j) + Y(ni, j + 1)); }
+                set_face(f, x0, y0, x1_, y1_, true, L, R, mLx, mLy, mx, my, -1);
+            } else {
+                int L = i > 0 ? j * ni + i - 1 : -1, R = i < ni ? j * ni + i : -1;
+                int side = L < 0 ? IDG_IMIN : (R < 0 ? IDG_IMAX : -1);
+                set_face(f, x0, y0, x1_, y1_, true, L, R, mx, my, mx, my, side);
+            }
+        }
+    for (int j = 0; j < nfj_rows; ++j)
+        for (int i = 0; i < ni; ++i, ++f) {
+            double x0 = X(i, j), y0 = Y(i, j), x1_ = X(i + 1, j), y1_ = Y(i + 1, j);
+            double mx = 0.5 * (x0 + x1_), my = 0.5 * (y0 + y1_);
+            if (per_j) {
+                int L = ((j + nj - 1) % nj) * ni + i, R = j * ni + i;
+                double mLx = mx, mLy = my;
+                if (j == 0) { mLx = 0.5 * (X(i, nj) + X(i + 1, nj)); mLy = 0.5 * (Y(i, nj) + Y(i + 1, nj)); }
+                set_face(f, x0, y0, x1_, y1_, false, L, R, mLx, mLy, mx, my, -1);
+            } else {
+                int L = j > 0 ? (j - 1) * ni + i : -1, R = j < nj ? j * ni + i : -1;
+                int side = L < 0 ? IDG_JMIN : (R < 0 ? IDG_JMAX : -1);
+                set_face(f, x0, y0, x1_, y1_, false, L, R, mx, my, mx, my, side);
+            }
+        }
+    c->ilist.clear();
+    c->blist.clear();
+    for (int q = 0; q < c->nf; ++q) (c->fL[q] >= 0 && c->fR[q] >= 0 ? c->ilist : c->blist).push_back(q);
+    // cell slots: west, east, south, north
+    c->cface.assign(4 * c->N, 0);
+    c->cnb.assign(4 * c->N, -1);
+    c->csign.assign(4 * c->N, 0);
+    c->cr.assign((size_t)8 * c->N, 0.0);
+    c->clsg.assign((size_t)8 * c->N, 0.0);
+    c->hcell.assign(c->N, 0.0);
+    c->dtimp.assign(c->N, 0.0);
+    double hmin = 1e300;
+    for (int j = 0; j < nj; ++j)
+        for (int i = 0; i < ni; ++i) {
+            int cc = j * ni + i;
+            int fw = j * nfi_row + i;
+            int fe = j * nfi_row + (per_i ? (i + 1) % ni : i + 1);
+            int fs = nfi_row * nj + j * ni + i;
+            int fn = nfi_row * nj + (per_j ? (j + 1) % nj : j + 1) * ni + i;
+            int fs4[4] = {fw, fe, fs, fn}, sg4[4] = {-1, +1, -1, +1};
+            double smax = 0, a11 = 0, a12 = 0, a22 = 0, d[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+            for (int m = 0; m < 4; ++m) {
+                int fi = fs4[m];
+                const double *g = &c->fgeo[(size_t)7 * fi];
+                c->cface[4 * cc + m] = fi;
+                c->csign[4 * cc + m] = sg4[m];
+                bool own_L = sg4[m] > 0;
+                c->cr[8 * cc + 2 * m] = own_L ? g[3] : g[5];
+                c->cr[8 * cc + 2 * m + 1] = own_L ? g[4] : g[6];
+                smax = std::max(smax, g[2]);
+                int other = own_L ? c->fR[fi] : c->fL[fi];
+                c->cnb[4 * cc + m] = other;
+                if (other < 0) continue;
+                // neighbour displacement through the face: r_own - r_other
+                d[m][0] = own_L ? g[3] - g[5] : g[5] - g[3];
+                d[m][1] = own_L ? g[4] - g[6] : g[6] - g[4];
+                a11 += d[m][0] * d[m][0];
+                a12 += d[m][0] * d[m][1];
+                a22 += d[m][1] * d[m][1];
+            }
+            double det = a11 * a22 - a12 * a12;
+            if (!(det > 0)) return fail(c, IDG_ERR_ARG, "singular least-squares stencil at cell (%d,%d)", i, j);
+            for (int m = 0; m < 4; ++m) {
+                if (c->cnb[4 * cc + m] < 0) continue;
+                c->clsg[8 * cc + 2 * m] = (a22 * d[m][0] - a12 * d[m][1]) / det;
+                c->clsg[8 * cc + 2 * m + 1] = (-a12 * d[m][0] + a11 * d[m][1]) / det;
+            }
+            c->hcell[cc] = c->area[cc] / smax;
+            hmin = std::min(hmin, c->hcell[cc]);
+        }
+    c->dt = c->cfl_phys * hmin / c->xi_max;
+    for (int q = 0; q < c->N; ++q) c->dtimp[q] = c->cfl_imp * c->hcell[q] / c->xi_max;
+    const double om = c->omega;
+    c->mu_ref = 15.0 * std::sqrt(2.0 * M_PI * c->RT_ref) * c->Kn / (2.0 * (5.0 - 2.0 * om) * (7.0 - 2.0 * om));
+    c->built = true;
+    return IDG_OK;
+}
+
+// -------------------------------------------------------------------------
+// workspace layout
+// -------------------------------------------------------------------------
+struct Layout {
+    size_t off = 0;
+    char *base = nullptr;
+    template <class P> P *take(size_t bytes)
+    {
+        off = (off + 255) & ~(size_t)255;
+        P *p = base ? (P *)(base + off) : nullptr;
+        off += bytes;
+        return p;
+    }
+};
+
+size_t layout(idg_ctx *c, char *base, KParams *kp)
+{
+    Layout L;
+    L.base = base;
+    const size_t N = c->N, Nv = c->Nv, nf = c->nf;
+    const size_t t2 = c->precision == IDG_FP64 ? 16 : 8;
+    KParams k{};
+    k.area = L.take<double>(8 * N);
+    k.dtimp = L.take<double>(8 * N);
+    k.cface = L.take<int>(16 * N);
+    k.cnb = L.take<int>(16 * N);
+    k.csign = L.take<int>(16 * N);
+    k.cr = L.take<double>(64 * N);
+    k.clsg = L.take<double>(64 * N);
+    k.fL = L.take<int>(4 * nf);
+    k.fR = L.take<int>(4 * nf);
+    k.fgeo = L.take<double>(56 * nf);
+    k.fbc = L.take<int>(4 * nf);
+    k.fside = L.take<int>(4 * nf);
+    k.ilist = L.take<int>(4 * nf + 4);
+    k.blist = L.take<int>(4 * nf + 4);
+    k.ux = L.take<double>(8 * Nv);
+    k.uy = L.take<double>(8 * Nv);
+    k.w = L.take<double>(8 * Nv);
+    k.gref = L.take<double>(8 * Nv);
+    k.lngref = L.take<double>(8 * Nv);
+    k.uxf = L.take<float>(4 * Nv);
+    k.uyf = L.take<float>(4 * Nv);
+    k.wf = L.take<float>(4 * Nv);
+    k.greff = L.take<float>(4 * Nv);
+    k.lngreff = L.take<float>(4 * Nv);
+    k.bndG = L.take<double>(32 * Nv);
+    k.bndH = L.take<double>(32 * Nv);
+    k.f = L.take<char>(t2 * N * Nv);
+    k.fbp = L.take<char>(t2 * N * Nv);
+    k.dst = L.take<char>(t2 * N * Nv);
+    k.F = L.take<char>(t2 * nf * Nv);
+    k.W = L.take<double>(32 * N);
+    k.cellq = L.take<double>(16 * N);
+    k.cellp = L.take<double>(8 * idg::kCellP * N);
+    k.phi = L.take<double>(32 * nf);
+    k.rw = L.take<double>(32 * N);
+    k.dW = L.take<double>(32 * N);
+    k.lam = L.take<double>(8 * nf);
+    k.Dm = L.take<double>(8 * N);
+    k.res = L.take<double>(8 * (size_t)idg::kMaxHist);
+    k.iter = L.take<int>(256);
+    k.status = k.iter + 1;
+    double *mom = L.take<double>(48 * N);
+    if (kp) {
+        *kp = k;
+        c->moments_dev = mom;
+    }
+    return L.off + 256;
+}
+
+// tables of the reference Maxwellian and its float64 moments
+void reference_tables(idg_ctx *c, std::vector<double> &gref, std::vector<double> &lng, KParams &k)
+{
+    const int Nv = c->Nv;
+    const double RTr = c->ref_T * c->RT_ref, lamr = 0.5 / RTr;
+    gref.resize(Nv);
+    lng.resize(Nv);
+    for (int q = 0; q < 11; ++q) k.mref_raw[q] = 0.0;
+    for (int a = 0; a < 4; ++a) k.mref_flux[a][0] = k.mref_flux[a][1] = 0.0;
+    const double kRTr = c->K * RTr;
+    for (int q = 0; q < Nv; ++q) {
+        double cx = c->ux[q] - c->ref_u, cy = c->uy[q] - c->ref_v;
+        lng[q] = std::log(c->ref_rho * lamr / M_PI) - lamr * (cx * cx + cy * cy);
+        gref[q] = std::exp(lng[q]);
+        double G = gref[q], H = kRTr * G, x = c->ux[q], y = c->uy[q], wq = c->w[q], s2 = x * x + y * y;
+        double r[11] = {G, x * G, y * G, x * x * G, x * y * G, y * y * G, x * s2 * G, y * s2 * G, H, x * H, y * H};
+        for (int m = 0; m < 11; ++m) k.mref_raw[m] += wq * r[m];
+        double psi[4] = {G, x * G, y * G, 0.5 * (s2 * G + H)};
+        for (int a = 0; a < 4; ++a) {
+            k.mref_flux[a][0] += wq * psi[a] * x;
+            k.mref_flux[a][1] += wq * psi[a] * y;
+        }
+    }
+    k.rho_r = c->ref_rho;
+    k.U_r = c->ref_u;
+    k.V_r = c->ref_v;
+    k.RT_r = RTr;
+}
+
+template <class T> cudaError_t up(T *dst, const std::vector<T> &src)
+{
+    return cudaMemcpy(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+idg_status upload_reference(idg_ctx *c)
+{
+    std::vector<double> gref, lng;
+    reference_tables(c, gref, lng, c->kp);
+    std::vector<float> gf(gref.begin(), gref.end()), lf(lng.begin(), lng.end());
+    cudaError_t e;
+    if ((e = up((double *)c->kp.gref, gref)) != cudaSuccess) return cuda_fail(c, e, "upload gref");
+    if ((e = up((double *)c->kp.lngref, lng)) != cudaSuccess) return cuda_fail(c, e, "upload lngref");
+    if ((e = up((float *)c->kp.greff, gf)) != cudaSuccess) return cuda_fail(c, e, "upload greff");
+    if ((e = up((float *)c->kp.lngreff, lf)) != cudaSuccess) return cuda_fail(c, e, "upload lngreff");
+    return IDG_OK;
+}
+
+idg_status check_ready(idg_ctx *c)
+{
+    if (!c) return IDG_ERR_ARG;
+    if (!c->bound) return fail(c, IDG_ERR_STATE, "workspace not bound");
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+    return IDG_OK;
+}
+
+void restart(idg_ctx *c)
+{
+    c->start_iter = c->host_iter;
+    c->hist.clear();
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+idg_status idg_create(idg_ctx **out, int precision, int device)
+{
+    if (!out) return IDG_ERR_ARG;
+    *out = nullptr;
+    if (precision != IDG_FP64 && precision != IDG_MIXED) return IDG_ERR_ARG;
+    if (device < 0) return IDG_ERR_ARG;
+    idg_ctx *c = new idg_ctx();
+    c->precision = precision;
+    c->device = device;
+    *out = c;
+    return IDG_OK;
+}
+
+void idg_destroy(idg_ctx *ctx) { delete ctx; }
+
+const char *idg_last_error(const idg_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+idg_status idg_set_mesh_structured(idg_ctx *c, int ni, int nj, const double *nodes_x,
+                                   const double *nodes_y)
+{
+    if (!c) return IDG_ERR_ARG;
+    if (c->bound) return fail(c, IDG_ERR_STATE, "setters are closed after idg_bind_workspace");
+    if (ni < 1 || nj < 1 || (long long)ni * nj > (1LL << 26) || !nodes_x || !nodes_y)
+        return fail(c, IDG_ERR_ARG, "invalid mesh size %d x %d or null nodes", ni, nj);
+    size_t nn = (size_t)(ni + 1) * (nj + 1);
+    for (size_t q = 0; q < nn; ++q)
+        if (!std::isfinite(nodes_x[q]) || !std::isfinite(nodes_y[q]))
+            return fail(c, IDG_ERR_ARG, "non-finite node coordinate at %zu", q);
+    c->ni = ni;
+    c->nj = nj;
+    c->nodes_x.assign(nodes_x, nodes_x + nn);
+    c->nodes_y.assign(nodes_y, nodes_y + nn);
+    c->built = false;
+    return IDG_OK;
+}
+
+idg_status idg_set_velocity_grid(idg_ctx *c, int rule, int nx, int ny, double xmin, double xmax,
+                                 double ymin, double ymax)
+{
+    if (!c) return IDG_ERR_ARG;
+    if (c->bound) return fail(c, IDG_ERR_STATE, "setters are closed after idg_bind_workspace");
+    if (rule < IDG_NC_TRAP || rule > IDG_GAUSS_HERMITE || nx < 1 || ny < 1 ||
+        (long long)nx * ny > idg::kMaxVel)
+        return fail(c, IDG_ERR_ARG, "invalid velocity grid (rule %d, %d x %d)", rule, nx, ny);
+    std::vector<double> a, b;
+    if (!rule_1d(rule, nx, xmin, xmax, 1.0, a, b) || !rule_1d(rule, ny, ymin, ymax, 1.0, a, b))
+        return fail(c, IDG_ERR_ARG, "invalid velocity grid (rule %d, %d x %d)", rule, nx, ny);
+    c->vrule = rule;
+    c->nvx = nx;
+    c->nvy = ny;
+    c->vx0 = xmin; c->vx1 = xmax; c->vy0 = ymin; c->vy1 = ymax;
+    c->built = false;
+    return IDG_OK;
+}
+
+idg_status idg_set_gas(idg_ctx *c, int K, double Pr, double omega, double Kn, double RT_ref, int model)
+{
+    if (!c) return IDG_ERR_ARG;
+    if (c->bound) return fail(c, IDG_ERR_STATE, "setters are closed after idg_bind_workspace");
+    if (K < 0 || K > 16 || !(Pr > 0) || !(omega >= 0 && omega <= 1.5) || !(Kn > 0) || !(RT_ref > 0) ||
+        (model != IDG_BGK && model != IDG_SHAKHOV))
+        return fail(c, IDG_ERR_ARG, "invalid gas parameters");
+    c->K = K; c->Pr = Pr; c->omega = omega; c->Kn = Kn; c->RT_ref = RT_ref; c->model = model;
+    c->gas_set = true;
+    c->built = false;
+    return IDG_OK;
+}
+
+idg_status idg_set_boundary(idg_ctx *c, int side, int kind, double rho, double u, double v, double T)
+{
+    if (!c) return IDG_ERR_ARG;
+    if (c->bound) return fail(c, IDG_ERR_STATE, "setters are closed after idg_bind_workspace");
+    if (side < 0 || side > 3 || kind < IDG_BC_PERIODIC || kind > IDG_BC_FARFIELD)
+        return fail(c, IDG_ERR_ARG, "invalid boundary side %d / kind %d", side, kind);
+    if (kind != IDG_BC_PERIODIC && (!(T > 0) || !std::isfinite(u) || !std::isfinite(v)))
+        return fail(c, IDG_ERR_ARG, "invalid boundary state");
+    if (kind == IDG_BC_FARFIELD && !(rho > 0)) return fail(c, IDG_ERR_ARG, "far field needs rho > 0");
+    c->bc_kind[side] = kind;
+    c->bc_rho[side] = rho; c->bc_u[side] = u; c->bc_v[side] = v; c->bc_T[side] = T;
+    c->built = false;
+    return IDG_OK;
+}
+
+idg_status idg_set_numerics(idg_ctx *c, double cfl_imp, double cfl_phys, int limiter,
+                            double lusgs_omega, int flags)
+{
+    if (!c) return IDG_ERR_ARG;
+    if (c->bound) return fail(c, IDG_ERR_STATE, "setters are closed after idg_bind_workspace");
+    if (!(cfl_imp > 0) || !(cfl_phys > 0) || (limiter != 0 && limiter != 1) || !(lusgs_omega >= 1.0) ||
+        flags != 0)
+        return fail(c, IDG_ERR_ARG, "invalid numerics");
+    c->cfl_imp = cfl_imp; c->cfl_phys = cfl_phys; c->limiter = limiter;
+    c->lusgs_omega = lusgs_omega; c->flags = flags;
+    c->built = false;
+    return IDG_OK;
+}
+
+idg_status idg_workspace_size(idg_ctx *c, size_t *bytes)
+{
+    if (!c || !bytes) return IDG_ERR_ARG;
+    idg_status s = build(c);
+    if (s) return s;
+    *bytes = layout(c, nullptr, nullptr);
+    return IDG_OK;
+}
+
+idg_status idg_get_sizes(const idg_ctx *cc, int *ncell, int *nvel, int *nface)
+{
+    idg_ctx *c = const_cast<idg_ctx *>(cc);
+    if (!c) return IDG_ERR_ARG;
+    idg_status s = build(c);
+    if (s) return s;
+    if (ncell) *ncell = c->N;
+    if (nvel) *nvel = c->Nv;
+    if (nface) *nface = c->nf;
+    return IDG_OK;
+}
+
+idg_status idg_get_dt(const idg_ctx *cc, double *dt)
+{
+    idg_ctx *c = const_cast<idg_ctx *>(cc);
+    if (!c || !dt) return IDG_ERR_ARG;
+    idg_status s = build(c);
+    if (s) return s;
+    *dt = c->dt;
+    return IDG_OK;
+}
+
+idg_status idg_velocity_grid(const idg_ctx *cc, double *ux, double *uy, double *w)
+{
+    idg_ctx *c = const_cast<idg_ctx *>(cc);
+    if (!c) return IDG_ERR_ARG;
+    idg_status s = build(c);
+    if (s) return s;
+    if (ux) std::memcpy(ux, c->ux.data(), c->Nv * sizeof(double));
+    if (uy) std::memcpy(uy, c->uy.data(), c->Nv * sizeof(double));
+    if (w) std::memcpy(w, c->w.data(), c->Nv * sizeof(double));
+    return IDG_OK;
+}
+
+idg_status idg_bind_workspace(idg_ctx *c, void *dev_ptr, size_t bytes)
+{
+    if (!c || !dev_ptr) return IDG_ERR_ARG;
+    idg_status s = build(c);
+    if (s) return s;
+    size_t need = layout(c, nullptr, nullptr);
+    if (bytes < need) return fail(c, IDG_ERR_OOM, "workspace of %zu bytes, need %zu", bytes, need);
+    if (((uintptr_t)dev_ptr) & 255) return fail(c, IDG_ERR_ARG, "workspace must be 256-byte aligned");
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+    cudaPointerAttributes at{};
+    e = cudaPointerGetAttributes(&at, dev_ptr);
+    if (e != cudaSuccess || at.type != cudaMemoryTypeDevice || at.device != c->device) {
+        cudaGetLastError();
+        return fail(c, IDG_ERR_ARG, "workspace is not device memory of device %d", c->device);
+    }
+    c->ws = (char *)dev_ptr;
+    c->ws_bytes = bytes;
+    KParams &k = c->kp;
+    layout(c, c->ws, &k);
+    k.N = c->N; k.Nv = c->Nv; k.nf = c->nf; k.ni = c->ni; k.nj = c->nj; k.nvx = c->nvx;
+    k.K = c->K; k.shakhov = c->model == IDG_SHAKHOV; k.limiter = c->limiter;
+    k.per_i = c->bc_kind[IDG_IMIN] == IDG_BC_PERIODIC;
+    k.per_j = c->bc_kind[IDG_JMIN] == IDG_BC_PERIODIC;
+    k.dt = c->dt; k.h = 0.5 * c->dt; k.mu_ref = c->mu_ref; k.RT_ref = c->RT_ref; k.omega = c->omega;
+    k.Pr = c->Pr; k.gam = (double)(c->K + 4) / (double)(c->K + 2); k.lusgs_omega = c->lusgs_omega;
+    k.nilist = (int)c->ilist.size();
+    k.nblist = (int)c->blist.size();
+    // sweep launch shape: cell slots cover the longest hyperplane up to 64
+    int maxlen = std::min(c->ni, c->nj);
+    k.sweep_pc = std::min(maxlen, 64);
+    k.sweep_tv = std::min(32, std::max(1, 512 / k.sweep_pc));
+    // uploads
+    std::vector<float> uxf(c->ux.begin(), c->ux.end()), uyf(c->uy.begin(), c->uy.end()),
+        wf(c->w.begin(), c->w.end());
+    std::vector<double> bG((size_t)4 * c->Nv, 0.0), bH((size_t)4 * c->Nv, 0.0);
+    for (int sd = 0; sd < 4; ++sd) {
+        if (c->bc_kind[sd] == IDG_BC_PERIODIC) continue;
+        double RT = c->bc_T[sd] * c->RT_ref, lam = 0.5 / RT;
+        double rho = c->bc_kind[sd] == IDG_BC_WALL ? 1.0 : c->bc_rho[sd];
+        for (int q = 0; q < c->Nv; ++q) {
+            double cx = c->ux[q] - c->bc_u[sd], cy = c->uy[q] - c->bc_v[sd];
+            double G = rho * lam / M_PI * std::exp(-lam * (cx * cx + cy * cy));
+            bG[(size_t)sd * c->Nv + q] = G;
+            bH[(size_t)sd * c->Nv + q] = c->K * RT * G;
+        }
+    }
+    cudaError_t errs[] = {
+        up((double *)k.area, c->area), up((double *)k.dtimp, c->dtimp), up((int *)k.cface, c->cface),
+        up((int *)k.cnb, c->cnb), up((int *)k.csign, c->csign), up((double *)k.cr, c->cr),
+        up((double *)k.clsg, c->clsg), up((int *)k.fL, c->fL), up((int *)k.fR, c->fR),
+        up((double *)k.fgeo, c->fgeo), up((int *)k.fbc, c->fbc), up((int *)k.fside, c->fside),
+        c->ilist.empty() ? cudaSuccess : up((int *)k.ilist, c->ilist),
+        c->blist.empty() ? cudaSuccess : up((int *)k.blist, c->blist),
+        up((double *)k.ux, c->ux), up((double *)k.uy, c->uy), up((double *)k.w, c->w),
+        up((float *)k.uxf, uxf), up((float *)k.uyf, uyf), up((float *)k.wf, wf),
+        up((double *)k.bndG, bG), up((double *)k.bndH, bH),
+        cudaMemset(k.iter, 0, 256), cudaMemset(k.phi, 0, 32 * (size_t)c->nf)};
+    for (cudaError_t x : errs)
+        if (x != cudaSuccess) return cuda_fail(c, x, "workspace upload");
+    c->stage = (double *)k.F;
+    c->stage_bytes = (c->precision == IDG_FP64 ? 16 : 8) * (size_t)c->nf * c->Nv;
+    c->bound = true;
+    idg_status st = upload_reference(c);
+    if (st) { c->bound = false; return st; }
+    c->host_iter = 0;
+    restart(c);
+    return IDG_OK;
+}
+
+idg_status idg_init_uniform(idg_ctx *c, double rho, double u, double v, double T, void *stream)
+{
+    idg_status s = check_ready(c);
+    if (s) return s;
+    if (!(rho > 0) || !(T > 0) || !std::isfinite(u) || !std::isfinite(v))
+        return fail(c, IDG_ERR_ARG, "invalid uniform state");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "sync");
+    c->ref_rho = rho; c->ref_u = u; c->ref_v = v; c->ref_T = T;
+    if ((s = upload_reference(c))) return s;
+    const size_t t2 = c->precision == IDG_FP64 ? 16 : 8;
+    // f~ = M_ref exactly: deviation zero
+    if ((e = cudaMemsetAsync(c->kp.f, 0, t2 * (size_t)c->N * c->Nv, st)) != cudaSuccess)
+        return cuda_fail(c, e, "memset f");
+    double RT = T * c->RT_ref;
+    std::vector<double> W((size_t)4 * c->N);
+    for (int q = 0; q < c->N; ++q) {
+        W[4 * q] = rho; W[4 * q + 1] = rho * u; W[4 * q + 2] = rho * v;
+        W[4 * q + 3] = 0.5 * rho * (u * u + v * v + (c->K + 2) * RT);
+    }
+    if ((e = cudaMemcpyAsync(c->kp.W, W.data(), W.size() * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return cuda_fail(c, e, "upload W");
+    if ((e = cudaMemsetAsync(c->kp.status, 0, sizeof(int), st)) != cudaSuccess) return cuda_fail(c, e, "status");
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(c, e, "sync");
+    restart(c);
+    return IDG_OK;
+}
+
+idg_status idg_set_state(idg_ctx *c, const double *G, const double *H, const double *W, void *stream)
+{
+    idg_status s = check_ready(c);
+    if (s) return s;
+    if (!G || !H || !W) return fail(c, IDG_ERR_ARG, "null state array");
+    cudaStream_t st = (cudaStream_t)stream;
+    size_t n = (size_t)c->N * c->Nv;
+    cudaError_t e;
+    // stage G and H as float64 in the face-flux buffer (large enough: nf >= 2N)
+    double *dG = c->stage, *dH = c->stage + n;
+    if (2 * n * sizeof(double) > c->stage_bytes) return fail(c, IDG_ERR_STATE, "staging buffer too small");
+    if ((e = cudaMemcpyAsync(dG, G, n * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess) return cuda_fail(c, e, "H2D G");
+    if ((e = cudaMemcpyAsync(dH, H, n * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess) return cuda_fail(c, e, "H2D H");
+    if ((e = cudaMemcpyAsync(c->kp.W, W, (size_t)c->N * 32, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return cuda_fail(c, e, "H2D W");
+    int rc = idg::launch_to_dev(c->kp, c->precision == IDG_FP64, dG, dH, st);
+    if (rc) return cuda_fail(c, (cudaError_t)rc, "to_dev");
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(c, e, "sync");
+    restart(c);
+    return IDG_OK;
+}
+
+idg_status idg_get_state(idg_ctx *c, double *G, double *H, double *W, void *stream)
+{
+    idg_status s = check_ready(c);
+    if (s) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    size_t n = (size_t)c->N * c->Nv;
+    cudaError_t e;
+    double *dG = c->stage, *dH = c->stage + n;
+    if (G || H) {
+        int rc = idg::launch_from_dev(c->kp, c->precision == IDG_FP64, dG, dH, st);
+        if (rc) return cuda_fail(c, (cudaError_t)rc, "from_dev");
+        if (G && (e = cudaMemcpyAsync(G, dG, n * 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return cuda_fail(c, e, "D2H G");
+        if (H && (e = cudaMemcpyAsync(H, dH, n * 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return cuda_fail(c, e, "D2H H");
+    }
+    if (W && (e = cudaMemcpyAsync(W, c->kp.W, (size_t)c->N * 32, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_fail(c, e, "D2H W");
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(c, e, "sync");
+    return IDG_OK;
+}
+
+idg_status idg_iterate(idg_ctx *c, int max_iter, double tol, void *stream, int *iters_done,
+                       double *residual)
+{
+    idg_status s = check_ready(c);
+    if (s) return s;
+    if (max_iter < 0) return fail(c, IDG_ERR_ARG, "max_iter < 0");
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool fp64 = c->precision == IDG_FP64;
+    const int chunk = 16;
+    int done = 0;
+    double rel = NAN;
+    std::vector<double> buf(chunk);
+    int status = 0;
+    bool converged = false;
+    while (done < max_iter) {
+        int n = std::min(chunk, max_iter - done);
+        long long it0 = c->host_iter;
+        for (int q = 0; q < n; ++q) {
+            int rc = idg::launch_iteration(c->kp, fp64, st);
+            if (rc) return cuda_fail(c, (cudaError_t)rc, "launch");
+        }
+        c->host_iter += n;
+        done += n;
+        // residuals of this chunk from the device ring
+        cudaError_t e;
+        for (int q = 0; q < n; ++q) {
+            long long slot = (it0 + q) & (idg::kMaxHist - 1);
+            e = cudaMemcpyAsync(&buf[q], c->kp.res + slot, 8, cudaMemcpyDeviceToHost, st);
+            if (e != cudaSuccess) return cuda_fail(c, e, "D2H residual");
+        }
+        if ((e = cudaMemcpyAsync(&status, c->kp.status, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+            return cuda_fail(c, e, "D2H status");
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(c, e, "iteration");
+        for (int q = 0; q < n; ++q) c->hist.push_back(buf[q]);
+        if (status) {
+            if (iters_done) *iters_done = done;
+            return fail(c, IDG_ERR_NONFINITE, "residual became non-finite");
+        }
+        double r1 = c->hist.front();
+        rel = r1 > 0 ? c->hist.back() / r1 : c->hist.back();
+        if (tol > 0 && rel <= tol) { converged = true; break; }
+    }
+    if (iters_done) *iters_done = done;
+    if (residual) *residual = rel;
+    if (tol > 0 && !converged) return fail(c, IDG_ERR_NOT_CONVERGED, "residual %.3e above tol %.3e", rel, tol);
+    return IDG_OK;
+}
+
+idg_status idg_iterate_profiled(idg_ctx *c, void *stream, double *kernel_ms)
+{
+    idg_status s = check_ready(c);
+    if (s) return s;
+    if (!kernel_ms) return IDG_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t ev[7];
+    for (int q = 0; q < 7; ++q) {
+        cudaError_t e = cudaEventCreate(&ev[q]);
+        if (e != cudaSuccess) {
+            for (int u = 0; u < q; ++u) cudaEventDestroy(ev[u]);
+            return cuda_fail(c, e, "cudaEventCreate");
+        }
+    }
+    int rc = idg::launch_iteration(c->kp, c->precision == IDG_FP64, st, (void **)ev);
+    cudaError_t e = rc ? (cudaError_t)rc : cudaStreamSynchronize(st);
+    double r = 0.0;
+    if (e == cudaSuccess) {
+        for (int q = 0; q < 6; ++q) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ev[q], ev[q + 1]);
+            kernel_ms[q] = ms;
+        }
+        long long slot = c->host_iter & (idg::kMaxHist - 1);
+        e = cudaMemcpy(&r, c->kp.res + slot, 8, cudaMemcpyDeviceToHost);
+    }
+    for (int q = 0; q < 7; ++q) cudaEventDestroy(ev[q]);
+    if (e != cudaSuccess) return cuda_fail(c, e, "profiled iteration");
+    c->host_iter += 1;
+    c->hist.push_back(r);
+    return IDG_OK;
+}
+
+idg_status idg_get_moments(idg_ctx *c, double *out6, void *stream)
+{
+    idg_status s = check_ready(c);
+    if (s) return s;
+    if (!out6) return IDG_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = idg::launch_cell_moments(c->kp, c->precision == IDG_FP64, c->moments_dev, st);
+    if (rc) return cuda_fail(c, (cudaError_t)rc, "moments");
+    cudaError_t e = cudaMemcpyAsync(out6, c->moments_dev, (size_t)c->N * 48, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "D2H moments");
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(c, e, "sync");
+    return IDG_OK;
+}
+
+idg_status idg_get_residual_history(idg_ctx *c, double *out, int cap, int *n)
+{
+    if (!c || (!out && cap > 0) || cap < 0) return IDG_ERR_ARG;
+    int m = std::min<int>(cap, (int)c->hist.size());
+    if (m > 0) std::memcpy(out, c->hist.data(), m * sizeof(double));
+    if (n) *n = m;
+    return IDG_OK;
+}
+
+idg_status idg_get_face_flux_moments(idg_ctx *c, double *phi4, void *stream)
+{
+    idg_status s = check_ready(c);
+    if (s) return s;
+    if (!phi4) return IDG_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(phi4, c->kp.phi, (size_t)c->nf * 32, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "D2H phi");
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(c, e, "sync");
+    return IDG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,99 @@
+"""Solver: one IDUGKS problem on one GPU through the C ABI.
+
+PyTorch only provides the device workspace and the CUDA stream; every step of
+the scheme runs in libidugks.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import binding as B
+from .inputs import Problem
+
+
+def configure(ctx, prob: Problem):
+    """Pass a Problem description to a fresh context (setters of include/idugks.h)."""
+    B.idg_set_mesh_structured(ctx, prob.nodes_x, prob.nodes_y)
+    x0, x1, y0, y1 = prob.vrange
+    B.idg_set_velocity_grid(ctx, prob.vrule, prob.nvx, prob.nvy, x0, x1, y0, y1)
+    B.idg_set_gas(ctx, prob.K, prob.Pr, prob.omega, prob.Kn, prob.RT_ref,
+                  B.IDG_SHAKHOV if prob.shakhov else B.IDG_BGK)
+    for side in range(4):
+        kind, rho, u, v, T = prob.bc[side]
+        B.idg_set_boundary(ctx, side, kind, rho, u, v, T)
+    B.idg_set_numerics(ctx, prob.cfl_imp, prob.cfl_phys, prob.limiter, prob.lusgs_omega, prob.flags)
+
+
+class Solver:
+    """IDUGKS steady solver for one Problem.
+
+    precision: "fp64" (f in float64) or "mixed" (f in float32, moments,
+    macroscopic predictor and residual in float64).
+    """
+
+    def __init__(self, prob: Problem, precision: str = "fp64", device: int = 0, stream=None):
+        import torch
+
+        self.prob = prob
+        self.device = device
+        self.torch = torch
+        p = B.IDG_FP64 if precision == "fp64" else B.IDG_MIXED
+        self.precision = precision
+        self.ctx = B.idg_create(p, device)
+        configure(self.ctx, prob)
+        self.N, self.Nv, self.nf = B.idg_get_sizes(self.ctx)
+        nbytes = B.idg_workspace_size(self.ctx)
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=f"cuda:{device}")
+        base = self.workspace.data_ptr()
+        aligned = (base + 255) & ~255
+        self._stream = stream
+        B.idg_bind_workspace(self.ctx, aligned, nbytes)
+
+    @property
+    def stream(self):
+        if self._stream is not None:
+            return self._stream
+        return self.torch.cuda.current_stream(self.device).cuda_stream
+
+    def __del__(self):
+        ctx = getattr(self, "ctx", None)
+        if ctx is not None:
+            B.idg_destroy(ctx)
+            self.ctx = None
+
+    @property
+    def dt(self) -> float:
+        return B.idg_get_dt(self.ctx)
+
+    def velocity_grid(self):
+        return B.idg_velocity_grid(self.ctx, self.Nv)
+
+    def init_uniform(self, rho=None, u=None, v=None, T=None):
+        r0, u0, v0, T0 = self.prob.init
+        B.idg_init_uniform(self.ctx, r0 if rho is None else rho, u0 if u is None else u,
+                           v0 if v is None else v, T0 if T is None else T, self.stream)
+
+    def set_state(self, G, H, W):
+        B.idg_set_state(self.ctx, G, H, W, self.stream)
+
+    def get_state(self):
+        return B.idg_get_state(self.ctx, self.N, self.Nv, self.stream)
+
+    def iterate(self, max_iter: int, tol: float = 0.0):
+        """Returns (converged, iterations, relative residual)."""
+        st, n, r = B.idg_iterate(self.ctx, max_iter, tol, self.stream)
+        return st == B.IDG_OK, n, r
+
+    def iterate_profiled(self) -> np.ndarray:
+        """One iteration; device ms of cell prep, interior faces, boundary faces,
+        macroscopic predictor, forward sweep, backward sweep."""
+        return B.idg_iterate_profiled(self.ctx, self.stream)
+
+    def moments(self) -> np.ndarray:
+        return B.idg_get_moments(self.ctx, self.N, self.stream)
+
+    def residual_history(self) -> np.ndarray:
+        return B.idg_get_residual_history(self.ctx, 1 << 20)
+
+    def face_flux_moments(self) -> np.ndarray:
+        return B.idg_get_face_flux_moments(self.ctx, self.nf, self.stream)

@@ -1,0 +1,143 @@
+"""GPU parity: libidugks through its C ABI against the FP64 oracle on the same
+seeded inputs.
+
+FP64 path: 1e-12 relative per iteration (max over all (cell, velocity) of
+|f_gpu - f_oracle| / max|f_oracle|, likewise for W), 1e-10 on converged fields.
+Mixed path: steady u and T within rel. L2 1e-5 of the FP64 oracle.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1709_01819_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1709_01819_gb300 import build
+    build.build()
+
+
+def _solver(prob, precision="fp64"):
+    from paper_1709_01819_gb300.solver import Solver
+    return Solver(prob, precision)
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def _cases():
+    c = {}
+    # ragged: non-square block, velocity count not a multiple of any tile
+    c["cavity_shakhov_12x9_v15x13"] = I.cavity(12, Kn=0.075, U=0.15, nv=15, vmax=4.0)
+    p = c["cavity_shakhov_12x9_v15x13"]
+    X, Y = I.uniform_nodes(12, 9, 0, 1, 0, 0.8)
+    p.nodes_x, p.nodes_y, p.nvy = X, Y, 13
+    c["couette_16_v16"] = I.couette(16, U=0.1, Kn=0.1, nv=16, vmax=4.0)
+    c["cavity_tanh_gh14"] = I.cavity(10, Kn=1e-3, U=0.15, nv=14, vrule=I.GAUSS_HERMITE,
+                                     stretch_beta=1.83297, cfl_imp=1e4)
+    c["cylinder_20x8_simpson11_limiter"] = I.cylinder(ntheta=20, nr=8, nv=11, vmax=8.0, Ma=2.0, Kn=0.5)
+    c["cavity_bgk_kn1_v24"] = I.cavity(8, Kn=1.0, U=0.3, nv=24, vmax=4.0, shakhov=0, Pr=1.0)
+    return c
+
+
+CASES = _cases()
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_fp64_matches_oracle_per_iteration_from_uniform(name):
+    prob = CASES[name]
+    o = O.Oracle(prob)
+    o.init_uniform()
+    s = _solver(prob, "fp64")
+    s.init_uniform()
+    for n in (1, 2, 5):
+        o.iterate(n)
+        s.iterate(n)
+        G, H, W = s.get_state()
+        Go, Ho, Wo = o.get_state()
+        assert _rel(G, Go) < 1e-12, (name, n, _rel(G, Go))
+        assert _rel(H, Ho) < 1e-12, (name, n, _rel(H, Ho))
+        for q in range(4):
+            assert _rel(W[:, q], Wo[:, q]) < 1e-12 or np.abs(W[:, q] - Wo[:, q]).max() < 1e-14
+    phi = s.face_flux_moments()
+    phio = o.face_phi()
+    assert np.abs(phi - phio).max() < 1e-12 * np.abs(phio).max()
+    ro = o.iterate(1)
+    s.iterate(1)
+    rg = s.residual_history()
+    assert abs(rg[-1] - ro[0]) <= 1e-10 * ro[0] + 1e-300
+
+
+@pytest.mark.parametrize("name", ["cavity_shakhov_12x9_v15x13", "cylinder_20x8_simpson11_limiter"])
+def test_fp64_matches_oracle_from_random_state(name):
+    prob = CASES[name]
+    G0, H0, W0 = I.random_state(prob, seed=1709)
+    o = O.Oracle(prob)
+    o.set_state(G0, H0, W0)
+    s = _solver(prob, "fp64")
+    s.init_uniform()      # fixes the storage reference; the state is replaced next
+    s.set_state(G0, H0, W0)
+    G, H, W = s.get_state()
+    assert _rel(G, G0) < 1e-15 and _rel(W, W0) == 0
+    o.iterate(2)
+    s.iterate(2)
+    G, H, W = s.get_state()
+    Go, Ho, Wo = o.get_state()
+    assert _rel(G, Go) < 1e-12
+    assert _rel(H, Ho) < 1e-12
+    assert _rel(W, Wo) < 1e-12
+
+
+def test_fp64_converged_couette_matches_oracle():
+    prob = I.couette(16, U=0.1, Kn=0.1, nv=16, vmax=4.0, cfl_imp=1000.0)
+    o = O.Oracle(prob)
+    o.init_uniform()
+    ro = o.iterate(400)
+    s = _solver(prob, "fp64")
+    s.init_uniform()
+    ok, n, r = s.iterate(400)
+    assert r < 1e-9 and ro[-1] < 1e-9 * ro[0]
+    m, mo = s.moments(), o.moments()
+    for q in range(4):
+        assert np.abs(m[:, q] - mo[:, q]).max() <= 1e-10 * np.abs(mo[:, q]).max()
+    hist = s.residual_history()
+    # identical convergence history while the residual is well above round-off
+    big = ro > 1e-6 * ro[0]
+    assert np.allclose(hist[big], ro[big], rtol=1e-8)
+
+
+def test_mixed_converged_cavity_within_1e5_of_fp64_oracle():
+    prob = I.cavity(16, Kn=0.075, U=0.15, nv=16, vmax=4.0, cfl_imp=1000.0)
+    o = O.Oracle(prob)
+    o.init_uniform()
+    o.iterate(300)
+    mo = o.moments()
+    s = _solver(prob, "mixed")
+    s.init_uniform()
+    ok, n, r = s.iterate(300)
+    m = s.moments()
+    speed = np.hypot(mo[:, 1], mo[:, 2])
+    du = np.sqrt(np.sum((m[:, 1] - mo[:, 1]) ** 2 + (m[:, 2] - mo[:, 2]) ** 2) / np.sum(speed ** 2))
+    dT = np.linalg.norm(m[:, 3] - mo[:, 3]) / np.linalg.norm(mo[:, 3])
+    assert du < 1e-5, du
+    assert dT < 1e-5, dT
+
+
+def test_uniform_maxwellian_fixed_point_on_gpu_both_precisions():
+    prob = I.cavity(12, Kn=0.075, U=0.0, nv=16)
+    for prec in ("fp64", "mixed"):
+        s = _solver(prob, prec)
+        s.init_uniform()
+        G0, H0, W0 = s.get_state()
+        s.iterate(20)
+        G, H, W = s.get_state()
+        tol = 1e-14 if prec == "fp64" else 1e-7
+        assert _rel(G, G0) < tol, (prec, _rel(G, G0))
+        assert np.abs(W - W0).max() < tol

@@ -1,0 +1,133 @@
+"""CPU-side checks of libidugks: the library loads, exports every entry point
+declared in include/idugks.h, validates its arguments, and its host-side
+setup (velocity quadrature, face count, time step) agrees with the oracle
+and with numpy's Gauss-Hermite rule.  No GPU work is launched here."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1709_01819_gb300 import binding as B
+from paper_1709_01819_gb300 import build as BUILD
+from paper_1709_01819_gb300 import inputs as I
+from paper_1709_01819_gb300.solver import configure
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    BUILD.build()
+
+
+def declared_symbols():
+    out = []
+    for name in os.listdir(os.path.join(ROOT, "include")):
+        if name.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", name)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            out += re.findall(r"\b(idg_[a-z0-9_]+)\s*\(", txt)
+    return sorted(set(out))
+
+
+def test_library_exports_every_declared_symbol():
+    names = declared_symbols()
+    assert "idg_iterate" in names and "idg_create" in names
+    L = B.lib()
+    for n in names:
+        assert hasattr(L, n), f"missing export {n}"
+    bound = {s[0] for s in B.SIGNATURES}
+    assert set(names) <= bound, f"binding lacks {set(names) - bound}"
+
+
+def test_nm_lists_every_symbol():
+    import subprocess
+    out = subprocess.run(["nm", "-D", "--defined-only", BUILD.LIB], capture_output=True, text=True).stdout
+    for n in declared_symbols():
+        assert re.search(rf"\bT {n}\b", out), n
+
+
+def _ctx(prob, precision=B.IDG_FP64):
+    ctx = B.idg_create(precision, 0)
+    configure(ctx, prob)
+    return ctx
+
+
+def test_argument_validation_returns_status_codes():
+    L = B.lib()
+    import ctypes as C
+    h = C.c_void_p()
+    assert L.idg_create(C.byref(h), 7, 0) == B.IDG_ERR_ARG
+    ctx = B.idg_create(B.IDG_MIXED, 0)
+    with pytest.raises(B.IdgError) as e:
+        B.idg_set_velocity_grid(ctx, B.IDG_NC_SIMPSON, 32, 32, -4, 4, -4, 4)  # Simpson needs odd n
+    assert e.value.status == B.IDG_ERR_ARG
+    with pytest.raises(B.IdgError) as e:
+        B.idg_set_gas(ctx, 1, -1.0, 0.5, 0.1, 0.5, B.IDG_BGK)
+    assert e.value.status == B.IDG_ERR_ARG
+    with pytest.raises(B.IdgError) as e:
+        B.idg_workspace_size(ctx)  # nothing configured yet
+    assert e.value.status == B.IDG_ERR_STATE
+    with pytest.raises(B.IdgError) as e:
+        B.idg_iterate(ctx, 1, 0.0)
+    assert e.value.status == B.IDG_ERR_STATE
+    assert "workspace" in B.idg_last_error(ctx)
+    # one-sided periodicity is rejected
+    p = I.cavity(4, nv=8)
+    p.bc[0] = (I.BC_PERIODIC, 0, 0, 0, 0)
+    ctx2 = _ctx(p)
+    with pytest.raises(B.IdgError) as e:
+        B.idg_workspace_size(ctx2)
+    assert e.value.status == B.IDG_ERR_ARG
+    B.idg_destroy(ctx)
+    B.idg_destroy(ctx2)
+
+
+def test_inverted_cells_are_rejected():
+    p = I.cavity(4, nv=8)
+    p.nodes_x = p.nodes_x[:, ::-1].copy()
+    ctx = _ctx(p)
+    with pytest.raises(B.IdgError) as e:
+        B.idg_workspace_size(ctx)
+    assert "area" in str(e.value)
+    B.idg_destroy(ctx)
+
+
+@pytest.mark.parametrize("n", [8, 28, 60])
+def test_library_gauss_hermite_matches_numpy(n):
+    p = I.cavity(4, nv=n, vrule=I.GAUSS_HERMITE)
+    ctx = _ctx(p)
+    N, Nv, nf = B.idg_get_sizes(ctx)
+    ux, uy, w = B.idg_velocity_grid(ctx, Nv)
+    xr, wr = np.polynomial.hermite.hermgauss(n)
+    x = ux[:n]
+    wx = w[:n] / w[0] * 1.0
+    assert np.allclose(x, xr, rtol=0, atol=1e-12 * max(1, abs(xr).max()))
+    # tensor weights: w[k] = w1[kx] w1[ky]; recover w1 from the first row
+    w1 = w[:n] / np.sqrt(w[0])
+    assert np.allclose(w1 * np.exp(-x * x), wr, rtol=1e-10)
+    B.idg_destroy(ctx)
+
+
+@pytest.mark.parametrize("case", ["couette", "cavity_tanh_gh", "cylinder"])
+def test_host_setup_agrees_with_oracle(case):
+    from oracle import oracle as O
+    if case == "couette":
+        p = I.couette(16, nv=16)
+    elif case == "cavity_tanh_gh":
+        p = I.cavity(12, nv=14, vrule=I.GAUSS_HERMITE, stretch_beta=1.5)
+    else:
+        p = I.cylinder(ntheta=20, nr=8, nv=11, vmax=6.0)
+    o = O.Oracle(p)
+    ctx = _ctx(p)
+    N, Nv, nf = B.idg_get_sizes(ctx)
+    assert (N, Nv, nf) == (o.N, o.Nv, o.nf)
+    ux, uy, w = B.idg_velocity_grid(ctx, Nv)
+    oux, ouy, ow = o.velocity_grid()
+    assert np.allclose(ux, oux, rtol=0, atol=1e-13)
+    assert np.allclose(uy, ouy, rtol=0, atol=1e-13)
+    assert np.allclose(w, ow, rtol=1e-12)
+    assert abs(B.idg_get_dt(ctx) - o.dt) <= 1e-14 * o.dt
+    assert B.idg_workspace_size(ctx) > 0
+    B.idg_destroy(ctx)
