@@ -417,6 +417,13 @@ size_t layout(idg_ctx *c, char *base, KParams *kp)
     k.dW = L.take<double>(32 * N);
     k.lam = L.take<double>(8 * nf);
     k.Dm = L.take<double>(8 * N);
+    k.mbase = L.take<char>(64 * N);
+    k.moff = L.take<char>(128 * N);
+    k.mD = L.take<char>(8 * N);
+    k.mR = L.take<char>(32 * N);
+    k.mdW = L.take<char>(32 * N);
+    k.mpart = L.take<double>(8 * (N / 256 + 2));
+    k.cellpT = L.take<char>(8 * idg::kCellP * N);
     k.res = L.take<double>(8 * (size_t)idg::kMaxHist);
     k.iter = L.take<int>(256);
     k.status = k.iter + 1;
@@ -667,8 +674,9 @@ idg_status idg_bind_workspace(idg_ctx *c, void *dev_ptr, size_t bytes)
     k.nblist = (int)c->blist.size();
     // sweep launch shape: cell slots cover the longest hyperplane up to 64
     int maxlen = std::min(c->ni, c->nj);
-    k.sweep_pc = std::min(maxlen, 64);
-    k.sweep_tv = std::min(32, std::max(1, 512 / k.sweep_pc));
+    k.sweep_pc = std::min(maxlen, 128);
+    k.sweep_tv = 8;
+    while (k.sweep_tv < 32 && 2 * k.sweep_tv * k.sweep_pc <= 256) k.sweep_tv *= 2;
     // uploads
     std::vector<float> uxf(c->ux.begin(), c->ux.end()), uyf(c->uy.begin(), c->uy.end()),
         wf(c->w.begin(), c->w.end());
@@ -697,6 +705,9 @@ idg_status idg_bind_workspace(idg_ctx *c, void *dev_ptr, size_t bytes)
         cudaMemset(k.iter, 0, 256), cudaMemset(k.phi, 0, 32 * (size_t)c->nf)};
     for (cudaError_t x : errs)
         if (x != cudaSuccess) return cuda_fail(c, x, "workspace upload");
+    int rcfg = idg::configure_kernels(k, c->precision == IDG_FP64);
+    if (rcfg) return fail(c, IDG_ERR_ARG, "mesh too wide for the sweep kernels' shared memory (%s)",
+                          cudaGetErrorString((cudaError_t)rcfg));
     c->stage = (double *)k.F;
     c->stage_bytes = (c->precision == IDG_FP64 ? 16 : 8) * (size_t)c->nf * c->Nv;
     c->bound = true;

@@ -57,6 +57,14 @@ struct KParams {
     double *dW;     // [N][4]
     double *lam;    // [nf]
     double *Dm;     // [N]
+    // macroscopic LU-SGS work (T = storage precision of the sweep)
+    void *mbase;    // [N][8] T: rho, m_x, m_y, E, u, v, p, E+p of W^n
+    void *moff;     // [N][4][4] T: (S/2) n_out, (omega/2) Lambda, 0 per slot
+    void *mD;       // [N] T diagonal
+    void *mR;       // [N][4] T residual
+    void *mdW;      // [N][4] T increments (Delta W* then Delta W)
+    double *mpart;  // [ceil(N/256)] block partial sums of ||R/Omega||^2
+    void *cellpT;   // [N][16] T copy of cellp for the sweeps
     double *res;    // [kMaxHist] absolute residual per iteration
     int *iter;      // [1] device iteration counter
     int *status;    // [1] device status word
@@ -71,6 +79,7 @@ struct KParams {
 constexpr int kCellP = 16;
 
 // kernel launchers (idugks_kernels.cu)
+int configure_kernels(const KParams &p, bool fp64);
 int launch_iteration(const KParams &p, bool fp64, void *stream, void **events = nullptr);
 int launch_cell_moments(const KParams &p, bool fp64, double *out6_dev, void *stream);
 int launch_to_dev(const KParams &p, bool fp64, const double *G, const double *H, void *stream);

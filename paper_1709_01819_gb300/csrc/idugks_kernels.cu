@@ -27,6 +27,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <algorithm>
+
 namespace idg {
 
 // ---------------------------------------------------------------------------
@@ -157,15 +159,6 @@ template <class T> __device__ __forceinline__ EqT<T> eq_cast(const EqD &d)
     e.e0 = (T)d.e0; e.ex = (T)d.ex; e.ey = (T)d.ey; e.e2 = (T)d.e2; e.U = (T)d.U; e.V = (T)d.V;
     e.invRT = (T)d.invRT; e.pqx = (T)d.pqx; e.pqy = (T)d.pqy; e.rr = (T)d.rr; e.rrm1 = (T)d.rrm1;
     e.kRT = (T)d.kRT; e.lnA = (T)d.lnA; e.lam = (T)d.lam;
-    return e;
-}
-
-template <class T> __device__ __forceinline__ EqT<T> eq_load(const double *cp)
-{
-    EqT<T> e;
-    e.e0 = (T)cp[0]; e.ex = (T)cp[1]; e.ey = (T)cp[2]; e.e2 = (T)cp[3]; e.U = (T)cp[4];
-    e.V = (T)cp[5]; e.invRT = (T)cp[6]; e.pqx = (T)cp[7]; e.pqy = (T)cp[8]; e.rr = (T)cp[9];
-    e.rrm1 = (T)cp[10]; e.kRT = (T)cp[11]; e.lnA = (T)cp[12]; e.lam = (T)cp[13];
     return e;
 }
 
@@ -552,20 +545,16 @@ __global__ void __launch_bounds__(256) k_face_boundary(KParams p, const int *lis
 }
 
 // ---------------------------------------------------------------------------
-// macroscopic predictor (Eq. 27-31), one CTA, float64                   [a5]
+// macroscopic predictor (Eq. 27-31)                                     [a5]
+//   k_macro_pre    (all cells, many CTAs): residual R_W = -sum Phi, partial
+//                  norms, spectral radii (Eq. 31 at the face average), the
+//                  LU-SGS diagonal D (Eq. 30) and per-neighbour coefficients
+//   k_macro_sweep  (one CTA): forward and backward sweeps on i+j hyperplanes,
+//                  the lexicographic dependency order, with the matrix-free
+//                  off-diagonal term 1/2 (dF S - omega Lambda dW) of Eq. (30)
+//   k_macro_post   (all cells): W^{n+1} = W + dW (Eq. 32) in float64 and the
+//                  micro coefficients at the predicted state
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void euler_flux(double gam, const double *W, double nx, double ny,
-                                           double *F)
-{
-    double rho = W[0], u = W[1] / rho, v = W[2] / rho;
-    double pr = (gam - 1.0) * (W[3] - 0.5 * rho * (u * u + v * v));
-    double vn = u * nx + v * ny;
-    F[0] = rho * vn;
-    F[1] = W[1] * vn + pr * nx;
-    F[2] = W[2] * vn + pr * ny;
-    F[3] = (W[3] + pr) * vn;
-}
-
 __device__ __forceinline__ void prim_uvc(const KParams &p, const double *W, double &u, double &v,
                                          double &cs)
 {
@@ -576,138 +565,210 @@ __device__ __forceinline__ void prim_uvc(const KParams &p, const double *W, doub
     cs = sqrt(p.gam * RT);
 }
 
-// off-diagonal LU-SGS term of one neighbour: 1/2 (dF S - omega Lambda dW)
-__device__ __forceinline__ void offdiag(const KParams &p, int c, int m, double *acc, double sgn)
+__device__ __forceinline__ double face_lambda(const KParams &p, int fi)
 {
-    int fi = p.cface[4 * c + m];
-    int nb = p.cnb[4 * c + m];
-    double s = p.csign[4 * c + m];
+    int L = p.fL[fi], R = p.fR[fi];
     const double *g = p.fgeo + 7 * fi;
-    double nx = s * g[0], ny = s * g[1], S = g[2];
-    const double *Wn = p.W + 4 * nb, *dWn = p.dW + 4 * nb;
-    double W1[4] = {Wn[0] + dWn[0], Wn[1] + dWn[1], Wn[2] + dWn[2], Wn[3] + dWn[3]};
-    double F1[4], F0[4];
-    euler_flux(p.gam, W1, nx, ny, F1);
-    euler_flux(p.gam, Wn, nx, ny, F0);
-    double lam = p.lam[fi];
-    for (int q = 0; q < 4; ++q)
-        acc[q] += sgn * 0.5 * ((F1[q] - F0[q]) * S - p.lusgs_omega * lam * dWn[q]);
+    double u, v, cs;
+    if (L >= 0 && R >= 0) {
+        double u1, v1, c1, u2, v2, c2;
+        prim_uvc(p, p.W + 4 * L, u1, v1, c1);
+        prim_uvc(p, p.W + 4 * R, u2, v2, c2);
+        u = 0.5 * (u1 + u2); v = 0.5 * (v1 + v2); cs = 0.5 * (c1 + c2);
+    } else {
+        prim_uvc(p, p.W + 4 * (L >= 0 ? L : R), u, v, cs);
+    }
+    return (fabs(u * g[0] + v * g[1]) + cs) * g[2];
 }
 
-__global__ void __launch_bounds__(1024) k_macro(KParams p)
+template <class T>
+__global__ void __launch_bounds__(256) k_macro_pre(KParams p)
 {
     __shared__ double sm[32];
-    const int tid = threadIdx.x, nt = blockDim.x;
-    // residual of Eq. (27): R_W = - sum_faces Phi (outward), and its norm
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
     double part[1] = {0.0};
-    for (int c = tid; c < p.N; c += nt) {
+    if (c < p.N) {
         double acc[4] = {0, 0, 0, 0};
         for (int m = 0; m < 4; ++m) {
             double s = p.csign[4 * c + m];
             const double *ph = p.phi + 4 * p.cface[4 * c + m];
             for (int q = 0; q < 4; ++q) acc[q] -= s * ph[q];
         }
+        T *R = (T *)p.mR + 4 * c;
         for (int q = 0; q < 4; ++q) {
             p.rw[4 * c + q] = acc[q];
+            R[q] = (T)acc[q];
             double rr = acc[q] / p.area[c];
             part[0] += rr * rr;
         }
+        const double *W = p.W + 4 * c;
+        double rho = W[0], u = W[1] / rho, v = W[2] / rho;
+        double pr = (p.gam - 1.0) * (W[3] - 0.5 * rho * (u * u + v * v));
+        T *b = (T *)p.mbase + 8 * c;
+        b[0] = (T)rho; b[1] = (T)W[1]; b[2] = (T)W[2]; b[3] = (T)W[3];
+        b[4] = (T)u; b[5] = (T)v; b[6] = (T)pr; b[7] = (T)(W[3] + pr);
+        double d = p.area[c] / p.dtimp[c];
+        T *o = (T *)p.moff + 16 * c;
+        for (int m = 0; m < 4; ++m) {
+            int fi = p.cface[4 * c + m];
+            double lam = face_lambda(p, fi);
+            if (p.fL[fi] != p.fR[fi]) d += 0.5 * p.lusgs_omega * lam;
+            double s = p.csign[4 * c + m];
+            const double *g = p.fgeo + 7 * fi;
+            o[4 * m + 0] = (T)(0.5 * g[2] * s * g[0]);
+            o[4 * m + 1] = (T)(0.5 * g[2] * s * g[1]);
+            o[4 * m + 2] = (T)(0.5 * p.lusgs_omega * lam);
+            o[4 * m + 3] = (T)0;
+        }
+        ((T *)p.mD)[c] = (T)d;
     }
     block_sum<1>(part, sm);
+    if (threadIdx.x == 0) p.mpart[blockIdx.x] = part[0];
+}
+
+// Exact increment F_n(W + dW) - F_n(W) of the Euler flux, written so that no
+// two O(1) quantities are subtracted (every term is an increment times a
+// base quantity); n is pre-scaled by S/2.
+template <class T>
+__device__ __forceinline__ void euler_dflux(T gm1, const T *b, const T *dW, T nx, T ny, T *dF)
+{
+    T rho = b[0], mx = b[1], my = b[2], u = b[4], v = b[5], H = b[7];
+    T r1 = rho + dW[0];
+    T du = (dW[1] - u * dW[0]) / r1, dv = (dW[2] - v * dW[0]) / r1;
+    T vn = u * nx + v * ny, dvn = du * nx + dv * ny, vn1 = vn + dvn;
+    T dmu = dW[1] * (u + du) + dW[2] * (v + dv) + mx * du + my * dv;
+    T dp = gm1 * (dW[3] - (T)0.5 * dmu);
+    dF[0] = dW[0] * vn1 + rho * dvn;
+    dF[1] = dW[1] * vn1 + mx * dvn + dp * nx;
+    dF[2] = dW[2] * vn1 + my * dvn + dp * ny;
+    dF[3] = (dW[3] + dp) * vn1 + H * dvn;
+}
+
+template <class T>
+__global__ void __launch_bounds__(1024) k_macro_sweep(KParams p)
+{
+    extern __shared__ unsigned char smraw[];
+    T *ring = (T *)smraw;  // [2][ni][4]: increments of the previous hyperplane
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int ni = p.ni, nj = p.nj;
     if (tid == 0) {
+        double s = 0.0;
+        int nb = (p.N + 255) / 256;
+        for (int q = 0; q < nb; ++q) s += p.mpart[q];
         int it = *p.iter;
-        double r = sqrt(part[0]);
+        double r = sqrt(s);
         p.res[it & (kMaxHist - 1)] = r;
         if (!isfinite(r)) *p.status = 5;
     }
-    // spectral radius per face, Eq. (31) at the face average
-    for (int fi = tid; fi < p.nf; fi += nt) {
-        int L = p.fL[fi], R = p.fR[fi];
-        const double *g = p.fgeo + 7 * fi;
-        double u, v, cs;
-        if (L >= 0 && R >= 0) {
-            double u1, v1, c1, u2, v2, c2;
-            prim_uvc(p, p.W + 4 * L, u1, v1, c1);
-            prim_uvc(p, p.W + 4 * R, u2, v2, c2);
-            u = 0.5 * (u1 + u2); v = 0.5 * (v1 + v2); cs = 0.5 * (c1 + c2);
-        } else {
-            prim_uvc(p, p.W + 4 * (L >= 0 ? L : R), u, v, cs);
-        }
-        p.lam[fi] = (fabs(u * g[0] + v * g[1]) + cs) * g[2];
-    }
-    __syncthreads();
-    for (int c = tid; c < p.N; c += nt) {
-        double d = p.area[c] / p.dtimp[c];
-        for (int m = 0; m < 4; ++m) {
-            int fi = p.cface[4 * c + m];
-            if (p.fL[fi] == p.fR[fi]) continue;
-            d += 0.5 * p.lusgs_omega * p.lam[fi];
-        }
-        p.Dm[c] = d;
-    }
-    __syncthreads();
-    // forward sweep over i+j hyperplanes: the lexicographic dependency order
-    const int nh = p.ni + p.nj - 1;
-    for (int dpl = 0; dpl < nh; ++dpl) {
-        int ilo = max(0, dpl - (p.nj - 1)), ihi = min(p.ni - 1, dpl);
+    const T gm1 = (T)(p.gam - 1.0);
+    const T *base = (const T *)p.mbase;
+    const T *off = (const T *)p.moff;
+    T *dWg = (T *)p.mdW;
+    const int nh = ni + nj - 1;
+    // forward: dW*_c = (R_c - sum_lower [dF - wL dW*_nb]) / D_c
+    for (int d = 0; d < nh; ++d) {
+        int ilo = max(0, d - (nj - 1)), ihi = min(ni - 1, d);
         for (int i = ilo + tid; i <= ihi; i += nt) {
-            int c = (dpl - i) * p.ni + i;
-            double acc[4] = {p.rw[4 * c], p.rw[4 * c + 1], p.rw[4 * c + 2], p.rw[4 * c + 3]};
+            int c = (d - i) * ni + i;
+            T acc[4];
+            for (int q = 0; q < 4; ++q) acc[q] = ((const T *)p.mR)[4 * c + q];
             for (int m = 0; m < 4; ++m) {
                 int nb = p.cnb[4 * c + m];
                 if (nb < 0 || nb >= c) continue;
-                offdiag(p, c, m, acc, -1.0);
+                int inb = nb % ni, jnb = nb / ni;
+                const T *dWn = (inb + jnb == d - 1) ? ring + 4 * (((d - 1) & 1) * ni + inb) : dWg + 4 * nb;
+                T dn[4] = {dWn[0], dWn[1], dWn[2], dWn[3]};
+                const T *o = off + 16 * c + 4 * m;
+                T dF[4];
+                euler_dflux<T>(gm1, base + 8 * nb, dn, o[0], o[1], dF);
+                for (int q = 0; q < 4; ++q) acc[q] -= dF[q] - o[2] * dn[q];
             }
-            for (int q = 0; q < 4; ++q) p.dW[4 * c + q] = acc[q] / p.Dm[c];
+            T Dc = ((const T *)p.mD)[c];
+            T *rs = ring + 4 * ((d & 1) * ni + i);
+            for (int q = 0; q < 4; ++q) {
+                T x = acc[q] / Dc;
+                rs[q] = x;
+                dWg[4 * c + q] = x;
+            }
         }
         __syncthreads();
     }
-    for (int dpl = nh - 1; dpl >= 0; --dpl) {
-        int ilo = max(0, dpl - (p.nj - 1)), ihi = min(p.ni - 1, dpl);
+    // backward: dW_c = dW*_c - sum_upper [dF - wL dW_nb] / D_c
+    for (int d = nh - 1; d >= 0; --d) {
+        int ilo = max(0, d - (nj - 1)), ihi = min(ni - 1, d);
         for (int i = ilo + tid; i <= ihi; i += nt) {
-            int c = (dpl - i) * p.ni + i;
-            double acc[4] = {0, 0, 0, 0};
+            int c = (d - i) * ni + i;
+            T acc[4] = {0, 0, 0, 0};
             for (int m = 0; m < 4; ++m) {
                 int nb = p.cnb[4 * c + m];
                 if (nb < 0 || nb <= c) continue;
-                offdiag(p, c, m, acc, 1.0);
+                int inb = nb % ni, jnb = nb / ni;
+                const T *dWn = (inb + jnb == d + 1) ? ring + 4 * (((d + 1) & 1) * ni + inb) : dWg + 4 * nb;
+                T dn[4] = {dWn[0], dWn[1], dWn[2], dWn[3]};
+                const T *o = off + 16 * c + 4 * m;
+                T dF[4];
+                euler_dflux<T>(gm1, base + 8 * nb, dn, o[0], o[1], dF);
+                for (int q = 0; q < 4; ++q) acc[q] += dF[q] - o[2] * dn[q];
             }
-            for (int q = 0; q < 4; ++q) p.dW[4 * c + q] -= acc[q] / p.Dm[c];
+            T Dc = ((const T *)p.mD)[c];
+            T *rs = ring + 4 * ((d & 1) * ni + i);
+            for (int q = 0; q < 4; ++q) {
+                T x = dWg[4 * c + q] - acc[q] / Dc;
+                rs[q] = x;
+                dWg[4 * c + q] = x;
+            }
         }
         __syncthreads();
     }
-    // update (Eq. 32) and micro coefficients at the predicted W^{n+1}
-    for (int c = tid; c < p.N; c += nt) {
-        double *W = p.W + 4 * c;
-        for (int q = 0; q < 4; ++q) W[q] += p.dW[4 * c + q];
-        double rho = W[0], U = W[1] / rho, V = W[2] / rho;
-        double RT = (2.0 * W[3] / rho - U * U - V * V) / (p.K + 2);
-        double taup = viscosity(p, RT) / (rho * RT);
-        EqD e = make_eq(p, rho, U, V, RT, p.cellq[2 * c], p.cellq[2 * c + 1]);
-        double *cp = p.cellp + kCellP * c;
-        eq_store(cp, e);
-        double cq = 2.0 * p.area[c] / (2.0 * taup + p.dt);
-        cp[14] = cq;
-        cp[15] = p.area[c] / p.dtimp[c] + cq;
-    }
-    __syncthreads();
     if (tid == 0) *p.iter += 1;
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_macro_post(KParams p)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= p.N) return;
+    double *W = p.W + 4 * c;
+    const T *dW = (const T *)p.mdW + 4 * c;
+    for (int q = 0; q < 4; ++q) W[q] += (double)dW[q];
+    double rho = W[0], U = W[1] / rho, V = W[2] / rho;
+    double RT = (2.0 * W[3] / rho - U * U - V * V) / (p.K + 2);
+    double taup = viscosity(p, RT) / (rho * RT);
+    EqD e = make_eq(p, rho, U, V, RT, p.cellq[2 * c], p.cellq[2 * c + 1]);
+    double *cp = p.cellp + kCellP * c;
+    eq_store(cp, e);
+    double cq = 2.0 * p.area[c] / (2.0 * taup + p.dt);
+    cp[14] = cq;
+    cp[15] = p.area[c] / p.dtimp[c] + cq;
+    T *ct = (T *)p.cellpT + kCellP * c;
+    for (int q = 0; q < kCellP; ++q) ct[q] = (T)cp[q];
 }
 
 // ---------------------------------------------------------------------------
 // micro LU-SGS sweeps (Eq. 22-26) on i+j hyperplanes                  [a6-a7]
 // one CTA per tile of sweep_tv velocities; sweep_pc cell slots per CTA
 // ---------------------------------------------------------------------------
-struct SlotGeo {
-    int face[4], nb[4];
-    double sign[4];
-};
+template <class T> __device__ __forceinline__ EqT<T> eq_loadT(const T *cp)
+{
+    EqT<T> e;
+    e.e0 = cp[0]; e.ex = cp[1]; e.ey = cp[2]; e.e2 = cp[3]; e.U = cp[4]; e.V = cp[5];
+    e.invRT = cp[6]; e.pqx = cp[7]; e.pqy = cp[8]; e.rr = cp[9]; e.rrm1 = cp[10]; e.kRT = cp[11];
+    e.lnA = cp[12]; e.lam = cp[13];
+    return e;
+}
 
+// Forward sweep: Delta*_c = (R_c + sum_{lower inflow nb} |xi.n| S Delta*_nb) / D_c
+// with R = -sum_faces F - (2 Omega/(2 tau' + dt)) (f~ - f^S(W^{n+1})) (Eq. 22-23)
+// and D = Omega/dt_imp + sum_{outflow} xi.n S + 2 Omega/(2 tau' + dt) (Eq. 26).
+// The previous hyperplane's Delta* sits in a shared-memory ring; neighbours
+// across a periodic seam (earlier hyperplanes) are read back from global.
 template <class T>
 __global__ void __launch_bounds__(1024) k_sweep_fwd(KParams p)
 {
     using T2 = typename V2<T>::t;
-    const int tv = p.sweep_tv, pc = p.sweep_pc;
+    extern __shared__ unsigned char smraw[];
+    T2 *ring = (T2 *)smraw;  // [2][ni][tv]
+    const int tv = p.sweep_tv, pc = p.sweep_pc, ni = p.ni, nj = p.nj;
     const int t = threadIdx.x % tv, slot = threadIdx.x / tv;
     const int k = blockIdx.x * tv + t;
     const bool act = k < p.Nv;
@@ -716,15 +777,16 @@ __global__ void __launch_bounds__(1024) k_sweep_fwd(KParams p)
     const T2 *F = (const T2 *)p.F;
     const T2 *f = (const T2 *)p.f;
     T2 *ds = (T2 *)p.dst;
-    const int nh = p.ni + p.nj - 1;
+    const T *cpT = (const T *)p.cellpT;
+    const int nh = ni + nj - 1;
     for (int dpl = 0; dpl < nh; ++dpl) {
-        int ilo = max(0, dpl - (p.nj - 1)), ihi = min(p.ni - 1, dpl);
+        int ilo = max(0, dpl - (nj - 1)), ihi = min(ni - 1, dpl);
         for (int i = ilo + slot; i <= ihi; i += pc) {
             if (!act) continue;
-            int c = (dpl - i) * p.ni + i;
-            const double *cp = p.cellp + kCellP * c;
-            EqT<T> e = eq_load<T>(cp);
-            T cq = (T)cp[14], D = (T)cp[15];
+            int c = (dpl - i) * ni + i;
+            const T *cp = cpT + kCellP * c;
+            EqT<T> e = eq_loadT<T>(cp);
+            T cq = cp[14], D = cp[15];
             T dG, dH;
             dev_equilibrium<T>(e, ux, uy, gref, kRTr, dG, dH);
             T2 fv = f[(size_t)c * p.Nv + k];
@@ -744,7 +806,9 @@ __global__ void __launch_bounds__(1024) k_sweep_fwd(KParams p)
                 T aS = so * (T)g[2];
                 if (so > (T)0) D += aS;
                 else if (so < (T)0 && nb >= 0 && nb < c) {
-                    T2 dn = ds[(size_t)nb * p.Nv + k];
+                    int inb = nb % ni, jnb = nb / ni;
+                    T2 dn = (inb + jnb == dpl - 1) ? ring[(((dpl - 1) & 1) * ni + inb) * tv + t]
+                                                   : ds[(size_t)nb * p.Nv + k];
                     ag -= aS * dn.x;
                     ah -= aS * dn.y;
                 }
@@ -753,16 +817,21 @@ __global__ void __launch_bounds__(1024) k_sweep_fwd(KParams p)
             o.x = (rg + ag) / D;
             o.y = (rh + ah) / D;
             ds[(size_t)c * p.Nv + k] = o;
+            ring[((dpl & 1) * ni + i) * tv + t] = o;
         }
         __syncthreads();
     }
 }
 
+// Backward sweep: Delta_c = Delta*_c + sum_{upper inflow nb} |xi.n| S Delta_nb / D_c,
+// then f~ += Delta (Eq. 32).
 template <class T>
 __global__ void __launch_bounds__(1024) k_sweep_bwd(KParams p)
 {
     using T2 = typename V2<T>::t;
-    const int tv = p.sweep_tv, pc = p.sweep_pc;
+    extern __shared__ unsigned char smraw[];
+    T2 *ring = (T2 *)smraw;  // [2][ni][tv]
+    const int tv = p.sweep_tv, pc = p.sweep_pc, ni = p.ni, nj = p.nj;
     const int t = threadIdx.x % tv, slot = threadIdx.x / tv;
     const int k = blockIdx.x * tv + t;
     const bool act = k < p.Nv;
@@ -770,14 +839,14 @@ __global__ void __launch_bounds__(1024) k_sweep_bwd(KParams p)
     const T ux = vx<T>(p, kk), uy = vy<T>(p, kk);
     T2 *f = (T2 *)p.f;
     T2 *ds = (T2 *)p.dst;
-    const int nh = p.ni + p.nj - 1;
+    const T *cpT = (const T *)p.cellpT;
+    const int nh = ni + nj - 1;
     for (int dpl = nh - 1; dpl >= 0; --dpl) {
-        int ilo = max(0, dpl - (p.nj - 1)), ihi = min(p.ni - 1, dpl);
+        int ilo = max(0, dpl - (nj - 1)), ihi = min(ni - 1, dpl);
         for (int i = ilo + slot; i <= ihi; i += pc) {
             if (!act) continue;
-            int c = (dpl - i) * p.ni + i;
-            const double *cp = p.cellp + kCellP * c;
-            T D = (T)cp[15];
+            int c = (dpl - i) * ni + i;
+            T D = cpT[kCellP * c + 15];
             T ag = 0, ah = 0;
 #pragma unroll
             for (int m = 0; m < 4; ++m) {
@@ -790,7 +859,9 @@ __global__ void __launch_bounds__(1024) k_sweep_bwd(KParams p)
                 T aS = so * (T)g[2];
                 if (so > (T)0) D += aS;
                 else if (so < (T)0 && nb > c) {
-                    T2 dn = ds[(size_t)nb * p.Nv + k];
+                    int inb = nb % ni, jnb = nb / ni;
+                    T2 dn = (inb + jnb == dpl + 1) ? ring[(((dpl + 1) & 1) * ni + inb) * tv + t]
+                                                   : ds[(size_t)nb * p.Nv + k];
                     ag -= aS * dn.x;
                     ah -= aS * dn.y;
                 }
@@ -801,6 +872,7 @@ __global__ void __launch_bounds__(1024) k_sweep_bwd(KParams p)
             d1.x = d0.x + ag / D;
             d1.y = d0.y + ah / D;
             ds[ck] = d1;
+            ring[((dpl & 1) * ni + i) * tv + t] = d1;
             T2 fv = f[ck];
             fv.x += d1.x;
             fv.y += d1.y;
@@ -910,16 +982,43 @@ static int iteration_t(const KParams &p, cudaStream_t st, void **events)
         else k_face_boundary<T, false><<<nb_, 256, 0, st>>>(p, blist, nb_);
     }
     mark(3);
-    k_macro<<<1, 1024, 0, st>>>(p);
+    {
+        int nb = (p.N + 255) / 256;
+        k_macro_pre<T><<<nb, 256, 0, st>>>(p);
+        int nthr = std::min(1024, ((std::min(p.ni, p.nj) + 31) / 32) * 32);
+        size_t smem = sizeof(T) * 8 * (size_t)p.ni;
+        k_macro_sweep<T><<<1, nthr, smem, st>>>(p);
+        k_macro_post<T><<<nb, 256, 0, st>>>(p);
+    }
     mark(4);
     int nblk = (p.Nv + p.sweep_tv - 1) / p.sweep_tv;
     int nthr = p.sweep_tv * p.sweep_pc;
-    k_sweep_fwd<T><<<nblk, nthr, 0, st>>>(p);
+    size_t ssm = 2 * sizeof(typename V2<T>::t) * (size_t)p.ni * p.sweep_tv;
+    k_sweep_fwd<T><<<nblk, nthr, ssm, st>>>(p);
     mark(5);
-    k_sweep_bwd<T><<<nblk, nthr, 0, st>>>(p);
+    k_sweep_bwd<T><<<nblk, nthr, ssm, st>>>(p);
     mark(6);
     return (int)cudaGetLastError();
 }
+
+template <class T> static int configure_t(const KParams &p)
+{
+    size_t macro = sizeof(T) * 8 * (size_t)p.ni;
+    size_t micro = 2 * sizeof(typename V2<T>::t) * (size_t)p.ni * p.sweep_tv;
+    const size_t lim = 227 * 1024;
+    if (macro > lim || micro > lim) return (int)cudaErrorInvalidValue;
+    cudaError_t e = cudaSuccess;
+    if (macro > 48 * 1024)
+        e = cudaFuncSetAttribute(k_macro_sweep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)macro);
+    if (e == cudaSuccess && micro > 48 * 1024) {
+        e = cudaFuncSetAttribute(k_sweep_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)micro);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_sweep_bwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)micro);
+    }
+    return (int)e;
+}
+
+int configure_kernels(const KParams &p, bool fp64) { return fp64 ? configure_t<double>(p) : configure_t<float>(p); }
 
 int launch_iteration(const KParams &p, bool fp64, void *stream, void **events)
 {
