@@ -32,7 +32,10 @@ import numpy as np  # noqa: E402
 from paper_1709_01819_gb300 import inputs as I  # noqa: E402
 
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-KERNELS = ["k_cell_prep", "k_face_interior", "k_face_boundary", "k_macro", "k_sweep_fwd", "k_sweep_bwd"]
+KERNELS = ["cell_prep", "face_moments", "face_flux", "macro", "k_sweep_fwd", "k_sweep_bwd"]
+# launch groups timed by idg_iterate_profiled: cell_prep = k_cell_moments + k_cell_params + k_fbp;
+# face_moments = k_face_moments + k_face_params; face_flux = k_face_flux + k_face_phi;
+# macro = k_macro_pre + k_macro_sweep + k_macro_post
 
 
 def workload(name: str) -> I.Problem:
@@ -48,15 +51,16 @@ def workload(name: str) -> I.Problem:
 
 
 def algorithmic_bytes(prob: I.Problem, s: int, nf: int):
-    """Bytes each kernel must move per launch (s = bytes per scalar of f).
-    k_cell_prep: read f~, write fb+ (2 scalars each per cell-velocity);
-    k_face_interior: read fb+ once, write the face flux (2 per face-velocity);
-    k_sweep_fwd: read the face fluxes once, read f~, write Delta*;
+    """Bytes each launch group must move (s = bytes per scalar of f).
+    cell_prep: read f~ twice (moments, fb+), write fb+ (2 scalars each per cell-velocity);
+    face_moments: read fb+ once;  face_flux: read fb+ once, write the face flux
+    (2 per face-velocity);  k_sweep_fwd: read the face fluxes once, read f~, write Delta*;
     k_sweep_bwd: read Delta* and f~, write Delta and f~."""
     N, Nv = prob.ncells, prob.nvel
     return {
-        "k_cell_prep": 4 * s * N * Nv,
-        "k_face_interior": 2 * s * N * Nv + 2 * s * nf * Nv,
+        "cell_prep": 6 * s * N * Nv,
+        "face_moments": 2 * s * N * Nv,
+        "face_flux": 2 * s * N * Nv + 2 * s * nf * Nv,
         "k_sweep_fwd": 2 * s * nf * Nv + 4 * s * N * Nv,
         "k_sweep_bwd": 8 * s * N * Nv,
     }

@@ -37,7 +37,7 @@ struct idg_ctx {
     bool built = false;
     int N = 0, Nv = 0, nf = 0;
     std::vector<double> area, cxc, cyc, hcell, dtimp, cr, clsg, fgeo;
-    std::vector<int> cface, cnb, csign, fL, fR, fbc, fside, ilist, blist;
+    std::vector<int> cface, cnb, csign, fL, fR, fbc, fside;
     std::vector<double> ux, uy, w;
     double xi_max = 0, dt = 0, mu_ref = 0;
     // reference Maxwellian of the storage
@@ -299,9 +299,6 @@ idg_status build(idg_ctx *c)
                 set_face(f, x0, y0, x1_, y1_, false, L, R, mx, my, mx, my, side);
             }
         }
-    c->ilist.clear();
-    c->blist.clear();
-    for (int q = 0; q < c->nf; ++q) (c->fL[q] >= 0 && c->fR[q] >= 0 ? c->ilist : c->blist).push_back(q);
     // cell slots: west, east, south, north
     c->cface.assign(4 * c->N, 0);
     c->cnb.assign(4 * c->N, -1);
@@ -377,53 +374,56 @@ size_t layout(idg_ctx *c, char *base, KParams *kp)
     Layout L;
     L.base = base;
     const size_t N = c->N, Nv = c->Nv, nf = c->nf;
-    const size_t t2 = c->precision == IDG_FP64 ? 16 : 8;
+    const size_t ts = c->precision == IDG_FP64 ? 8 : 4;  // storage scalar
+    const size_t t2 = 2 * ts;
     KParams k{};
     k.area = L.take<double>(8 * N);
     k.dtimp = L.take<double>(8 * N);
     k.cface = L.take<int>(16 * N);
     k.cnb = L.take<int>(16 * N);
     k.csign = L.take<int>(16 * N);
-    k.cr = L.take<double>(64 * N);
-    k.clsg = L.take<double>(64 * N);
+    k.crT = L.take<char>(8 * ts * N);
+    k.clsgT = L.take<char>(8 * ts * N);
+    k.cslotT = L.take<char>(16 * ts * N);
     k.fL = L.take<int>(4 * nf);
     k.fR = L.take<int>(4 * nf);
     k.fgeo = L.take<double>(56 * nf);
+    k.fgeoT = L.take<char>(8 * ts * nf);
     k.fbc = L.take<int>(4 * nf);
     k.fside = L.take<int>(4 * nf);
-    k.ilist = L.take<int>(4 * nf + 4);
-    k.blist = L.take<int>(4 * nf + 4);
+    k.bconst = L.take<double>(16 * nf);
     k.ux = L.take<double>(8 * Nv);
     k.uy = L.take<double>(8 * Nv);
     k.w = L.take<double>(8 * Nv);
     k.gref = L.take<double>(8 * Nv);
-    k.lngref = L.take<double>(8 * Nv);
     k.uxf = L.take<float>(4 * Nv);
     k.uyf = L.take<float>(4 * Nv);
     k.wf = L.take<float>(4 * Nv);
     k.greff = L.take<float>(4 * Nv);
-    k.lngreff = L.take<float>(4 * Nv);
-    k.bndG = L.take<double>(32 * Nv);
-    k.bndH = L.take<double>(32 * Nv);
+    k.bdevG = L.take<char>(4 * ts * Nv);
+    k.bdevH = L.take<char>(4 * ts * Nv);
     k.f = L.take<char>(t2 * N * Nv);
     k.fbp = L.take<char>(t2 * N * Nv);
     k.dst = L.take<char>(t2 * N * Nv);
     k.F = L.take<char>(t2 * nf * Nv);
     k.W = L.take<double>(32 * N);
+    k.cellraw = L.take<char>(8 * idg::kRaw * N);
+    k.cellA = L.take<char>(ts * idg::kCellP * N);
     k.cellq = L.take<double>(16 * N);
     k.cellp = L.take<double>(8 * idg::kCellP * N);
+    k.cellpT = L.take<char>(ts * idg::kCellP * N);
+    k.faceraw = L.take<char>(8 * 12 * nf);
+    k.facerw = L.take<double>(8 * nf);
+    k.faceA = L.take<char>(ts * idg::kCellP * nf);
+    k.phiraw = L.take<char>(32 * nf);
     k.phi = L.take<double>(32 * nf);
     k.rw = L.take<double>(32 * N);
-    k.dW = L.take<double>(32 * N);
-    k.lam = L.take<double>(8 * nf);
-    k.Dm = L.take<double>(8 * N);
-    k.mbase = L.take<char>(64 * N);
-    k.moff = L.take<char>(128 * N);
-    k.mD = L.take<char>(8 * N);
-    k.mR = L.take<char>(32 * N);
-    k.mdW = L.take<char>(32 * N);
+    k.mbase = L.take<char>(8 * ts * N);
+    k.moff = L.take<char>(16 * ts * N);
+    k.mD = L.take<char>(ts * N);
+    k.mR = L.take<char>(4 * ts * N);
+    k.mdW = L.take<char>(4 * ts * N);
     k.mpart = L.take<double>(8 * (N / 256 + 2));
-    k.cellpT = L.take<char>(8 * idg::kCellP * N);
     k.res = L.take<double>(8 * (size_t)idg::kMaxHist);
     k.iter = L.take<int>(256);
     k.status = k.iter + 1;
@@ -436,22 +436,20 @@ size_t layout(idg_ctx *c, char *base, KParams *kp)
 }
 
 // tables of the reference Maxwellian and its float64 moments
-void reference_tables(idg_ctx *c, std::vector<double> &gref, std::vector<double> &lng, KParams &k)
+void reference_tables(idg_ctx *c, std::vector<double> &gref, KParams &k)
 {
     const int Nv = c->Nv;
     const double RTr = c->ref_T * c->RT_ref, lamr = 0.5 / RTr;
     gref.resize(Nv);
-    lng.resize(Nv);
-    for (int q = 0; q < 11; ++q) k.mref_raw[q] = 0.0;
+    for (int q = 0; q < idg::kRaw; ++q) k.mref_raw[q] = 0.0;
     for (int a = 0; a < 4; ++a) k.mref_flux[a][0] = k.mref_flux[a][1] = 0.0;
     const double kRTr = c->K * RTr;
     for (int q = 0; q < Nv; ++q) {
         double cx = c->ux[q] - c->ref_u, cy = c->uy[q] - c->ref_v;
-        lng[q] = std::log(c->ref_rho * lamr / M_PI) - lamr * (cx * cx + cy * cy);
-        gref[q] = std::exp(lng[q]);
+        gref[q] = c->ref_rho * lamr / M_PI * std::exp(-lamr * (cx * cx + cy * cy));
         double G = gref[q], H = kRTr * G, x = c->ux[q], y = c->uy[q], wq = c->w[q], s2 = x * x + y * y;
-        double r[11] = {G, x * G, y * G, x * x * G, x * y * G, y * y * G, x * s2 * G, y * s2 * G, H, x * H, y * H};
-        for (int m = 0; m < 11; ++m) k.mref_raw[m] += wq * r[m];
+        double r[idg::kRaw] = {G, x * G, y * G, x * x * G, x * y * G, y * y * G, x * s2 * G, y * s2 * G, H, x * H, y * H};
+        for (int m = 0; m < idg::kRaw; ++m) k.mref_raw[m] += wq * r[m];
         double psi[4] = {G, x * G, y * G, 0.5 * (s2 * G + H)};
         for (int a = 0; a < 4; ++a) {
             k.mref_flux[a][0] += wq * psi[a] * x;
@@ -469,16 +467,66 @@ template <class T> cudaError_t up(T *dst, const std::vector<T> &src)
     return cudaMemcpy(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
 }
 
+template <class T> std::vector<T> cast(const std::vector<double> &v) { return std::vector<T>(v.begin(), v.end()); }
+
+template <class T> cudaError_t upT(const void *dst, const std::vector<double> &src)
+{
+    std::vector<T> t = cast<T>(src);
+    return cudaMemcpy(const_cast<void *>(dst), t.data(), t.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+cudaError_t up_storage(idg_ctx *c, const void *dst, const std::vector<double> &src)
+{
+    return c->precision == IDG_FP64 ? upT<double>(dst, src) : upT<float>(dst, src);
+}
+
+// Everything that depends on the reference Maxwellian: its table and moments,
+// the boundary Maxwellians relative to it, and the per-face half-range sums
+// of the diffuse wall (Eq. 35).
 idg_status upload_reference(idg_ctx *c)
 {
-    std::vector<double> gref, lng;
-    reference_tables(c, gref, lng, c->kp);
-    std::vector<float> gf(gref.begin(), gref.end()), lf(lng.begin(), lng.end());
+    std::vector<double> gref;
+    reference_tables(c, gref, c->kp);
+    const int Nv = c->Nv;
+    const double kRTr = c->K * c->ref_T * c->RT_ref;
+    std::vector<double> bG((size_t)4 * Nv, 0.0), bH((size_t)4 * Nv, 0.0), dG((size_t)4 * Nv, 0.0),
+        dH((size_t)4 * Nv, 0.0);
+    for (int sd = 0; sd < 4; ++sd) {
+        if (c->bc_kind[sd] == IDG_BC_PERIODIC) continue;
+        double RT = c->bc_T[sd] * c->RT_ref, lam = 0.5 / RT;
+        double rho = c->bc_kind[sd] == IDG_BC_WALL ? 1.0 : c->bc_rho[sd];
+        for (int q = 0; q < Nv; ++q) {
+            double cx = c->ux[q] - c->bc_u[sd], cy = c->uy[q] - c->bc_v[sd];
+            double G = rho * lam / M_PI * std::exp(-lam * (cx * cx + cy * cy));
+            size_t i = (size_t)sd * Nv + q;
+            bG[i] = G;
+            bH[i] = c->K * RT * G;
+            dG[i] = G - gref[q];
+            dH[i] = c->K * RT * G - kRTr * gref[q];
+        }
+    }
+    std::vector<double> bconst((size_t)2 * c->nf, 0.0);
+    for (int f = 0; f < c->nf; ++f) {
+        if (c->fbc[f] < 0) continue;
+        const double *g = &c->fgeo[(size_t)7 * f];
+        double on = c->fL[f] >= 0 ? 1.0 : -1.0;
+        int sd = c->fside[f];
+        double out = 0.0, in = 0.0;
+        for (int q = 0; q < Nv; ++q) {
+            double so = on * (c->ux[q] * g[0] + c->uy[q] * g[1]);
+            if (so > 0) out += c->w[q] * so * gref[q];
+            else if (so < 0) in += c->w[q] * (-so) * bG[(size_t)sd * Nv + q];
+        }
+        bconst[2 * f] = out;
+        bconst[2 * f + 1] = in;
+    }
+    std::vector<float> gf(gref.begin(), gref.end());
     cudaError_t e;
     if ((e = up((double *)c->kp.gref, gref)) != cudaSuccess) return cuda_fail(c, e, "upload gref");
-    if ((e = up((double *)c->kp.lngref, lng)) != cudaSuccess) return cuda_fail(c, e, "upload lngref");
     if ((e = up((float *)c->kp.greff, gf)) != cudaSuccess) return cuda_fail(c, e, "upload greff");
-    if ((e = up((float *)c->kp.lngreff, lf)) != cudaSuccess) return cuda_fail(c, e, "upload lngreff");
+    if ((e = up_storage(c, c->kp.bdevG, dG)) != cudaSuccess) return cuda_fail(c, e, "upload bdevG");
+    if ((e = up_storage(c, c->kp.bdevH, dH)) != cudaSuccess) return cuda_fail(c, e, "upload bdevH");
+    if ((e = up((double *)c->kp.bconst, bconst)) != cudaSuccess) return cuda_fail(c, e, "upload bconst");
     return IDG_OK;
 }
 
@@ -670,8 +718,6 @@ idg_status idg_bind_workspace(idg_ctx *c, void *dev_ptr, size_t bytes)
     k.per_j = c->bc_kind[IDG_JMIN] == IDG_BC_PERIODIC;
     k.dt = c->dt; k.h = 0.5 * c->dt; k.mu_ref = c->mu_ref; k.RT_ref = c->RT_ref; k.omega = c->omega;
     k.Pr = c->Pr; k.gam = (double)(c->K + 4) / (double)(c->K + 2); k.lusgs_omega = c->lusgs_omega;
-    k.nilist = (int)c->ilist.size();
-    k.nblist = (int)c->blist.size();
     // sweep launch shape: cell slots cover the longest hyperplane up to 64
     int maxlen = std::min(c->ni, c->nj);
     k.sweep_pc = std::min(maxlen, 128);
@@ -680,28 +726,25 @@ idg_status idg_bind_workspace(idg_ctx *c, void *dev_ptr, size_t bytes)
     // uploads
     std::vector<float> uxf(c->ux.begin(), c->ux.end()), uyf(c->uy.begin(), c->uy.end()),
         wf(c->w.begin(), c->w.end());
-    std::vector<double> bG((size_t)4 * c->Nv, 0.0), bH((size_t)4 * c->Nv, 0.0);
-    for (int sd = 0; sd < 4; ++sd) {
-        if (c->bc_kind[sd] == IDG_BC_PERIODIC) continue;
-        double RT = c->bc_T[sd] * c->RT_ref, lam = 0.5 / RT;
-        double rho = c->bc_kind[sd] == IDG_BC_WALL ? 1.0 : c->bc_rho[sd];
-        for (int q = 0; q < c->Nv; ++q) {
-            double cx = c->ux[q] - c->bc_u[sd], cy = c->uy[q] - c->bc_v[sd];
-            double G = rho * lam / M_PI * std::exp(-lam * (cx * cx + cy * cy));
-            bG[(size_t)sd * c->Nv + q] = G;
-            bH[(size_t)sd * c->Nv + q] = c->K * RT * G;
+    std::vector<double> fgeo8((size_t)8 * c->nf, 0.0), cslot((size_t)16 * c->N, 0.0);
+    for (int q = 0; q < c->nf; ++q)
+        for (int m = 0; m < 7; ++m) fgeo8[(size_t)8 * q + m] = c->fgeo[(size_t)7 * q + m];
+    for (int q = 0; q < c->N; ++q)
+        for (int m = 0; m < 4; ++m) {
+            int fi = c->cface[4 * q + m];
+            double s = c->csign[4 * q + m];
+            cslot[16 * q + 4 * m] = s * c->fgeo[(size_t)7 * fi];
+            cslot[16 * q + 4 * m + 1] = s * c->fgeo[(size_t)7 * fi + 1];
+            cslot[16 * q + 4 * m + 2] = c->fgeo[(size_t)7 * fi + 2];
         }
-    }
     cudaError_t errs[] = {
         up((double *)k.area, c->area), up((double *)k.dtimp, c->dtimp), up((int *)k.cface, c->cface),
-        up((int *)k.cnb, c->cnb), up((int *)k.csign, c->csign), up((double *)k.cr, c->cr),
-        up((double *)k.clsg, c->clsg), up((int *)k.fL, c->fL), up((int *)k.fR, c->fR),
-        up((double *)k.fgeo, c->fgeo), up((int *)k.fbc, c->fbc), up((int *)k.fside, c->fside),
-        c->ilist.empty() ? cudaSuccess : up((int *)k.ilist, c->ilist),
-        c->blist.empty() ? cudaSuccess : up((int *)k.blist, c->blist),
+        up((int *)k.cnb, c->cnb), up((int *)k.csign, c->csign), up_storage(c, k.crT, c->cr),
+        up_storage(c, k.clsgT, c->clsg), up_storage(c, k.cslotT, cslot), up((int *)k.fL, c->fL),
+        up((int *)k.fR, c->fR), up((double *)k.fgeo, c->fgeo), up_storage(c, k.fgeoT, fgeo8),
+        up((int *)k.fbc, c->fbc), up((int *)k.fside, c->fside),
         up((double *)k.ux, c->ux), up((double *)k.uy, c->uy), up((double *)k.w, c->w),
         up((float *)k.uxf, uxf), up((float *)k.uyf, uyf), up((float *)k.wf, wf),
-        up((double *)k.bndG, bG), up((double *)k.bndH, bH),
         cudaMemset(k.iter, 0, 256), cudaMemset(k.phi, 0, 32 * (size_t)c->nf)};
     for (cudaError_t x : errs)
         if (x != cudaSuccess) return cuda_fail(c, x, "workspace upload");

@@ -9,11 +9,14 @@ namespace idg {
 
 constexpr int kMaxVel = 16384;
 constexpr int kMaxHist = 1 << 16;  // residual-history ring (iterations)
+constexpr int kCellP = 16;         // per-cell / per-face coefficient records
+constexpr int kRaw = 11;           // raw velocity moments kept per cell / face
 
 // Everything one kernel launch needs, passed by value.  Device pointers point
-// into the caller's workspace.  "dev" quantities are relative to the global
-// reference Maxwellian M_ref (f = M_ref + dev), see storage in DESIGN notes of
-// the kernels file.
+// into the caller's workspace.  "T" below is the storage precision (float for
+// IDG_MIXED, double for IDG_FP64); "acc" entries are 8 bytes: a float-float
+// pair (hi, lo) in mixed precision, a double in FP64.  Distributions are kept
+// relative to one reference Maxwellian M_ref (f = M_ref + dev).
 struct KParams {
     // sizes
     int N, Nv, nf, ni, nj, nvx;
@@ -25,24 +28,26 @@ struct KParams {
     const int *cface;      // [N][4] faces in slots west, east, south, north
     const int *cnb;        // [N][4] neighbour across the slot (-1 ghost)
     const int *csign;      // [N][4] +1 if the cell is the L side of that face
-    const double *cr;      // [N][4][2] face midpoint minus centroid, per slot
-    const double *clsg;    // [N][4][2] least-squares weight vector per slot
+    const void *crT;       // [N][8] T: face midpoint minus centroid, per slot
+    const void *clsgT;     // [N][8] T: least-squares weight vector per slot
+    const void *cslotT;    // [N][4][4] T: sign*nx, sign*ny, S, 0 per slot
     // faces
     const int *fL, *fR;    // [nf]
     const double *fgeo;    // [nf][7] nx, ny, S, rLx, rLy, rRx, rRy
+    const void *fgeoT;     // [nf][8] T copy of fgeo
     const int *fbc;        // [nf] -1 interior, else boundary kind
     const int *fside;      // [nf] boundary side or -1
+    const double *bconst;  // [nf][2] boundary faces: sum_out w (xi.n_out) G_ref, sum_in w |xi.n_out| G_bnd
     // velocity tables
     const double *ux, *uy, *w;   // [Nv]
     const double *gref;          // [Nv] reduced reference Maxwellian G
-    const double *lngref;        // [Nv] log of it
-    const float *uxf, *uyf, *wf, *greff, *lngreff;  // float copies
-    const double *bndG, *bndH;   // [4][Nv] boundary Maxwellians (wall: unit density)
+    const float *uxf, *uyf, *wf, *greff;  // float copies
+    const void *bdevG, *bdevH;   // [4][Nv] T: boundary Maxwellian minus M_ref (wall: unit density)
     // gas and numerics
     double dt, h, mu_ref, RT_ref, omega, Pr, gam, lusgs_omega;
     // reference Maxwellian parameters and its discrete moments
     double rho_r, U_r, V_r, RT_r;
-    double mref_raw[11];       // raw moments: G: 1,x,y,xx,xy,yy,x|xi|^2,y|xi|^2; H: 1,x,y
+    double mref_raw[kRaw];     // raw moments: G: 1,x,y,xx,xy,yy,x|xi|^2,y|xi|^2; H: 1,x,y
     double mref_flux[4][2];    // sum w psi xi_a M_ref, psi = 1, xi_x, xi_y, energy
     // state and work (T2 = {G, H} deviation pairs of the storage type)
     void *f;        // [N][Nv] T2 state f~ - M_ref
@@ -50,13 +55,17 @@ struct KParams {
     void *F;        // [nf][Nv] T2 flux of (f_face - M_ref)
     void *dst;      // [N][Nv] T2 Delta* then Delta
     double *W;      // [N][4]
+    void *cellraw;  // [N][kRaw] acc raw moments of f~ - M_ref
+    void *cellA;    // [N][16] T: equilibrium at W^n (14), c1, c2 of fb+
     double *cellq;  // [N][2]  heat flux of f at cells (from f~^n)
-    double *cellp;  // [N][16] post-predictor cell coefficients
+    double *cellp;  // [N][16] post-predictor cell coefficients (float64)
+    void *cellpT;   // [N][16] T copy of cellp for the sweeps
+    void *faceraw;  // [nf][12] acc raw moments of fb - M_ref, wall outgoing sum
+    double *facerw; // [nf] wall density rho_w (1 elsewhere)
+    void *faceA;    // [nf][16] T: face equilibrium (14), a, b of Eq. (18)
+    void *phiraw;   // [nf][4] acc moments of the deviation flux
     double *phi;    // [nf][4]
     double *rw;     // [N][4]
-    double *dW;     // [N][4]
-    double *lam;    // [nf]
-    double *Dm;     // [N]
     // macroscopic LU-SGS work (T = storage precision of the sweep)
     void *mbase;    // [N][8] T: rho, m_x, m_y, E, u, v, p, E+p of W^n
     void *moff;     // [N][4][4] T: (S/2) n_out, (omega/2) Lambda, 0 per slot
@@ -64,24 +73,19 @@ struct KParams {
     void *mR;       // [N][4] T residual
     void *mdW;      // [N][4] T increments (Delta W* then Delta W)
     double *mpart;  // [ceil(N/256)] block partial sums of ||R/Omega||^2
-    void *cellpT;   // [N][16] T copy of cellp for the sweeps
     double *res;    // [kMaxHist] absolute residual per iteration
     int *iter;      // [1] device iteration counter
     int *status;    // [1] device status word
-    // face lists: interior faces, boundary faces
-    const int *ilist, *blist;
-    int nilist, nblist;
     // launch shape of the sweeps
     int sweep_tv, sweep_pc;
 };
 
-// coefficients of the deviation equilibrium (see dev_equilibrium in kernels)
-constexpr int kCellP = 16;
-
 // kernel launchers (idugks_kernels.cu)
 int configure_kernels(const KParams &p, bool fp64);
+constexpr int kProfiled = 6;  // timed groups in launch_iteration(events)
 int launch_iteration(const KParams &p, bool fp64, void *stream, void **events = nullptr);
 int launch_cell_moments(const KParams &p, bool fp64, double *out6_dev, void *stream);
+int launch_face_phi(const KParams &p, bool fp64, void *stream);
 int launch_to_dev(const KParams &p, bool fp64, const double *G, const double *H, void *stream);
 int launch_from_dev(const KParams &p, bool fp64, double *G, double *H, void *stream);
 

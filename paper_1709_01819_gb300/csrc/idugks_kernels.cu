@@ -8,20 +8,34 @@
 // form (dev_equilibrium), so float32 storage rounds relative to the deviation
 // and not to f.  The flux of M_ref through the closed surface of a cell
 // vanishes (sum_f n_f S_f = 0), so stored face fluxes are fluxes of
-// (f_face - M_ref); the macroscopic face moments add M_ref's exact float64
-// moments back.  Layouts are velocity-contiguous: [cell][velocity]{G,H}.
+// (f_face - M_ref); the macroscopic face moments add M_ref's float64 moments
+// back.  Layouts are velocity-contiguous: [cell][velocity]{G,H}.
 //
-// One iteration = five launches on the caller's stream:
-//   k_cell_prep       per cell: raw moments of f~ (heat flux), equilibrium at
-//                     W^n, fb+ of Eq. (10)/(12)                      [a1]
-//   k_face_interior   per interior face: least-squares gradient (Eq. 14-15),
-//   k_face_boundary   limiter (Eq. 16-17), characteristic reconstruction
-//                     (Eq. 11-13), face moments, Eq. (18)-(19) flux  [a2-a4]
-//   k_macro           residual of Eq. (27), LU-SGS predictor of Eq. (28)-(31)
-//                     on i+j hyperplanes, W^{n+1}, micro coefficients [a5]
-//   k_sweep_fwd/bwd   micro residual M + Q (Eq. 22-23), LU-SGS forward and
-//                     backward sweeps (Eq. 24-26) on i+j hyperplanes, one CTA
-//                     per velocity tile, update of Eq. (32)          [a6-a7]
+// Precision.  GB300 runs float64 at 1/64 of the float32 rate (a warp-wide
+// float64 instruction occupies an SM for ~16 cycles), so in mixed precision
+// every per-velocity operation is float32 and the velocity sums are
+// accumulated in float32 over at most 8 terms per lane, then in a compensated
+// float-float pair (about 48 significant bits) across lanes; the pair is
+// widened to float64 by the lane-parallel per-cell / per-face kernels, which
+// do all scalar physics (state from moments, tau, equilibrium coefficients)
+// in float64.  In FP64 mode the same code runs in float64 throughout.
+//
+// One iteration, in launch order on the caller's stream:
+//   k_cell_moments   warp per cell: raw moments of f~                     [a1]
+//   k_cell_params    thread per cell: heat flux (q of Eq. 20), tau,
+//                    equilibrium at W^n, coefficients of fb+ (Eq. 10, 12)
+//   k_fbp            per (cell, velocity): fb+ = c1 f~ + c2 f^S
+//   k_face_moments   warp per face: least-squares gradient (Eq. 14-15),
+//                    limiter (Eq. 16-17), characteristic reconstruction of fb
+//                    at the half step (Eq. 11, 13), wall density (Eq. 35),
+//                    raw moments of fb                                 [a2-a3]
+//   k_face_params    thread per face: face state, tau, q, equilibrium, and
+//                    the weights of Eq. (18)                              [a4]
+//   k_face_flux      warp per face: f at the face (Eq. 18), flux (Eq. 19),
+//                    flux moments
+//   k_face_phi       thread per face: Phi_f = sum_k w psi F_k (Eq. 27)
+//   k_macro_pre, k_macro_sweep, k_macro_post: macroscopic LU-SGS          [a5]
+//   k_sweep_fwd, k_sweep_bwd: micro LU-SGS sweeps and update           [a6-a7]
 #include "idugks_internal.h"
 
 #include <cuda_runtime.h>
@@ -68,8 +82,67 @@ template <class T> __device__ __forceinline__ T xi_dot_n(T ux, T uy, T nx, T ny)
 }
 
 // ---------------------------------------------------------------------------
-// block reductions (fixed tree: deterministic)
+// accumulators: float-float pairs in mixed precision, double in FP64
 // ---------------------------------------------------------------------------
+struct FF {
+    float hi, lo;
+};
+// error-free sum of two floats (Knuth's two-sum)
+__device__ __forceinline__ FF two_sum(float a, float b)
+{
+    float s = a + b;
+    float bb = s - a;
+    float e = (a - (s - bb)) + (b - bb);
+    return {s, e};
+}
+__device__ __forceinline__ FF ff_add(FF a, FF b)
+{
+    FF s = two_sum(a.hi, b.hi);
+    float e = s.lo + (a.lo + b.lo);
+    float hi = s.hi + e;
+    return {hi, e - (hi - s.hi)};
+}
+
+template <class T> struct Acc;
+template <> struct Acc<float> {
+    FF v;
+    __device__ __forceinline__ void zero() { v = {0.f, 0.f}; }
+    __device__ __forceinline__ void add(float x) { v = ff_add(v, FF{x, 0.f}); }
+    __device__ __forceinline__ void warp_sum()
+    {
+        for (int o = 16; o > 0; o >>= 1) {
+            FF u{__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)};
+            v = ff_add(v, u);
+        }
+    }
+    __device__ __forceinline__ void store(void *base, size_t i) const { ((float2 *)base)[i] = make_float2(v.hi, v.lo); }
+    __device__ __forceinline__ double value() const { return (double)v.hi + (double)v.lo; }
+};
+template <> struct Acc<double> {
+    double v;
+    __device__ __forceinline__ void zero() { v = 0.0; }
+    __device__ __forceinline__ void add(double x) { v += x; }
+    __device__ __forceinline__ void warp_sum()
+    {
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    }
+    __device__ __forceinline__ void store(void *base, size_t i) const { ((double *)base)[i] = v; }
+    __device__ __forceinline__ double value() const { return v; }
+};
+
+// an accumulator entry widened to float64
+template <class T> __device__ __forceinline__ double acc_load(const void *base, size_t i);
+template <> __device__ __forceinline__ double acc_load<float>(const void *base, size_t i)
+{
+    float2 a = ((const float2 *)base)[i];
+    return (double)a.x + (double)a.y;
+}
+template <> __device__ __forceinline__ double acc_load<double>(const void *base, size_t i)
+{
+    return ((const double *)base)[i];
+}
+
+// block sum of float64 values (fixed tree: deterministic); result in thread 0
 template <int NV>
 __device__ void block_sum(double (&v)[NV], double *sm /* >= 32*NV */)
 {
@@ -99,8 +172,20 @@ __device__ __forceinline__ double viscosity(const KParams &p, double RT)
     return p.mu_ref * pow(RT / p.RT_ref, p.omega);
 }
 
-// Raw moments (G: 1,x,y,xx,xy,yy,x|xi|^2,y|xi|^2; H: 1,x,y) -> rho,U,V,RT and
-// the heat flux q = 1/2 sum w c (c^2 G + H) about U (Eq. 4-5).
+// heat flux q = 1/2 sum w c (c^2 G + H) about (U, V) from raw moments
+// (G: 1,x,y,xx,xy,yy,x|xi|^2,y|xi|^2; H: 1,x,y), Eq. (4)-(5)
+__device__ __forceinline__ void raw_heat_flux(const double *r, double U, double V, double &qx,
+                                              double &qy)
+{
+    double U2 = U * U + V * V;
+    double sx = r[6] - 2.0 * U * r[3] - 2.0 * V * r[4] + U2 * r[1] - U * (r[3] + r[5]) +
+                2.0 * U * U * r[1] + 2.0 * U * V * r[2] - U * U2 * r[0];
+    double sy = r[7] - 2.0 * U * r[4] - 2.0 * V * r[5] + U2 * r[2] - V * (r[3] + r[5]) +
+                2.0 * U * V * r[1] + 2.0 * V * V * r[2] - V * U2 * r[0];
+    qx = 0.5 * (sx + r[9] - U * r[8]);
+    qy = 0.5 * (sy + r[10] - V * r[8]);
+}
+
 __device__ void raw_to_state(const double *r, int K, double &rho, double &U, double &V,
                              double &RT, double &qx, double &qy)
 {
@@ -109,13 +194,7 @@ __device__ void raw_to_state(const double *r, int K, double &rho, double &U, dou
     V = r[2] / rho;
     double rhoE = 0.5 * (r[3] + r[5] + r[8]);
     RT = (2.0 * rhoE / rho - U * U - V * V) / (K + 2);
-    double U2 = U * U + V * V;
-    double sx = r[6] - 2.0 * U * r[3] - 2.0 * V * r[4] + U2 * r[1] - U * (r[3] + r[5]) +
-                2.0 * U * U * r[1] + 2.0 * U * V * r[2] - U * U2 * r[0];
-    double sy = r[7] - 2.0 * U * r[4] - 2.0 * V * r[5] + U2 * r[2] - V * (r[3] + r[5]) +
-                2.0 * U * V * r[1] + 2.0 * V * V * r[2] - V * U2 * r[0];
-    qx = 0.5 * (sx + r[9] - U * r[8]);
-    qy = 0.5 * (sy + r[10] - V * r[8]);
+    raw_heat_flux(r, U, V, qx, qy);
 }
 
 // Coefficients of the deviation equilibrium at (rho, U, V, RT, q):
@@ -153,20 +232,22 @@ template <class T> struct EqT {
     T e0, ex, ey, e2, U, V, invRT, pqx, pqy, rr, rrm1, kRT, lnA, lam;
 };
 
-template <class T> __device__ __forceinline__ EqT<T> eq_cast(const EqD &d)
+template <class T> __device__ __forceinline__ void eq_storeT(T *cp, const EqD &e)
 {
-    EqT<T> e;
-    e.e0 = (T)d.e0; e.ex = (T)d.ex; e.ey = (T)d.ey; e.e2 = (T)d.e2; e.U = (T)d.U; e.V = (T)d.V;
-    e.invRT = (T)d.invRT; e.pqx = (T)d.pqx; e.pqy = (T)d.pqy; e.rr = (T)d.rr; e.rrm1 = (T)d.rrm1;
-    e.kRT = (T)d.kRT; e.lnA = (T)d.lnA; e.lam = (T)d.lam;
-    return e;
+    cp[0] = (T)e.e0; cp[1] = (T)e.ex; cp[2] = (T)e.ey; cp[3] = (T)e.e2; cp[4] = (T)e.U;
+    cp[5] = (T)e.V; cp[6] = (T)e.invRT; cp[7] = (T)e.pqx; cp[8] = (T)e.pqy; cp[9] = (T)e.rr;
+    cp[10] = (T)e.rrm1; cp[11] = (T)e.kRT; cp[12] = (T)e.lnA; cp[13] = (T)e.lam;
 }
 
-__device__ __forceinline__ void eq_store(double *cp, const EqD &e)
+__device__ __forceinline__ void eq_store(double *cp, const EqD &e) { eq_storeT<double>(cp, e); }
+
+template <class T> __device__ __forceinline__ EqT<T> eq_loadT(const T *cp)
 {
-    cp[0] = e.e0; cp[1] = e.ex; cp[2] = e.ey; cp[3] = e.e2; cp[4] = e.U; cp[5] = e.V;
-    cp[6] = e.invRT; cp[7] = e.pqx; cp[8] = e.pqy; cp[9] = e.rr; cp[10] = e.rrm1;
-    cp[11] = e.kRT; cp[12] = e.lnA; cp[13] = e.lam;
+    EqT<T> e;
+    e.e0 = cp[0]; e.ex = cp[1]; e.ey = cp[2]; e.e2 = cp[3]; e.U = cp[4]; e.V = cp[5];
+    e.invRT = cp[6]; e.pqx = cp[7]; e.pqy = cp[8]; e.rr = cp[9]; e.rrm1 = cp[10]; e.kRT = cp[11];
+    e.lnA = cp[12]; e.lam = cp[13];
+    return e;
 }
 
 // f^S(k) - M_ref(k) for G and H.  Near M_ref (|E| < 1/2) through expm1 of the
@@ -195,74 +276,103 @@ __device__ __forceinline__ void dev_equilibrium(const EqT<T> &e, T ux, T uy, T g
     }
 }
 
-// ---------------------------------------------------------------------------
-// cell prep: raw moments of f~, equilibrium at W^n, fb+ (Eq. 10, 12)     [a1]
-// ---------------------------------------------------------------------------
+// raw-moment partials of one velocity: G: 1,x,y,xx,xy,yy,x|xi|^2,y|xi|^2; H: 1,x,y
 template <class T>
-__global__ void __launch_bounds__(256) k_cell_prep(KParams p)
+__device__ __forceinline__ void raw_terms(T (&a)[kRaw], T w, T ux, T uy, T g, T h)
 {
-    using T2 = typename V2<T>::t;
-    __shared__ double sm[32 * 11];
-    __shared__ EqD seq;
-    __shared__ double sc[2];
-    const int c = blockIdx.x;
-    const T2 *f = (const T2 *)p.f + (size_t)c * p.Nv;
-    T2 *fb = (T2 *)p.fbp + (size_t)c * p.Nv;
-    T a[11];
-#pragma unroll
-    for (int q = 0; q < 11; ++q) a[q] = 0;
-    for (int k = threadIdx.x; k < p.Nv; k += blockDim.x) {
-        T2 v = f[k];
-        T ux = vx<T>(p, k), uy = vy<T>(p, k), w = vw<T>(p, k);
-        T wg = w * v.x, wh = w * v.y, s2 = ux * ux + uy * uy;
-        a[0] += wg; a[1] += wg * ux; a[2] += wg * uy; a[3] += wg * ux * ux; a[4] += wg * ux * uy;
-        a[5] += wg * uy * uy; a[6] += wg * ux * s2; a[7] += wg * uy * s2;
-        a[8] += wh; a[9] += wh * ux; a[10] += wh * uy;
-    }
-    double r[11];
-#pragma unroll
-    for (int q = 0; q < 11; ++q) r[q] = (double)a[q];
-    block_sum<11>(r, sm);
-    if (threadIdx.x == 0) {
-        for (int q = 0; q < 11; ++q) r[q] += p.mref_raw[q];
-        const double *W = p.W + 4 * c;
-        double rho = W[0], U = W[1] / rho, V = W[2] / rho;
-        double RT = (2.0 * W[3] / rho - U * U - V * V) / (p.K + 2);
-        double tau = viscosity(p, RT) / (rho * RT);
-        // heat flux of f~ about U from W (not about the moments' own velocity)
-        double U2 = U * U + V * V;
-        double sx = r[6] - 2.0 * U * r[3] - 2.0 * V * r[4] + U2 * r[1] - U * (r[3] + r[5]) +
-                    2.0 * U * U * r[1] + 2.0 * U * V * r[2] - U * U2 * r[0];
-        double sy = r[7] - 2.0 * U * r[4] - 2.0 * V * r[5] + U2 * r[2] - V * (r[3] + r[5]) +
-                    2.0 * U * V * r[1] + 2.0 * V * V * r[2] - V * U2 * r[0];
-        double qtx = 0.5 * (sx + r[9] - U * r[8]), qty = 0.5 * (sy + r[10] - V * r[8]);
-        double Pr = p.shakhov ? p.Pr : 1.0;
-        double qx = 2.0 * tau * qtx / (2.0 * tau + p.dt * Pr);
-        double qy = 2.0 * tau * qty / (2.0 * tau + p.dt * Pr);
-        p.cellq[2 * c] = qx;
-        p.cellq[2 * c + 1] = qy;
-        seq = make_eq(p, rho, U, V, RT, qx, qy);
-        sc[0] = (2.0 * tau - p.h) / (2.0 * tau + p.dt);
-        sc[1] = 3.0 * p.h / (2.0 * tau + p.dt);
-    }
-    __syncthreads();
-    const EqT<T> e = eq_cast<T>(seq);
-    const T c1 = (T)sc[0], c2 = (T)sc[1], kRTr = (T)(p.K * p.RT_r);
-    for (int k = threadIdx.x; k < p.Nv; k += blockDim.x) {
-        T2 v = f[k];
-        T dG, dH;
-        dev_equilibrium<T>(e, vx<T>(p, k), vy<T>(p, k), vgref<T>(p, k), kRTr, dG, dH);
-        T2 o;
-        o.x = c1 * v.x + c2 * dG;
-        o.y = c1 * v.y + c2 * dH;
-        fb[k] = o;
-    }
+    T wg = w * g, wh = w * h, s2 = ux * ux + uy * uy;
+    a[0] += wg; a[1] += wg * ux; a[2] += wg * uy; a[3] += wg * ux * ux; a[4] += wg * ux * uy;
+    a[5] += wg * uy * uy; a[6] += wg * ux * s2; a[7] += wg * uy * s2;
+    a[8] += wh; a[9] += wh * ux; a[10] += wh * uy;
 }
 
 // ---------------------------------------------------------------------------
-// reconstruction from one cell along the characteristic (Eq. 11, 13-17)
+// cell moments and cell prep (Eq. 10, 12)                                [a1]
 // ---------------------------------------------------------------------------
-template <class T> struct CellRec {
+template <class T>
+__global__ void __launch_bounds__(256) k_cell_moments(KParams p)
+{
+    using T2 = typename V2<T>::t;
+    const int lane = threadIdx.x & 31;
+    const int c = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (c >= p.N) return;  // whole warp
+    const T2 *f = (const T2 *)p.f + (size_t)c * p.Nv;
+    Acc<T> acc[kRaw];
+#pragma unroll
+    for (int q = 0; q < kRaw; ++q) acc[q].zero();
+    for (int k0 = 0; k0 < p.Nv; k0 += 256) {
+        T a[kRaw];
+#pragma unroll
+        for (int q = 0; q < kRaw; ++q) a[q] = 0;
+#pragma unroll 4
+        for (int u = 0; u < 8; ++u) {
+            int k = k0 + 32 * u + lane;
+            if (k < p.Nv) {
+                T2 v = f[k];
+                raw_terms<T>(a, vw<T>(p, k), vx<T>(p, k), vy<T>(p, k), v.x, v.y);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < kRaw; ++q) acc[q].add(a[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < kRaw; ++q) acc[q].warp_sum();
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < kRaw; ++q) acc[q].store(p.cellraw, (size_t)c * kRaw + q);
+}
+
+// per cell: heat flux of f from f~ (about U of W), tau, equilibrium at W^n,
+// and the two coefficients of fb+ = (2tau-h)/(2tau+dt) f~ + 3h/(2tau+dt) f^S
+template <class T>
+__global__ void __launch_bounds__(256) k_cell_params(KParams p)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= p.N) return;
+    double r[kRaw];
+    for (int q = 0; q < kRaw; ++q) r[q] = acc_load<T>(p.cellraw, (size_t)c * kRaw + q) + p.mref_raw[q];
+    const double *W = p.W + 4 * c;
+    double rho = W[0], U = W[1] / rho, V = W[2] / rho;
+    double RT = (2.0 * W[3] / rho - U * U - V * V) / (p.K + 2);
+    double tau = viscosity(p, RT) / (rho * RT);
+    double qtx, qty;
+    raw_heat_flux(r, U, V, qtx, qty);
+    double Pr = p.shakhov ? p.Pr : 1.0;
+    double qx = 2.0 * tau * qtx / (2.0 * tau + p.dt * Pr);
+    double qy = 2.0 * tau * qty / (2.0 * tau + p.dt * Pr);
+    p.cellq[2 * c] = qx;
+    p.cellq[2 * c + 1] = qy;
+    T *cA = (T *)p.cellA + kCellP * c;
+    eq_storeT<T>(cA, make_eq(p, rho, U, V, RT, qx, qy));
+    cA[14] = (T)((2.0 * tau - p.h) / (2.0 * tau + p.dt));
+    cA[15] = (T)(3.0 * p.h / (2.0 * tau + p.dt));
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_fbp(KParams p)
+{
+    using T2 = typename V2<T>::t;
+    const int c = blockIdx.x;
+    const int k = blockIdx.y * blockDim.x + threadIdx.x;
+    if (k >= p.Nv) return;
+    const T *cA = (const T *)p.cellA + kCellP * c;
+    EqT<T> e = eq_loadT<T>(cA);
+    T c1 = cA[14], c2 = cA[15];
+    size_t ck = (size_t)c * p.Nv + k;
+    T2 v = ((const T2 *)p.f)[ck];
+    T dG, dH;
+    dev_equilibrium<T>(e, vx<T>(p, k), vy<T>(p, k), vgref<T>(p, k), (T)(p.K * p.RT_r), dG, dH);
+    T2 o;
+    o.x = c1 * v.x + c2 * dG;
+    o.y = c1 * v.y + c2 * dH;
+    ((T2 *)p.fbp)[ck] = o;
+}
+
+// ---------------------------------------------------------------------------
+// faces: reconstruction from one cell along the characteristic (Eq. 11,
+// 13-17), moments, face equilibrium and flux (Eq. 18-19)            [a2-a4]
+// ---------------------------------------------------------------------------
+template <class T> struct SideRec {
     int c;
     int nb[4];
     T gx[4], gy[4];    // least-squares weights: sigma = sum_m g_m (phi_nb - phi_c)
@@ -271,24 +381,27 @@ template <class T> struct CellRec {
 };
 
 template <class T>
-__device__ void load_rec(const KParams &p, int c, double rx, double ry, CellRec<T> &r)
+__device__ __forceinline__ void load_side(const KParams &p, int c, T rx, T ry, SideRec<T> &r)
 {
+    const T *g = (const T *)p.clsgT + 8 * c;
+    const T *o = (const T *)p.crT + 8 * c;
     r.c = c;
+#pragma unroll
     for (int m = 0; m < 4; ++m) {
         r.nb[m] = p.cnb[4 * c + m];
-        r.gx[m] = (T)p.clsg[8 * c + 2 * m];
-        r.gy[m] = (T)p.clsg[8 * c + 2 * m + 1];
-        r.frx[m] = (T)p.cr[8 * c + 2 * m];
-        r.fry[m] = (T)p.cr[8 * c + 2 * m + 1];
+        r.gx[m] = g[2 * m];
+        r.gy[m] = g[2 * m + 1];
+        r.frx[m] = o[2 * m];
+        r.fry[m] = o[2 * m + 1];
     }
-    r.rx = (T)rx;
-    r.ry = (T)ry;
+    r.rx = rx;
+    r.ry = ry;
 }
 
 template <class T> __device__ __forceinline__ T venkat(T x) { return (x * x + (T)2 * x) / (x * x + x + (T)2); }
 
 template <class T>
-__device__ __forceinline__ T limit_scalar(const CellRec<T> &r, T v0, T vmax, T vmin, T sx, T sy)
+__device__ __forceinline__ T limit_scalar(const SideRec<T> &r, T v0, T vmax, T vmin, T sx, T sy)
 {
     T phi = (T)1;
 #pragma unroll
@@ -302,8 +415,11 @@ __device__ __forceinline__ T limit_scalar(const CellRec<T> &r, T v0, T vmax, T v
     return phi;
 }
 
+// fb at the face from side r: fb+_c + phi sigma_c . (x_f - xi h - x_c).  The
+// limiter ratios only involve differences of fb+ between cells at one
+// velocity, so the M_ref offset cancels and deviations serve as is.
 template <class T, bool LIM>
-__device__ __forceinline__ typename V2<T>::t reconstruct(const KParams &p, const CellRec<T> &r,
+__device__ __forceinline__ typename V2<T>::t reconstruct(const KParams &p, const SideRec<T> &r,
                                                          int k, T ux, T uy, T h)
 {
     using T2 = typename V2<T>::t;
@@ -326,8 +442,6 @@ __device__ __forceinline__ typename V2<T>::t reconstruct(const KParams &p, const
     T ax = r.rx - ux * h, ay = r.ry - uy * h;
     T pg = (T)1, ph = (T)1;
     if (LIM) {
-        // the limiter ratios only involve differences of fb+ between cells at
-        // one velocity, so the M_ref offset cancels and deviations serve as is
         pg = limit_scalar<T>(r, f0.x, gmax, gmin, sgx, sgy);
         ph = limit_scalar<T>(r, f0.y, hmax, hmin, shx, shy);
     }
@@ -338,210 +452,244 @@ __device__ __forceinline__ typename V2<T>::t reconstruct(const KParams &p, const
 }
 
 template <class T>
-__device__ __forceinline__ void acc_raw(T (&a)[11], T w, T ux, T uy, T g, T h)
+__device__ __forceinline__ void select_side(bool left, const SideRec<T> &L, const SideRec<T> &R,
+                                            SideRec<T> &o)
 {
-    T wg = w * g, wh = w * h, s2 = ux * ux + uy * uy;
-    a[0] += wg; a[1] += wg * ux; a[2] += wg * uy; a[3] += wg * ux * ux; a[4] += wg * ux * uy;
-    a[5] += wg * uy * uy; a[6] += wg * ux * s2; a[7] += wg * uy * s2;
-    a[8] += wh; a[9] += wh * ux; a[10] += wh * uy;
+    o.c = left ? L.c : R.c;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        o.nb[m] = left ? L.nb[m] : R.nb[m];
+        o.gx[m] = left ? L.gx[m] : R.gx[m];
+        o.gy[m] = left ? L.gy[m] : R.gy[m];
+        o.frx[m] = left ? L.frx[m] : R.frx[m];
+        o.fry[m] = left ? L.fry[m] : R.fry[m];
+    }
+    o.rx = left ? L.rx : R.rx;
+    o.ry = left ? L.ry : R.ry;
 }
 
-// ---------------------------------------------------------------------------
-// interior faces (Eq. 11-19)                                          [a2-a4]
-// ---------------------------------------------------------------------------
-template <class T, bool LIM>
-__global__ void __launch_bounds__(256) k_face_interior(KParams p, const int *list, int nlist)
+// Everything a warp needs about one face.
+template <class T> struct FaceCtx {
+    int kind;          // -1 interior, 1 wall, 2 far field
+    int side;
+    T nx, ny, S, on;   // normal L->R, length; boundary: +1 if the interior cell is L
+    SideRec<T> L, R;   // boundary faces use L for the interior cell
+};
+
+template <class T>
+__device__ __forceinline__ void load_face(const KParams &p, int f, FaceCtx<T> &fc)
 {
-    using T2 = typename V2<T>::t;
-    __shared__ double sm[32 * 11];
-    __shared__ CellRec<T> recL, recR;
-    __shared__ EqD seq;
-    __shared__ double sab[2];
-    const int f = list[blockIdx.x];
-    const double *g = p.fgeo + 7 * f;
-    if (threadIdx.x == 0) load_rec<T>(p, p.fL[f], g[3], g[4], recL);
-    if (threadIdx.x == 1) load_rec<T>(p, p.fR[f], g[5], g[6], recR);
-    __syncthreads();
-    const T nx = (T)g[0], ny = (T)g[1], S = (T)g[2], h = (T)p.h;
-    T a[11];
-#pragma unroll
-    for (int q = 0; q < 11; ++q) a[q] = 0;
-    for (int k = threadIdx.x; k < p.Nv; k += blockDim.x) {
-        T ux = vx<T>(p, k), uy = vy<T>(p, k);
-        T s = xi_dot_n<T>(ux, uy, nx, ny);
-        T2 fb;
-        if (s > (T)0) fb = reconstruct<T, LIM>(p, recL, k, ux, uy, h);
-        else if (s < (T)0) fb = reconstruct<T, LIM>(p, recR, k, ux, uy, h);
-        else {
-            T2 l = reconstruct<T, LIM>(p, recL, k, ux, uy, h);
-            T2 rr = reconstruct<T, LIM>(p, recR, k, ux, uy, h);
-            fb.x = (T)0.5 * (l.x + rr.x);
-            fb.y = (T)0.5 * (l.y + rr.y);
-        }
-        acc_raw<T>(a, vw<T>(p, k), ux, uy, fb.x, fb.y);
-    }
-    double r[11];
-#pragma unroll
-    for (int q = 0; q < 11; ++q) r[q] = (double)a[q];
-    block_sum<11>(r, sm);
-    if (threadIdx.x == 0) {
-        for (int q = 0; q < 11; ++q) r[q] += p.mref_raw[q];
-        double rho, U, V, RT, qbx, qby;
-        raw_to_state(r, p.K, rho, U, V, RT, qbx, qby);
-        double tau = viscosity(p, RT) / (rho * RT);
-        double Pr = p.shakhov ? p.Pr : 1.0;
-        double qx = 2.0 * tau * qbx / (2.0 * tau + p.h * Pr);
-        double qy = 2.0 * tau * qby / (2.0 * tau + p.h * Pr);
-        seq = make_eq(p, rho, U, V, RT, qx, qy);
-        sab[0] = 2.0 * tau / (2.0 * tau + p.h);
-        sab[1] = p.h / (2.0 * tau + p.h);
-    }
-    __syncthreads();
-    const EqT<T> e = eq_cast<T>(seq);
-    const T fa = (T)sab[0], fbw = (T)sab[1], kRTr = (T)(p.K * p.RT_r);
-    T2 *Fo = (T2 *)p.F + (size_t)f * p.Nv;
-    T pa[4] = {0, 0, 0, 0};
-    for (int k = threadIdx.x; k < p.Nv; k += blockDim.x) {
-        T ux = vx<T>(p, k), uy = vy<T>(p, k);
-        T s = xi_dot_n<T>(ux, uy, nx, ny);
-        T2 fb;
-        if (s > (T)0) fb = reconstruct<T, LIM>(p, recL, k, ux, uy, h);
-        else if (s < (T)0) fb = reconstruct<T, LIM>(p, recR, k, ux, uy, h);
-        else {
-            T2 l = reconstruct<T, LIM>(p, recL, k, ux, uy, h);
-            T2 rr = reconstruct<T, LIM>(p, recR, k, ux, uy, h);
-            fb.x = (T)0.5 * (l.x + rr.x);
-            fb.y = (T)0.5 * (l.y + rr.y);
-        }
-        T dG, dH;
-        dev_equilibrium<T>(e, ux, uy, vgref<T>(p, k), kRTr, dG, dH);
-        T sS = s * S;
-        T2 Fk;
-        Fk.x = sS * (fa * fb.x + fbw * dG);
-        Fk.y = sS * (fa * fb.y + fbw * dH);
-        Fo[k] = Fk;
-        T w = vw<T>(p, k), wg = w * Fk.x;
-        pa[0] += wg; pa[1] += wg * ux; pa[2] += wg * uy;
-        pa[3] += (T)0.5 * w * ((ux * ux + uy * uy) * Fk.x + Fk.y);
-    }
-    double rp[4] = {(double)pa[0], (double)pa[1], (double)pa[2], (double)pa[3]};
-    block_sum<4>(rp, sm);
-    if (threadIdx.x == 0) {
-        double nxd = g[0], nyd = g[1], Sd = g[2];
-        for (int q = 0; q < 4; ++q)
-            p.phi[4 * f + q] = rp[q] + Sd * (nxd * p.mref_flux[q][0] + nyd * p.mref_flux[q][1]);
+    const T *g = (const T *)p.fgeoT + 8 * f;
+    fc.nx = g[0];
+    fc.ny = g[1];
+    fc.S = g[2];
+    fc.kind = p.fbc[f];
+    fc.side = p.fside[f];
+    const int L = p.fL[f], R = p.fR[f];
+    if (fc.kind < 0) {
+        load_side<T>(p, L, g[3], g[4], fc.L);
+        load_side<T>(p, R, g[5], g[6], fc.R);
+        fc.on = (T)1;
+    } else if (L >= 0) {
+        load_side<T>(p, L, g[3], g[4], fc.L);
+        fc.on = (T)1;
+    } else {
+        load_side<T>(p, R, g[5], g[6], fc.L);
+        fc.on = (T)-1;
     }
 }
 
-// ---------------------------------------------------------------------------
-// boundary faces: diffuse wall (Eq. 34-35) or far field, in float64    [a4]
-// ---------------------------------------------------------------------------
+// fb - M_ref at velocity k.  Interior: upwind side by sign(xi.n), average at
+// a tie.  Boundary: outgoing from the interior cell; incoming from the wall
+// Maxwellian rho_w M_w (rho_w - 1 passed as rwm1) or the far-field state.
 template <class T, bool LIM>
-__global__ void __launch_bounds__(256) k_face_boundary(KParams p, const int *list, int nlist)
+__device__ __forceinline__ typename V2<T>::t face_fbar(const KParams &p, const FaceCtx<T> &fc, int k,
+                                                       T ux, T uy, T s, T rhow, T rwm1)
 {
     using T2 = typename V2<T>::t;
-    __shared__ double sm[32 * 11];
-    __shared__ CellRec<T> rec;
-    __shared__ EqD seq;
-    __shared__ double sab[3];
-    const int f = list[blockIdx.x];
-    const double *g = p.fgeo + 7 * f;
-    const bool isL = p.fL[f] >= 0;
-    const int c = isL ? p.fL[f] : p.fR[f];
-    const double on = isL ? 1.0 : -1.0;
-    const int side = p.fside[f], kind = p.fbc[f];
-    if (threadIdx.x == 0) load_rec<T>(p, c, isL ? g[3] : g[5], isL ? g[4] : g[6], rec);
-    __syncthreads();
-    const double nx = g[0], ny = g[1], S = g[2];
     const T h = (T)p.h;
-    const double kRTr = p.K * p.RT_r;
-    const double *bG = p.bndG + (size_t)side * p.Nv, *bH = p.bndH + (size_t)side * p.Nv;
-    // zero net mass flux through the wall fixes the wall density (Eq. 35)
-    double bw = 1.0;
-    if (kind == 1) {
-        double io[2] = {0.0, 0.0};
-        for (int k = threadIdx.x; k < p.Nv; k += blockDim.x) {
-            double ux = p.ux[k], uy = p.uy[k];
-            double so = on * xi_dot_n<double>(ux, uy, nx, ny);
-            if (so > 0.0) {
-                typename V2<T>::t fb = reconstruct<T, LIM>(p, rec, k, (T)ux, (T)uy, h);
-                io[0] += p.w[k] * so * (p.gref[k] + (double)fb.x);
-            } else if (so < 0.0) {
-                io[1] += p.w[k] * (-so) * bG[k];
+    if (fc.kind < 0) {
+        SideRec<T> r;
+        select_side<T>(s > (T)0, fc.L, fc.R, r);
+        T2 fb = reconstruct<T, LIM>(p, r, k, ux, uy, h);
+        if (s == (T)0) {
+            T2 o = reconstruct<T, LIM>(p, fc.L, k, ux, uy, h);
+            fb.x = (T)0.5 * (o.x + fb.x);
+            fb.y = (T)0.5 * (o.y + fb.y);
+        }
+        return fb;
+    }
+    T so = fc.on * s;
+    T2 in;
+    if (so <= (T)0) {
+        const T *bG = (const T *)p.bdevG + (size_t)fc.side * p.Nv;
+        const T *bH = (const T *)p.bdevH + (size_t)fc.side * p.Nv;
+        T gref = vgref<T>(p, k);
+        in.x = rhow * bG[k] + rwm1 * gref;
+        in.y = rhow * bH[k] + rwm1 * (T)(p.K * p.RT_r) * gref;
+        if (so < (T)0) return in;
+    }
+    T2 fb = reconstruct<T, LIM>(p, fc.L, k, ux, uy, h);
+    if (so == (T)0) {
+        fb.x = (T)0.5 * (fb.x + in.x);
+        fb.y = (T)0.5 * (fb.y + in.y);
+    }
+    return fb;
+}
+
+// raw moments of fb - M_ref at every face (plus the wall density, Eq. 35)
+template <class T, bool LIM>
+__global__ void __launch_bounds__(256) k_face_moments(KParams p)
+{
+    using T2 = typename V2<T>::t;
+    const int lane = threadIdx.x & 31;
+    const int f = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (f >= p.nf) return;  // whole warp
+    FaceCtx<T> fc;
+    load_face<T>(p, f, fc);
+    T rhow = (T)1, rwm1 = (T)0;
+    double rw = 1.0;
+    Acc<T> outsum;
+    outsum.zero();
+    if (fc.kind == 1) {
+        // zero net mass flux: rho_w sum_in w |xi.n| G_w = sum_out w (xi.n) fb
+        for (int k0 = 0; k0 < p.Nv; k0 += 256) {
+            T a = 0;
+            for (int u = 0; u < 8; ++u) {
+                int k = k0 + 32 * u + lane;
+                if (k >= p.Nv) break;
+                T ux = vx<T>(p, k), uy = vy<T>(p, k);
+                T so = fc.on * xi_dot_n<T>(ux, uy, fc.nx, fc.ny);
+                if (so > (T)0) {
+                    T2 fb = reconstruct<T, LIM>(p, fc.L, k, ux, uy, (T)p.h);
+                    a += vw<T>(p, k) * so * fb.x;
+                }
             }
+            outsum.add(a);
         }
-        block_sum<2>(io, sm);
-        if (threadIdx.x == 0) sab[2] = io[0] / io[1];
-        __syncthreads();
-        bw = sab[2];
+        outsum.warp_sum();
+        double o = __shfl_sync(0xffffffffu, outsum.value(), 0);
+        const double *bc = p.bconst + 2 * f;
+        rw = (bc[0] + o) / bc[1];
+        rhow = (T)rw;
+        rwm1 = (T)((bc[0] - bc[1] + o) / bc[1]);
     }
-    double r[11];
-    for (int q = 0; q < 11; ++q) r[q] = 0.0;
-    for (int k = threadIdx.x; k < p.Nv; k += blockDim.x) {
-        double ux = p.ux[k], uy = p.uy[k];
-        double so = on * xi_dot_n<double>(ux, uy, nx, ny);
-        double G, H;
-        if (so < 0.0) { G = bw * bG[k]; H = bw * bH[k]; }
-        else {
-            typename V2<T>::t fb = reconstruct<T, LIM>(p, rec, k, (T)ux, (T)uy, h);
-            G = p.gref[k] + (double)fb.x;
-            H = kRTr * p.gref[k] + (double)fb.y;
-            if (so == 0.0) { G = 0.5 * (G + bw * bG[k]); H = 0.5 * (H + bw * bH[k]); }
+    Acc<T> acc[kRaw];
+#pragma unroll
+    for (int q = 0; q < kRaw; ++q) acc[q].zero();
+    for (int k0 = 0; k0 < p.Nv; k0 += 256) {
+        T a[kRaw];
+#pragma unroll
+        for (int q = 0; q < kRaw; ++q) a[q] = 0;
+        for (int u = 0; u < 8; ++u) {
+            int k = k0 + 32 * u + lane;
+            if (k >= p.Nv) break;
+            T ux = vx<T>(p, k), uy = vy<T>(p, k);
+            T s = xi_dot_n<T>(ux, uy, fc.nx, fc.ny);
+            T2 fb = face_fbar<T, LIM>(p, fc, k, ux, uy, s, rhow, rwm1);
+            raw_terms<T>(a, vw<T>(p, k), ux, uy, fb.x, fb.y);
         }
-        double w = p.w[k], wg = w * G, wh = w * H, s2 = ux * ux + uy * uy;
-        r[0] += wg; r[1] += wg * ux; r[2] += wg * uy; r[3] += wg * ux * ux; r[4] += wg * ux * uy;
-        r[5] += wg * uy * uy; r[6] += wg * ux * s2; r[7] += wg * uy * s2;
-        r[8] += wh; r[9] += wh * ux; r[10] += wh * uy;
+#pragma unroll
+        for (int q = 0; q < kRaw; ++q) acc[q].add(a[q]);
     }
-    block_sum<11>(r, sm);
-    if (threadIdx.x == 0) {
-        double rho, U, V, RT, qbx, qby;
-        raw_to_state(r, p.K, rho, U, V, RT, qbx, qby);
-        double tau = viscosity(p, RT) / (rho * RT);
-        double Pr = p.shakhov ? p.Pr : 1.0;
-        double qx = 2.0 * tau * qbx / (2.0 * tau + p.h * Pr);
-        double qy = 2.0 * tau * qby / (2.0 * tau + p.h * Pr);
-        seq = make_eq(p, rho, U, V, RT, qx, qy);
-        sab[0] = 2.0 * tau / (2.0 * tau + p.h);
-        sab[1] = p.h / (2.0 * tau + p.h);
+#pragma unroll
+    for (int q = 0; q < kRaw; ++q) acc[q].warp_sum();
+    if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < kRaw; ++q) acc[q].store(p.faceraw, (size_t)f * 12 + q);
+        outsum.store(p.faceraw, (size_t)f * 12 + 11);
+        p.facerw[f] = rw;
     }
-    __syncthreads();
-    const EqD e = seq;
-    const double fa = sab[0], fbw = sab[1];
+}
+
+// per face: state from the moments of fb, tau, q = 2 tau qbar/(2 tau + h Pr),
+// equilibrium, and the weights a, b of f = a fb + b f^S (Eq. 18)
+template <class T>
+__global__ void __launch_bounds__(256) k_face_params(KParams p)
+{
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= p.nf) return;
+    double r[kRaw];
+    for (int q = 0; q < kRaw; ++q) r[q] = acc_load<T>(p.faceraw, (size_t)f * 12 + q) + p.mref_raw[q];
+    double rho, U, V, RT, qbx, qby;
+    raw_to_state(r, p.K, rho, U, V, RT, qbx, qby);
+    double tau = viscosity(p, RT) / (rho * RT);
+    double Pr = p.shakhov ? p.Pr : 1.0;
+    double qx = 2.0 * tau * qbx / (2.0 * tau + p.h * Pr);
+    double qy = 2.0 * tau * qby / (2.0 * tau + p.h * Pr);
+    T *fA = (T *)p.faceA + kCellP * f;
+    eq_storeT<T>(fA, make_eq(p, rho, U, V, RT, qx, qy));
+    fA[14] = (T)(2.0 * tau / (2.0 * tau + p.h));
+    fA[15] = (T)(p.h / (2.0 * tau + p.h));
+}
+
+// face flux of (f_face - M_ref), Eq. (18)-(19), and its moments
+template <class T, bool LIM>
+__global__ void __launch_bounds__(256) k_face_flux(KParams p)
+{
+    using T2 = typename V2<T>::t;
+    const int lane = threadIdx.x & 31;
+    const int f = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (f >= p.nf) return;  // whole warp
+    FaceCtx<T> fc;
+    load_face<T>(p, f, fc);
+    double rw = p.facerw[f];
+    T rhow = (T)rw, rwm1 = (T)(rw - 1.0);
+    if (fc.kind == 1) {
+        const double *bc = p.bconst + 2 * f;
+        double o = acc_load<T>(p.faceraw, (size_t)f * 12 + 11);
+        rwm1 = (T)((bc[0] - bc[1] + o) / bc[1]);
+    }
+    const T *fA = (const T *)p.faceA + kCellP * f;
+    const EqT<T> e = eq_loadT<T>(fA);
+    const T wa = fA[14], wb = fA[15], kRTr = (T)(p.K * p.RT_r);
     T2 *Fo = (T2 *)p.F + (size_t)f * p.Nv;
-    double pa[4] = {0, 0, 0, 0};
-    for (int k = threadIdx.x; k < p.Nv; k += blockDim.x) {
-        double ux = p.ux[k], uy = p.uy[k];
-        double s = xi_dot_n<double>(ux, uy, nx, ny);
-        double so = on * s;
-        double G, H;
-        if (so < 0.0) { G = bw * bG[k]; H = bw * bH[k]; }
-        else {
-            typename V2<T>::t fb = reconstruct<T, LIM>(p, rec, k, (T)ux, (T)uy, h);
-            G = p.gref[k] + (double)fb.x;
-            H = kRTr * p.gref[k] + (double)fb.y;
-            if (so == 0.0) { G = 0.5 * (G + bw * bG[k]); H = 0.5 * (H + bw * bH[k]); }
+    Acc<T> acc[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q].zero();
+    for (int k0 = 0; k0 < p.Nv; k0 += 256) {
+        T a[4] = {0, 0, 0, 0};
+        for (int u = 0; u < 8; ++u) {
+            int k = k0 + 32 * u + lane;
+            if (k >= p.Nv) break;
+            T ux = vx<T>(p, k), uy = vy<T>(p, k);
+            T s = xi_dot_n<T>(ux, uy, fc.nx, fc.ny);
+            T2 fb = face_fbar<T, LIM>(p, fc, k, ux, uy, s, rhow, rwm1);
+            T dG, dH;
+            dev_equilibrium<T>(e, ux, uy, vgref<T>(p, k), kRTr, dG, dH);
+            T sS = s * fc.S;
+            T2 Fk;
+            Fk.x = sS * (wa * fb.x + wb * dG);
+            Fk.y = sS * (wa * fb.y + wb * dH);
+            Fo[k] = Fk;
+            T w = vw<T>(p, k), wg = w * Fk.x;
+            a[0] += wg;
+            a[1] += wg * ux;
+            a[2] += wg * uy;
+            a[3] += (T)0.5 * w * ((ux * ux + uy * uy) * Fk.x + Fk.y);
         }
-        // face equilibrium in full float64 (few faces)
-        double cx = ux - e.U, cy = uy - e.V, q2 = cx * cx + cy * cy;
-        double P = e.pqx * cx + e.pqy * cy, t = q2 * e.invRT;
-        double geq = exp(e.lnA - e.lam * q2);
-        double GS = geq * (1.0 + P * (t - 4.0)), HS = e.kRT * geq * (1.0 + P * (t - 2.0));
-        double FG = s * S * (fa * G + fbw * GS), FH = s * S * (fa * H + fbw * HS);
-        double Fref = s * S * p.gref[k];
-        T2 Fk;
-        Fk.x = (T)(FG - Fref);
-        Fk.y = (T)(FH - kRTr * Fref);
-        Fo[k] = Fk;
-        double w = p.w[k], wg = w * FG;
-        pa[0] += wg; pa[1] += wg * ux; pa[2] += wg * uy;
-        pa[3] += 0.5 * w * ((ux * ux + uy * uy) * FG + FH);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[q].add(a[q]);
     }
-    block_sum<4>(pa, sm);
-    if (threadIdx.x == 0) {
-        if (kind == 1) pa[0] = 0.0;  // impermeable wall
-        for (int q = 0; q < 4; ++q) p.phi[4 * f + q] = pa[q];
-    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q].warp_sum();
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[q].store(p.phiraw, (size_t)f * 4 + q);
+}
+
+// Phi_f = sum_k w psi F_k (Eq. 27): deviation part plus the flux of M_ref;
+// the mass flux through an impermeable wall is exactly zero
+template <class T>
+__global__ void __launch_bounds__(256) k_face_phi(KParams p)
+{
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= p.nf) return;
+    const double *g = p.fgeo + 7 * f;
+    for (int q = 0; q < 4; ++q)
+        p.phi[4 * f + q] = acc_load<T>(p.phiraw, (size_t)f * 4 + q) +
+                           g[2] * (g[0] * p.mref_flux[q][0] + g[1] * p.mref_flux[q][1]);
+    if (p.fbc[f] == 1) p.phi[4 * f] = 0.0;
 }
 
 // ---------------------------------------------------------------------------
@@ -748,14 +896,10 @@ __global__ void __launch_bounds__(256) k_macro_post(KParams p)
 // micro LU-SGS sweeps (Eq. 22-26) on i+j hyperplanes                  [a6-a7]
 // one CTA per tile of sweep_tv velocities; sweep_pc cell slots per CTA
 // ---------------------------------------------------------------------------
-template <class T> __device__ __forceinline__ EqT<T> eq_loadT(const T *cp)
-{
-    EqT<T> e;
-    e.e0 = cp[0]; e.ex = cp[1]; e.ey = cp[2]; e.e2 = cp[3]; e.U = cp[4]; e.V = cp[5];
-    e.invRT = cp[6]; e.pqx = cp[7]; e.pqy = cp[8]; e.rr = cp[9]; e.rrm1 = cp[10]; e.kRT = cp[11];
-    e.lnA = cp[12]; e.lam = cp[13];
-    return e;
-}
+// ---------------------------------------------------------------------------
+// micro LU-SGS sweeps (Eq. 22-26) on i+j hyperplanes                  [a6-a7]
+// one CTA per tile of sweep_tv velocities; sweep_pc cell slots per CTA
+// ---------------------------------------------------------------------------
 
 // Forward sweep: Delta*_c = (R_c + sum_{lower inflow nb} |xi.n| S Delta*_nb) / D_c
 // with R = -sum_faces F - (2 Omega/(2 tau' + dt)) (f~ - f^S(W^{n+1})) (Eq. 22-23)
@@ -778,6 +922,7 @@ __global__ void __launch_bounds__(1024) k_sweep_fwd(KParams p)
     const T2 *f = (const T2 *)p.f;
     T2 *ds = (T2 *)p.dst;
     const T *cpT = (const T *)p.cellpT;
+    const T *sl = (const T *)p.cslotT;
     const int nh = ni + nj - 1;
     for (int dpl = 0; dpl < nh; ++dpl) {
         int ilo = max(0, dpl - (nj - 1)), ihi = min(ni - 1, dpl);
@@ -796,14 +941,14 @@ __global__ void __launch_bounds__(1024) k_sweep_fwd(KParams p)
             for (int m = 0; m < 4; ++m) {
                 int fi = p.cface[4 * c + m];
                 int nb = p.cnb[4 * c + m];
-                T sg = (T)p.csign[4 * c + m];
-                const double *g = p.fgeo + 7 * fi;
+                const T *g = sl + 16 * c + 4 * m;  // sign*nx, sign*ny, S
                 T2 Fv = F[(size_t)fi * p.Nv + k];
+                T sg = (T)p.csign[4 * c + m];
                 rg -= sg * Fv.x;
                 rh -= sg * Fv.y;
                 if (nb == c) continue;  // a cell wrapped onto itself: no net implicit term
-                T so = sg * xi_dot_n<T>(ux, uy, (T)g[0], (T)g[1]);
-                T aS = so * (T)g[2];
+                T so = xi_dot_n<T>(ux, uy, g[0], g[1]);
+                T aS = so * g[2];
                 if (so > (T)0) D += aS;
                 else if (so < (T)0 && nb >= 0 && nb < c) {
                     int inb = nb % ni, jnb = nb / ni;
@@ -840,6 +985,7 @@ __global__ void __launch_bounds__(1024) k_sweep_bwd(KParams p)
     T2 *f = (T2 *)p.f;
     T2 *ds = (T2 *)p.dst;
     const T *cpT = (const T *)p.cellpT;
+    const T *sl = (const T *)p.cslotT;
     const int nh = ni + nj - 1;
     for (int dpl = nh - 1; dpl >= 0; --dpl) {
         int ilo = max(0, dpl - (nj - 1)), ihi = min(ni - 1, dpl);
@@ -850,13 +996,11 @@ __global__ void __launch_bounds__(1024) k_sweep_bwd(KParams p)
             T ag = 0, ah = 0;
 #pragma unroll
             for (int m = 0; m < 4; ++m) {
-                int fi = p.cface[4 * c + m];
                 int nb = p.cnb[4 * c + m];
                 if (nb == c) continue;
-                T sg = (T)p.csign[4 * c + m];
-                const double *g = p.fgeo + 7 * fi;
-                T so = sg * xi_dot_n<T>(ux, uy, (T)g[0], (T)g[1]);
-                T aS = so * (T)g[2];
+                const T *g = sl + 16 * c + 4 * m;
+                T so = xi_dot_n<T>(ux, uy, g[0], g[1]);
+                T aS = so * g[2];
                 if (so > (T)0) D += aS;
                 else if (so < (T)0 && nb > c) {
                     int inb = nb % ni, jnb = nb / ni;
@@ -916,74 +1060,57 @@ __global__ void k_from_dev(KParams p, double *G, double *H)
     }
 }
 
+// per cell: rho, u, v, T/T_ref from W; heat flux of f from f~ (cellraw)
 template <class T>
-__global__ void __launch_bounds__(256) k_cell_moments(KParams p, double *out6)
+__global__ void __launch_bounds__(256) k_moments_out(KParams p, double *out6)
 {
-    using T2 = typename V2<T>::t;
-    __shared__ double sm[32 * 11];
-    const int c = blockIdx.x;
-    const T2 *f = (const T2 *)p.f + (size_t)c * p.Nv;
-    double r[11];
-    for (int q = 0; q < 11; ++q) r[q] = 0.0;
-    for (int k = threadIdx.x; k < p.Nv; k += blockDim.x) {
-        T2 v = f[k];
-        double ux = p.ux[k], uy = p.uy[k], w = p.w[k];
-        double wg = w * (double)v.x, wh = w * (double)v.y, s2 = ux * ux + uy * uy;
-        r[0] += wg; r[1] += wg * ux; r[2] += wg * uy; r[3] += wg * ux * ux; r[4] += wg * ux * uy;
-        r[5] += wg * uy * uy; r[6] += wg * ux * s2; r[7] += wg * uy * s2;
-        r[8] += wh; r[9] += wh * ux; r[10] += wh * uy;
-    }
-    block_sum<11>(r, sm);
-    if (threadIdx.x == 0) {
-        for (int q = 0; q < 11; ++q) r[q] += p.mref_raw[q];
-        const double *W = p.W + 4 * c;
-        double rho = W[0], U = W[1] / rho, V = W[2] / rho;
-        double RT = (2.0 * W[3] / rho - U * U - V * V) / (p.K + 2);
-        double tau = viscosity(p, RT) / (rho * RT);
-        double U2 = U * U + V * V;
-        double sx = r[6] - 2.0 * U * r[3] - 2.0 * V * r[4] + U2 * r[1] - U * (r[3] + r[5]) +
-                    2.0 * U * U * r[1] + 2.0 * U * V * r[2] - U * U2 * r[0];
-        double sy = r[7] - 2.0 * U * r[4] - 2.0 * V * r[5] + U2 * r[2] - V * (r[3] + r[5]) +
-                    2.0 * U * V * r[1] + 2.0 * V * V * r[2] - V * U2 * r[0];
-        double qtx = 0.5 * (sx + r[9] - U * r[8]), qty = 0.5 * (sy + r[10] - V * r[8]);
-        double Pr = p.shakhov ? p.Pr : 1.0;
-        out6[6 * c + 0] = rho;
-        out6[6 * c + 1] = U;
-        out6[6 * c + 2] = V;
-        out6[6 * c + 3] = RT / p.RT_ref;
-        out6[6 * c + 4] = 2.0 * tau * qtx / (2.0 * tau + p.dt * Pr);
-        out6[6 * c + 5] = 2.0 * tau * qty / (2.0 * tau + p.dt * Pr);
-    }
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= p.N) return;
+    double r[kRaw];
+    for (int q = 0; q < kRaw; ++q) r[q] = acc_load<T>(p.cellraw, (size_t)c * kRaw + q) + p.mref_raw[q];
+    const double *W = p.W + 4 * c;
+    double rho = W[0], U = W[1] / rho, V = W[2] / rho;
+    double RT = (2.0 * W[3] / rho - U * U - V * V) / (p.K + 2);
+    double tau = viscosity(p, RT) / (rho * RT);
+    double qtx, qty;
+    raw_heat_flux(r, U, V, qtx, qty);
+    double Pr = p.shakhov ? p.Pr : 1.0;
+    out6[6 * c + 0] = rho;
+    out6[6 * c + 1] = U;
+    out6[6 * c + 2] = V;
+    out6[6 * c + 3] = RT / p.RT_ref;
+    out6[6 * c + 4] = 2.0 * tau * qtx / (2.0 * tau + p.dt * Pr);
+    out6[6 * c + 5] = 2.0 * tau * qty / (2.0 * tau + p.dt * Pr);
 }
 
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-// events (optional): 7 cudaEvent_t recorded before the first and after each
-// of the six launches, for per-kernel timing
+static inline int nblk(int n, int per) { return (n + per - 1) / per; }
+
+// events (optional): kProfiled+1 cudaEvent_t recorded between the six groups
+// cell prep | faces (moments, params, flux, phi) | macro | fwd | bwd | (spare)
 template <class T>
 static int iteration_t(const KParams &p, cudaStream_t st, void **events)
 {
-    const int *ilist = p.ilist, *blist = p.blist;
-    const int ni_ = p.nilist, nb_ = p.nblist;
     auto mark = [&](int q) {
         if (events) cudaEventRecord((cudaEvent_t)events[q], st);
     };
     mark(0);
-    k_cell_prep<T><<<p.N, 256, 0, st>>>(p);
+    k_cell_moments<T><<<nblk(p.N, 8), 256, 0, st>>>(p);
+    k_cell_params<T><<<nblk(p.N, 256), 256, 0, st>>>(p);
+    k_fbp<T><<<dim3(p.N, nblk(p.Nv, 256)), 256, 0, st>>>(p);
     mark(1);
-    if (ni_) {
-        if (p.limiter) k_face_interior<T, true><<<ni_, 256, 0, st>>>(p, ilist, ni_);
-        else k_face_interior<T, false><<<ni_, 256, 0, st>>>(p, ilist, ni_);
-    }
+    if (p.limiter) k_face_moments<T, true><<<nblk(p.nf, 8), 256, 0, st>>>(p);
+    else k_face_moments<T, false><<<nblk(p.nf, 8), 256, 0, st>>>(p);
+    k_face_params<T><<<nblk(p.nf, 256), 256, 0, st>>>(p);
     mark(2);
-    if (nb_) {
-        if (p.limiter) k_face_boundary<T, true><<<nb_, 256, 0, st>>>(p, blist, nb_);
-        else k_face_boundary<T, false><<<nb_, 256, 0, st>>>(p, blist, nb_);
-    }
+    if (p.limiter) k_face_flux<T, true><<<nblk(p.nf, 8), 256, 0, st>>>(p);
+    else k_face_flux<T, false><<<nblk(p.nf, 8), 256, 0, st>>>(p);
+    k_face_phi<T><<<nblk(p.nf, 256), 256, 0, st>>>(p);
     mark(3);
     {
-        int nb = (p.N + 255) / 256;
+        int nb = nblk(p.N, 256);
         k_macro_pre<T><<<nb, 256, 0, st>>>(p);
         int nthr = std::min(1024, ((std::min(p.ni, p.nj) + 31) / 32) * 32);
         size_t smem = sizeof(T) * 8 * (size_t)p.ni;
@@ -991,12 +1118,12 @@ static int iteration_t(const KParams &p, cudaStream_t st, void **events)
         k_macro_post<T><<<nb, 256, 0, st>>>(p);
     }
     mark(4);
-    int nblk = (p.Nv + p.sweep_tv - 1) / p.sweep_tv;
+    int nb = nblk(p.Nv, p.sweep_tv);
     int nthr = p.sweep_tv * p.sweep_pc;
     size_t ssm = 2 * sizeof(typename V2<T>::t) * (size_t)p.ni * p.sweep_tv;
-    k_sweep_fwd<T><<<nblk, nthr, ssm, st>>>(p);
+    k_sweep_fwd<T><<<nb, nthr, ssm, st>>>(p);
     mark(5);
-    k_sweep_bwd<T><<<nblk, nthr, ssm, st>>>(p);
+    k_sweep_bwd<T><<<nb, nthr, ssm, st>>>(p);
     mark(6);
     return (int)cudaGetLastError();
 }
@@ -1029,8 +1156,21 @@ int launch_iteration(const KParams &p, bool fp64, void *stream, void **events)
 int launch_cell_moments(const KParams &p, bool fp64, double *out6_dev, void *stream)
 {
     cudaStream_t st = (cudaStream_t)stream;
-    if (fp64) k_cell_moments<double><<<p.N, 256, 0, st>>>(p, out6_dev);
-    else k_cell_moments<float><<<p.N, 256, 0, st>>>(p, out6_dev);
+    if (fp64) {
+        k_cell_moments<double><<<nblk(p.N, 8), 256, 0, st>>>(p);
+        k_moments_out<double><<<nblk(p.N, 256), 256, 0, st>>>(p, out6_dev);
+    } else {
+        k_cell_moments<float><<<nblk(p.N, 8), 256, 0, st>>>(p);
+        k_moments_out<float><<<nblk(p.N, 256), 256, 0, st>>>(p, out6_dev);
+    }
+    return (int)cudaGetLastError();
+}
+
+int launch_face_phi(const KParams &p, bool fp64, void *stream)
+{
+    cudaStream_t st = (cudaStream_t)stream;
+    if (fp64) k_face_phi<double><<<nblk(p.nf, 256), 256, 0, st>>>(p);
+    else k_face_phi<float><<<nblk(p.nf, 256), 256, 0, st>>>(p);
     return (int)cudaGetLastError();
 }
 
