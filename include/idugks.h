@@ -154,6 +154,16 @@ idg_status idg_get_face_flux_moments(idg_ctx *ctx, double *phi4, void *stream);
  * predictor, forward sweep, backward sweep (0 for a kernel not launched). */
 idg_status idg_iterate_profiled(idg_ctx *ctx, void *stream, double *kernel_ms);
 
+/* Launch-shape tuning of the wavefront kernels (after idg_bind_workspace;
+ * no effect on results).  IDG_TUNE_SWEEP_TV: discrete velocities per thread
+ * block of the micro LU-SGS sweeps (power of two, 1..32, times min(ni, nj)
+ * at most 1024).  IDG_TUNE_SWEEP_STAGES / IDG_TUNE_MACRO_STAGES: hyperplanes
+ * prefetched ahead by the micro / macroscopic sweeps (4 or 8).  Returns
+ * IDG_ERR_ARG for a value that is invalid or does not fit in shared memory. */
+enum { IDG_TUNE_SWEEP_TV = 1, IDG_TUNE_SWEEP_STAGES = 2, IDG_TUNE_MACRO_STAGES = 3 };
+idg_status idg_set_tuning(idg_ctx *ctx, int key, int value);
+idg_status idg_get_tuning(const idg_ctx *ctx, int key, int *value);
+
 /* Sizes and host-side tables (valid after the corresponding setters). */
 idg_status idg_get_sizes(const idg_ctx *ctx, int *ncell, int *nvel, int *nface);
 idg_status idg_get_dt(const idg_ctx *ctx, double *dt);

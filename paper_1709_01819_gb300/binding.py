@@ -19,6 +19,7 @@ IDG_BC_PERIODIC, IDG_BC_WALL, IDG_BC_FARFIELD = 0, 1, 2
 IDG_NC_TRAP, IDG_NC_SIMPSON, IDG_GAUSS_HERMITE = 0, 1, 2
 IDG_IMIN, IDG_IMAX, IDG_JMIN, IDG_JMAX = 0, 1, 2, 3
 IDG_BGK, IDG_SHAKHOV = 0, 1
+IDG_TUNE_SWEEP_TV, IDG_TUNE_SWEEP_STAGES, IDG_TUNE_MACRO_STAGES = 1, 2, 3
 
 _STATUS = {0: "IDG_OK", 1: "IDG_ERR_ARG", 2: "IDG_ERR_STATE", 3: "IDG_ERR_CUDA", 4: "IDG_ERR_OOM",
            5: "IDG_ERR_NONFINITE", 6: "IDG_ERR_TIMEOUT", 7: "IDG_ERR_NOT_CONVERGED"}
@@ -42,6 +43,8 @@ SIGNATURES = [
     ("idg_get_state", _i, [_vp, _P(_d), _P(_d), _P(_d), _vp]),
     ("idg_iterate", _i, [_vp, _i, _d, _vp, _P(_i), _P(_d)]),
     ("idg_iterate_profiled", _i, [_vp, _vp, _P(_d)]),
+    ("idg_set_tuning", _i, [_vp, _i, _i]),
+    ("idg_get_tuning", _i, [_vp, _i, _P(_i)]),
     ("idg_get_moments", _i, [_vp, _P(_d), _vp]),
     ("idg_get_residual_history", _i, [_vp, _P(_d), _i, _P(_i)]),
     ("idg_get_face_flux_moments", _i, [_vp, _P(_d), _vp]),
@@ -166,6 +169,16 @@ def idg_iterate_profiled(ctx, stream=None):
     ms = np.zeros(6)
     check(ctx, lib().idg_iterate_profiled(ctx, stream, dptr(ms)))
     return ms
+
+
+def idg_set_tuning(ctx, key, value):
+    return check(ctx, lib().idg_set_tuning(ctx, key, value))
+
+
+def idg_get_tuning(ctx, key):
+    v = C.c_int()
+    check(ctx, lib().idg_get_tuning(ctx, key, C.byref(v)))
+    return v.value
 
 
 def idg_get_moments(ctx, N, stream=None):

@@ -418,12 +418,10 @@ size_t layout(idg_ctx *c, char *base, KParams *kp)
     k.phiraw = L.take<char>(32 * nf);
     k.phi = L.take<double>(32 * nf);
     k.rw = L.take<double>(32 * N);
-    k.mbase = L.take<char>(8 * ts * N);
-    k.moff = L.take<char>(16 * ts * N);
-    k.mD = L.take<char>(ts * N);
-    k.mR = L.take<char>(4 * ts * N);
+    k.clink = L.take<int>(48 * N);
+    k.mrec = L.take<char>(44 * ts * N);
     k.mdW = L.take<char>(4 * ts * N);
-    k.mpart = L.take<double>(8 * (N / 256 + 2));
+    k.mpart = L.take<double>(8 * (N / 32 + 2));
     k.res = L.take<double>(8 * (size_t)idg::kMaxHist);
     k.iter = L.take<int>(256);
     k.status = k.iter + 1;
@@ -719,14 +717,33 @@ idg_status idg_bind_workspace(idg_ctx *c, void *dev_ptr, size_t bytes)
     k.dt = c->dt; k.h = 0.5 * c->dt; k.mu_ref = c->mu_ref; k.RT_ref = c->RT_ref; k.omega = c->omega;
     k.Pr = c->Pr; k.gam = (double)(c->K + 4) / (double)(c->K + 2); k.lusgs_omega = c->lusgs_omega;
     // sweep launch shape: cell slots cover the longest hyperplane up to 64
+    // micro sweeps: one thread per cell of the longest hyperplane and tv
+    // velocities per CTA (8 by default, more on very narrow blocks)
     int maxlen = std::min(c->ni, c->nj);
-    k.sweep_pc = std::min(maxlen, 128);
+    if (maxlen > 1024) return fail(c, IDG_ERR_ARG, "min(ni, nj) = %d exceeds 1024", maxlen);
+    k.sweep_pc = maxlen;
     k.sweep_tv = 8;
+    while (k.sweep_tv > 1 && k.sweep_tv * k.sweep_pc > 1024) k.sweep_tv /= 2;
     while (k.sweep_tv < 32 && 2 * k.sweep_tv * k.sweep_pc <= 256) k.sweep_tv *= 2;
+    // deepest prefetch pipeline that fits in shared memory
+    const bool fp64 = c->precision == IDG_FP64;
+    k.macro_stages = 8;
+    if (idg::sweep_smem_need(k, fp64, 0) > 227 * 1024) k.macro_stages = 4;
+    k.sweep_stages = 8;
+    if (idg::sweep_smem_need(k, fp64, 1) > 227 * 1024) k.sweep_stages = 4;
     // uploads
     std::vector<float> uxf(c->ux.begin(), c->ux.end()), uyf(c->uy.begin(), c->uy.end()),
         wf(c->w.begin(), c->w.end());
     std::vector<double> fgeo8((size_t)8 * c->nf, 0.0), cslot((size_t)16 * c->N, 0.0);
+    std::vector<int> clink((size_t)12 * c->N, -1);
+    for (int q = 0; q < c->N; ++q)
+        for (int m = 0; m < 4; ++m) {
+            int nb = c->cnb[4 * q + m];
+            if (nb < 0) continue;
+            clink[12 * q + m] = nb;
+            clink[12 * q + 4 + m] = nb % c->ni;
+            clink[12 * q + 8 + m] = nb % c->ni + nb / c->ni;
+        }
     for (int q = 0; q < c->nf; ++q)
         for (int m = 0; m < 7; ++m) fgeo8[(size_t)8 * q + m] = c->fgeo[(size_t)7 * q + m];
     for (int q = 0; q < c->N; ++q)
@@ -742,7 +759,7 @@ idg_status idg_bind_workspace(idg_ctx *c, void *dev_ptr, size_t bytes)
         up((int *)k.cnb, c->cnb), up((int *)k.csign, c->csign), up_storage(c, k.crT, c->cr),
         up_storage(c, k.clsgT, c->clsg), up_storage(c, k.cslotT, cslot), up((int *)k.fL, c->fL),
         up((int *)k.fR, c->fR), up((double *)k.fgeo, c->fgeo), up_storage(c, k.fgeoT, fgeo8),
-        up((int *)k.fbc, c->fbc), up((int *)k.fside, c->fside),
+        up((int *)k.fbc, c->fbc), up((int *)k.fside, c->fside), up((int *)k.clink, clink),
         up((double *)k.ux, c->ux), up((double *)k.uy, c->uy), up((double *)k.w, c->w),
         up((float *)k.uxf, uxf), up((float *)k.uyf, uyf), up((float *)k.wf, wf),
         cudaMemset(k.iter, 0, 256), cudaMemset(k.phi, 0, 32 * (size_t)c->nf)};
@@ -910,6 +927,41 @@ idg_status idg_iterate_profiled(idg_ctx *c, void *stream, double *kernel_ms)
     if (e != cudaSuccess) return cuda_fail(c, e, "profiled iteration");
     c->host_iter += 1;
     c->hist.push_back(r);
+    return IDG_OK;
+}
+
+idg_status idg_set_tuning(idg_ctx *c, int key, int value)
+{
+    idg_status s = check_ready(c);
+    if (s) return s;
+    KParams k = c->kp;
+    if (key == IDG_TUNE_SWEEP_TV) {
+        if (value < 1 || value > 32 || (value & (value - 1)) || value * k.sweep_pc > 1024)
+            return fail(c, IDG_ERR_ARG, "sweep velocities per block %d invalid for %d cell slots", value, k.sweep_pc);
+        k.sweep_tv = value;
+    } else if (key == IDG_TUNE_SWEEP_STAGES) {
+        if (value != 4 && value != 8) return fail(c, IDG_ERR_ARG, "sweep stages must be 4 or 8");
+        k.sweep_stages = value;
+    } else if (key == IDG_TUNE_MACRO_STAGES) {
+        if (value != 4 && value != 8) return fail(c, IDG_ERR_ARG, "macro stages must be 4 or 8");
+        k.macro_stages = value;
+    } else {
+        return fail(c, IDG_ERR_ARG, "unknown tuning key %d", key);
+    }
+    int rc = idg::configure_kernels(k, c->precision == IDG_FP64);
+    if (rc) return fail(c, IDG_ERR_ARG, "launch shape does not fit in shared memory");
+    c->kp = k;
+    return IDG_OK;
+}
+
+idg_status idg_get_tuning(const idg_ctx *c, int key, int *value)
+{
+    if (!c || !value) return IDG_ERR_ARG;
+    if (!c->bound) return IDG_ERR_STATE;
+    if (key == IDG_TUNE_SWEEP_TV) *value = c->kp.sweep_tv;
+    else if (key == IDG_TUNE_SWEEP_STAGES) *value = c->kp.sweep_stages;
+    else if (key == IDG_TUNE_MACRO_STAGES) *value = c->kp.macro_stages;
+    else return IDG_ERR_ARG;
     return IDG_OK;
 }
 

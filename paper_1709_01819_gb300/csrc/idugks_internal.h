@@ -66,22 +66,23 @@ struct KParams {
     void *phiraw;   // [nf][4] acc moments of the deviation flux
     double *phi;    // [nf][4]
     double *rw;     // [N][4]
+    const int *clink;  // [N][12] per slot: neighbour, its i, its hyperplane i+j (-1 ghost)
     // macroscopic LU-SGS work (T = storage precision of the sweep)
-    void *mbase;    // [N][8] T: rho, m_x, m_y, E, u, v, p, E+p of W^n
-    void *moff;     // [N][4][4] T: (S/2) n_out, (omega/2) Lambda, 0 per slot
-    void *mD;       // [N] T diagonal
-    void *mR;       // [N][4] T residual
+    void *mrec;     // [N][44] T: R, D, per slot (S/2) n_out, (omega/2) Lambda, neighbour base state
     void *mdW;      // [N][4] T increments (Delta W* then Delta W)
     double *mpart;  // [ceil(N/256)] block partial sums of ||R/Omega||^2
     double *res;    // [kMaxHist] absolute residual per iteration
     int *iter;      // [1] device iteration counter
     int *status;    // [1] device status word
-    // launch shape of the sweeps
-    int sweep_tv, sweep_pc;
+    // launch shape of the wavefront kernels: velocities per CTA and cell
+    // slots of the micro sweeps, prefetch depths (hyperplanes; 4 or 8)
+    int sweep_tv, sweep_pc, sweep_stages, macro_stages;
 };
 
 // kernel launchers (idugks_kernels.cu)
 int configure_kernels(const KParams &p, bool fp64);
+// shared memory of the macro sweep (which = 0) or of the backward micro sweep (1)
+size_t sweep_smem_need(const KParams &p, bool fp64, int which);
 constexpr int kProfiled = 6;  // timed groups in launch_iteration(events)
 int launch_iteration(const KParams &p, bool fp64, void *stream, void **events = nullptr);
 int launch_cell_moments(const KParams &p, bool fp64, double *out6_dev, void *stream);

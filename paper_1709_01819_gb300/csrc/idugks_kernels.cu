@@ -286,6 +286,37 @@ __device__ __forceinline__ void raw_terms(T (&a)[kRaw], T w, T ux, T uy, T g, T 
     a[8] += wh; a[9] += wh * ux; a[10] += wh * uy;
 }
 
+// Warp loop over the discrete velocities: lane l takes k = k0 + 32u + l,
+// u < 8, for chunks of 256 velocities; each chunk's per-lane partial sums
+// (at most 8 terms, storage precision) are folded into the accumulators.
+// Full chunks run unchecked and unrolled so several velocities' loads are in
+// flight; the ragged last chunk is bounds-checked.
+template <int NA, class T, class Body>
+__device__ __forceinline__ void vel_loop(int Nv, int lane, Acc<T> (&acc)[NA], Body body)
+{
+    int k0 = 0;
+    for (; k0 + 256 <= Nv; k0 += 256) {
+        T a[NA];
+#pragma unroll
+        for (int q = 0; q < NA; ++q) a[q] = (T)0;
+#pragma unroll 4
+        for (int u = 0; u < 8; ++u) body(k0 + 32 * u + lane, a);
+#pragma unroll
+        for (int q = 0; q < NA; ++q) acc[q].add(a[q]);
+    }
+    if (k0 < Nv) {
+        T a[NA];
+#pragma unroll
+        for (int q = 0; q < NA; ++q) a[q] = (T)0;
+        for (int u = 0; u < 8; ++u) {
+            int k = k0 + 32 * u + lane;
+            if (k < Nv) body(k, a);
+        }
+#pragma unroll
+        for (int q = 0; q < NA; ++q) acc[q].add(a[q]);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // cell moments and cell prep (Eq. 10, 12)                                [a1]
 // ---------------------------------------------------------------------------
@@ -300,21 +331,10 @@ __global__ void __launch_bounds__(256) k_cell_moments(KParams p)
     Acc<T> acc[kRaw];
 #pragma unroll
     for (int q = 0; q < kRaw; ++q) acc[q].zero();
-    for (int k0 = 0; k0 < p.Nv; k0 += 256) {
-        T a[kRaw];
-#pragma unroll
-        for (int q = 0; q < kRaw; ++q) a[q] = 0;
-#pragma unroll 4
-        for (int u = 0; u < 8; ++u) {
-            int k = k0 + 32 * u + lane;
-            if (k < p.Nv) {
-                T2 v = f[k];
-                raw_terms<T>(a, vw<T>(p, k), vx<T>(p, k), vy<T>(p, k), v.x, v.y);
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < kRaw; ++q) acc[q].add(a[q]);
-    }
+    vel_loop<kRaw, T>(p.Nv, lane, acc, [&](int k, T(&a)[kRaw]) {
+        T2 v = f[k];
+        raw_terms<T>(a, vw<T>(p, k), vx<T>(p, k), vy<T>(p, k), v.x, v.y);
+    });
 #pragma unroll
     for (int q = 0; q < kRaw; ++q) acc[q].warp_sum();
     if (lane == 0)
@@ -325,7 +345,7 @@ __global__ void __launch_bounds__(256) k_cell_moments(KParams p)
 // per cell: heat flux of f from f~ (about U of W), tau, equilibrium at W^n,
 // and the two coefficients of fb+ = (2tau-h)/(2tau+dt) f~ + 3h/(2tau+dt) f^S
 template <class T>
-__global__ void __launch_bounds__(256) k_cell_params(KParams p)
+__global__ void __launch_bounds__(32) k_cell_params(KParams p)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= p.N) return;
@@ -451,34 +471,19 @@ __device__ __forceinline__ typename V2<T>::t reconstruct(const KParams &p, const
     return o;
 }
 
-template <class T>
-__device__ __forceinline__ void select_side(bool left, const SideRec<T> &L, const SideRec<T> &R,
-                                            SideRec<T> &o)
-{
-    o.c = left ? L.c : R.c;
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-        o.nb[m] = left ? L.nb[m] : R.nb[m];
-        o.gx[m] = left ? L.gx[m] : R.gx[m];
-        o.gy[m] = left ? L.gy[m] : R.gy[m];
-        o.frx[m] = left ? L.frx[m] : R.frx[m];
-        o.fry[m] = left ? L.fry[m] : R.fry[m];
-    }
-    o.rx = left ? L.rx : R.rx;
-    o.ry = left ? L.ry : R.ry;
-}
-
-// Everything a warp needs about one face.
+// The two side records live in shared memory (one pair per warp) so the
+// per-lane choice of the upwind side is an indexed shared-memory read.
 template <class T> struct FaceCtx {
     int kind;          // -1 interior, 1 wall, 2 far field
     int side;
     T nx, ny, S, on;   // normal L->R, length; boundary: +1 if the interior cell is L
-    SideRec<T> L, R;   // boundary faces use L for the interior cell
+    const SideRec<T> *rec;  // [2]: L, R (boundary faces: [0] is the interior cell)
 };
 
 template <class T>
-__device__ __forceinline__ void load_face(const KParams &p, int f, FaceCtx<T> &fc)
+__device__ __forceinline__ void load_face(const KParams &p, int f, SideRec<T> *srec, FaceCtx<T> &fc)
 {
+    const int lane = threadIdx.x & 31;
     const T *g = (const T *)p.fgeoT + 8 * f;
     fc.nx = g[0];
     fc.ny = g[1];
@@ -486,17 +491,15 @@ __device__ __forceinline__ void load_face(const KParams &p, int f, FaceCtx<T> &f
     fc.kind = p.fbc[f];
     fc.side = p.fside[f];
     const int L = p.fL[f], R = p.fR[f];
-    if (fc.kind < 0) {
-        load_side<T>(p, L, g[3], g[4], fc.L);
-        load_side<T>(p, R, g[5], g[6], fc.R);
-        fc.on = (T)1;
-    } else if (L >= 0) {
-        load_side<T>(p, L, g[3], g[4], fc.L);
-        fc.on = (T)1;
-    } else {
-        load_side<T>(p, R, g[5], g[6], fc.L);
-        fc.on = (T)-1;
+    fc.on = (fc.kind < 0 || L >= 0) ? (T)1 : (T)-1;
+    if (lane == 0) {
+        if (L >= 0) load_side<T>(p, L, g[3], g[4], srec[0]);
+        else load_side<T>(p, R, g[5], g[6], srec[0]);
+    } else if (lane == 1 && fc.kind < 0) {
+        load_side<T>(p, R, g[5], g[6], srec[1]);
     }
+    __syncwarp();
+    fc.rec = srec;
 }
 
 // fb - M_ref at velocity k.  Interior: upwind side by sign(xi.n), average at
@@ -509,11 +512,9 @@ __device__ __forceinline__ typename V2<T>::t face_fbar(const KParams &p, const F
     using T2 = typename V2<T>::t;
     const T h = (T)p.h;
     if (fc.kind < 0) {
-        SideRec<T> r;
-        select_side<T>(s > (T)0, fc.L, fc.R, r);
-        T2 fb = reconstruct<T, LIM>(p, r, k, ux, uy, h);
+        T2 fb = reconstruct<T, LIM>(p, fc.rec[s > (T)0 ? 0 : 1], k, ux, uy, h);
         if (s == (T)0) {
-            T2 o = reconstruct<T, LIM>(p, fc.L, k, ux, uy, h);
+            T2 o = reconstruct<T, LIM>(p, fc.rec[0], k, ux, uy, h);
             fb.x = (T)0.5 * (o.x + fb.x);
             fb.y = (T)0.5 * (o.y + fb.y);
         }
@@ -529,7 +530,7 @@ __device__ __forceinline__ typename V2<T>::t face_fbar(const KParams &p, const F
         in.y = rhow * bH[k] + rwm1 * (T)(p.K * p.RT_r) * gref;
         if (so < (T)0) return in;
     }
-    T2 fb = reconstruct<T, LIM>(p, fc.L, k, ux, uy, h);
+    T2 fb = reconstruct<T, LIM>(p, fc.rec[0], k, ux, uy, h);
     if (so == (T)0) {
         fb.x = (T)0.5 * (fb.x + in.x);
         fb.y = (T)0.5 * (fb.y + in.y);
@@ -542,33 +543,29 @@ template <class T, bool LIM>
 __global__ void __launch_bounds__(256) k_face_moments(KParams p)
 {
     using T2 = typename V2<T>::t;
-    const int lane = threadIdx.x & 31;
-    const int f = blockIdx.x * 8 + (threadIdx.x >> 5);
+    __shared__ SideRec<T> srec[8][2];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int f = blockIdx.x * 8 + wid;
     if (f >= p.nf) return;  // whole warp
     FaceCtx<T> fc;
-    load_face<T>(p, f, fc);
+    load_face<T>(p, f, srec[wid], fc);
+    const T h = (T)p.h;
     T rhow = (T)1, rwm1 = (T)0;
     double rw = 1.0;
-    Acc<T> outsum;
-    outsum.zero();
+    Acc<T> outsum[1];
+    outsum[0].zero();
     if (fc.kind == 1) {
         // zero net mass flux: rho_w sum_in w |xi.n| G_w = sum_out w (xi.n) fb
-        for (int k0 = 0; k0 < p.Nv; k0 += 256) {
-            T a = 0;
-            for (int u = 0; u < 8; ++u) {
-                int k = k0 + 32 * u + lane;
-                if (k >= p.Nv) break;
-                T ux = vx<T>(p, k), uy = vy<T>(p, k);
-                T so = fc.on * xi_dot_n<T>(ux, uy, fc.nx, fc.ny);
-                if (so > (T)0) {
-                    T2 fb = reconstruct<T, LIM>(p, fc.L, k, ux, uy, (T)p.h);
-                    a += vw<T>(p, k) * so * fb.x;
-                }
+        vel_loop<1, T>(p.Nv, lane, outsum, [&](int k, T(&a)[1]) {
+            T ux = vx<T>(p, k), uy = vy<T>(p, k);
+            T so = fc.on * xi_dot_n<T>(ux, uy, fc.nx, fc.ny);
+            if (so > (T)0) {
+                T2 fb = reconstruct<T, LIM>(p, fc.rec[0], k, ux, uy, h);
+                a[0] += vw<T>(p, k) * so * fb.x;
             }
-            outsum.add(a);
-        }
-        outsum.warp_sum();
-        double o = __shfl_sync(0xffffffffu, outsum.value(), 0);
+        });
+        outsum[0].warp_sum();
+        double o = __shfl_sync(0xffffffffu, outsum[0].value(), 0);
         const double *bc = p.bconst + 2 * f;
         rw = (bc[0] + o) / bc[1];
         rhow = (T)rw;
@@ -577,27 +574,18 @@ __global__ void __launch_bounds__(256) k_face_moments(KParams p)
     Acc<T> acc[kRaw];
 #pragma unroll
     for (int q = 0; q < kRaw; ++q) acc[q].zero();
-    for (int k0 = 0; k0 < p.Nv; k0 += 256) {
-        T a[kRaw];
-#pragma unroll
-        for (int q = 0; q < kRaw; ++q) a[q] = 0;
-        for (int u = 0; u < 8; ++u) {
-            int k = k0 + 32 * u + lane;
-            if (k >= p.Nv) break;
-            T ux = vx<T>(p, k), uy = vy<T>(p, k);
-            T s = xi_dot_n<T>(ux, uy, fc.nx, fc.ny);
-            T2 fb = face_fbar<T, LIM>(p, fc, k, ux, uy, s, rhow, rwm1);
-            raw_terms<T>(a, vw<T>(p, k), ux, uy, fb.x, fb.y);
-        }
-#pragma unroll
-        for (int q = 0; q < kRaw; ++q) acc[q].add(a[q]);
-    }
+    vel_loop<kRaw, T>(p.Nv, lane, acc, [&](int k, T(&a)[kRaw]) {
+        T ux = vx<T>(p, k), uy = vy<T>(p, k);
+        T s = xi_dot_n<T>(ux, uy, fc.nx, fc.ny);
+        T2 fb = face_fbar<T, LIM>(p, fc, k, ux, uy, s, rhow, rwm1);
+        raw_terms<T>(a, vw<T>(p, k), ux, uy, fb.x, fb.y);
+    });
 #pragma unroll
     for (int q = 0; q < kRaw; ++q) acc[q].warp_sum();
     if (lane == 0) {
 #pragma unroll
         for (int q = 0; q < kRaw; ++q) acc[q].store(p.faceraw, (size_t)f * 12 + q);
-        outsum.store(p.faceraw, (size_t)f * 12 + 11);
+        outsum[0].store(p.faceraw, (size_t)f * 12 + 11);
         p.facerw[f] = rw;
     }
 }
@@ -605,7 +593,7 @@ __global__ void __launch_bounds__(256) k_face_moments(KParams p)
 // per face: state from the moments of fb, tau, q = 2 tau qbar/(2 tau + h Pr),
 // equilibrium, and the weights a, b of f = a fb + b f^S (Eq. 18)
 template <class T>
-__global__ void __launch_bounds__(256) k_face_params(KParams p)
+__global__ void __launch_bounds__(32) k_face_params(KParams p)
 {
     const int f = blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= p.nf) return;
@@ -628,11 +616,12 @@ template <class T, bool LIM>
 __global__ void __launch_bounds__(256) k_face_flux(KParams p)
 {
     using T2 = typename V2<T>::t;
-    const int lane = threadIdx.x & 31;
-    const int f = blockIdx.x * 8 + (threadIdx.x >> 5);
+    __shared__ SideRec<T> srec[8][2];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int f = blockIdx.x * 8 + wid;
     if (f >= p.nf) return;  // whole warp
     FaceCtx<T> fc;
-    load_face<T>(p, f, fc);
+    load_face<T>(p, f, srec[wid], fc);
     double rw = p.facerw[f];
     T rhow = (T)rw, rwm1 = (T)(rw - 1.0);
     if (fc.kind == 1) {
@@ -647,30 +636,23 @@ __global__ void __launch_bounds__(256) k_face_flux(KParams p)
     Acc<T> acc[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) acc[q].zero();
-    for (int k0 = 0; k0 < p.Nv; k0 += 256) {
-        T a[4] = {0, 0, 0, 0};
-        for (int u = 0; u < 8; ++u) {
-            int k = k0 + 32 * u + lane;
-            if (k >= p.Nv) break;
-            T ux = vx<T>(p, k), uy = vy<T>(p, k);
-            T s = xi_dot_n<T>(ux, uy, fc.nx, fc.ny);
-            T2 fb = face_fbar<T, LIM>(p, fc, k, ux, uy, s, rhow, rwm1);
-            T dG, dH;
-            dev_equilibrium<T>(e, ux, uy, vgref<T>(p, k), kRTr, dG, dH);
-            T sS = s * fc.S;
-            T2 Fk;
-            Fk.x = sS * (wa * fb.x + wb * dG);
-            Fk.y = sS * (wa * fb.y + wb * dH);
-            Fo[k] = Fk;
-            T w = vw<T>(p, k), wg = w * Fk.x;
-            a[0] += wg;
-            a[1] += wg * ux;
-            a[2] += wg * uy;
-            a[3] += (T)0.5 * w * ((ux * ux + uy * uy) * Fk.x + Fk.y);
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) acc[q].add(a[q]);
-    }
+    vel_loop<4, T>(p.Nv, lane, acc, [&](int k, T(&a)[4]) {
+        T ux = vx<T>(p, k), uy = vy<T>(p, k);
+        T s = xi_dot_n<T>(ux, uy, fc.nx, fc.ny);
+        T2 fb = face_fbar<T, LIM>(p, fc, k, ux, uy, s, rhow, rwm1);
+        T dG, dH;
+        dev_equilibrium<T>(e, ux, uy, vgref<T>(p, k), kRTr, dG, dH);
+        T sS = s * fc.S;
+        T2 Fk;
+        Fk.x = sS * (wa * fb.x + wb * dG);
+        Fk.y = sS * (wa * fb.y + wb * dH);
+        Fo[k] = Fk;
+        T w = vw<T>(p, k), wg = w * Fk.x;
+        a[0] += wg;
+        a[1] += wg * ux;
+        a[2] += wg * uy;
+        a[3] += (T)0.5 * w * ((ux * ux + uy * uy) * Fk.x + Fk.y);
+    });
 #pragma unroll
     for (int q = 0; q < 4; ++q) acc[q].warp_sum();
     if (lane == 0)
@@ -729,46 +711,77 @@ __device__ __forceinline__ double face_lambda(const KParams &p, int fi)
     return (fabs(u * g[0] + v * g[1]) + cs) * g[2];
 }
 
+// cp.async helpers: asynchronous global -> shared copies used to prefetch
+// the next hyperplanes of a wavefront while the current one is computed
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void cp_async16(void *s, const void *g)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(s)), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *s, const void *g)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_addr(s)), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *s, const void *g)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_addr(s)), "l"(g) : "memory");
+}
+template <int B> __device__ __forceinline__ void cp_async_b(void *s, const void *g);
+template <> __device__ __forceinline__ void cp_async_b<4>(void *s, const void *g) { cp_async4(s, g); }
+template <> __device__ __forceinline__ void cp_async_b<8>(void *s, const void *g) { cp_async8(s, g); }
+template <> __device__ __forceinline__ void cp_async_b<16>(void *s, const void *g) { cp_async16(s, g); }
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+constexpr int kMRec = 44;    // macro sweep record: R[4], D, pad[3], 4 x (off[3], base[6])
+
+// per cell: R_W, ||R_W/Omega||^2 partials, and the packed record of the
+// macroscopic sweep (diagonal, neighbour coefficients, neighbour base state)
 template <class T>
-__global__ void __launch_bounds__(256) k_macro_pre(KParams p)
+__global__ void __launch_bounds__(32) k_macro_pre(KParams p)
 {
     __shared__ double sm[32];
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     double part[1] = {0.0};
     if (c < p.N) {
+        T *rec = (T *)p.mrec + (size_t)kMRec * c;
         double acc[4] = {0, 0, 0, 0};
         for (int m = 0; m < 4; ++m) {
             double s = p.csign[4 * c + m];
             const double *ph = p.phi + 4 * p.cface[4 * c + m];
             for (int q = 0; q < 4; ++q) acc[q] -= s * ph[q];
         }
-        T *R = (T *)p.mR + 4 * c;
         for (int q = 0; q < 4; ++q) {
             p.rw[4 * c + q] = acc[q];
-            R[q] = (T)acc[q];
+            rec[q] = (T)acc[q];
             double rr = acc[q] / p.area[c];
             part[0] += rr * rr;
         }
-        const double *W = p.W + 4 * c;
-        double rho = W[0], u = W[1] / rho, v = W[2] / rho;
-        double pr = (p.gam - 1.0) * (W[3] - 0.5 * rho * (u * u + v * v));
-        T *b = (T *)p.mbase + 8 * c;
-        b[0] = (T)rho; b[1] = (T)W[1]; b[2] = (T)W[2]; b[3] = (T)W[3];
-        b[4] = (T)u; b[5] = (T)v; b[6] = (T)pr; b[7] = (T)(W[3] + pr);
         double d = p.area[c] / p.dtimp[c];
-        T *o = (T *)p.moff + 16 * c;
         for (int m = 0; m < 4; ++m) {
             int fi = p.cface[4 * c + m];
             double lam = face_lambda(p, fi);
             if (p.fL[fi] != p.fR[fi]) d += 0.5 * p.lusgs_omega * lam;
             double s = p.csign[4 * c + m];
             const double *g = p.fgeo + 7 * fi;
-            o[4 * m + 0] = (T)(0.5 * g[2] * s * g[0]);
-            o[4 * m + 1] = (T)(0.5 * g[2] * s * g[1]);
-            o[4 * m + 2] = (T)(0.5 * p.lusgs_omega * lam);
-            o[4 * m + 3] = (T)0;
+            T *o = rec + 8 + 9 * m;
+            o[0] = (T)(0.5 * g[2] * s * g[0]);
+            o[1] = (T)(0.5 * g[2] * s * g[1]);
+            o[2] = (T)(0.5 * p.lusgs_omega * lam);
+            int nb = p.cnb[4 * c + m];
+            if (nb >= 0) {
+                const double *W = p.W + 4 * nb;
+                double rho = W[0], u = W[1] / rho, v = W[2] / rho;
+                double pr = (p.gam - 1.0) * (W[3] - 0.5 * rho * (u * u + v * v));
+                o[3] = (T)rho; o[4] = (T)W[1]; o[5] = (T)W[2];
+                o[6] = (T)u; o[7] = (T)v; o[8] = (T)(W[3] + pr);
+            } else {
+                for (int q = 3; q < 9; ++q) o[q] = (T)0;
+            }
         }
-        ((T *)p.mD)[c] = (T)d;
+        rec[4] = (T)d;
+        rec[5] = (T)(1.0 / d);
+        rec[6] = rec[7] = (T)0;
     }
     block_sum<1>(part, sm);
     if (threadIdx.x == 0) p.mpart[blockIdx.x] = part[0];
@@ -776,13 +789,13 @@ __global__ void __launch_bounds__(256) k_macro_pre(KParams p)
 
 // Exact increment F_n(W + dW) - F_n(W) of the Euler flux, written so that no
 // two O(1) quantities are subtracted (every term is an increment times a
-// base quantity); n is pre-scaled by S/2.
+// base quantity); n is pre-scaled by S/2.  b = rho, m_x, m_y, u, v, E+p.
 template <class T>
 __device__ __forceinline__ void euler_dflux(T gm1, const T *b, const T *dW, T nx, T ny, T *dF)
 {
-    T rho = b[0], mx = b[1], my = b[2], u = b[4], v = b[5], H = b[7];
-    T r1 = rho + dW[0];
-    T du = (dW[1] - u * dW[0]) / r1, dv = (dW[2] - v * dW[0]) / r1;
+    T rho = b[0], mx = b[1], my = b[2], u = b[3], v = b[4], H = b[5];
+    T ir1 = (T)1 / (rho + dW[0]);
+    T du = (dW[1] - u * dW[0]) * ir1, dv = (dW[2] - v * dW[0]) * ir1;
     T vn = u * nx + v * ny, dvn = du * nx + dv * ny, vn1 = vn + dvn;
     T dmu = dW[1] * (u + du) + dW[2] * (v + dv) + mx * du + my * dv;
     T dp = gm1 * (dW[3] - (T)0.5 * dmu);
@@ -792,16 +805,53 @@ __device__ __forceinline__ void euler_dflux(T gm1, const T *b, const T *dW, T nx
     dF[3] = (dW[3] + dp) * vn1 + H * dvn;
 }
 
+// one hyperplane step of the macroscopic sweep for the cell whose record
+// and links sit in shared memory (dir = +1 forward, -1 backward)
 template <class T>
+__device__ __forceinline__ void macro_cell(const KParams &p, int d, int i, int c, const T *rec,
+                                           const int *lk, const T *dWs, T *ring, T *dWg, int dir, T gm1)
+{
+    const int ni = p.ni;
+    T acc[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        int nb = lk[m];
+        if (nb < 0 || (dir > 0 ? nb >= c : nb <= c)) continue;
+        int nbi = lk[4 + m], nbd = lk[8 + m];
+        const T *dWn = (nbd == d - dir) ? ring + 4 * (((d - dir) & 1) * ni + nbi) : dWg + 4 * nb;
+        T dn[4] = {dWn[0], dWn[1], dWn[2], dWn[3]};
+        const T *o = rec + 8 + 9 * m;
+        T dF[4];
+        euler_dflux<T>(gm1, o + 3, dn, o[0], o[1], dF);
+        for (int q = 0; q < 4; ++q) acc[q] += dF[q] - o[2] * dn[q];
+    }
+    // forward: dW*_c = (R_c - sum_lower) / D_c;  backward: dW_c = dW*_c - sum_upper / D_c
+    const T iD = rec[5];
+    T *rs = ring + 4 * ((d & 1) * ni + i);
+    for (int q = 0; q < 4; ++q) {
+        T x = dir > 0 ? (rec[q] - acc[q]) * iD : dWs[q] - acc[q] * iD;
+        rs[q] = x;
+        dWg[4 * c + q] = x;
+    }
+}
+
+// One CTA: forward then backward sweep over the i+j hyperplanes (the
+// lexicographic dependency order).  Thread s owns cell (ilo + s) of each
+// hyperplane; its record and links are prefetched kStages-1 hyperplanes ahead
+// with cp.async; the previous hyperplane's increments sit in a ring.
+template <class T, int kStages>
 __global__ void __launch_bounds__(1024) k_macro_sweep(KParams p)
 {
-    extern __shared__ unsigned char smraw[];
-    T *ring = (T *)smraw;  // [2][ni][4]: increments of the previous hyperplane
+    extern __shared__ __align__(16) unsigned char smraw[];
     const int tid = threadIdx.x, nt = blockDim.x;
-    const int ni = p.ni, nj = p.nj;
+    const int ni = p.ni, nj = p.nj, nh = ni + nj - 1;
+    T *srec = (T *)smraw;                                   // [kStages][nt][kMRec]
+    int *slnk = (int *)(srec + (size_t)kStages * nt * kMRec);  // [kStages][nt][12]
+    T *sdw = (T *)(slnk + (size_t)kStages * nt * 12);        // [kStages][nt][4] own dW* (backward)
+    T *ring = sdw + (size_t)kStages * nt * 4;                // [2][ni][4]
     if (tid == 0) {
         double s = 0.0;
-        int nb = (p.N + 255) / 256;
+        int nb = (p.N + 31) / 32;
         for (int q = 0; q < nb; ++q) s += p.mpart[q];
         int it = *p.iter;
         double r = sqrt(s);
@@ -809,70 +859,55 @@ __global__ void __launch_bounds__(1024) k_macro_sweep(KParams p)
         if (!isfinite(r)) *p.status = 5;
     }
     const T gm1 = (T)(p.gam - 1.0);
-    const T *base = (const T *)p.mbase;
-    const T *off = (const T *)p.moff;
     T *dWg = (T *)p.mdW;
-    const int nh = ni + nj - 1;
-    // forward: dW*_c = (R_c - sum_lower [dF - wL dW*_nb]) / D_c
-    for (int d = 0; d < nh; ++d) {
-        int ilo = max(0, d - (nj - 1)), ihi = min(ni - 1, d);
-        for (int i = ilo + tid; i <= ihi; i += nt) {
-            int c = (d - i) * ni + i;
-            T acc[4];
-            for (int q = 0; q < 4; ++q) acc[q] = ((const T *)p.mR)[4 * c + q];
-            for (int m = 0; m < 4; ++m) {
-                int nb = p.cnb[4 * c + m];
-                if (nb < 0 || nb >= c) continue;
-                int inb = nb % ni, jnb = nb / ni;
-                const T *dWn = (inb + jnb == d - 1) ? ring + 4 * (((d - 1) & 1) * ni + inb) : dWg + 4 * nb;
-                T dn[4] = {dWn[0], dWn[1], dWn[2], dWn[3]};
-                const T *o = off + 16 * c + 4 * m;
-                T dF[4];
-                euler_dflux<T>(gm1, base + 8 * nb, dn, o[0], o[1], dF);
-                for (int q = 0; q < 4; ++q) acc[q] -= dF[q] - o[2] * dn[q];
+    constexpr int RB = kMRec * sizeof(T);  // bytes of one record (multiple of 16)
+    for (int dir = 1; dir >= -1; dir -= 2) {
+        auto step_d = [&](int s) { return dir > 0 ? s : nh - 1 - s; };
+        auto issue = [&](int s) {
+            if (s < nh) {
+                int d = step_d(s);
+                int ilo = max(0, d - (nj - 1)), ihi = min(ni - 1, d);
+                int i = ilo + tid;
+                if (i <= ihi) {
+                    int c = (d - i) * ni + i;
+                    int st = s & (kStages - 1);
+                    const char *gr = (const char *)((const T *)p.mrec + (size_t)kMRec * c);
+                    char *sr = (char *)(srec + ((size_t)st * nt + tid) * kMRec);
+                    for (int b = 0; b < RB; b += 16) cp_async16(sr + b, gr + b);
+                    const char *gl = (const char *)(p.clink + 12 * c);
+                    char *sl = (char *)(slnk + ((size_t)st * nt + tid) * 12);
+                    for (int b = 0; b < 48; b += 16) cp_async16(sl + b, gl + b);
+                    if (dir < 0) {
+                        const char *gd = (const char *)(dWg + 4 * (size_t)c);
+                        char *sd = (char *)(sdw + ((size_t)st * nt + tid) * 4);
+                        for (int b = 0; b < 4 * (int)sizeof(T); b += 16) cp_async16(sd + b, gd + b);
+                    }
+                }
             }
-            T Dc = ((const T *)p.mD)[c];
-            T *rs = ring + 4 * ((d & 1) * ni + i);
-            for (int q = 0; q < 4; ++q) {
-                T x = acc[q] / Dc;
-                rs[q] = x;
-                dWg[4 * c + q] = x;
-            }
-        }
-        __syncthreads();
-    }
-    // backward: dW_c = dW*_c - sum_upper [dF - wL dW_nb] / D_c
-    for (int d = nh - 1; d >= 0; --d) {
-        int ilo = max(0, d - (nj - 1)), ihi = min(ni - 1, d);
-        for (int i = ilo + tid; i <= ihi; i += nt) {
-            int c = (d - i) * ni + i;
-            T acc[4] = {0, 0, 0, 0};
-            for (int m = 0; m < 4; ++m) {
-                int nb = p.cnb[4 * c + m];
-                if (nb < 0 || nb <= c) continue;
-                int inb = nb % ni, jnb = nb / ni;
-                const T *dWn = (inb + jnb == d + 1) ? ring + 4 * (((d + 1) & 1) * ni + inb) : dWg + 4 * nb;
-                T dn[4] = {dWn[0], dWn[1], dWn[2], dWn[3]};
-                const T *o = off + 16 * c + 4 * m;
-                T dF[4];
-                euler_dflux<T>(gm1, base + 8 * nb, dn, o[0], o[1], dF);
-                for (int q = 0; q < 4; ++q) acc[q] += dF[q] - o[2] * dn[q];
-            }
-            T Dc = ((const T *)p.mD)[c];
-            T *rs = ring + 4 * ((d & 1) * ni + i);
-            for (int q = 0; q < 4; ++q) {
-                T x = dWg[4 * c + q] - acc[q] / Dc;
-                rs[q] = x;
-                dWg[4 * c + q] = x;
+            cp_commit();
+        };
+        for (int s = 0; s < kStages - 1; ++s) issue(s);
+        for (int s = 0; s < nh; ++s) {
+            cp_wait<kStages - 2>();
+            __syncthreads();
+            issue(s + kStages - 1);
+            int d = step_d(s);
+            int ilo = max(0, d - (nj - 1)), ihi = min(ni - 1, d);
+            int i = ilo + tid;
+            if (i <= ihi) {
+                size_t e = (size_t)(s & (kStages - 1)) * nt + tid;
+                macro_cell<T>(p, d, i, (d - i) * ni + i, srec + e * kMRec, slnk + e * 12, sdw + e * 4,
+                              ring, dWg, dir, gm1);
             }
         }
+        cp_wait<0>();
         __syncthreads();
     }
     if (tid == 0) *p.iter += 1;
 }
 
 template <class T>
-__global__ void __launch_bounds__(256) k_macro_post(KParams p)
+__global__ void __launch_bounds__(32) k_macro_post(KParams p)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= p.N) return;
@@ -893,137 +928,177 @@ __global__ void __launch_bounds__(256) k_macro_post(KParams p)
 }
 
 // ---------------------------------------------------------------------------
-// micro LU-SGS sweeps (Eq. 22-26) on i+j hyperplanes                  [a6-a7]
-// one CTA per tile of sweep_tv velocities; sweep_pc cell slots per CTA
+// micro LU-SGS (Eq. 22-26)                                            [a6-a7]
+//   k_micro_residual  per (cell, velocity), fully parallel:
+//                     R = -sum_faces F - (2 Omega/(2 tau' + dt)) (f~ - f^S(W^{n+1})),
+//                     written into the increment buffer
+//   k_sweep_fwd       Delta*_c = (R_c + sum_{lower inflow nb} |xi.n| S Delta*_nb) / D_c
+//   k_sweep_bwd       Delta_c = Delta*_c + sum_{upper inflow nb} |xi.n| S Delta_nb / D_c,
+//                     f~ += Delta (Eq. 32)
+// with D = Omega/dt_imp + sum_{outflow} xi.n S + 2 Omega/(2 tau' + dt).
+// The sweeps run one CTA per tile of sweep_tv velocities over the i+j
+// hyperplanes; thread (slot, t) owns cell (ilo + slot) of each hyperplane at
+// velocity t.  Everything a step reads except the neighbours' increments is
+// prefetched kStages-1 hyperplanes ahead with cp.async; the previous
+// hyperplane's increments sit in a shared-memory ring, and neighbours across
+// a periodic seam (earlier hyperplanes) are read back from global memory.
 // ---------------------------------------------------------------------------
-// ---------------------------------------------------------------------------
-// micro LU-SGS sweeps (Eq. 22-26) on i+j hyperplanes                  [a6-a7]
-// one CTA per tile of sweep_tv velocities; sweep_pc cell slots per CTA
-// ---------------------------------------------------------------------------
-
-// Forward sweep: Delta*_c = (R_c + sum_{lower inflow nb} |xi.n| S Delta*_nb) / D_c
-// with R = -sum_faces F - (2 Omega/(2 tau' + dt)) (f~ - f^S(W^{n+1})) (Eq. 22-23)
-// and D = Omega/dt_imp + sum_{outflow} xi.n S + 2 Omega/(2 tau' + dt) (Eq. 26).
-// The previous hyperplane's Delta* sits in a shared-memory ring; neighbours
-// across a periodic seam (earlier hyperplanes) are read back from global.
 template <class T>
-__global__ void __launch_bounds__(1024) k_sweep_fwd(KParams p)
+__global__ void __launch_bounds__(256) k_micro_residual(KParams p)
 {
     using T2 = typename V2<T>::t;
-    extern __shared__ unsigned char smraw[];
-    T2 *ring = (T2 *)smraw;  // [2][ni][tv]
-    const int tv = p.sweep_tv, pc = p.sweep_pc, ni = p.ni, nj = p.nj;
-    const int t = threadIdx.x % tv, slot = threadIdx.x / tv;
-    const int k = blockIdx.x * tv + t;
-    const bool act = k < p.Nv;
-    const int kk = act ? k : 0;
-    const T ux = vx<T>(p, kk), uy = vy<T>(p, kk), kRTr = (T)(p.K * p.RT_r), gref = vgref<T>(p, kk);
+    const int c = blockIdx.x;
+    const int k = blockIdx.y * blockDim.x + threadIdx.x;
+    if (k >= p.Nv) return;
+    const T *cp = (const T *)p.cellpT + kCellP * c;
+    const EqT<T> e = eq_loadT<T>(cp);
+    const T cq = cp[14];
+    T dG, dH;
+    const T ux = vx<T>(p, k), uy = vy<T>(p, k);
+    dev_equilibrium<T>(e, ux, uy, vgref<T>(p, k), (T)(p.K * p.RT_r), dG, dH);
+    const size_t ck = (size_t)c * p.Nv + k;
+    const T2 fv = ((const T2 *)p.f)[ck];
+    T rg = -cq * (fv.x - dG), rh = -cq * (fv.y - dH);
     const T2 *F = (const T2 *)p.F;
-    const T2 *f = (const T2 *)p.f;
-    T2 *ds = (T2 *)p.dst;
-    const T *cpT = (const T *)p.cellpT;
-    const T *sl = (const T *)p.cslotT;
-    const int nh = ni + nj - 1;
-    for (int dpl = 0; dpl < nh; ++dpl) {
-        int ilo = max(0, dpl - (nj - 1)), ihi = min(ni - 1, dpl);
-        for (int i = ilo + slot; i <= ihi; i += pc) {
-            if (!act) continue;
-            int c = (dpl - i) * ni + i;
-            const T *cp = cpT + kCellP * c;
-            EqT<T> e = eq_loadT<T>(cp);
-            T cq = cp[14], D = cp[15];
-            T dG, dH;
-            dev_equilibrium<T>(e, ux, uy, gref, kRTr, dG, dH);
-            T2 fv = f[(size_t)c * p.Nv + k];
-            T rg = -cq * (fv.x - dG), rh = -cq * (fv.y - dH);
-            T ag = 0, ah = 0;
 #pragma unroll
-            for (int m = 0; m < 4; ++m) {
-                int fi = p.cface[4 * c + m];
-                int nb = p.cnb[4 * c + m];
-                const T *g = sl + 16 * c + 4 * m;  // sign*nx, sign*ny, S
-                T2 Fv = F[(size_t)fi * p.Nv + k];
-                T sg = (T)p.csign[4 * c + m];
-                rg -= sg * Fv.x;
-                rh -= sg * Fv.y;
-                if (nb == c) continue;  // a cell wrapped onto itself: no net implicit term
-                T so = xi_dot_n<T>(ux, uy, g[0], g[1]);
-                T aS = so * g[2];
-                if (so > (T)0) D += aS;
-                else if (so < (T)0 && nb >= 0 && nb < c) {
-                    int inb = nb % ni, jnb = nb / ni;
-                    T2 dn = (inb + jnb == dpl - 1) ? ring[(((dpl - 1) & 1) * ni + inb) * tv + t]
-                                                   : ds[(size_t)nb * p.Nv + k];
-                    ag -= aS * dn.x;
-                    ah -= aS * dn.y;
-                }
-            }
-            T2 o;
-            o.x = (rg + ag) / D;
-            o.y = (rh + ah) / D;
-            ds[(size_t)c * p.Nv + k] = o;
-            ring[((dpl & 1) * ni + i) * tv + t] = o;
-        }
-        __syncthreads();
+    for (int m = 0; m < 4; ++m) {
+        T2 Fv = F[(size_t)p.cface[4 * c + m] * p.Nv + k];
+        T sg = (T)p.csign[4 * c + m];
+        rg -= sg * Fv.x;
+        rh -= sg * Fv.y;
     }
+    T2 o;
+    o.x = rg;
+    o.y = rh;
+    ((T2 *)p.dst)[ck] = o;
 }
 
-// Backward sweep: Delta_c = Delta*_c + sum_{upper inflow nb} |xi.n| S Delta_nb / D_c,
-// then f~ += Delta (Eq. 32).
-template <class T>
-__global__ void __launch_bounds__(1024) k_sweep_bwd(KParams p)
+// shared-memory layout of the micro sweeps
+template <class T, int kStages> struct SweepSmem {
+    using T2 = typename V2<T>::t;
+    T2 *R;      // [kStages][pc][tv]  R (forward) / Delta* (backward)
+    T2 *F;      // [kStages][pc][tv]  f~ (backward only)
+    T *geo;     // [kStages][pc][16]  sign*nx, sign*ny, S, 0 per slot
+    int *lnk;   // [kStages][pc][12]  neighbour, its i, its hyperplane
+    T2 *ring;   // [2][ni][tv]
+    T *D0;      // [kStages][pc]
+    __device__ SweepSmem(unsigned char *base, int pc, int tv, int ni, bool withF)
+    {
+        size_t o = 0;
+        R = (T2 *)(base + o); o += (size_t)kStages * pc * tv * sizeof(T2);
+        F = (T2 *)(base + o); if (withF) o += (size_t)kStages * pc * tv * sizeof(T2);
+        geo = (T *)(base + o); o += (size_t)kStages * pc * 16 * sizeof(T);
+        lnk = (int *)(base + o); o += (size_t)kStages * pc * 12 * sizeof(int);
+        ring = (T2 *)(base + o); o += (size_t)2 * ni * tv * sizeof(T2);
+        D0 = (T *)(base + o);
+    }
+};
+
+template <class T, int kStages> static size_t sweep_smem_bytes(int pc, int tv, int ni, bool withF)
 {
     using T2 = typename V2<T>::t;
-    extern __shared__ unsigned char smraw[];
-    T2 *ring = (T2 *)smraw;  // [2][ni][tv]
+    size_t o = (size_t)kStages * pc * tv * sizeof(T2) * (withF ? 2 : 1);
+    o += (size_t)kStages * pc * 16 * sizeof(T) + (size_t)kStages * pc * 12 * sizeof(int);
+    o += (size_t)2 * ni * tv * sizeof(T2) + (size_t)kStages * pc * sizeof(T);
+    return o;
+}
+
+// asynchronous copy of one step's data for the thread's cell
+template <class T, int kStages>
+__device__ __forceinline__ void sweep_issue(const KParams &p, const SweepSmem<T, kStages> &sm, int s, int d,
+                                            int slot, int t, int k, bool act, bool withF)
+{
+    using T2 = typename V2<T>::t;
+    const int ni = p.ni, nj = p.nj, tv = p.sweep_tv, pc = p.sweep_pc;
+    const int nh = ni + nj - 1;
+    if (s < nh) {
+        int ilo = max(0, d - (nj - 1)), ihi = min(ni - 1, d);
+        int i = ilo + slot;
+        if (i <= ihi) {
+            int c = (d - i) * ni + i;
+            int st = s & (kStages - 1);
+            size_t e = ((size_t)st * pc + slot);
+            if (act) {
+                size_t ck = (size_t)c * p.Nv + k;
+                cp_async_b<sizeof(T2)>(sm.R + e * tv + t, (const T2 *)p.dst + ck);
+                if (withF) cp_async_b<sizeof(T2)>(sm.F + e * tv + t, (const T2 *)p.f + ck);
+            }
+            constexpr int ng = 16 * sizeof(T) / 16;  // 16-byte chunks of the geometry record
+            for (int q = t; q < ng + 4; q += tv) {
+                if (q < ng) cp_async16((char *)(sm.geo + e * 16) + 16 * q, (const char *)((const T *)p.cslotT + 16 * (size_t)c) + 16 * q);
+                else if (q < ng + 3) cp_async16((char *)(sm.lnk + e * 12) + 16 * (q - ng), (const char *)(p.clink + 12 * (size_t)c) + 16 * (q - ng));
+                else cp_async_b<sizeof(T)>(sm.D0 + e, (const T *)p.cellpT + kCellP * (size_t)c + 15);
+            }
+        }
+    }
+    cp_commit();
+}
+
+template <class T, bool FWD, int kStages>
+__global__ void __launch_bounds__(1024) k_sweep(KParams p)
+{
+    using T2 = typename V2<T>::t;
+    extern __shared__ __align__(16) unsigned char smraw[];
     const int tv = p.sweep_tv, pc = p.sweep_pc, ni = p.ni, nj = p.nj;
+    const SweepSmem<T, kStages> sm(smraw, pc, tv, ni, !FWD);
     const int t = threadIdx.x % tv, slot = threadIdx.x / tv;
     const int k = blockIdx.x * tv + t;
     const bool act = k < p.Nv;
     const int kk = act ? k : 0;
     const T ux = vx<T>(p, kk), uy = vy<T>(p, kk);
-    T2 *f = (T2 *)p.f;
     T2 *ds = (T2 *)p.dst;
-    const T *cpT = (const T *)p.cellpT;
-    const T *sl = (const T *)p.cslotT;
+    T2 *f = (T2 *)p.f;
     const int nh = ni + nj - 1;
-    for (int dpl = nh - 1; dpl >= 0; --dpl) {
-        int ilo = max(0, dpl - (nj - 1)), ihi = min(ni - 1, dpl);
-        for (int i = ilo + slot; i <= ihi; i += pc) {
-            if (!act) continue;
-            int c = (dpl - i) * ni + i;
-            T D = cpT[kCellP * c + 15];
-            T ag = 0, ah = 0;
+    const int dir = FWD ? 1 : -1;
+    auto step_d = [&](int s) { return FWD ? s : nh - 1 - s; };
+    for (int s = 0; s < kStages - 1; ++s) sweep_issue<T, kStages>(p, sm, s, step_d(s), slot, t, k, act, !FWD);
+    for (int s = 0; s < nh; ++s) {
+        cp_wait<kStages - 2>();
+        __syncthreads();
+        sweep_issue<T, kStages>(p, sm, s + kStages - 1, step_d(s + kStages - 1), slot, t, k, act, !FWD);
+        const int d = step_d(s);
+        const int ilo = max(0, d - (nj - 1)), ihi = min(ni - 1, d);
+        const int i = ilo + slot;
+        if (i > ihi || !act) continue;
+        const int c = (d - i) * ni + i;
+        const size_t e = (size_t)(s & (kStages - 1)) * pc + slot;
+        const T *g = sm.geo + e * 16;
+        const int *lk = sm.lnk + e * 12;
+        T D = sm.D0[e];
+        T ag = 0, ah = 0;
 #pragma unroll
-            for (int m = 0; m < 4; ++m) {
-                int nb = p.cnb[4 * c + m];
-                if (nb == c) continue;
-                const T *g = sl + 16 * c + 4 * m;
-                T so = xi_dot_n<T>(ux, uy, g[0], g[1]);
-                T aS = so * g[2];
-                if (so > (T)0) D += aS;
-                else if (so < (T)0 && nb > c) {
-                    int inb = nb % ni, jnb = nb / ni;
-                    T2 dn = (inb + jnb == dpl + 1) ? ring[(((dpl + 1) & 1) * ni + inb) * tv + t]
-                                                   : ds[(size_t)nb * p.Nv + k];
-                    ag -= aS * dn.x;
-                    ah -= aS * dn.y;
-                }
+        for (int m = 0; m < 4; ++m) {
+            int nb = lk[m];
+            if (nb == c) continue;  // a cell wrapped onto itself: no net implicit term
+            T so = xi_dot_n<T>(ux, uy, g[4 * m], g[4 * m + 1]);
+            T aS = so * g[4 * m + 2];
+            if (so > (T)0) D += aS;
+            else if (so < (T)0 && nb >= 0 && (FWD ? nb < c : nb > c)) {
+                T2 dn = (lk[8 + m] == d - dir) ? sm.ring[(((d - dir) & 1) * ni + lk[4 + m]) * tv + t]
+                                               : ds[(size_t)nb * p.Nv + k];
+                ag -= aS * dn.x;
+                ah -= aS * dn.y;
             }
-            size_t ck = (size_t)c * p.Nv + k;
-            T2 d0 = ds[ck];
-            T2 d1;
-            d1.x = d0.x + ag / D;
-            d1.y = d0.y + ah / D;
-            ds[ck] = d1;
-            ring[((dpl & 1) * ni + i) * tv + t] = d1;
-            T2 fv = f[ck];
-            fv.x += d1.x;
-            fv.y += d1.y;
+        }
+        const T2 r = sm.R[e * tv + t];
+        const size_t ck = (size_t)c * p.Nv + k;
+        const T iD = (T)1 / D;
+        T2 o;
+        if (FWD) {
+            o.x = (r.x + ag) * iD;
+            o.y = (r.y + ah) * iD;
+        } else {
+            o.x = r.x + ag * iD;
+            o.y = r.y + ah * iD;
+            T2 fv = sm.F[e * tv + t];
+            fv.x += o.x;
+            fv.y += o.y;
             f[ck] = fv;
         }
-        __syncthreads();
+        ds[ck] = o;
+        sm.ring[((d & 1) * ni + i) * tv + t] = o;
     }
+    cp_wait<0>();
 }
 
 // ---------------------------------------------------------------------------
@@ -1088,6 +1163,35 @@ __global__ void __launch_bounds__(256) k_moments_out(KParams p, double *out6)
 // ---------------------------------------------------------------------------
 static inline int nblk(int n, int per) { return (n + per - 1) / per; }
 
+static int macro_threads(const KParams &p) { return std::min(1024, ((std::min(p.ni, p.nj) + 31) / 32) * 32); }
+
+template <class T> static size_t macro_smem_bytes(const KParams &p, int nt, int stages)
+{
+    return (size_t)stages * nt * ((kMRec + 4) * sizeof(T) + 12 * sizeof(int)) + (size_t)2 * p.ni * 4 * sizeof(T);
+}
+
+template <class T> static size_t sweep_bytes(const KParams &p, bool withF, int stages)
+{
+    return stages == 8 ? sweep_smem_bytes<T, 8>(p.sweep_pc, p.sweep_tv, p.ni, withF)
+                       : sweep_smem_bytes<T, 4>(p.sweep_pc, p.sweep_tv, p.ni, withF);
+}
+
+template <class T> static void launch_macro_sweep(const KParams &p, cudaStream_t st)
+{
+    int nt = macro_threads(p);
+    if (p.macro_stages == 8) k_macro_sweep<T, 8><<<1, nt, macro_smem_bytes<T>(p, nt, 8), st>>>(p);
+    else k_macro_sweep<T, 4><<<1, nt, macro_smem_bytes<T>(p, nt, 4), st>>>(p);
+}
+
+template <class T, bool FWD> static void launch_sweep(const KParams &p, cudaStream_t st)
+{
+    int nb = (p.Nv + p.sweep_tv - 1) / p.sweep_tv;
+    int nthr = p.sweep_tv * p.sweep_pc;
+    size_t sm = sweep_bytes<T>(p, !FWD, p.sweep_stages);
+    if (p.sweep_stages == 8) k_sweep<T, FWD, 8><<<nb, nthr, sm, st>>>(p);
+    else k_sweep<T, FWD, 4><<<nb, nthr, sm, st>>>(p);
+}
+
 // events (optional): kProfiled+1 cudaEvent_t recorded between the six groups
 // cell prep | faces (moments, params, flux, phi) | macro | fwd | bwd | (spare)
 template <class T>
@@ -1098,51 +1202,61 @@ static int iteration_t(const KParams &p, cudaStream_t st, void **events)
     };
     mark(0);
     k_cell_moments<T><<<nblk(p.N, 8), 256, 0, st>>>(p);
-    k_cell_params<T><<<nblk(p.N, 256), 256, 0, st>>>(p);
+    k_cell_params<T><<<nblk(p.N, 32), 32, 0, st>>>(p);
     k_fbp<T><<<dim3(p.N, nblk(p.Nv, 256)), 256, 0, st>>>(p);
     mark(1);
     if (p.limiter) k_face_moments<T, true><<<nblk(p.nf, 8), 256, 0, st>>>(p);
     else k_face_moments<T, false><<<nblk(p.nf, 8), 256, 0, st>>>(p);
-    k_face_params<T><<<nblk(p.nf, 256), 256, 0, st>>>(p);
+    k_face_params<T><<<nblk(p.nf, 32), 32, 0, st>>>(p);
     mark(2);
     if (p.limiter) k_face_flux<T, true><<<nblk(p.nf, 8), 256, 0, st>>>(p);
     else k_face_flux<T, false><<<nblk(p.nf, 8), 256, 0, st>>>(p);
-    k_face_phi<T><<<nblk(p.nf, 256), 256, 0, st>>>(p);
+    k_face_phi<T><<<nblk(p.nf, 64), 64, 0, st>>>(p);
     mark(3);
     {
-        int nb = nblk(p.N, 256);
-        k_macro_pre<T><<<nb, 256, 0, st>>>(p);
-        int nthr = std::min(1024, ((std::min(p.ni, p.nj) + 31) / 32) * 32);
-        size_t smem = sizeof(T) * 8 * (size_t)p.ni;
-        k_macro_sweep<T><<<1, nthr, smem, st>>>(p);
-        k_macro_post<T><<<nb, 256, 0, st>>>(p);
+        k_macro_pre<T><<<nblk(p.N, 32), 32, 0, st>>>(p);
+        launch_macro_sweep<T>(p, st);
+        k_macro_post<T><<<nblk(p.N, 32), 32, 0, st>>>(p);
     }
     mark(4);
-    int nb = nblk(p.Nv, p.sweep_tv);
-    int nthr = p.sweep_tv * p.sweep_pc;
-    size_t ssm = 2 * sizeof(typename V2<T>::t) * (size_t)p.ni * p.sweep_tv;
-    k_sweep_fwd<T><<<nb, nthr, ssm, st>>>(p);
+    k_micro_residual<T><<<dim3(p.N, nblk(p.Nv, 256)), 256, 0, st>>>(p);
+    launch_sweep<T, true>(p, st);
     mark(5);
-    k_sweep_bwd<T><<<nb, nthr, ssm, st>>>(p);
+    launch_sweep<T, false>(p, st);
     mark(6);
     return (int)cudaGetLastError();
 }
 
+// checks that the sweep shapes fit in shared memory and opts the kernels in
+// to more than 48 KB of it
 template <class T> static int configure_t(const KParams &p)
 {
-    size_t macro = sizeof(T) * 8 * (size_t)p.ni;
-    size_t micro = 2 * sizeof(typename V2<T>::t) * (size_t)p.ni * p.sweep_tv;
     const size_t lim = 227 * 1024;
-    if (macro > lim || micro > lim) return (int)cudaErrorInvalidValue;
+    int nt = macro_threads(p);
+    size_t macro = macro_smem_bytes<T>(p, nt, p.macro_stages);
+    size_t fwd = sweep_bytes<T>(p, false, p.sweep_stages), bwd = sweep_bytes<T>(p, true, p.sweep_stages);
+    if (macro > lim || fwd > lim || bwd > lim) return (int)cudaErrorInvalidValue;
     cudaError_t e = cudaSuccess;
-    if (macro > 48 * 1024)
-        e = cudaFuncSetAttribute(k_macro_sweep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)macro);
-    if (e == cudaSuccess && micro > 48 * 1024) {
-        e = cudaFuncSetAttribute(k_sweep_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)micro);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_sweep_bwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)micro);
+    auto opt = [&](const void *fn, size_t b) {
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b);
+    };
+    if (p.macro_stages == 8) opt((const void *)k_macro_sweep<T, 8>, macro);
+    else opt((const void *)k_macro_sweep<T, 4>, macro);
+    if (p.sweep_stages == 8) {
+        opt((const void *)k_sweep<T, true, 8>, fwd);
+        opt((const void *)k_sweep<T, false, 8>, bwd);
+    } else {
+        opt((const void *)k_sweep<T, true, 4>, fwd);
+        opt((const void *)k_sweep<T, false, 4>, bwd);
     }
     return (int)e;
+}
+
+size_t sweep_smem_need(const KParams &p, bool fp64, int which)
+{
+    if (which == 0) return fp64 ? macro_smem_bytes<double>(p, macro_threads(p), p.macro_stages)
+                                : macro_smem_bytes<float>(p, macro_threads(p), p.macro_stages);
+    return fp64 ? sweep_bytes<double>(p, true, p.sweep_stages) : sweep_bytes<float>(p, true, p.sweep_stages);
 }
 
 int configure_kernels(const KParams &p, bool fp64) { return fp64 ? configure_t<double>(p) : configure_t<float>(p); }

@@ -89,6 +89,18 @@ class Solver:
         macroscopic predictor, forward sweep, backward sweep."""
         return B.idg_iterate_profiled(self.ctx, self.stream)
 
+    def set_tuning(self, **kw):
+        """sweep_tv=, sweep_stages=, macro_stages= (launch shapes only)."""
+        keys = {"sweep_tv": B.IDG_TUNE_SWEEP_TV, "sweep_stages": B.IDG_TUNE_SWEEP_STAGES,
+                "macro_stages": B.IDG_TUNE_MACRO_STAGES}
+        for k, v in kw.items():
+            B.idg_set_tuning(self.ctx, keys[k], int(v))
+
+    def tuning(self) -> dict:
+        return {"sweep_tv": B.idg_get_tuning(self.ctx, B.IDG_TUNE_SWEEP_TV),
+                "sweep_stages": B.idg_get_tuning(self.ctx, B.IDG_TUNE_SWEEP_STAGES),
+                "macro_stages": B.idg_get_tuning(self.ctx, B.IDG_TUNE_MACRO_STAGES)}
+
     def moments(self) -> np.ndarray:
         return B.idg_get_moments(self.ctx, self.N, self.stream)
 
