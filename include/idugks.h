@@ -159,8 +159,12 @@ idg_status idg_iterate_profiled(idg_ctx *ctx, void *stream, double *kernel_ms);
  * block of the micro LU-SGS sweeps (power of two, 1..32, times min(ni, nj)
  * at most 1024).  IDG_TUNE_SWEEP_STAGES / IDG_TUNE_MACRO_STAGES: hyperplanes
  * prefetched ahead by the micro / macroscopic sweeps (4 or 8).  Returns
- * IDG_ERR_ARG for a value that is invalid or does not fit in shared memory. */
-enum { IDG_TUNE_SWEEP_TV = 1, IDG_TUNE_SWEEP_STAGES = 2, IDG_TUNE_MACRO_STAGES = 3 };
+ * IDG_ERR_ARG for a value that is invalid or does not fit in shared memory.
+ * IDG_TUNE_GRAPH (1 default, 0 off): idg_iterate replays chunks of 16
+ * iterations (and single iterations) as captured CUDA graphs on a
+ * library-owned stream that is ordered after, and before, the caller's
+ * stream by events. */
+enum { IDG_TUNE_SWEEP_TV = 1, IDG_TUNE_SWEEP_STAGES = 2, IDG_TUNE_MACRO_STAGES = 3, IDG_TUNE_GRAPH = 4 };
 idg_status idg_set_tuning(idg_ctx *ctx, int key, int value);
 idg_status idg_get_tuning(const idg_ctx *ctx, int key, int *value);
 

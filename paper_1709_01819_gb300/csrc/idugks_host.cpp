@@ -50,6 +50,13 @@ struct idg_ctx {
     double *moments_dev = nullptr;
     double *stage = nullptr;  // staging for host<->device state copies (aliases F)
     size_t stage_bytes = 0;
+    // CUDA graph of kGraphChunk iterations, replayed on a library-owned stream
+    // that is event-ordered with the caller's stream
+    int use_graph = 1;
+    cudaStream_t gstream = nullptr;
+    cudaGraphExec_t gexec = nullptr;   // kGraphChunk iterations
+    cudaGraphExec_t gexec1 = nullptr;  // one iteration
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     // iteration bookkeeping
     long long host_iter = 0;   // iterations launched since bind
     long long start_iter = 0;  // iteration index of the last (re)start
@@ -537,6 +544,66 @@ idg_status check_ready(idg_ctx *c)
     return IDG_OK;
 }
 
+constexpr int kGraphChunk = 16;
+
+void drop_graph(idg_ctx *c)
+{
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->gexec1) cudaGraphExecDestroy(c->gexec1);
+    c->gexec = c->gexec1 = nullptr;
+}
+
+void free_graph_state(idg_ctx *c)
+{
+    drop_graph(c);
+    if (c->ev_in) cudaEventDestroy(c->ev_in);
+    if (c->ev_out) cudaEventDestroy(c->ev_out);
+    if (c->gstream) cudaStreamDestroy(c->gstream);
+    c->ev_in = c->ev_out = nullptr;
+    c->gstream = nullptr;
+}
+
+// n (kGraphChunk or 1) iterations captured once (the launch parameters are
+// baked in; any change of them drops the graphs)
+idg_status launch_chunk_graph(idg_ctx *c, cudaStream_t st, int n)
+{
+    cudaGraphExec_t &gx = n == 1 ? c->gexec1 : c->gexec;
+    cudaError_t e;
+    if (!c->gstream) {
+        if ((e = cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking)) != cudaSuccess)
+            return cuda_fail(c, e, "cudaStreamCreate");
+        if ((e = cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming)) != cudaSuccess)
+            return cuda_fail(c, e, "cudaEventCreate");
+        if ((e = cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming)) != cudaSuccess)
+            return cuda_fail(c, e, "cudaEventCreate");
+    }
+    if (!gx) {
+        cudaGraph_t g = nullptr;
+        if ((e = cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+            return cuda_fail(c, e, "cudaStreamBeginCapture");
+        int rc = 0;
+        for (int q = 0; q < n && !rc; ++q)
+            rc = idg::launch_iteration(c->kp, c->precision == IDG_FP64, c->gstream);
+        e = cudaStreamEndCapture(c->gstream, &g);
+        if (rc || e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return cuda_fail(c, rc ? (cudaError_t)rc : e, "graph capture");
+        }
+        e = cudaGraphInstantiate(&gx, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            gx = nullptr;
+            return cuda_fail(c, e, "cudaGraphInstantiate");
+        }
+    }
+    if ((e = cudaEventRecord(c->ev_in, st)) != cudaSuccess) return cuda_fail(c, e, "event");
+    if ((e = cudaStreamWaitEvent(c->gstream, c->ev_in, 0)) != cudaSuccess) return cuda_fail(c, e, "wait");
+    if ((e = cudaGraphLaunch(gx, c->gstream)) != cudaSuccess) return cuda_fail(c, e, "cudaGraphLaunch");
+    if ((e = cudaEventRecord(c->ev_out, c->gstream)) != cudaSuccess) return cuda_fail(c, e, "event");
+    if ((e = cudaStreamWaitEvent(st, c->ev_out, 0)) != cudaSuccess) return cuda_fail(c, e, "wait");
+    return IDG_OK;
+}
+
 void restart(idg_ctx *c)
 {
     c->start_iter = c->host_iter;
@@ -563,7 +630,15 @@ idg_status idg_create(idg_ctx **out, int precision, int device)
     return IDG_OK;
 }
 
-void idg_destroy(idg_ctx *ctx) { delete ctx; }
+void idg_destroy(idg_ctx *ctx)
+{
+    if (!ctx) return;
+    if (ctx->bound) {
+        cudaSetDevice(ctx->device);
+        free_graph_state(ctx);
+    }
+    delete ctx;
+}
 
 const char *idg_last_error(const idg_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
@@ -788,6 +863,7 @@ idg_status idg_init_uniform(idg_ctx *c, double rho, double u, double v, double T
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(c, e, "sync");
     c->ref_rho = rho; c->ref_u = u; c->ref_v = v; c->ref_T = T;
+    drop_graph(c);
     if ((s = upload_reference(c))) return s;
     const size_t t2 = c->precision == IDG_FP64 ? 16 : 8;
     // f~ = M_ref exactly: deviation zero
@@ -857,7 +933,7 @@ idg_status idg_iterate(idg_ctx *c, int max_iter, double tol, void *stream, int *
     if (max_iter < 0) return fail(c, IDG_ERR_ARG, "max_iter < 0");
     cudaStream_t st = (cudaStream_t)stream;
     const bool fp64 = c->precision == IDG_FP64;
-    const int chunk = 16;
+    const int chunk = kGraphChunk;
     int done = 0;
     double rel = NAN;
     std::vector<double> buf(chunk);
@@ -866,9 +942,13 @@ idg_status idg_iterate(idg_ctx *c, int max_iter, double tol, void *stream, int *
     while (done < max_iter) {
         int n = std::min(chunk, max_iter - done);
         long long it0 = c->host_iter;
-        for (int q = 0; q < n; ++q) {
-            int rc = idg::launch_iteration(c->kp, fp64, st);
-            if (rc) return cuda_fail(c, (cudaError_t)rc, "launch");
+        if ((n == kGraphChunk || n == 1) && c->use_graph) {
+            if ((s = launch_chunk_graph(c, st, n))) return s;
+        } else {
+            for (int q = 0; q < n; ++q) {
+                int rc = idg::launch_iteration(c->kp, fp64, st);
+                if (rc) return cuda_fail(c, (cudaError_t)rc, "launch");
+            }
         }
         c->host_iter += n;
         done += n;
@@ -935,6 +1015,11 @@ idg_status idg_set_tuning(idg_ctx *c, int key, int value)
     idg_status s = check_ready(c);
     if (s) return s;
     KParams k = c->kp;
+    if (key == IDG_TUNE_GRAPH) {
+        if (value != 0 && value != 1) return fail(c, IDG_ERR_ARG, "graph flag must be 0 or 1");
+        c->use_graph = value;
+        return IDG_OK;
+    }
     if (key == IDG_TUNE_SWEEP_TV) {
         if (value < 1 || value > 32 || (value & (value - 1)) || value * k.sweep_pc > 1024)
             return fail(c, IDG_ERR_ARG, "sweep velocities per block %d invalid for %d cell slots", value, k.sweep_pc);
@@ -951,6 +1036,7 @@ idg_status idg_set_tuning(idg_ctx *c, int key, int value)
     int rc = idg::configure_kernels(k, c->precision == IDG_FP64);
     if (rc) return fail(c, IDG_ERR_ARG, "launch shape does not fit in shared memory");
     c->kp = k;
+    drop_graph(c);
     return IDG_OK;
 }
 
@@ -958,7 +1044,8 @@ idg_status idg_get_tuning(const idg_ctx *c, int key, int *value)
 {
     if (!c || !value) return IDG_ERR_ARG;
     if (!c->bound) return IDG_ERR_STATE;
-    if (key == IDG_TUNE_SWEEP_TV) *value = c->kp.sweep_tv;
+    if (key == IDG_TUNE_GRAPH) *value = c->use_graph;
+    else if (key == IDG_TUNE_SWEEP_TV) *value = c->kp.sweep_tv;
     else if (key == IDG_TUNE_SWEEP_STAGES) *value = c->kp.sweep_stages;
     else if (key == IDG_TUNE_MACRO_STAGES) *value = c->kp.macro_stages;
     else return IDG_ERR_ARG;

@@ -571,6 +571,8 @@ __global__ void __launch_bounds__(256) k_face_moments(KParams p)
         rhow = (T)rw;
         rwm1 = (T)((bc[0] - bc[1] + o) / bc[1]);
     }
+    // fb - M_ref is kept in the face-flux buffer for k_face_flux
+    T2 *Fo = (T2 *)p.F + (size_t)f * p.Nv;
     Acc<T> acc[kRaw];
 #pragma unroll
     for (int q = 0; q < kRaw; ++q) acc[q].zero();
@@ -578,6 +580,7 @@ __global__ void __launch_bounds__(256) k_face_moments(KParams p)
         T ux = vx<T>(p, k), uy = vy<T>(p, k);
         T s = xi_dot_n<T>(ux, uy, fc.nx, fc.ny);
         T2 fb = face_fbar<T, LIM>(p, fc, k, ux, uy, s, rhow, rwm1);
+        Fo[k] = fb;
         raw_terms<T>(a, vw<T>(p, k), ux, uy, fb.x, fb.y);
     });
 #pragma unroll
@@ -611,24 +614,17 @@ __global__ void __launch_bounds__(32) k_face_params(KParams p)
     fA[15] = (T)(p.h / (2.0 * tau + p.h));
 }
 
-// face flux of (f_face - M_ref), Eq. (18)-(19), and its moments
-template <class T, bool LIM>
+// face flux of (f_face - M_ref), Eq. (18)-(19), and its moments; fb - M_ref
+// comes from k_face_moments through the same buffer and is overwritten
+template <class T>
 __global__ void __launch_bounds__(256) k_face_flux(KParams p)
 {
     using T2 = typename V2<T>::t;
-    __shared__ SideRec<T> srec[8][2];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int f = blockIdx.x * 8 + wid;
     if (f >= p.nf) return;  // whole warp
-    FaceCtx<T> fc;
-    load_face<T>(p, f, srec[wid], fc);
-    double rw = p.facerw[f];
-    T rhow = (T)rw, rwm1 = (T)(rw - 1.0);
-    if (fc.kind == 1) {
-        const double *bc = p.bconst + 2 * f;
-        double o = acc_load<T>(p.faceraw, (size_t)f * 12 + 11);
-        rwm1 = (T)((bc[0] - bc[1] + o) / bc[1]);
-    }
+    const T *g = (const T *)p.fgeoT + 8 * f;
+    const T nx = g[0], ny = g[1], S = g[2];
     const T *fA = (const T *)p.faceA + kCellP * f;
     const EqT<T> e = eq_loadT<T>(fA);
     const T wa = fA[14], wb = fA[15], kRTr = (T)(p.K * p.RT_r);
@@ -638,11 +634,11 @@ __global__ void __launch_bounds__(256) k_face_flux(KParams p)
     for (int q = 0; q < 4; ++q) acc[q].zero();
     vel_loop<4, T>(p.Nv, lane, acc, [&](int k, T(&a)[4]) {
         T ux = vx<T>(p, k), uy = vy<T>(p, k);
-        T s = xi_dot_n<T>(ux, uy, fc.nx, fc.ny);
-        T2 fb = face_fbar<T, LIM>(p, fc, k, ux, uy, s, rhow, rwm1);
+        T s = xi_dot_n<T>(ux, uy, nx, ny);
+        T2 fb = Fo[k];
         T dG, dH;
         dev_equilibrium<T>(e, ux, uy, vgref<T>(p, k), kRTr, dG, dH);
-        T sS = s * fc.S;
+        T sS = s * S;
         T2 Fk;
         Fk.x = sS * (wa * fb.x + wb * dG);
         Fk.y = sS * (wa * fb.y + wb * dH);
@@ -1209,8 +1205,7 @@ static int iteration_t(const KParams &p, cudaStream_t st, void **events)
     else k_face_moments<T, false><<<nblk(p.nf, 8), 256, 0, st>>>(p);
     k_face_params<T><<<nblk(p.nf, 32), 32, 0, st>>>(p);
     mark(2);
-    if (p.limiter) k_face_flux<T, true><<<nblk(p.nf, 8), 256, 0, st>>>(p);
-    else k_face_flux<T, false><<<nblk(p.nf, 8), 256, 0, st>>>(p);
+    k_face_flux<T><<<nblk(p.nf, 8), 256, 0, st>>>(p);
     k_face_phi<T><<<nblk(p.nf, 64), 64, 0, st>>>(p);
     mark(3);
     {

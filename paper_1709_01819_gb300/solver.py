@@ -90,16 +90,17 @@ class Solver:
         return B.idg_iterate_profiled(self.ctx, self.stream)
 
     def set_tuning(self, **kw):
-        """sweep_tv=, sweep_stages=, macro_stages= (launch shapes only)."""
+        """sweep_tv=, sweep_stages=, macro_stages=, graph= (launch shapes only)."""
         keys = {"sweep_tv": B.IDG_TUNE_SWEEP_TV, "sweep_stages": B.IDG_TUNE_SWEEP_STAGES,
-                "macro_stages": B.IDG_TUNE_MACRO_STAGES}
+                "macro_stages": B.IDG_TUNE_MACRO_STAGES, "graph": B.IDG_TUNE_GRAPH}
         for k, v in kw.items():
             B.idg_set_tuning(self.ctx, keys[k], int(v))
 
     def tuning(self) -> dict:
         return {"sweep_tv": B.idg_get_tuning(self.ctx, B.IDG_TUNE_SWEEP_TV),
                 "sweep_stages": B.idg_get_tuning(self.ctx, B.IDG_TUNE_SWEEP_STAGES),
-                "macro_stages": B.idg_get_tuning(self.ctx, B.IDG_TUNE_MACRO_STAGES)}
+                "macro_stages": B.idg_get_tuning(self.ctx, B.IDG_TUNE_MACRO_STAGES),
+                "graph": B.idg_get_tuning(self.ctx, B.IDG_TUNE_GRAPH)}
 
     def moments(self) -> np.ndarray:
         return B.idg_get_moments(self.ctx, self.N, self.stream)

@@ -142,3 +142,23 @@ def test_uniform_maxwellian_fixed_point_on_gpu_both_precisions():
         tol = 1e-14 if prec == "fp64" else 1e-7
         assert _rel(G, G0) < tol, (prec, _rel(G, G0))
         assert np.abs(W - W0).max() < tol
+
+
+def test_graph_replay_and_tuning_do_not_change_results():
+    """Launch shapes and CUDA-graph replay only reorder launches, never arithmetic."""
+    prob = I.cavity(12, Kn=0.075, U=0.15, nv=16, vmax=4.0)
+    prob.nodes_x, prob.nodes_y = I.uniform_nodes(12, 10, 0, 1, 0, 0.9)
+    out = []
+    for graph, tv, stages in ((1, 8, 8), (0, 8, 8), (1, 2, 4), (0, 4, 4)):
+        for prec in ("fp64", "mixed"):
+            s = _solver(prob, prec)
+            s.set_tuning(graph=graph, sweep_tv=tv, sweep_stages=stages, macro_stages=stages)
+            s.init_uniform()
+            s.iterate(37)
+            G, H, W = s.get_state()
+            out.append((prec, G, W, s.residual_history()))
+    for prec in ("fp64", "mixed"):
+        ref = [o for o in out if o[0] == prec]
+        for o in ref[1:]:
+            assert np.array_equal(o[1], ref[0][1]) and np.array_equal(o[2], ref[0][2])
+            assert np.array_equal(o[3], ref[0][3])
