@@ -46,6 +46,7 @@ SIGNATURES = [
     ("idg_set_tuning", _i, [_vp, _i, _i]),
     ("idg_get_tuning", _i, [_vp, _i, _P(_i)]),
     ("idg_get_moments", _i, [_vp, _P(_d), _vp]),
+    ("idg_get_moments_noalloc", _i, [_vp, _vp, _vp]),
     ("idg_get_residual_history", _i, [_vp, _P(_d), _i, _P(_i)]),
     ("idg_get_face_flux_moments", _i, [_vp, _P(_d), _vp]),
     ("idg_get_sizes", _i, [_vp, _P(_i), _P(_i), _P(_i)]),
@@ -185,6 +186,10 @@ def idg_get_moments(ctx, N, stream=None):
     out = np.zeros((N, 6))
     check(ctx, lib().idg_get_moments(ctx, dptr(out), stream))
     return out
+
+
+def idg_get_moments_noalloc(ctx, out6_dev_ptr: int, stream=None):
+    return check(ctx, lib().idg_get_moments_noalloc(ctx, C.c_void_p(out6_dev_ptr), stream))
 
 
 def idg_get_residual_history(ctx, cap):

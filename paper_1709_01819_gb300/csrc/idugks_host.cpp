@@ -1066,6 +1066,25 @@ idg_status idg_get_moments(idg_ctx *c, double *out6, void *stream)
     return IDG_OK;
 }
 
+idg_status idg_get_moments_noalloc(idg_ctx *c, double *out6_dev, void *stream)
+{
+    idg_status s = check_ready(c);
+    if (s) return s;
+    if (!out6_dev) return fail(c, IDG_ERR_ARG, "null output");
+    if (c->N > idg::kNoAllocMaxCells)
+        return fail(c, IDG_ERR_ARG, "idg_get_moments_noalloc handles at most %d cells (this mesh has %d)",
+                    idg::kNoAllocMaxCells, c->N);
+    cudaPointerAttributes at{};
+    cudaError_t e = cudaPointerGetAttributes(&at, out6_dev);
+    if (e != cudaSuccess || at.type != cudaMemoryTypeDevice || at.device != c->device) {
+        cudaGetLastError();
+        return fail(c, IDG_ERR_ARG, "output is not device memory of device %d", c->device);
+    }
+    int rc = idg::launch_cell_moments_noalloc(c->kp, c->precision == IDG_FP64, c->device, out6_dev, stream);
+    if (rc) return cuda_fail(c, (cudaError_t)rc, "moments (no-allocation variant)");
+    return IDG_OK;
+}
+
 idg_status idg_get_residual_history(idg_ctx *c, double *out, int cap, int *n)
 {
     if (!c || (!out && cap > 0) || cap < 0) return IDG_ERR_ARG;

@@ -11,6 +11,7 @@ constexpr int kMaxVel = 16384;
 constexpr int kMaxHist = 1 << 16;  // residual-history ring (iterations)
 constexpr int kCellP = 16;         // per-cell / per-face coefficient records
 constexpr int kRaw = 11;           // raw velocity moments kept per cell / face
+constexpr int kNoAllocMaxCells = 16384;  // cell limit of idg_get_moments_noalloc
 
 // Everything one kernel launch needs, passed by value.  Device pointers point
 // into the caller's workspace.  "T" below is the storage precision (float for
@@ -87,6 +88,8 @@ constexpr int kProfiled = 6;  // timed groups in launch_iteration(events)
 int launch_iteration(const KParams &p, bool fp64, void *stream, void **events = nullptr);
 int launch_cell_moments(const KParams &p, bool fp64, double *out6_dev, void *stream);
 int launch_face_phi(const KParams &p, bool fp64, void *stream);
+// idg_get_moments_noalloc: raw moments in a static device array (no workspace)
+int launch_cell_moments_noalloc(const KParams &p, bool fp64, int device, double *out6_dev, void *stream);
 int launch_to_dev(const KParams &p, bool fp64, const double *G, const double *H, void *stream);
 int launch_from_dev(const KParams &p, bool fp64, double *G, double *H, void *stream);
 

@@ -1275,6 +1275,56 @@ int launch_cell_moments(const KParams &p, bool fp64, double *out6_dev, void *str
     return (int)cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// moments without a workspace scratch region
+// ---------------------------------------------------------------------------
+// Raw-moment scratch of idg_get_moments_noalloc: kNoAllocMaxCells cells x
+// kRaw accumulators of 8 bytes (1.375 MiB), held by every GPU that loads the
+// library until the process exits.  Every call overwrites all entries it
+// reads, so nothing needs clearing; calls that overlap on the GPU race on it.
+static __device__ __align__(256) unsigned char g_noalloc_raw[(size_t)kNoAllocMaxCells * kRaw * 8];
+
+// Device address of the scratch, resolved once per device with that device
+// current (a host-side use of the symbol's name is not a device address).
+static void *noalloc_scratch(int device, int *err)
+{
+    static void *addr[64] = {nullptr};
+    *err = 0;
+    if (device < 0 || device >= 64) {
+        *err = (int)cudaErrorInvalidDevice;
+        return nullptr;
+    }
+    if (!addr[device]) {
+        void *ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_raw);
+        if (e != cudaSuccess) {
+            *err = (int)e;
+            return nullptr;
+        }
+        addr[device] = ptr;
+    }
+    return addr[device];
+}
+
+int launch_cell_moments_noalloc(const KParams &p0, bool fp64, int device, double *out6_dev, void *stream)
+{
+    if (p0.N > kNoAllocMaxCells) return (int)cudaErrorInvalidValue;
+    int err = 0;
+    void *scratch = noalloc_scratch(device, &err);
+    if (!scratch) return err;
+    KParams p = p0;
+    p.cellraw = scratch;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (fp64) {
+        k_cell_moments<double><<<nblk(p.N, 8), 256, 0, st>>>(p);
+        k_moments_out<double><<<nblk(p.N, 256), 256, 0, st>>>(p, out6_dev);
+    } else {
+        k_cell_moments<float><<<nblk(p.N, 8), 256, 0, st>>>(p);
+        k_moments_out<float><<<nblk(p.N, 256), 256, 0, st>>>(p, out6_dev);
+    }
+    return (int)cudaGetLastError();
+}
+
 int launch_face_phi(const KParams &p, bool fp64, void *stream)
 {
     cudaStream_t st = (cudaStream_t)stream;
