@@ -192,6 +192,30 @@ idg_status idg_get_sizes(const idg_ctx *ctx, int *ncell, int *nvel, int *nface);
 idg_status idg_get_dt(const idg_ctx *ctx, double *dt);
 idg_status idg_velocity_grid(const idg_ctx *ctx, double *ux, double *uy, double *w);
 
+/* ---------------------------------------------------------------------------
+ * Batches: several bound contexts (same precision and device; sizes, gases,
+ * boundaries and tunings may differ) advanced together, each kernel of an
+ * iteration launched once over all of them (blocks map to instances through
+ * prefix sums), chunks of iterations replayed as CUDA graphs.  An instance
+ * stops iterating once its own relative residual is <= tol; the others go
+ * on.  Residual histories and states stay in each context (idg_get_*).
+ * A context may belong to one batch at a time and must not be iterated on
+ * its own while a batch call is running.
+ * ------------------------------------------------------------------------- */
+typedef struct idg_batch idg_batch;
+idg_status idg_batch_create(idg_batch **out, idg_ctx *const *ctxs, int n);
+void idg_batch_destroy(idg_batch *b);
+const char *idg_batch_last_error(const idg_batch *b);
+/* small device workspace for the batch's tables (caller-owned, 256-B aligned) */
+idg_status idg_batch_workspace_size(idg_batch *b, size_t *bytes);
+idg_status idg_batch_bind_workspace(idg_batch *b, void *dev_ptr, size_t bytes);
+/* Up to max_iter iterations of every unconverged instance.  converged (may
+ * be NULL): per instance 1 if its relative residual is <= tol.  max_residual:
+ * the largest relative residual.  Returns IDG_ERR_NOT_CONVERGED if tol > 0
+ * and an instance is left above it, IDG_ERR_NONFINITE if one diverged. */
+idg_status idg_batch_iterate(idg_batch *b, int max_iter, double tol, void *stream, int *iters_done,
+                             double *max_residual, int *converged);
+
 #ifdef __cplusplus
 }
 #endif

@@ -52,6 +52,12 @@ SIGNATURES = [
     ("idg_get_sizes", _i, [_vp, _P(_i), _P(_i), _P(_i)]),
     ("idg_get_dt", _i, [_vp, _P(_d)]),
     ("idg_velocity_grid", _i, [_vp, _P(_d), _P(_d), _P(_d)]),
+    ("idg_batch_create", _i, [_P(_vp), _P(_vp), _i]),
+    ("idg_batch_destroy", None, [_vp]),
+    ("idg_batch_last_error", C.c_char_p, [_vp]),
+    ("idg_batch_workspace_size", _i, [_vp, _P(_sz)]),
+    ("idg_batch_bind_workspace", _i, [_vp, _vp, _sz]),
+    ("idg_batch_iterate", _i, [_vp, _i, _d, _vp, _P(_i), _P(_d), _P(_i)]),
 ]
 
 _lib = None
@@ -221,3 +227,47 @@ def idg_velocity_grid(ctx, Nv):
     ux, uy, w = np.zeros(Nv), np.zeros(Nv), np.zeros(Nv)
     check(ctx, lib().idg_velocity_grid(ctx, dptr(ux), dptr(uy), dptr(w)))
     return ux, uy, w
+
+
+# ---- batches ----
+
+def _bcheck(b, status: int, allow=()):
+    if status != IDG_OK and status not in allow:
+        msg = lib().idg_batch_last_error(b)
+        raise IdgError(status, msg.decode() if msg else "")
+    return status
+
+
+def idg_batch_create(ctxs):
+    arr = (C.c_void_p * len(ctxs))(*[c.value if isinstance(c, C.c_void_p) else c for c in ctxs])
+    h = C.c_void_p()
+    _bcheck(None, lib().idg_batch_create(C.byref(h), arr, len(ctxs)))
+    return h
+
+
+def idg_batch_destroy(b):
+    lib().idg_batch_destroy(b)
+
+
+def idg_batch_last_error(b) -> str:
+    m = lib().idg_batch_last_error(b)
+    return m.decode() if m else ""
+
+
+def idg_batch_workspace_size(b) -> int:
+    n = C.c_size_t()
+    _bcheck(b, lib().idg_batch_workspace_size(b, C.byref(n)))
+    return n.value
+
+
+def idg_batch_bind_workspace(b, dev_ptr: int, nbytes: int):
+    return _bcheck(b, lib().idg_batch_bind_workspace(b, C.c_void_p(dev_ptr), nbytes))
+
+
+def idg_batch_iterate(b, n_inst, max_iter, tol, stream=None):
+    it = C.c_int()
+    r = C.c_double()
+    conv = (C.c_int * n_inst)()
+    st = _bcheck(b, lib().idg_batch_iterate(b, max_iter, tol, stream, C.byref(it), C.byref(r), conv),
+                 allow=(IDG_ERR_NOT_CONVERGED,))
+    return st, it.value, r.value, [bool(x) for x in conv]

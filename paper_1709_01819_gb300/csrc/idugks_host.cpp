@@ -47,6 +47,8 @@ struct idg_ctx {
     char *ws = nullptr;
     size_t ws_bytes = 0;
     KParams kp{};
+    KParams *kp_dev = nullptr;  // device copy of kp read by the iteration kernels
+    idg::Plan plan{};           // single-instance launch plan
     double *moments_dev = nullptr;
     double *stage = nullptr;  // staging for host<->device state copies (aliases F)
     size_t stage_bytes = 0;
@@ -433,9 +435,11 @@ size_t layout(idg_ctx *c, char *base, KParams *kp)
     k.iter = L.take<int>(256);
     k.status = k.iter + 1;
     double *mom = L.take<double>(48 * N);
+    KParams *kdev = L.take<KParams>(sizeof(KParams));
     if (kp) {
         *kp = k;
         c->moments_dev = mom;
+        c->kp_dev = kdev;
     }
     return L.off + 256;
 }
@@ -583,7 +587,7 @@ idg_status launch_chunk_graph(idg_ctx *c, cudaStream_t st, int n)
             return cuda_fail(c, e, "cudaStreamBeginCapture");
         int rc = 0;
         for (int q = 0; q < n && !rc; ++q)
-            rc = idg::launch_iteration(c->kp, c->precision == IDG_FP64, c->gstream);
+            rc = idg::launch_iteration(c->plan, c->precision == IDG_FP64, c->gstream);
         e = cudaStreamEndCapture(c->gstream, &g);
         if (rc || e != cudaSuccess) {
             if (g) cudaGraphDestroy(g);
@@ -601,6 +605,30 @@ idg_status launch_chunk_graph(idg_ctx *c, cudaStream_t st, int n)
     if ((e = cudaGraphLaunch(gx, c->gstream)) != cudaSuccess) return cuda_fail(c, e, "cudaGraphLaunch");
     if ((e = cudaEventRecord(c->ev_out, c->gstream)) != cudaSuccess) return cuda_fail(c, e, "event");
     if ((e = cudaStreamWaitEvent(st, c->ev_out, 0)) != cudaSuccess) return cuda_fail(c, e, "wait");
+    return IDG_OK;
+}
+
+// Single-instance launch plan and the device copy of the parameters; call
+// whenever kp changes (no iteration may be in flight: the library's own
+// stream is drained first).
+idg_status refresh_plan(idg_ctx *c)
+{
+    idg::Plan pl{};
+    pl.dparams = c->kp_dev;
+    pl.doff = nullptr;
+    pl.dactive = nullptr;
+    pl.ninst = 1;
+    idg::blocks_per_instance(c->kp, pl.nblocks);
+    if (idg::plan_shapes(&c->kp, 1, c->precision == IDG_FP64, pl))
+        return fail(c, IDG_ERR_ARG, "launch shape does not fit in shared memory");
+    c->kp.macro_stages = pl.macro_stages;
+    c->kp.sweep_stages = pl.sweep_stages;
+    cudaError_t e;
+    if (c->gstream && (e = cudaStreamSynchronize(c->gstream)) != cudaSuccess) return cuda_fail(c, e, "sync");
+    if ((e = cudaMemcpy(c->kp_dev, &c->kp, sizeof(KParams), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cuda_fail(c, e, "upload parameters");
+    c->plan = pl;
+    drop_graph(c);
     return IDG_OK;
 }
 
@@ -800,12 +828,10 @@ idg_status idg_bind_workspace(idg_ctx *c, void *dev_ptr, size_t bytes)
     k.sweep_tv = 8;
     while (k.sweep_tv > 1 && k.sweep_tv * k.sweep_pc > 1024) k.sweep_tv /= 2;
     while (k.sweep_tv < 32 && 2 * k.sweep_tv * k.sweep_pc <= 256) k.sweep_tv *= 2;
-    // deepest prefetch pipeline that fits in shared memory
-    const bool fp64 = c->precision == IDG_FP64;
+    // prefetch depth: 8 hyperplanes where shared memory allows (the plan
+    // falls back to 4)
     k.macro_stages = 8;
-    if (idg::sweep_smem_need(k, fp64, 0) > 227 * 1024) k.macro_stages = 4;
     k.sweep_stages = 8;
-    if (idg::sweep_smem_need(k, fp64, 1) > 227 * 1024) k.sweep_stages = 4;
     // uploads
     std::vector<float> uxf(c->ux.begin(), c->ux.end()), uyf(c->uy.begin(), c->uy.end()),
         wf(c->w.begin(), c->w.end());
@@ -840,13 +866,13 @@ idg_status idg_bind_workspace(idg_ctx *c, void *dev_ptr, size_t bytes)
         cudaMemset(k.iter, 0, 256), cudaMemset(k.phi, 0, 32 * (size_t)c->nf)};
     for (cudaError_t x : errs)
         if (x != cudaSuccess) return cuda_fail(c, x, "workspace upload");
-    int rcfg = idg::configure_kernels(k, c->precision == IDG_FP64);
-    if (rcfg) return fail(c, IDG_ERR_ARG, "mesh too wide for the sweep kernels' shared memory (%s)",
-                          cudaGetErrorString((cudaError_t)rcfg));
+    int rcfg = idg::configure_kernels(c->precision == IDG_FP64);
+    if (rcfg) return cuda_fail(c, (cudaError_t)rcfg, "configure kernels");
     c->stage = (double *)k.F;
     c->stage_bytes = (c->precision == IDG_FP64 ? 16 : 8) * (size_t)c->nf * c->Nv;
     c->bound = true;
     idg_status st = upload_reference(c);
+    if (!st) st = refresh_plan(c);
     if (st) { c->bound = false; return st; }
     c->host_iter = 0;
     restart(c);
@@ -863,8 +889,8 @@ idg_status idg_init_uniform(idg_ctx *c, double rho, double u, double v, double T
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(c, e, "sync");
     c->ref_rho = rho; c->ref_u = u; c->ref_v = v; c->ref_T = T;
-    drop_graph(c);
     if ((s = upload_reference(c))) return s;
+    if ((s = refresh_plan(c))) return s;
     const size_t t2 = c->precision == IDG_FP64 ? 16 : 8;
     // f~ = M_ref exactly: deviation zero
     if ((e = cudaMemsetAsync(c->kp.f, 0, t2 * (size_t)c->N * c->Nv, st)) != cudaSuccess)
@@ -946,7 +972,7 @@ idg_status idg_iterate(idg_ctx *c, int max_iter, double tol, void *stream, int *
             if ((s = launch_chunk_graph(c, st, n))) return s;
         } else {
             for (int q = 0; q < n; ++q) {
-                int rc = idg::launch_iteration(c->kp, fp64, st);
+                int rc = idg::launch_iteration(c->plan, fp64, st);
                 if (rc) return cuda_fail(c, (cudaError_t)rc, "launch");
             }
         }
@@ -991,7 +1017,7 @@ idg_status idg_iterate_profiled(idg_ctx *c, void *stream, double *kernel_ms)
             return cuda_fail(c, e, "cudaEventCreate");
         }
     }
-    int rc = idg::launch_iteration(c->kp, c->precision == IDG_FP64, st, (void **)ev);
+    int rc = idg::launch_iteration(c->plan, c->precision == IDG_FP64, st, (void **)ev);
     cudaError_t e = rc ? (cudaError_t)rc : cudaStreamSynchronize(st);
     double r = 0.0;
     if (e == cudaSuccess) {
@@ -1033,10 +1059,17 @@ idg_status idg_set_tuning(idg_ctx *c, int key, int value)
     } else {
         return fail(c, IDG_ERR_ARG, "unknown tuning key %d", key);
     }
-    int rc = idg::configure_kernels(k, c->precision == IDG_FP64);
-    if (rc) return fail(c, IDG_ERR_ARG, "launch shape does not fit in shared memory");
+    idg::Plan trial{};
+    idg::blocks_per_instance(k, trial.nblocks);
+    if (idg::plan_shapes(&k, 1, c->precision == IDG_FP64, trial) ||
+        trial.sweep_stages != k.sweep_stages || trial.macro_stages != k.macro_stages)
+        return fail(c, IDG_ERR_ARG, "launch shape does not fit in shared memory");
+    KParams old = c->kp;
     c->kp = k;
-    drop_graph(c);
+    if ((s = refresh_plan(c))) {
+        c->kp = old;
+        return s;
+    }
     return IDG_OK;
 }
 
@@ -1046,8 +1079,8 @@ idg_status idg_get_tuning(const idg_ctx *c, int key, int *value)
     if (!c->bound) return IDG_ERR_STATE;
     if (key == IDG_TUNE_GRAPH) *value = c->use_graph;
     else if (key == IDG_TUNE_SWEEP_TV) *value = c->kp.sweep_tv;
-    else if (key == IDG_TUNE_SWEEP_STAGES) *value = c->kp.sweep_stages;
-    else if (key == IDG_TUNE_MACRO_STAGES) *value = c->kp.macro_stages;
+    else if (key == IDG_TUNE_SWEEP_STAGES) *value = c->plan.sweep_stages;
+    else if (key == IDG_TUNE_MACRO_STAGES) *value = c->plan.macro_stages;
     else return IDG_ERR_ARG;
     return IDG_OK;
 }
@@ -1103,6 +1136,297 @@ idg_status idg_get_face_flux_moments(idg_ctx *c, double *phi4, void *stream)
     cudaError_t e = cudaMemcpyAsync(phi4, c->kp.phi, (size_t)c->nf * 32, cudaMemcpyDeviceToHost, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "D2H phi");
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(c, e, "sync");
+    return IDG_OK;
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// batches: many contexts advanced by one launch per kernel
+// ===========================================================================
+struct idg_batch {
+    std::vector<idg_ctx *> ctx;
+    int precision = IDG_FP64, device = 0;
+    std::string err;
+    bool bound = false;
+    char *ws = nullptr;
+    size_t ws_bytes = 0;
+    KParams *dparams = nullptr;
+    int *doff = nullptr, *dactive = nullptr;
+    int *dstatus = nullptr;     // [n] gathered status words
+    double *dres = nullptr;     // [n][kGraphChunk] gathered residuals of the last chunk
+    std::vector<KParams> hparams;
+    std::vector<int> active;
+    idg::Plan plan{};
+    int use_graph = 1;
+    cudaStream_t gstream = nullptr;
+    cudaGraphExec_t gexec = nullptr, gexec1 = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+};
+
+namespace idg {
+int launch_batch_gather(const KParams *dparams, int n, int last, double *dres, int *dstatus, void *stream);
+}
+
+namespace {
+
+idg_status bfail(idg_batch *b, idg_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (b) b->err = buf;
+    return s;
+}
+
+size_t batch_layout(idg_batch *b, char *base)
+{
+    Layout L;
+    L.base = base;
+    const size_t n = b->ctx.size();
+    KParams *dp = L.take<KParams>(n * sizeof(KParams));
+    int *doff = L.take<int>((size_t)idg::KT_COUNT * (n + 1) * sizeof(int));
+    int *dact = L.take<int>(n * sizeof(int));
+    int *dst = L.take<int>(n * sizeof(int));
+    double *dres = L.take<double>(n * kGraphChunk * sizeof(double));
+    if (base) {
+        b->dparams = dp;
+        b->doff = doff;
+        b->dactive = dact;
+        b->dstatus = dst;
+        b->dres = dres;
+    }
+    return L.off + 256;
+}
+
+void batch_drop_graph(idg_batch *b)
+{
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->gexec1) cudaGraphExecDestroy(b->gexec1);
+    b->gexec = b->gexec1 = nullptr;
+}
+
+// (re)upload the instances' parameters and offsets, rebuild the plan
+idg_status batch_refresh(idg_batch *b)
+{
+    const int n = (int)b->ctx.size();
+    b->hparams.resize(n);
+    std::vector<int> off((size_t)idg::KT_COUNT * (n + 1), 0);
+    idg::Plan pl{};
+    for (int i = 0; i < n; ++i) {
+        b->hparams[i] = b->ctx[i]->kp;
+        int nbk[idg::KT_COUNT];
+        idg::blocks_per_instance(b->hparams[i], nbk);
+        for (int t = 0; t < idg::KT_COUNT; ++t) off[(size_t)t * (n + 1) + i + 1] = off[(size_t)t * (n + 1) + i] + nbk[t];
+    }
+    for (int t = 0; t < idg::KT_COUNT; ++t) pl.nblocks[t] = off[(size_t)t * (n + 1) + n];
+    if (idg::plan_shapes(b->hparams.data(), n, b->precision == IDG_FP64, pl))
+        return bfail(b, IDG_ERR_ARG, "batch launch shape does not fit in shared memory");
+    pl.dparams = b->dparams;
+    pl.doff = b->doff;
+    pl.dactive = b->dactive;
+    pl.ninst = n;
+    cudaError_t e;
+    if (b->gstream && (e = cudaStreamSynchronize(b->gstream)) != cudaSuccess)
+        return bfail(b, IDG_ERR_CUDA, "sync: %s", cudaGetErrorString(e));
+    if ((e = cudaMemcpy(b->dparams, b->hparams.data(), n * sizeof(KParams), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(b->doff, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(b->dactive, b->active.data(), n * sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return bfail(b, IDG_ERR_CUDA, "batch upload: %s", cudaGetErrorString(e));
+    b->plan = pl;
+    batch_drop_graph(b);
+    return IDG_OK;
+}
+
+idg_status batch_launch(idg_batch *b, cudaStream_t st, int n)
+{
+    const bool fp64 = b->precision == IDG_FP64;
+    if (!b->use_graph || (n != 1 && n != kGraphChunk)) {
+        for (int q = 0; q < n; ++q) {
+            int rc = idg::launch_iteration(b->plan, fp64, st);
+            if (rc) return bfail(b, IDG_ERR_CUDA, "launch: %s", cudaGetErrorString((cudaError_t)rc));
+        }
+        return IDG_OK;
+    }
+    cudaError_t e;
+    if (!b->gstream) {
+        if ((e = cudaStreamCreateWithFlags(&b->gstream, cudaStreamNonBlocking)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming)) != cudaSuccess)
+            return bfail(b, IDG_ERR_CUDA, "stream/event: %s", cudaGetErrorString(e));
+    }
+    cudaGraphExec_t &gx = n == 1 ? b->gexec1 : b->gexec;
+    if (!gx) {
+        cudaGraph_t g = nullptr;
+        if ((e = cudaStreamBeginCapture(b->gstream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+            return bfail(b, IDG_ERR_CUDA, "capture: %s", cudaGetErrorString(e));
+        int rc = 0;
+        for (int q = 0; q < n && !rc; ++q) rc = idg::launch_iteration(b->plan, fp64, b->gstream);
+        e = cudaStreamEndCapture(b->gstream, &g);
+        if (rc || e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return bfail(b, IDG_ERR_CUDA, "graph capture failed");
+        }
+        e = cudaGraphInstantiate(&gx, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            gx = nullptr;
+            return bfail(b, IDG_ERR_CUDA, "instantiate: %s", cudaGetErrorString(e));
+        }
+    }
+    if ((e = cudaEventRecord(b->ev_in, st)) != cudaSuccess || (e = cudaStreamWaitEvent(b->gstream, b->ev_in, 0)) != cudaSuccess ||
+        (e = cudaGraphLaunch(gx, b->gstream)) != cudaSuccess || (e = cudaEventRecord(b->ev_out, b->gstream)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(st, b->ev_out, 0)) != cudaSuccess)
+        return bfail(b, IDG_ERR_CUDA, "graph launch: %s", cudaGetErrorString(e));
+    return IDG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+idg_status idg_batch_create(idg_batch **out, idg_ctx *const *ctxs, int n)
+{
+    if (!out || !ctxs || n < 1) return IDG_ERR_ARG;
+    *out = nullptr;
+    for (int i = 0; i < n; ++i) {
+        if (!ctxs[i] || !ctxs[i]->bound) return IDG_ERR_STATE;
+        if (ctxs[i]->precision != ctxs[0]->precision || ctxs[i]->device != ctxs[0]->device) return IDG_ERR_ARG;
+        for (int j = 0; j < i; ++j)
+            if (ctxs[j] == ctxs[i]) return IDG_ERR_ARG;
+    }
+    idg_batch *b = new idg_batch();
+    b->ctx.assign(ctxs, ctxs + n);
+    b->precision = ctxs[0]->precision;
+    b->device = ctxs[0]->device;
+    b->active.assign(n, 1);
+    *out = b;
+    return IDG_OK;
+}
+
+void idg_batch_destroy(idg_batch *b)
+{
+    if (!b) return;
+    if (b->bound) {
+        cudaSetDevice(b->device);
+        batch_drop_graph(b);
+        if (b->ev_in) cudaEventDestroy(b->ev_in);
+        if (b->ev_out) cudaEventDestroy(b->ev_out);
+        if (b->gstream) cudaStreamDestroy(b->gstream);
+    }
+    delete b;
+}
+
+const char *idg_batch_last_error(const idg_batch *b) { return b ? b->err.c_str() : "null batch"; }
+
+idg_status idg_batch_workspace_size(idg_batch *b, size_t *bytes)
+{
+    if (!b || !bytes) return IDG_ERR_ARG;
+    *bytes = batch_layout(b, nullptr);
+    return IDG_OK;
+}
+
+idg_status idg_batch_bind_workspace(idg_batch *b, void *dev_ptr, size_t bytes)
+{
+    if (!b || !dev_ptr) return IDG_ERR_ARG;
+    size_t need = batch_layout(b, nullptr);
+    if (bytes < need) return bfail(b, IDG_ERR_OOM, "batch workspace of %zu bytes, need %zu", bytes, need);
+    if (((uintptr_t)dev_ptr) & 255) return bfail(b, IDG_ERR_ARG, "workspace must be 256-byte aligned");
+    cudaError_t e = cudaSetDevice(b->device);
+    if (e != cudaSuccess) return bfail(b, IDG_ERR_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+    b->ws = (char *)dev_ptr;
+    b->ws_bytes = bytes;
+    batch_layout(b, b->ws);
+    b->bound = true;
+    idg_status s = batch_refresh(b);
+    if (s) b->bound = false;
+    return s;
+}
+
+idg_status idg_batch_iterate(idg_batch *b, int max_iter, double tol, void *stream, int *iters_done,
+                             double *max_residual, int *converged)
+{
+    if (!b || max_iter < 0) return IDG_ERR_ARG;
+    if (!b->bound) return bfail(b, IDG_ERR_STATE, "batch workspace not bound");
+    cudaError_t e = cudaSetDevice(b->device);
+    if (e != cudaSuccess) return bfail(b, IDG_ERR_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n = (int)b->ctx.size();
+    // pick up any change of an instance (restart, tuning) since the last call
+    bool stale = false;
+    for (int i = 0; i < n; ++i)
+        if (std::memcmp(&b->hparams[i], &b->ctx[i]->kp, sizeof(KParams))) stale = true;
+    std::vector<int> act(n);
+    for (int i = 0; i < n; ++i) {
+        const idg_ctx *c = b->ctx[i];
+        double rel = c->hist.empty() ? INFINITY : (c->hist.front() > 0 ? c->hist.back() / c->hist.front() : c->hist.back());
+        act[i] = !(tol > 0 && rel <= tol);
+    }
+    if (stale || act != b->active) {
+        b->active = act;
+        idg_status s = batch_refresh(b);
+        if (s) return s;
+    }
+    std::vector<double> res((size_t)n * kGraphChunk);
+    std::vector<int> status(n);
+    int done = 0;
+    idg_status ret = IDG_OK;
+    while (done < max_iter) {
+        int any = 0;
+        for (int i = 0; i < n; ++i) any |= b->active[i];
+        if (!any) break;
+        int m = std::min(kGraphChunk, max_iter - done);
+        idg_status s = batch_launch(b, st, m);
+        if (s) return s;
+        done += m;
+        int rc = idg::launch_batch_gather(b->dparams, n, m, b->dres, b->dstatus, st);
+        if (rc) return bfail(b, IDG_ERR_CUDA, "gather: %s", cudaGetErrorString((cudaError_t)rc));
+        if ((e = cudaMemcpyAsync(res.data(), b->dres, res.size() * 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(status.data(), b->dstatus, n * sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(st)) != cudaSuccess)
+            return bfail(b, IDG_ERR_CUDA, "batch residuals: %s", cudaGetErrorString(e));
+        bool changed = false;
+        for (int i = 0; i < n; ++i) {
+            if (!b->active[i]) continue;
+            idg_ctx *c = b->ctx[i];
+            for (int q = 0; q < m; ++q) c->hist.push_back(res[(size_t)i * kGraphChunk + q]);
+            c->host_iter += m;
+            if (status[i]) {
+                ret = IDG_ERR_NONFINITE;
+                fail(c, IDG_ERR_NONFINITE, "residual became non-finite");
+                b->active[i] = 0;
+                changed = true;
+                continue;
+            }
+            double r1 = c->hist.front();
+            double rel = r1 > 0 ? c->hist.back() / r1 : c->hist.back();
+            if (tol > 0 && rel <= tol) {
+                b->active[i] = 0;
+                changed = true;
+            }
+        }
+        if (changed && done < max_iter) {
+            if ((e = cudaMemcpyAsync(b->dactive, b->active.data(), n * sizeof(int), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+                (e = cudaStreamSynchronize(st)) != cudaSuccess)
+                return bfail(b, IDG_ERR_CUDA, "active flags: %s", cudaGetErrorString(e));
+        }
+    }
+    double worst = 0.0;
+    int all = 1;
+    for (int i = 0; i < n; ++i) {
+        const idg_ctx *c = b->ctx[i];
+        double rel = c->hist.empty() ? INFINITY : (c->hist.front() > 0 ? c->hist.back() / c->hist.front() : c->hist.back());
+        int conv = tol > 0 && rel <= tol;
+        if (converged) converged[i] = conv;
+        all &= conv;
+        worst = std::max(worst, rel);
+    }
+    if (iters_done) *iters_done = done;
+    if (max_residual) *max_residual = worst;
+    if (ret) return bfail(b, ret, "an instance became non-finite");
+    if (tol > 0 && !all) return bfail(b, IDG_ERR_NOT_CONVERGED, "largest residual %.3e above tol %.3e", worst, tol);
     return IDG_OK;
 }
 

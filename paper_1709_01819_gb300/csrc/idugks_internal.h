@@ -80,14 +80,34 @@ struct KParams {
     int sweep_tv, sweep_pc, sweep_stages, macro_stages;
 };
 
+// kernels of one iteration, in launch order
+enum KType {
+    KT_CELL_MOM, KT_CELL_PAR, KT_FBP, KT_FACE_MOM, KT_FACE_PAR, KT_FACE_FLUX, KT_FACE_PHI,
+    KT_MACRO_PRE, KT_MACRO_SWEEP, KT_MACRO_POST, KT_MICRO_RES, KT_SWEEP, KT_COUNT
+};
+
+// How one iteration is launched over one or many instances: the instances'
+// parameters in device memory, per-kernel prefix sums of blocks per instance
+// (null for a single instance), activity flags (null: all active), and the
+// block shapes common to all instances.
+struct Plan {
+    const KParams *dparams;
+    const int *doff;     // [KT_COUNT][ninst + 1]
+    const int *dactive;  // [ninst]
+    int ninst;
+    int nblocks[KT_COUNT];
+    int macro_threads, sweep_threads;
+    size_t macro_smem, fwd_smem, bwd_smem;
+    int macro_stages, sweep_stages, limiter_any;
+};
+
 // kernel launchers (idugks_kernels.cu)
-int configure_kernels(const KParams &p, bool fp64);
-// shared memory of the macro sweep (which = 0) or of the backward micro sweep (1)
-size_t sweep_smem_need(const KParams &p, bool fp64, int which);
+int configure_kernels(bool fp64);
+void blocks_per_instance(const KParams &p, int out[KT_COUNT]);
+int plan_shapes(const KParams *hp, int n, bool fp64, Plan &plan);
 constexpr int kProfiled = 6;  // timed groups in launch_iteration(events)
-int launch_iteration(const KParams &p, bool fp64, void *stream, void **events = nullptr);
+int launch_iteration(const Plan &plan, bool fp64, void *stream, void **events = nullptr);
 int launch_cell_moments(const KParams &p, bool fp64, double *out6_dev, void *stream);
-int launch_face_phi(const KParams &p, bool fp64, void *stream);
 // idg_get_moments_noalloc: raw moments in a static device array (no workspace)
 int launch_cell_moments_noalloc(const KParams &p, bool fp64, int device, double *out6_dev, void *stream);
 int launch_to_dev(const KParams &p, bool fp64, const double *G, const double *H, void *stream);

@@ -165,6 +165,44 @@ __device__ void block_sum(double (&v)[NV], double *sm /* >= 32*NV */)
 }
 
 // ---------------------------------------------------------------------------
+// launches over one or many problem instances
+// ---------------------------------------------------------------------------
+// Every iteration kernel takes a Launch: the instances' parameters in device
+// memory, the prefix sums of blocks per instance for this kernel (null for a
+// single instance) and per-instance activity flags (converged instances of a
+// batch are skipped).  A block finds its instance by binary search.
+struct Launch {
+    const KParams *params;
+    const int *off;     // [ninst + 1] or null
+    const int *active;  // [ninst] or null
+    int ninst;
+};
+
+__device__ __forceinline__ bool locate(const Launch &L, const KParams *&pp, int &blk)
+{
+    int b = blockIdx.x, inst = 0;
+    if (L.off) {
+        int lo = 0, hi = L.ninst;
+        while (hi - lo > 1) {
+            int mid = (lo + hi) >> 1;
+            if (L.off[mid] <= b) lo = mid;
+            else hi = mid;
+        }
+        inst = lo;
+        b -= L.off[lo];
+    }
+    pp = L.params + inst;
+    blk = b;
+    return !L.active || L.active[inst];
+}
+
+#define IDG_LOCATE()                                   \
+    const KParams *pp_;                                \
+    int blk;                                           \
+    if (!locate(L, pp_, blk)) return;                  \
+    const KParams &__restrict__ p = *pp_;
+
+// ---------------------------------------------------------------------------
 // kinetic model in float64 (per cell / per face quantities)
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double viscosity(const KParams &p, double RT)
@@ -321,11 +359,11 @@ __device__ __forceinline__ void vel_loop(int Nv, int lane, Acc<T> (&acc)[NA], Bo
 // cell moments and cell prep (Eq. 10, 12)                                [a1]
 // ---------------------------------------------------------------------------
 template <class T>
-__global__ void __launch_bounds__(256) k_cell_moments(KParams p)
+__device__ __forceinline__ void cell_moments_body(const KParams &__restrict__ p, int blk)
 {
     using T2 = typename V2<T>::t;
     const int lane = threadIdx.x & 31;
-    const int c = blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int c = blk * 8 + (threadIdx.x >> 5);
     if (c >= p.N) return;  // whole warp
     const T2 *f = (const T2 *)p.f + (size_t)c * p.Nv;
     Acc<T> acc[kRaw];
@@ -342,12 +380,27 @@ __global__ void __launch_bounds__(256) k_cell_moments(KParams p)
         for (int q = 0; q < kRaw; ++q) acc[q].store(p.cellraw, (size_t)c * kRaw + q);
 }
 
+template <class T>
+__global__ void __launch_bounds__(256) k_cell_moments(Launch L)
+{
+    IDG_LOCATE();
+    cell_moments_body<T>(p, blk);
+}
+
+// the same with the parameters passed by value (moment queries)
+template <class T>
+__global__ void __launch_bounds__(256) k_cell_moments_v(KParams p)
+{
+    cell_moments_body<T>(p, blockIdx.x);
+}
+
 // per cell: heat flux of f from f~ (about U of W), tau, equilibrium at W^n,
 // and the two coefficients of fb+ = (2tau-h)/(2tau+dt) f~ + 3h/(2tau+dt) f^S
 template <class T>
-__global__ void __launch_bounds__(32) k_cell_params(KParams p)
+__global__ void __launch_bounds__(32) k_cell_params(Launch L)
 {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    IDG_LOCATE();
+    const int c = blk * blockDim.x + threadIdx.x;
     if (c >= p.N) return;
     double r[kRaw];
     for (int q = 0; q < kRaw; ++q) r[q] = acc_load<T>(p.cellraw, (size_t)c * kRaw + q) + p.mref_raw[q];
@@ -369,11 +422,13 @@ __global__ void __launch_bounds__(32) k_cell_params(KParams p)
 }
 
 template <class T>
-__global__ void __launch_bounds__(256) k_fbp(KParams p)
+__global__ void __launch_bounds__(256) k_fbp(Launch L)
 {
+    IDG_LOCATE();
     using T2 = typename V2<T>::t;
-    const int c = blockIdx.x;
-    const int k = blockIdx.y * blockDim.x + threadIdx.x;
+    const int nvb = (p.Nv + 255) / 256;
+    const int c = blk / nvb;
+    const int k = (blk - c * nvb) * blockDim.x + threadIdx.x;
     if (k >= p.Nv) return;
     const T *cA = (const T *)p.cellA + kCellP * c;
     EqT<T> e = eq_loadT<T>(cA);
@@ -461,7 +516,7 @@ __device__ __forceinline__ typename V2<T>::t reconstruct(const KParams &p, const
     }
     T ax = r.rx - ux * h, ay = r.ry - uy * h;
     T pg = (T)1, ph = (T)1;
-    if (LIM) {
+    if (LIM && p.limiter) {
         pg = limit_scalar<T>(r, f0.x, gmax, gmin, sgx, sgy);
         ph = limit_scalar<T>(r, f0.y, hmax, hmin, shx, shy);
     }
@@ -540,12 +595,13 @@ __device__ __forceinline__ typename V2<T>::t face_fbar(const KParams &p, const F
 
 // raw moments of fb - M_ref at every face (plus the wall density, Eq. 35)
 template <class T, bool LIM>
-__global__ void __launch_bounds__(256) k_face_moments(KParams p)
+__global__ void __launch_bounds__(256) k_face_moments(Launch L)
 {
+    IDG_LOCATE();
     using T2 = typename V2<T>::t;
     __shared__ SideRec<T> srec[8][2];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int f = blockIdx.x * 8 + wid;
+    const int f = blk * 8 + wid;
     if (f >= p.nf) return;  // whole warp
     FaceCtx<T> fc;
     load_face<T>(p, f, srec[wid], fc);
@@ -596,9 +652,10 @@ __global__ void __launch_bounds__(256) k_face_moments(KParams p)
 // per face: state from the moments of fb, tau, q = 2 tau qbar/(2 tau + h Pr),
 // equilibrium, and the weights a, b of f = a fb + b f^S (Eq. 18)
 template <class T>
-__global__ void __launch_bounds__(32) k_face_params(KParams p)
+__global__ void __launch_bounds__(32) k_face_params(Launch L)
 {
-    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    IDG_LOCATE();
+    const int f = blk * blockDim.x + threadIdx.x;
     if (f >= p.nf) return;
     double r[kRaw];
     for (int q = 0; q < kRaw; ++q) r[q] = acc_load<T>(p.faceraw, (size_t)f * 12 + q) + p.mref_raw[q];
@@ -617,11 +674,12 @@ __global__ void __launch_bounds__(32) k_face_params(KParams p)
 // face flux of (f_face - M_ref), Eq. (18)-(19), and its moments; fb - M_ref
 // comes from k_face_moments through the same buffer and is overwritten
 template <class T>
-__global__ void __launch_bounds__(256) k_face_flux(KParams p)
+__global__ void __launch_bounds__(256) k_face_flux(Launch L)
 {
+    IDG_LOCATE();
     using T2 = typename V2<T>::t;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int f = blockIdx.x * 8 + wid;
+    const int f = blk * 8 + wid;
     if (f >= p.nf) return;  // whole warp
     const T *g = (const T *)p.fgeoT + 8 * f;
     const T nx = g[0], ny = g[1], S = g[2];
@@ -659,9 +717,10 @@ __global__ void __launch_bounds__(256) k_face_flux(KParams p)
 // Phi_f = sum_k w psi F_k (Eq. 27): deviation part plus the flux of M_ref;
 // the mass flux through an impermeable wall is exactly zero
 template <class T>
-__global__ void __launch_bounds__(256) k_face_phi(KParams p)
+__global__ void __launch_bounds__(256) k_face_phi(Launch L)
 {
-    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    IDG_LOCATE();
+    const int f = blk * blockDim.x + threadIdx.x;
     if (f >= p.nf) return;
     const double *g = p.fgeo + 7 * f;
     for (int q = 0; q < 4; ++q)
@@ -734,10 +793,11 @@ constexpr int kMRec = 44;    // macro sweep record: R[4], D, pad[3], 4 x (off[3]
 // per cell: R_W, ||R_W/Omega||^2 partials, and the packed record of the
 // macroscopic sweep (diagonal, neighbour coefficients, neighbour base state)
 template <class T>
-__global__ void __launch_bounds__(32) k_macro_pre(KParams p)
+__global__ void __launch_bounds__(32) k_macro_pre(Launch L)
 {
+    IDG_LOCATE();
     __shared__ double sm[32];
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blk * blockDim.x + threadIdx.x;
     double part[1] = {0.0};
     if (c < p.N) {
         T *rec = (T *)p.mrec + (size_t)kMRec * c;
@@ -780,7 +840,7 @@ __global__ void __launch_bounds__(32) k_macro_pre(KParams p)
         rec[6] = rec[7] = (T)0;
     }
     block_sum<1>(part, sm);
-    if (threadIdx.x == 0) p.mpart[blockIdx.x] = part[0];
+    if (threadIdx.x == 0) p.mpart[blk] = part[0];
 }
 
 // Exact increment F_n(W + dW) - F_n(W) of the Euler flux, written so that no
@@ -804,10 +864,9 @@ __device__ __forceinline__ void euler_dflux(T gm1, const T *b, const T *dW, T nx
 // one hyperplane step of the macroscopic sweep for the cell whose record
 // and links sit in shared memory (dir = +1 forward, -1 backward)
 template <class T>
-__device__ __forceinline__ void macro_cell(const KParams &p, int d, int i, int c, const T *rec,
+__device__ __forceinline__ void macro_cell(int ni, int d, int i, int c, const T *rec,
                                            const int *lk, const T *dWs, T *ring, T *dWg, int dir, T gm1)
 {
-    const int ni = p.ni;
     T acc[4] = {0, 0, 0, 0};
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
@@ -836,8 +895,9 @@ __device__ __forceinline__ void macro_cell(const KParams &p, int d, int i, int c
 // hyperplane; its record and links are prefetched kStages-1 hyperplanes ahead
 // with cp.async; the previous hyperplane's increments sit in a ring.
 template <class T, int kStages>
-__global__ void __launch_bounds__(1024) k_macro_sweep(KParams p)
+__global__ void __launch_bounds__(1024) k_macro_sweep(Launch L)
 {
+    IDG_LOCATE();
     extern __shared__ __align__(16) unsigned char smraw[];
     const int tid = threadIdx.x, nt = blockDim.x;
     const int ni = p.ni, nj = p.nj, nh = ni + nj - 1;
@@ -856,6 +916,8 @@ __global__ void __launch_bounds__(1024) k_macro_sweep(KParams p)
     }
     const T gm1 = (T)(p.gam - 1.0);
     T *dWg = (T *)p.mdW;
+    const T *mrec = (const T *)p.mrec;
+    const int *clink = p.clink;
     constexpr int RB = kMRec * sizeof(T);  // bytes of one record (multiple of 16)
     for (int dir = 1; dir >= -1; dir -= 2) {
         auto step_d = [&](int s) { return dir > 0 ? s : nh - 1 - s; };
@@ -867,10 +929,10 @@ __global__ void __launch_bounds__(1024) k_macro_sweep(KParams p)
                 if (i <= ihi) {
                     int c = (d - i) * ni + i;
                     int st = s & (kStages - 1);
-                    const char *gr = (const char *)((const T *)p.mrec + (size_t)kMRec * c);
+                    const char *gr = (const char *)(mrec + (size_t)kMRec * c);
                     char *sr = (char *)(srec + ((size_t)st * nt + tid) * kMRec);
                     for (int b = 0; b < RB; b += 16) cp_async16(sr + b, gr + b);
-                    const char *gl = (const char *)(p.clink + 12 * c);
+                    const char *gl = (const char *)(clink + 12 * c);
                     char *sl = (char *)(slnk + ((size_t)st * nt + tid) * 12);
                     for (int b = 0; b < 48; b += 16) cp_async16(sl + b, gl + b);
                     if (dir < 0) {
@@ -892,7 +954,7 @@ __global__ void __launch_bounds__(1024) k_macro_sweep(KParams p)
             int i = ilo + tid;
             if (i <= ihi) {
                 size_t e = (size_t)(s & (kStages - 1)) * nt + tid;
-                macro_cell<T>(p, d, i, (d - i) * ni + i, srec + e * kMRec, slnk + e * 12, sdw + e * 4,
+                macro_cell<T>(ni, d, i, (d - i) * ni + i, srec + e * kMRec, slnk + e * 12, sdw + e * 4,
                               ring, dWg, dir, gm1);
             }
         }
@@ -903,9 +965,10 @@ __global__ void __launch_bounds__(1024) k_macro_sweep(KParams p)
 }
 
 template <class T>
-__global__ void __launch_bounds__(32) k_macro_post(KParams p)
+__global__ void __launch_bounds__(32) k_macro_post(Launch L)
 {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    IDG_LOCATE();
+    const int c = blk * blockDim.x + threadIdx.x;
     if (c >= p.N) return;
     double *W = p.W + 4 * c;
     const T *dW = (const T *)p.mdW + 4 * c;
@@ -940,11 +1003,13 @@ __global__ void __launch_bounds__(32) k_macro_post(KParams p)
 // a periodic seam (earlier hyperplanes) are read back from global memory.
 // ---------------------------------------------------------------------------
 template <class T>
-__global__ void __launch_bounds__(256) k_micro_residual(KParams p)
+__global__ void __launch_bounds__(256) k_micro_residual(Launch L)
 {
+    IDG_LOCATE();
     using T2 = typename V2<T>::t;
-    const int c = blockIdx.x;
-    const int k = blockIdx.y * blockDim.x + threadIdx.x;
+    const int nvb = (p.Nv + 255) / 256;
+    const int c = blk / nvb;
+    const int k = (blk - c * nvb) * blockDim.x + threadIdx.x;
     if (k >= p.Nv) return;
     const T *cp = (const T *)p.cellpT + kCellP * c;
     const EqT<T> e = eq_loadT<T>(cp);
@@ -999,13 +1064,21 @@ template <class T, int kStages> static size_t sweep_smem_bytes(int pc, int tv, i
     return o;
 }
 
+// the parameters a sweep touches every step, held in registers
+struct SweepArgs {
+    int Nv, ni, nj, tv, pc;
+    void *dst, *f;
+    const void *cslotT, *cellpT;
+    const int *clink;
+};
+
 // asynchronous copy of one step's data for the thread's cell
 template <class T, int kStages>
-__device__ __forceinline__ void sweep_issue(const KParams &p, const SweepSmem<T, kStages> &sm, int s, int d,
+__device__ __forceinline__ void sweep_issue(const SweepArgs &p, const SweepSmem<T, kStages> &sm, int s, int d,
                                             int slot, int t, int k, bool act, bool withF)
 {
     using T2 = typename V2<T>::t;
-    const int ni = p.ni, nj = p.nj, tv = p.sweep_tv, pc = p.sweep_pc;
+    const int ni = p.ni, nj = p.nj, tv = p.tv, pc = p.pc;
     const int nh = ni + nj - 1;
     if (s < nh) {
         int ilo = max(0, d - (nj - 1)), ihi = min(ni - 1, d);
@@ -1031,27 +1104,29 @@ __device__ __forceinline__ void sweep_issue(const KParams &p, const SweepSmem<T,
 }
 
 template <class T, bool FWD, int kStages>
-__global__ void __launch_bounds__(1024) k_sweep(KParams p)
+__global__ void __launch_bounds__(1024) k_sweep(Launch L)
 {
+    IDG_LOCATE();
     using T2 = typename V2<T>::t;
     extern __shared__ __align__(16) unsigned char smraw[];
-    const int tv = p.sweep_tv, pc = p.sweep_pc, ni = p.ni, nj = p.nj;
+    const SweepArgs a{p.Nv, p.ni, p.nj, p.sweep_tv, p.sweep_pc, p.dst, p.f, p.cslotT, p.cellpT, p.clink};
+    const int tv = a.tv, pc = a.pc, ni = a.ni, nj = a.nj, Nv = a.Nv;
     const SweepSmem<T, kStages> sm(smraw, pc, tv, ni, !FWD);
     const int t = threadIdx.x % tv, slot = threadIdx.x / tv;
-    const int k = blockIdx.x * tv + t;
-    const bool act = k < p.Nv;
+    const int k = blk * tv + t;
+    const bool act = k < Nv;
     const int kk = act ? k : 0;
     const T ux = vx<T>(p, kk), uy = vy<T>(p, kk);
-    T2 *ds = (T2 *)p.dst;
-    T2 *f = (T2 *)p.f;
+    T2 *ds = (T2 *)a.dst;
+    T2 *f = (T2 *)a.f;
     const int nh = ni + nj - 1;
     const int dir = FWD ? 1 : -1;
     auto step_d = [&](int s) { return FWD ? s : nh - 1 - s; };
-    for (int s = 0; s < kStages - 1; ++s) sweep_issue<T, kStages>(p, sm, s, step_d(s), slot, t, k, act, !FWD);
+    for (int s = 0; s < kStages - 1; ++s) sweep_issue<T, kStages>(a, sm, s, step_d(s), slot, t, k, act, !FWD);
     for (int s = 0; s < nh; ++s) {
         cp_wait<kStages - 2>();
         __syncthreads();
-        sweep_issue<T, kStages>(p, sm, s + kStages - 1, step_d(s + kStages - 1), slot, t, k, act, !FWD);
+        sweep_issue<T, kStages>(a, sm, s + kStages - 1, step_d(s + kStages - 1), slot, t, k, act, !FWD);
         const int d = step_d(s);
         const int ilo = max(0, d - (nj - 1)), ihi = min(ni - 1, d);
         const int i = ilo + slot;
@@ -1071,13 +1146,13 @@ __global__ void __launch_bounds__(1024) k_sweep(KParams p)
             if (so > (T)0) D += aS;
             else if (so < (T)0 && nb >= 0 && (FWD ? nb < c : nb > c)) {
                 T2 dn = (lk[8 + m] == d - dir) ? sm.ring[(((d - dir) & 1) * ni + lk[4 + m]) * tv + t]
-                                               : ds[(size_t)nb * p.Nv + k];
+                                               : ds[(size_t)nb * Nv + k];
                 ag -= aS * dn.x;
                 ah -= aS * dn.y;
             }
         }
         const T2 r = sm.R[e * tv + t];
-        const size_t ck = (size_t)c * p.Nv + k;
+        const size_t ck = (size_t)c * Nv + k;
         const T iD = (T)1 / D;
         T2 o;
         if (FWD) {
@@ -1172,104 +1247,141 @@ template <class T> static size_t sweep_bytes(const KParams &p, bool withF, int s
                        : sweep_smem_bytes<T, 4>(p.sweep_pc, p.sweep_tv, p.ni, withF);
 }
 
-template <class T> static void launch_macro_sweep(const KParams &p, cudaStream_t st)
+void blocks_per_instance(const KParams &p, int out[KT_COUNT])
 {
-    int nt = macro_threads(p);
-    if (p.macro_stages == 8) k_macro_sweep<T, 8><<<1, nt, macro_smem_bytes<T>(p, nt, 8), st>>>(p);
-    else k_macro_sweep<T, 4><<<1, nt, macro_smem_bytes<T>(p, nt, 4), st>>>(p);
+    const int nvb = nblk(p.Nv, 256);
+    out[KT_CELL_MOM] = nblk(p.N, 8);
+    out[KT_CELL_PAR] = nblk(p.N, 32);
+    out[KT_FBP] = p.N * nvb;
+    out[KT_FACE_MOM] = nblk(p.nf, 8);
+    out[KT_FACE_PAR] = nblk(p.nf, 32);
+    out[KT_FACE_FLUX] = nblk(p.nf, 8);
+    out[KT_FACE_PHI] = nblk(p.nf, 64);
+    out[KT_MACRO_PRE] = nblk(p.N, 32);
+    out[KT_MACRO_SWEEP] = 1;
+    out[KT_MACRO_POST] = nblk(p.N, 32);
+    out[KT_MICRO_RES] = p.N * nvb;
+    out[KT_SWEEP] = nblk(p.Nv, p.sweep_tv);
 }
 
-template <class T, bool FWD> static void launch_sweep(const KParams &p, cudaStream_t st)
+// block shape, shared memory and prefetch depth common to all instances of
+// a plan (the maxima of the instances; the deepest pipeline that fits all)
+int plan_shapes(const KParams *hp, int n, bool fp64, Plan &pl)
 {
-    int nb = (p.Nv + p.sweep_tv - 1) / p.sweep_tv;
-    int nthr = p.sweep_tv * p.sweep_pc;
-    size_t sm = sweep_bytes<T>(p, !FWD, p.sweep_stages);
-    if (p.sweep_stages == 8) k_sweep<T, FWD, 8><<<nb, nthr, sm, st>>>(p);
-    else k_sweep<T, FWD, 4><<<nb, nthr, sm, st>>>(p);
+    const size_t lim = 227 * 1024;
+    pl.macro_threads = pl.sweep_threads = 0;
+    pl.limiter_any = 0;
+    for (int i = 0; i < n; ++i) {
+        pl.macro_threads = std::max(pl.macro_threads, macro_threads(hp[i]));
+        pl.sweep_threads = std::max(pl.sweep_threads, hp[i].sweep_tv * hp[i].sweep_pc);
+        pl.limiter_any |= hp[i].limiter;
+    }
+    for (int stages : {std::min(hp[0].macro_stages, 8), 4}) {
+        size_t m = 0;
+        for (int i = 0; i < n; ++i)
+            m = std::max(m, fp64 ? macro_smem_bytes<double>(hp[i], pl.macro_threads, stages)
+                                 : macro_smem_bytes<float>(hp[i], pl.macro_threads, stages));
+        pl.macro_stages = stages;
+        pl.macro_smem = m;
+        if (m <= lim) break;
+    }
+    for (int stages : {std::min(hp[0].sweep_stages, 8), 4}) {
+        size_t f = 0, b = 0;
+        for (int i = 0; i < n; ++i) {
+            f = std::max(f, fp64 ? sweep_bytes<double>(hp[i], false, stages) : sweep_bytes<float>(hp[i], false, stages));
+            b = std::max(b, fp64 ? sweep_bytes<double>(hp[i], true, stages) : sweep_bytes<float>(hp[i], true, stages));
+        }
+        pl.sweep_stages = stages;
+        pl.fwd_smem = f;
+        pl.bwd_smem = b;
+        if (b <= lim) break;
+    }
+    if (pl.macro_smem > lim || pl.bwd_smem > lim) return (int)cudaErrorInvalidValue;
+    return 0;
+}
+
+template <class T> static Launch launch_of(const Plan &pl, int kt)
+{
+    Launch L;
+    L.params = pl.dparams;
+    L.off = pl.doff ? pl.doff + (size_t)kt * (pl.ninst + 1) : nullptr;
+    L.active = pl.dactive;
+    L.ninst = pl.ninst;
+    return L;
 }
 
 // events (optional): kProfiled+1 cudaEvent_t recorded between the six groups
-// cell prep | faces (moments, params, flux, phi) | macro | fwd | bwd | (spare)
+// cell prep | face moments+params | face flux+phi | macro | residual+fwd | bwd
 template <class T>
-static int iteration_t(const KParams &p, cudaStream_t st, void **events)
+static int iteration_t(const Plan &pl, cudaStream_t st, void **events)
 {
     auto mark = [&](int q) {
         if (events) cudaEventRecord((cudaEvent_t)events[q], st);
     };
+    auto L = [&](int kt) { return launch_of<T>(pl, kt); };
+    const int *nb = pl.nblocks;
     mark(0);
-    k_cell_moments<T><<<nblk(p.N, 8), 256, 0, st>>>(p);
-    k_cell_params<T><<<nblk(p.N, 32), 32, 0, st>>>(p);
-    k_fbp<T><<<dim3(p.N, nblk(p.Nv, 256)), 256, 0, st>>>(p);
+    k_cell_moments<T><<<nb[KT_CELL_MOM], 256, 0, st>>>(L(KT_CELL_MOM));
+    k_cell_params<T><<<nb[KT_CELL_PAR], 32, 0, st>>>(L(KT_CELL_PAR));
+    k_fbp<T><<<nb[KT_FBP], 256, 0, st>>>(L(KT_FBP));
     mark(1);
-    if (p.limiter) k_face_moments<T, true><<<nblk(p.nf, 8), 256, 0, st>>>(p);
-    else k_face_moments<T, false><<<nblk(p.nf, 8), 256, 0, st>>>(p);
-    k_face_params<T><<<nblk(p.nf, 32), 32, 0, st>>>(p);
+    if (pl.limiter_any) k_face_moments<T, true><<<nb[KT_FACE_MOM], 256, 0, st>>>(L(KT_FACE_MOM));
+    else k_face_moments<T, false><<<nb[KT_FACE_MOM], 256, 0, st>>>(L(KT_FACE_MOM));
+    k_face_params<T><<<nb[KT_FACE_PAR], 32, 0, st>>>(L(KT_FACE_PAR));
     mark(2);
-    k_face_flux<T><<<nblk(p.nf, 8), 256, 0, st>>>(p);
-    k_face_phi<T><<<nblk(p.nf, 64), 64, 0, st>>>(p);
+    k_face_flux<T><<<nb[KT_FACE_FLUX], 256, 0, st>>>(L(KT_FACE_FLUX));
+    k_face_phi<T><<<nb[KT_FACE_PHI], 64, 0, st>>>(L(KT_FACE_PHI));
     mark(3);
-    {
-        k_macro_pre<T><<<nblk(p.N, 32), 32, 0, st>>>(p);
-        launch_macro_sweep<T>(p, st);
-        k_macro_post<T><<<nblk(p.N, 32), 32, 0, st>>>(p);
-    }
+    k_macro_pre<T><<<nb[KT_MACRO_PRE], 32, 0, st>>>(L(KT_MACRO_PRE));
+    if (pl.macro_stages == 8)
+        k_macro_sweep<T, 8><<<nb[KT_MACRO_SWEEP], pl.macro_threads, pl.macro_smem, st>>>(L(KT_MACRO_SWEEP));
+    else
+        k_macro_sweep<T, 4><<<nb[KT_MACRO_SWEEP], pl.macro_threads, pl.macro_smem, st>>>(L(KT_MACRO_SWEEP));
+    k_macro_post<T><<<nb[KT_MACRO_POST], 32, 0, st>>>(L(KT_MACRO_POST));
     mark(4);
-    k_micro_residual<T><<<dim3(p.N, nblk(p.Nv, 256)), 256, 0, st>>>(p);
-    launch_sweep<T, true>(p, st);
+    k_micro_residual<T><<<nb[KT_MICRO_RES], 256, 0, st>>>(L(KT_MICRO_RES));
+    if (pl.sweep_stages == 8) k_sweep<T, true, 8><<<nb[KT_SWEEP], pl.sweep_threads, pl.fwd_smem, st>>>(L(KT_SWEEP));
+    else k_sweep<T, true, 4><<<nb[KT_SWEEP], pl.sweep_threads, pl.fwd_smem, st>>>(L(KT_SWEEP));
     mark(5);
-    launch_sweep<T, false>(p, st);
+    if (pl.sweep_stages == 8) k_sweep<T, false, 8><<<nb[KT_SWEEP], pl.sweep_threads, pl.bwd_smem, st>>>(L(KT_SWEEP));
+    else k_sweep<T, false, 4><<<nb[KT_SWEEP], pl.sweep_threads, pl.bwd_smem, st>>>(L(KT_SWEEP));
     mark(6);
     return (int)cudaGetLastError();
 }
 
-// checks that the sweep shapes fit in shared memory and opts the kernels in
-// to more than 48 KB of it
-template <class T> static int configure_t(const KParams &p)
+// opt the wavefront kernels in to the largest dynamic shared memory once
+template <class T> static int configure_t()
 {
-    const size_t lim = 227 * 1024;
-    int nt = macro_threads(p);
-    size_t macro = macro_smem_bytes<T>(p, nt, p.macro_stages);
-    size_t fwd = sweep_bytes<T>(p, false, p.sweep_stages), bwd = sweep_bytes<T>(p, true, p.sweep_stages);
-    if (macro > lim || fwd > lim || bwd > lim) return (int)cudaErrorInvalidValue;
+    const int lim = 227 * 1024;
     cudaError_t e = cudaSuccess;
-    auto opt = [&](const void *fn, size_t b) {
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b);
+    auto opt = [&](const void *fn) {
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     };
-    if (p.macro_stages == 8) opt((const void *)k_macro_sweep<T, 8>, macro);
-    else opt((const void *)k_macro_sweep<T, 4>, macro);
-    if (p.sweep_stages == 8) {
-        opt((const void *)k_sweep<T, true, 8>, fwd);
-        opt((const void *)k_sweep<T, false, 8>, bwd);
-    } else {
-        opt((const void *)k_sweep<T, true, 4>, fwd);
-        opt((const void *)k_sweep<T, false, 4>, bwd);
-    }
+    opt((const void *)k_macro_sweep<T, 8>);
+    opt((const void *)k_macro_sweep<T, 4>);
+    opt((const void *)k_sweep<T, true, 8>);
+    opt((const void *)k_sweep<T, false, 8>);
+    opt((const void *)k_sweep<T, true, 4>);
+    opt((const void *)k_sweep<T, false, 4>);
     return (int)e;
 }
 
-size_t sweep_smem_need(const KParams &p, bool fp64, int which)
-{
-    if (which == 0) return fp64 ? macro_smem_bytes<double>(p, macro_threads(p), p.macro_stages)
-                                : macro_smem_bytes<float>(p, macro_threads(p), p.macro_stages);
-    return fp64 ? sweep_bytes<double>(p, true, p.sweep_stages) : sweep_bytes<float>(p, true, p.sweep_stages);
-}
+int configure_kernels(bool fp64) { return fp64 ? configure_t<double>() : configure_t<float>(); }
 
-int configure_kernels(const KParams &p, bool fp64) { return fp64 ? configure_t<double>(p) : configure_t<float>(p); }
-
-int launch_iteration(const KParams &p, bool fp64, void *stream, void **events)
+int launch_iteration(const Plan &pl, bool fp64, void *stream, void **events)
 {
     cudaStream_t st = (cudaStream_t)stream;
-    return fp64 ? iteration_t<double>(p, st, events) : iteration_t<float>(p, st, events);
+    return fp64 ? iteration_t<double>(pl, st, events) : iteration_t<float>(pl, st, events);
 }
 
 int launch_cell_moments(const KParams &p, bool fp64, double *out6_dev, void *stream)
 {
     cudaStream_t st = (cudaStream_t)stream;
     if (fp64) {
-        k_cell_moments<double><<<nblk(p.N, 8), 256, 0, st>>>(p);
+        k_cell_moments_v<double><<<nblk(p.N, 8), 256, 0, st>>>(p);
         k_moments_out<double><<<nblk(p.N, 256), 256, 0, st>>>(p, out6_dev);
     } else {
-        k_cell_moments<float><<<nblk(p.N, 8), 256, 0, st>>>(p);
+        k_cell_moments_v<float><<<nblk(p.N, 8), 256, 0, st>>>(p);
         k_moments_out<float><<<nblk(p.N, 256), 256, 0, st>>>(p, out6_dev);
     }
     return (int)cudaGetLastError();
@@ -1316,20 +1428,31 @@ int launch_cell_moments_noalloc(const KParams &p0, bool fp64, int device, double
     p.cellraw = scratch;
     cudaStream_t st = (cudaStream_t)stream;
     if (fp64) {
-        k_cell_moments<double><<<nblk(p.N, 8), 256, 0, st>>>(p);
+        k_cell_moments_v<double><<<nblk(p.N, 8), 256, 0, st>>>(p);
         k_moments_out<double><<<nblk(p.N, 256), 256, 0, st>>>(p, out6_dev);
     } else {
-        k_cell_moments<float><<<nblk(p.N, 8), 256, 0, st>>>(p);
+        k_cell_moments_v<float><<<nblk(p.N, 8), 256, 0, st>>>(p);
         k_moments_out<float><<<nblk(p.N, 256), 256, 0, st>>>(p, out6_dev);
     }
     return (int)cudaGetLastError();
 }
 
-int launch_face_phi(const KParams &p, bool fp64, void *stream)
+// residuals of the last `last` iterations and the status word of every
+// instance of a batch (inactive instances repeat their last values)
+__global__ void k_batch_gather(const KParams *ps, int n, int last, double *res, int *status)
 {
-    cudaStream_t st = (cudaStream_t)stream;
-    if (fp64) k_face_phi<double><<<nblk(p.nf, 256), 256, 0, st>>>(p);
-    else k_face_phi<float><<<nblk(p.nf, 256), 256, 0, st>>>(p);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const KParams &p = ps[i];
+    const int it = *p.iter;
+    for (int q = 0; q < last; ++q) res[(size_t)i * 16 + q] = p.res[(it - last + q) & (kMaxHist - 1)];
+    status[i] = *p.status;
+}
+
+int launch_batch_gather(const KParams *dparams, int n, int last, double *dres, int *dstatus, void *stream)
+{
+    if (last > 16) return (int)cudaErrorInvalidValue;
+    k_batch_gather<<<nblk(n, 64), 64, 0, (cudaStream_t)stream>>>(dparams, n, last, dres, dstatus);
     return (int)cudaGetLastError();
 }
 

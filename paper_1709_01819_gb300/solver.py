@@ -110,3 +110,83 @@ class Solver:
 
     def face_flux_moments(self) -> np.ndarray:
         return B.idg_get_face_flux_moments(self.ctx, self.nf, self.stream)
+
+
+class BatchSolver:
+    """Many Problems advanced together: each kernel of an iteration is launched
+    once over all instances (idg_batch_*).  Instances may differ in size, gas,
+    boundaries and tuning; all use one precision on one device."""
+
+    def __init__(self, problems, precision: str = "mixed", device: int = 0, autotune: bool = False):
+        import torch
+
+        self.torch = torch
+        self.device = device
+        self.solvers = [Solver(p, precision, device) for p in problems]
+        for s in self.solvers:
+            s.init_uniform()
+        if autotune:
+            tuner = Autotuner()
+            for s in self.solvers:
+                tuner.tune(s)
+        self._make_batch()
+
+    def _make_batch(self):
+        self.handle = B.idg_batch_create([s.ctx for s in self.solvers])
+        nbytes = B.idg_batch_workspace_size(self.handle)
+        self.workspace = self.torch.empty(nbytes + 256, dtype=self.torch.uint8, device=f"cuda:{self.device}")
+        aligned = (self.workspace.data_ptr() + 255) & ~255
+        B.idg_batch_bind_workspace(self.handle, aligned, nbytes)
+
+    @property
+    def stream(self):
+        return self.torch.cuda.current_stream(self.device).cuda_stream
+
+    @property
+    def cell_velocities(self) -> int:
+        return sum(s.N * s.Nv for s in self.solvers)
+
+    def iterate(self, max_iter: int, tol: float = 0.0):
+        """Returns (all converged, iterations launched, largest relative residual, per-instance flags)."""
+        st, n, r, conv = B.idg_batch_iterate(self.handle, len(self.solvers), max_iter, tol, self.stream)
+        return st == B.IDG_OK, n, r, conv
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None:
+            B.idg_batch_destroy(h)
+            self.handle = None
+
+
+class Autotuner:
+    """Picks the micro-sweep tile (velocities per thread block) and the
+    prefetch depths of a Solver by timing one profiled iteration of each
+    candidate on the problem itself; results are cached per (cells in i, in j,
+    velocities, precision) so a batch of same-sized problems is timed once."""
+
+    def __init__(self, candidates_tv=(2, 4, 8, 16, 32), repeats: int = 3):
+        self.candidates_tv = candidates_tv
+        self.repeats = repeats
+        self.cache = {}
+
+    def tune(self, solver: "Solver") -> dict:
+        key = (solver.prob.ni, solver.prob.nj, solver.Nv, solver.precision)
+        if key in self.cache:
+            solver.set_tuning(**self.cache[key])
+            return self.cache[key]
+        G, H, W = solver.get_state()
+        best, best_t = None, float("inf")
+        for tv in self.candidates_tv:
+            for stages in (8, 4):
+                try:
+                    solver.set_tuning(sweep_tv=tv, sweep_stages=stages, macro_stages=stages)
+                except B.IdgError:
+                    continue
+                solver.iterate_profiled()  # warm-up
+                t = min(float(np.sum(solver.iterate_profiled())) for _ in range(self.repeats))
+                if t < best_t:
+                    best, best_t = dict(sweep_tv=tv, sweep_stages=stages, macro_stages=stages), t
+        solver.set_tuning(**best)
+        solver.set_state(G, H, W)  # timing iterations leave no trace
+        self.cache[key] = best
+        return best
