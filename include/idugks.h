@@ -69,7 +69,8 @@ idg_status idg_create(idg_ctx **out, int precision, int device);
 void idg_destroy(idg_ctx *ctx);
 const char *idg_last_error(const idg_ctx *ctx);
 
-/* Structured quadrilateral block of ni x nj cells (Fig. 1 and Section 2.3).
+/* Structured quadrilateral block of ni x nj cells (Fig. 1 and Section 2.3),
+ * min(ni, nj) <= 256.
  * nodes_x/nodes_y: (ni+1)*(nj+1) host float64, node (i,j) at j*(ni+1)+i, cells
  * counter-clockwise (positive area).  A periodic direction is declared with
  * idg_set_boundary(kind = IDG_BC_PERIODIC) on both of its sides; the last node
@@ -176,14 +177,18 @@ idg_status idg_iterate_profiled(idg_ctx *ctx, void *stream, double *kernel_ms);
 /* Launch-shape tuning of the wavefront kernels (after idg_bind_workspace;
  * no effect on results).  IDG_TUNE_SWEEP_TV: discrete velocities per thread
  * block of the micro LU-SGS sweeps (power of two, 1..32, times min(ni, nj)
- * at most 1024).  IDG_TUNE_SWEEP_STAGES / IDG_TUNE_MACRO_STAGES: hyperplanes
+ * at most 512).  IDG_TUNE_SWEEP_STAGES / IDG_TUNE_MACRO_STAGES: hyperplanes
  * prefetched ahead by the micro / macroscopic sweeps (4 or 8).  Returns
  * IDG_ERR_ARG for a value that is invalid or does not fit in shared memory.
+ * IDG_TUNE_SWEEP_VPT: consecutive velocities per thread of the micro sweeps
+ * (1, 2 or 4; must divide the number of velocities; all instances of a
+ * batch must agree).
  * IDG_TUNE_GRAPH (1 default, 0 off): idg_iterate replays chunks of 16
  * iterations (and single iterations) as captured CUDA graphs on a
  * library-owned stream that is ordered after, and before, the caller's
  * stream by events. */
-enum { IDG_TUNE_SWEEP_TV = 1, IDG_TUNE_SWEEP_STAGES = 2, IDG_TUNE_MACRO_STAGES = 3, IDG_TUNE_GRAPH = 4 };
+enum { IDG_TUNE_SWEEP_TV = 1, IDG_TUNE_SWEEP_STAGES = 2, IDG_TUNE_MACRO_STAGES = 3, IDG_TUNE_GRAPH = 4,
+       IDG_TUNE_SWEEP_VPT = 5 };
 idg_status idg_set_tuning(idg_ctx *ctx, int key, int value);
 idg_status idg_get_tuning(const idg_ctx *ctx, int key, int *value);
 

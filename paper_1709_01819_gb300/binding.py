@@ -19,7 +19,7 @@ IDG_BC_PERIODIC, IDG_BC_WALL, IDG_BC_FARFIELD = 0, 1, 2
 IDG_NC_TRAP, IDG_NC_SIMPSON, IDG_GAUSS_HERMITE = 0, 1, 2
 IDG_IMIN, IDG_IMAX, IDG_JMIN, IDG_JMAX = 0, 1, 2, 3
 IDG_BGK, IDG_SHAKHOV = 0, 1
-IDG_TUNE_SWEEP_TV, IDG_TUNE_SWEEP_STAGES, IDG_TUNE_MACRO_STAGES, IDG_TUNE_GRAPH = 1, 2, 3, 4
+IDG_TUNE_SWEEP_TV, IDG_TUNE_SWEEP_STAGES, IDG_TUNE_MACRO_STAGES, IDG_TUNE_GRAPH, IDG_TUNE_SWEEP_VPT = 1, 2, 3, 4, 5
 
 _STATUS = {0: "IDG_OK", 1: "IDG_ERR_ARG", 2: "IDG_ERR_STATE", 3: "IDG_ERR_CUDA", 4: "IDG_ERR_OOM",
            5: "IDG_ERR_NONFINITE", 6: "IDG_ERR_TIMEOUT", 7: "IDG_ERR_NOT_CONVERGED"}

@@ -823,10 +823,11 @@ idg_status idg_bind_workspace(idg_ctx *c, void *dev_ptr, size_t bytes)
     // micro sweeps: one thread per cell of the longest hyperplane and tv
     // velocities per CTA (8 by default, more on very narrow blocks)
     int maxlen = std::min(c->ni, c->nj);
-    if (maxlen > 1024) return fail(c, IDG_ERR_ARG, "min(ni, nj) = %d exceeds 1024", maxlen);
+    if (maxlen > 256) return fail(c, IDG_ERR_ARG, "min(ni, nj) = %d exceeds 256", maxlen);
     k.sweep_pc = maxlen;
+    k.sweep_vpt = 1;
     k.sweep_tv = 8;
-    while (k.sweep_tv > 1 && k.sweep_tv * k.sweep_pc > 1024) k.sweep_tv /= 2;
+    while (k.sweep_tv > 1 && k.sweep_tv * k.sweep_pc > 512) k.sweep_tv /= 2;
     while (k.sweep_tv < 32 && 2 * k.sweep_tv * k.sweep_pc <= 256) k.sweep_tv *= 2;
     // prefetch depth: 8 hyperplanes where shared memory allows (the plan
     // falls back to 4)
@@ -1047,9 +1048,13 @@ idg_status idg_set_tuning(idg_ctx *c, int key, int value)
         return IDG_OK;
     }
     if (key == IDG_TUNE_SWEEP_TV) {
-        if (value < 1 || value > 32 || (value & (value - 1)) || value * k.sweep_pc > 1024)
+        if (value < 1 || value > 32 || (value & (value - 1)) || value * k.sweep_pc > 512)
             return fail(c, IDG_ERR_ARG, "sweep velocities per block %d invalid for %d cell slots", value, k.sweep_pc);
         k.sweep_tv = value;
+    } else if (key == IDG_TUNE_SWEEP_VPT) {
+        if ((value != 1 && value != 2 && value != 4) || k.Nv % value)
+            return fail(c, IDG_ERR_ARG, "velocities per thread %d must be 1, 2 or 4 and divide %d", value, k.Nv);
+        k.sweep_vpt = value;
     } else if (key == IDG_TUNE_SWEEP_STAGES) {
         if (value != 4 && value != 8) return fail(c, IDG_ERR_ARG, "sweep stages must be 4 or 8");
         k.sweep_stages = value;
@@ -1079,6 +1084,7 @@ idg_status idg_get_tuning(const idg_ctx *c, int key, int *value)
     if (!c->bound) return IDG_ERR_STATE;
     if (key == IDG_TUNE_GRAPH) *value = c->use_graph;
     else if (key == IDG_TUNE_SWEEP_TV) *value = c->kp.sweep_tv;
+    else if (key == IDG_TUNE_SWEEP_VPT) *value = c->kp.sweep_vpt;
     else if (key == IDG_TUNE_SWEEP_STAGES) *value = c->plan.sweep_stages;
     else if (key == IDG_TUNE_MACRO_STAGES) *value = c->plan.macro_stages;
     else return IDG_ERR_ARG;

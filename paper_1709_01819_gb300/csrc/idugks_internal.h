@@ -78,6 +78,7 @@ struct KParams {
     // launch shape of the wavefront kernels: velocities per CTA and cell
     // slots of the micro sweeps, prefetch depths (hyperplanes; 4 or 8)
     int sweep_tv, sweep_pc, sweep_stages, macro_stages;
+    int sweep_vpt;  // consecutive velocities per thread in the micro sweeps (1, 2, 4)
 };
 
 // kernels of one iteration, in launch order
@@ -98,7 +99,7 @@ struct Plan {
     int nblocks[KT_COUNT];
     int macro_threads, sweep_threads;
     size_t macro_smem, fwd_smem, bwd_smem;
-    int macro_stages, sweep_stages, limiter_any;
+    int macro_stages, sweep_stages, limiter_any, sweep_vpt;
 };
 
 // kernel launchers (idugks_kernels.cu)

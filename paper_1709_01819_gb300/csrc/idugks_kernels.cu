@@ -861,50 +861,26 @@ __device__ __forceinline__ void euler_dflux(T gm1, const T *b, const T *dW, T nx
     dF[3] = (dW[3] + dp) * vn1 + H * dvn;
 }
 
-// one hyperplane step of the macroscopic sweep for the cell whose record
-// and links sit in shared memory (dir = +1 forward, -1 backward)
-template <class T>
-__device__ __forceinline__ void macro_cell(int ni, int d, int i, int c, const T *rec,
-                                           const int *lk, const T *dWs, T *ring, T *dWg, int dir, T gm1)
-{
-    T acc[4] = {0, 0, 0, 0};
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-        int nb = lk[m];
-        if (nb < 0 || (dir > 0 ? nb >= c : nb <= c)) continue;
-        int nbi = lk[4 + m], nbd = lk[8 + m];
-        const T *dWn = (nbd == d - dir) ? ring + 4 * (((d - dir) & 1) * ni + nbi) : dWg + 4 * nb;
-        T dn[4] = {dWn[0], dWn[1], dWn[2], dWn[3]};
-        const T *o = rec + 8 + 9 * m;
-        T dF[4];
-        euler_dflux<T>(gm1, o + 3, dn, o[0], o[1], dF);
-        for (int q = 0; q < 4; ++q) acc[q] += dF[q] - o[2] * dn[q];
-    }
-    // forward: dW*_c = (R_c - sum_lower) / D_c;  backward: dW_c = dW*_c - sum_upper / D_c
-    const T iD = rec[5];
-    T *rs = ring + 4 * ((d & 1) * ni + i);
-    for (int q = 0; q < 4; ++q) {
-        T x = dir > 0 ? (rec[q] - acc[q]) * iD : dWs[q] - acc[q] * iD;
-        rs[q] = x;
-        dWg[4 * c + q] = x;
-    }
-}
-
 // One CTA: forward then backward sweep over the i+j hyperplanes (the
-// lexicographic dependency order).  Thread s owns cell (ilo + s) of each
-// hyperplane; its record and links are prefetched kStages-1 hyperplanes ahead
-// with cp.async; the previous hyperplane's increments sit in a ring.
+// lexicographic dependency order).  Four threads own one cell of the
+// hyperplane, thread m handling the neighbour across slot m; the four
+// off-diagonal terms 1/2 (dF S - omega Lambda dW_nb) are summed by a quad
+// shuffle and thread m then writes component m of the increment.  Records,
+// links and (backward) the cell's own dW* are prefetched kStages-1
+// hyperplanes ahead with cp.async; the previous hyperplane's increments sit
+// in a shared-memory ring.
 template <class T, int kStages>
 __global__ void __launch_bounds__(1024) k_macro_sweep(Launch L)
 {
     IDG_LOCATE();
     extern __shared__ __align__(16) unsigned char smraw[];
-    const int tid = threadIdx.x, nt = blockDim.x;
+    const int tid = threadIdx.x, ncs = blockDim.x >> 2;  // cell slots
+    const int cs = tid >> 2, m = tid & 3;
     const int ni = p.ni, nj = p.nj, nh = ni + nj - 1;
-    T *srec = (T *)smraw;                                   // [kStages][nt][kMRec]
-    int *slnk = (int *)(srec + (size_t)kStages * nt * kMRec);  // [kStages][nt][12]
-    T *sdw = (T *)(slnk + (size_t)kStages * nt * 12);        // [kStages][nt][4] own dW* (backward)
-    T *ring = sdw + (size_t)kStages * nt * 4;                // [2][ni][4]
+    T *srec = (T *)smraw;                                     // [kStages][ncs][kMRec]
+    int *slnk = (int *)(srec + (size_t)kStages * ncs * kMRec);  // [kStages][ncs][12]
+    T *sdw = (T *)(slnk + (size_t)kStages * ncs * 12);        // [kStages][ncs][4] own dW* (backward)
+    T *ring = sdw + (size_t)kStages * ncs * 4;                // [2][ni][4]
     if (tid == 0) {
         double s = 0.0;
         int nb = (p.N + 31) / 32;
@@ -918,27 +894,23 @@ __global__ void __launch_bounds__(1024) k_macro_sweep(Launch L)
     T *dWg = (T *)p.mdW;
     const T *mrec = (const T *)p.mrec;
     const int *clink = p.clink;
-    constexpr int RB = kMRec * sizeof(T);  // bytes of one record (multiple of 16)
+    constexpr int RC = kMRec * sizeof(T) / 16;  // 16-byte chunks of one record
+    constexpr int DC = 4 * sizeof(T) / 16;      // chunks of one dW
     for (int dir = 1; dir >= -1; dir -= 2) {
         auto step_d = [&](int s) { return dir > 0 ? s : nh - 1 - s; };
         auto issue = [&](int s) {
             if (s < nh) {
                 int d = step_d(s);
                 int ilo = max(0, d - (nj - 1)), ihi = min(ni - 1, d);
-                int i = ilo + tid;
+                int i = ilo + cs;
                 if (i <= ihi) {
                     int c = (d - i) * ni + i;
-                    int st = s & (kStages - 1);
-                    const char *gr = (const char *)(mrec + (size_t)kMRec * c);
-                    char *sr = (char *)(srec + ((size_t)st * nt + tid) * kMRec);
-                    for (int b = 0; b < RB; b += 16) cp_async16(sr + b, gr + b);
-                    const char *gl = (const char *)(clink + 12 * c);
-                    char *sl = (char *)(slnk + ((size_t)st * nt + tid) * 12);
-                    for (int b = 0; b < 48; b += 16) cp_async16(sl + b, gl + b);
-                    if (dir < 0) {
-                        const char *gd = (const char *)(dWg + 4 * (size_t)c);
-                        char *sd = (char *)(sdw + ((size_t)st * nt + tid) * 4);
-                        for (int b = 0; b < 4 * (int)sizeof(T); b += 16) cp_async16(sd + b, gd + b);
+                    size_t e = (size_t)(s & (kStages - 1)) * ncs + cs;
+                    const int nch = RC + 3 + (dir < 0 ? DC : 0);
+                    for (int q = m; q < nch; q += 4) {
+                        if (q < RC) cp_async16((char *)(srec + e * kMRec) + 16 * q, (const char *)(mrec + (size_t)kMRec * c) + 16 * q);
+                        else if (q < RC + 3) cp_async16((char *)(slnk + e * 12) + 16 * (q - RC), (const char *)(clink + 12 * (size_t)c) + 16 * (q - RC));
+                        else cp_async16((char *)(sdw + e * 4) + 16 * (q - RC - 3), (const char *)(dWg + 4 * (size_t)c) + 16 * (q - RC - 3));
                     }
                 }
             }
@@ -949,13 +921,45 @@ __global__ void __launch_bounds__(1024) k_macro_sweep(Launch L)
             cp_wait<kStages - 2>();
             __syncthreads();
             issue(s + kStages - 1);
-            int d = step_d(s);
-            int ilo = max(0, d - (nj - 1)), ihi = min(ni - 1, d);
-            int i = ilo + tid;
-            if (i <= ihi) {
-                size_t e = (size_t)(s & (kStages - 1)) * nt + tid;
-                macro_cell<T>(ni, d, i, (d - i) * ni + i, srec + e * kMRec, slnk + e * 12, sdw + e * 4,
-                              ring, dWg, dir, gm1);
+            const int d = step_d(s);
+            const int ilo = max(0, d - (nj - 1)), ihi = min(ni - 1, d);
+            const int i = ilo + cs;
+            const bool valid = i <= ihi;
+            const int c = (d - i) * ni + i;
+            const size_t e = (size_t)(s & (kStages - 1)) * ncs + cs;
+            const T *rec = srec + e * kMRec;
+            const int *lk = slnk + e * 12;
+            T acc0 = 0, acc1 = 0, acc2 = 0, acc3 = 0;
+            if (valid) {
+                int nb = lk[m];
+                if (nb >= 0 && (dir > 0 ? nb < c : nb > c)) {
+                    int nbi = lk[4 + m], nbd = lk[8 + m];
+                    const T *dWn = (nbd == d - dir) ? ring + 4 * (((d - dir) & 1) * ni + nbi) : dWg + 4 * (size_t)nb;
+                    T dn[4] = {dWn[0], dWn[1], dWn[2], dWn[3]};
+                    const T *o = rec + 8 + 9 * m;
+                    T dF[4];
+                    euler_dflux<T>(gm1, o + 3, dn, o[0], o[1], dF);
+                    acc0 = dF[0] - o[2] * dn[0];
+                    acc1 = dF[1] - o[2] * dn[1];
+                    acc2 = dF[2] - o[2] * dn[2];
+                    acc3 = dF[3] - o[2] * dn[3];
+                }
+            }
+            // sum over the four slots of the cell (fixed butterfly order)
+#pragma unroll
+            for (int o = 1; o <= 2; o <<= 1) {
+                acc0 += __shfl_xor_sync(0xffffffffu, acc0, o);
+                acc1 += __shfl_xor_sync(0xffffffffu, acc1, o);
+                acc2 += __shfl_xor_sync(0xffffffffu, acc2, o);
+                acc3 += __shfl_xor_sync(0xffffffffu, acc3, o);
+            }
+            if (valid) {
+                // forward: dW*_c = (R_c - sum_lower) / D_c;  backward: dW_c = dW*_c - sum_upper / D_c
+                const T am = m == 0 ? acc0 : (m == 1 ? acc1 : (m == 2 ? acc2 : acc3));
+                const T iD = rec[5];
+                const T x = dir > 0 ? (rec[m] - am) * iD : sdw[e * 4 + m] - am * iD;
+                ring[4 * ((d & 1) * ni + i) + m] = x;
+                dWg[4 * (size_t)c + m] = x;
             }
         }
         cp_wait<0>();
@@ -1034,33 +1038,56 @@ __global__ void __launch_bounds__(256) k_micro_residual(Launch L)
     ((T2 *)p.dst)[ck] = o;
 }
 
-// shared-memory layout of the micro sweeps
-template <class T, int kStages> struct SweepSmem {
+// 16 storage scalars from 16-byte-aligned shared memory
+template <class T> __device__ __forceinline__ void load16(T (&r)[16], const T *s);
+template <> __device__ __forceinline__ void load16<float>(float (&r)[16], const float *s)
+{
+    const float4 *q = (const float4 *)s;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        float4 a = q[u];
+        r[4 * u] = a.x; r[4 * u + 1] = a.y; r[4 * u + 2] = a.z; r[4 * u + 3] = a.w;
+    }
+}
+template <> __device__ __forceinline__ void load16<double>(double (&r)[16], const double *s)
+{
+    const double2 *q = (const double2 *)s;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        double2 a = q[u];
+        r[2 * u] = a.x; r[2 * u + 1] = a.y;
+    }
+}
+
+// shared-memory layout of the micro sweeps (VPT consecutive velocities per thread)
+template <class T, int kStages, int VPT> struct SweepSmem {
     using T2 = typename V2<T>::t;
-    T2 *R;      // [kStages][pc][tv]  R (forward) / Delta* (backward)
-    T2 *F;      // [kStages][pc][tv]  f~ (backward only)
+    T2 *R;      // [kStages][pc][tv*VPT]  R (forward) / Delta* (backward)
+    T2 *F;      // [kStages][pc][tv*VPT]  f~ (backward only)
     T *geo;     // [kStages][pc][16]  sign*nx, sign*ny, S, 0 per slot
     int *lnk;   // [kStages][pc][12]  neighbour, its i, its hyperplane
-    T2 *ring;   // [2][ni][tv]
+    T2 *ring;   // [2][ni][tv*VPT]
     T *D0;      // [kStages][pc]
     __device__ SweepSmem(unsigned char *base, int pc, int tv, int ni, bool withF)
     {
         size_t o = 0;
-        R = (T2 *)(base + o); o += (size_t)kStages * pc * tv * sizeof(T2);
-        F = (T2 *)(base + o); if (withF) o += (size_t)kStages * pc * tv * sizeof(T2);
+        const size_t w = (size_t)tv * VPT;
+        R = (T2 *)(base + o); o += (size_t)kStages * pc * w * sizeof(T2);
+        F = (T2 *)(base + o); if (withF) o += (size_t)kStages * pc * w * sizeof(T2);
         geo = (T *)(base + o); o += (size_t)kStages * pc * 16 * sizeof(T);
         lnk = (int *)(base + o); o += (size_t)kStages * pc * 12 * sizeof(int);
-        ring = (T2 *)(base + o); o += (size_t)2 * ni * tv * sizeof(T2);
+        ring = (T2 *)(base + o); o += (size_t)2 * ni * w * sizeof(T2);
         D0 = (T *)(base + o);
     }
 };
 
-template <class T, int kStages> static size_t sweep_smem_bytes(int pc, int tv, int ni, bool withF)
+template <class T, int kStages, int VPT> static size_t sweep_smem_bytes(int pc, int tv, int ni, bool withF)
 {
     using T2 = typename V2<T>::t;
-    size_t o = (size_t)kStages * pc * tv * sizeof(T2) * (withF ? 2 : 1);
+    const size_t w = (size_t)tv * VPT;
+    size_t o = (size_t)kStages * pc * w * sizeof(T2) * (withF ? 2 : 1);
     o += (size_t)kStages * pc * 16 * sizeof(T) + (size_t)kStages * pc * 12 * sizeof(int);
-    o += (size_t)2 * ni * tv * sizeof(T2) + (size_t)kStages * pc * sizeof(T);
+    o += (size_t)2 * ni * w * sizeof(T2) + (size_t)kStages * pc * sizeof(T);
     return o;
 }
 
@@ -1072,10 +1099,12 @@ struct SweepArgs {
     const int *clink;
 };
 
-// asynchronous copy of one step's data for the thread's cell
-template <class T, int kStages>
-__device__ __forceinline__ void sweep_issue(const SweepArgs &p, const SweepSmem<T, kStages> &sm, int s, int d,
-                                            int slot, int t, int k, bool act, bool withF)
+// asynchronous copy of one step's data for the thread's cell: its VPT
+// consecutive velocities of R (or Delta*, f~), and the cell's geometry,
+// links and diagonal base spread over the cell's tv threads
+template <class T, int kStages, int VPT>
+__device__ __forceinline__ void sweep_issue(const SweepArgs &p, const SweepSmem<T, kStages, VPT> &sm, int s, int d,
+                                            int slot, int t, int k0, bool act, bool withF)
 {
     using T2 = typename V2<T>::t;
     const int ni = p.ni, nj = p.nj, tv = p.tv, pc = p.pc;
@@ -1088,9 +1117,19 @@ __device__ __forceinline__ void sweep_issue(const SweepArgs &p, const SweepSmem<
             int st = s & (kStages - 1);
             size_t e = ((size_t)st * pc + slot);
             if (act) {
-                size_t ck = (size_t)c * p.Nv + k;
-                cp_async_b<sizeof(T2)>(sm.R + e * tv + t, (const T2 *)p.dst + ck);
-                if (withF) cp_async_b<sizeof(T2)>(sm.F + e * tv + t, (const T2 *)p.f + ck);
+                constexpr int B = VPT * sizeof(T2);
+                constexpr int CH = B < 16 ? B : 16;
+                size_t ck = (size_t)c * p.Nv + k0;
+                char *sr = (char *)(sm.R + e * tv * VPT + (size_t)t * VPT);
+                const char *gr = (const char *)((const T2 *)p.dst + ck);
+#pragma unroll
+                for (int b = 0; b < B; b += CH) cp_async_b<CH>(sr + b, gr + b);
+                if (withF) {
+                    char *sf = (char *)(sm.F + e * tv * VPT + (size_t)t * VPT);
+                    const char *gf = (const char *)((const T2 *)p.f + ck);
+#pragma unroll
+                    for (int b = 0; b < B; b += CH) cp_async_b<CH>(sf + b, gf + b);
+                }
             }
             constexpr int ng = 16 * sizeof(T) / 16;  // 16-byte chunks of the geometry record
             for (int q = t; q < ng + 4; q += tv) {
@@ -1103,71 +1142,101 @@ __device__ __forceinline__ void sweep_issue(const SweepArgs &p, const SweepSmem<
     cp_commit();
 }
 
-template <class T, bool FWD, int kStages>
-__global__ void __launch_bounds__(1024) k_sweep(Launch L)
+template <class T, bool FWD, int kStages, int VPT>
+__global__ void __launch_bounds__(512) k_sweep(Launch L)
 {
     IDG_LOCATE();
     using T2 = typename V2<T>::t;
     extern __shared__ __align__(16) unsigned char smraw[];
     const SweepArgs a{p.Nv, p.ni, p.nj, p.sweep_tv, p.sweep_pc, p.dst, p.f, p.cslotT, p.cellpT, p.clink};
     const int tv = a.tv, pc = a.pc, ni = a.ni, nj = a.nj, Nv = a.Nv;
-    const SweepSmem<T, kStages> sm(smraw, pc, tv, ni, !FWD);
+    const SweepSmem<T, kStages, VPT> sm(smraw, pc, tv, ni, !FWD);
     const int t = threadIdx.x % tv, slot = threadIdx.x / tv;
-    const int k = blk * tv + t;
-    const bool act = k < Nv;
-    const int kk = act ? k : 0;
-    const T ux = vx<T>(p, kk), uy = vy<T>(p, kk);
+    const int k0 = (blk * tv + t) * VPT;  // Nv is a multiple of VPT
+    const bool act = k0 < Nv;
+    T ux[VPT], uy[VPT];
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+        const int kk = act ? k0 + v : 0;
+        ux[v] = vx<T>(p, kk);
+        uy[v] = vy<T>(p, kk);
+    }
     T2 *ds = (T2 *)a.dst;
     T2 *f = (T2 *)a.f;
     const int nh = ni + nj - 1;
     const int dir = FWD ? 1 : -1;
+    const size_t w = (size_t)tv * VPT;
     auto step_d = [&](int s) { return FWD ? s : nh - 1 - s; };
-    for (int s = 0; s < kStages - 1; ++s) sweep_issue<T, kStages>(a, sm, s, step_d(s), slot, t, k, act, !FWD);
+    for (int s = 0; s < kStages - 1; ++s) sweep_issue<T, kStages, VPT>(a, sm, s, step_d(s), slot, t, k0, act, !FWD);
     for (int s = 0; s < nh; ++s) {
         cp_wait<kStages - 2>();
         __syncthreads();
-        sweep_issue<T, kStages>(a, sm, s + kStages - 1, step_d(s + kStages - 1), slot, t, k, act, !FWD);
+        sweep_issue<T, kStages, VPT>(a, sm, s + kStages - 1, step_d(s + kStages - 1), slot, t, k0, act, !FWD);
         const int d = step_d(s);
         const int ilo = max(0, d - (nj - 1)), ihi = min(ni - 1, d);
         const int i = ilo + slot;
         if (i > ihi || !act) continue;
         const int c = (d - i) * ni + i;
         const size_t e = (size_t)(s & (kStages - 1)) * pc + slot;
-        const T *g = sm.geo + e * 16;
-        const int *lk = sm.lnk + e * 12;
-        T D = sm.D0[e];
-        T ag = 0, ah = 0;
+        // the whole cell record at once (vector shared-memory loads)
+        T g[16];
+        load16<T>(g, sm.geo + e * 16);
+        const int4 lnb = *(const int4 *)(sm.lnk + e * 12);
+        const int4 lni = *(const int4 *)(sm.lnk + e * 12 + 4);
+        const int4 lnd = *(const int4 *)(sm.lnk + e * 12 + 8);
+        const int nbv[4] = {lnb.x, lnb.y, lnb.z, lnb.w};
+        const int niv[4] = {lni.x, lni.y, lni.z, lni.w};
+        const int ndv[4] = {lnd.x, lnd.y, lnd.z, lnd.w};
+        const T D0 = sm.D0[e];
+        const size_t ck = (size_t)c * Nv + k0;
+        const size_t rbase = e * w + (size_t)t * VPT;
+        const size_t rprev = (size_t)(((d - dir) & 1) * ni) * w + (size_t)t * VPT;
 #pragma unroll
-        for (int m = 0; m < 4; ++m) {
-            int nb = lk[m];
-            if (nb == c) continue;  // a cell wrapped onto itself: no net implicit term
-            T so = xi_dot_n<T>(ux, uy, g[4 * m], g[4 * m + 1]);
-            T aS = so * g[4 * m + 2];
-            if (so > (T)0) D += aS;
-            else if (so < (T)0 && nb >= 0 && (FWD ? nb < c : nb > c)) {
-                T2 dn = (lk[8 + m] == d - dir) ? sm.ring[(((d - dir) & 1) * ni + lk[4 + m]) * tv + t]
-                                               : ds[(size_t)nb * Nv + k];
-                ag -= aS * dn.x;
-                ah -= aS * dn.y;
+        for (int v = 0; v < VPT; ++v) {
+            // slot terms, branch-free: outflow adds to D, inflow from the
+            // already-swept side adds |xi.n| S Delta_nb
+            T D = D0;
+            T aS[4];
+            bool in[4];
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const bool self = nbv[m] == c;
+                const T so = xi_dot_n<T>(ux[v], uy[v], g[4 * m], g[4 * m + 1]);
+                aS[m] = so * g[4 * m + 2];
+                D += (so > (T)0 && !self) ? aS[m] : (T)0;
+                in[m] = so < (T)0 && !self && nbv[m] >= 0 && (FWD ? nbv[m] < c : nbv[m] > c);
             }
+            T2 dn[4];
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                dn[m].x = (T)0;
+                dn[m].y = (T)0;
+                if (in[m]) dn[m] = (ndv[m] == d - dir) ? sm.ring[rprev + (size_t)niv[m] * w + v]
+                                                       : ds[(size_t)nbv[m] * Nv + k0 + v];
+            }
+            T ag = 0, ah = 0;
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                ag -= aS[m] * dn[m].x;
+                ah -= aS[m] * dn[m].y;
+            }
+            const T2 r = sm.R[rbase + v];
+            const T iD = (T)1 / D;
+            T2 o;
+            if (FWD) {
+                o.x = (r.x + ag) * iD;
+                o.y = (r.y + ah) * iD;
+            } else {
+                o.x = r.x + ag * iD;
+                o.y = r.y + ah * iD;
+                T2 fv = sm.F[rbase + v];
+                fv.x += o.x;
+                fv.y += o.y;
+                f[ck + v] = fv;
+            }
+            ds[ck + v] = o;
+            sm.ring[((d & 1) * ni + i) * w + (size_t)t * VPT + v] = o;
         }
-        const T2 r = sm.R[e * tv + t];
-        const size_t ck = (size_t)c * Nv + k;
-        const T iD = (T)1 / D;
-        T2 o;
-        if (FWD) {
-            o.x = (r.x + ag) * iD;
-            o.y = (r.y + ah) * iD;
-        } else {
-            o.x = r.x + ag * iD;
-            o.y = r.y + ah * iD;
-            T2 fv = sm.F[e * tv + t];
-            fv.x += o.x;
-            fv.y += o.y;
-            f[ck] = fv;
-        }
-        ds[ck] = o;
-        sm.ring[((d & 1) * ni + i) * tv + t] = o;
     }
     cp_wait<0>();
 }
@@ -1234,17 +1303,25 @@ __global__ void __launch_bounds__(256) k_moments_out(KParams p, double *out6)
 // ---------------------------------------------------------------------------
 static inline int nblk(int n, int per) { return (n + per - 1) / per; }
 
-static int macro_threads(const KParams &p) { return std::min(1024, ((std::min(p.ni, p.nj) + 31) / 32) * 32); }
+static int macro_threads(const KParams &p) { return std::min(1024, ((4 * std::min(p.ni, p.nj) + 31) / 32) * 32); }
 
 template <class T> static size_t macro_smem_bytes(const KParams &p, int nt, int stages)
 {
-    return (size_t)stages * nt * ((kMRec + 4) * sizeof(T) + 12 * sizeof(int)) + (size_t)2 * p.ni * 4 * sizeof(T);
+    return (size_t)stages * (nt / 4) * ((kMRec + 4) * sizeof(T) + 12 * sizeof(int)) + (size_t)2 * p.ni * 4 * sizeof(T);
+}
+
+template <class T, int S> static size_t sweep_bytes_s(const KParams &p, bool withF)
+{
+    switch (p.sweep_vpt) {
+    case 4: return sweep_smem_bytes<T, S, 4>(p.sweep_pc, p.sweep_tv, p.ni, withF);
+    case 2: return sweep_smem_bytes<T, S, 2>(p.sweep_pc, p.sweep_tv, p.ni, withF);
+    default: return sweep_smem_bytes<T, S, 1>(p.sweep_pc, p.sweep_tv, p.ni, withF);
+    }
 }
 
 template <class T> static size_t sweep_bytes(const KParams &p, bool withF, int stages)
 {
-    return stages == 8 ? sweep_smem_bytes<T, 8>(p.sweep_pc, p.sweep_tv, p.ni, withF)
-                       : sweep_smem_bytes<T, 4>(p.sweep_pc, p.sweep_tv, p.ni, withF);
+    return stages == 8 ? sweep_bytes_s<T, 8>(p, withF) : sweep_bytes_s<T, 4>(p, withF);
 }
 
 void blocks_per_instance(const KParams &p, int out[KT_COUNT])
@@ -1261,7 +1338,7 @@ void blocks_per_instance(const KParams &p, int out[KT_COUNT])
     out[KT_MACRO_SWEEP] = 1;
     out[KT_MACRO_POST] = nblk(p.N, 32);
     out[KT_MICRO_RES] = p.N * nvb;
-    out[KT_SWEEP] = nblk(p.Nv, p.sweep_tv);
+    out[KT_SWEEP] = nblk(p.Nv, p.sweep_tv * p.sweep_vpt);
 }
 
 // block shape, shared memory and prefetch depth common to all instances of
@@ -1271,10 +1348,12 @@ int plan_shapes(const KParams *hp, int n, bool fp64, Plan &pl)
     const size_t lim = 227 * 1024;
     pl.macro_threads = pl.sweep_threads = 0;
     pl.limiter_any = 0;
+    pl.sweep_vpt = hp[0].sweep_vpt;
     for (int i = 0; i < n; ++i) {
         pl.macro_threads = std::max(pl.macro_threads, macro_threads(hp[i]));
         pl.sweep_threads = std::max(pl.sweep_threads, hp[i].sweep_tv * hp[i].sweep_pc);
         pl.limiter_any |= hp[i].limiter;
+        if (hp[i].sweep_vpt != pl.sweep_vpt) return (int)cudaErrorInvalidValue;
     }
     for (int stages : {std::min(hp[0].macro_stages, 8), 4}) {
         size_t m = 0;
@@ -1298,6 +1377,24 @@ int plan_shapes(const KParams *hp, int n, bool fp64, Plan &pl)
     }
     if (pl.macro_smem > lim || pl.bwd_smem > lim) return (int)cudaErrorInvalidValue;
     return 0;
+}
+
+template <class T, bool FWD, int S>
+static void launch_sweep_s(const Plan &pl, cudaStream_t st, const Launch &L)
+{
+    const size_t sm = FWD ? pl.fwd_smem : pl.bwd_smem;
+    const int nb = pl.nblocks[KT_SWEEP], nt = pl.sweep_threads;
+    switch (pl.sweep_vpt) {
+    case 4: k_sweep<T, FWD, S, 4><<<nb, nt, sm, st>>>(L); break;
+    case 2: k_sweep<T, FWD, S, 2><<<nb, nt, sm, st>>>(L); break;
+    default: k_sweep<T, FWD, S, 1><<<nb, nt, sm, st>>>(L); break;
+    }
+}
+
+template <class T, bool FWD> static void launch_sweep(const Plan &pl, cudaStream_t st, const Launch &L)
+{
+    if (pl.sweep_stages == 8) launch_sweep_s<T, FWD, 8>(pl, st, L);
+    else launch_sweep_s<T, FWD, 4>(pl, st, L);
 }
 
 template <class T> static Launch launch_of(const Plan &pl, int kt)
@@ -1340,11 +1437,9 @@ static int iteration_t(const Plan &pl, cudaStream_t st, void **events)
     k_macro_post<T><<<nb[KT_MACRO_POST], 32, 0, st>>>(L(KT_MACRO_POST));
     mark(4);
     k_micro_residual<T><<<nb[KT_MICRO_RES], 256, 0, st>>>(L(KT_MICRO_RES));
-    if (pl.sweep_stages == 8) k_sweep<T, true, 8><<<nb[KT_SWEEP], pl.sweep_threads, pl.fwd_smem, st>>>(L(KT_SWEEP));
-    else k_sweep<T, true, 4><<<nb[KT_SWEEP], pl.sweep_threads, pl.fwd_smem, st>>>(L(KT_SWEEP));
+    launch_sweep<T, true>(pl, st, L(KT_SWEEP));
     mark(5);
-    if (pl.sweep_stages == 8) k_sweep<T, false, 8><<<nb[KT_SWEEP], pl.sweep_threads, pl.bwd_smem, st>>>(L(KT_SWEEP));
-    else k_sweep<T, false, 4><<<nb[KT_SWEEP], pl.sweep_threads, pl.bwd_smem, st>>>(L(KT_SWEEP));
+    launch_sweep<T, false>(pl, st, L(KT_SWEEP));
     mark(6);
     return (int)cudaGetLastError();
 }
@@ -1359,10 +1454,18 @@ template <class T> static int configure_t()
     };
     opt((const void *)k_macro_sweep<T, 8>);
     opt((const void *)k_macro_sweep<T, 4>);
-    opt((const void *)k_sweep<T, true, 8>);
-    opt((const void *)k_sweep<T, false, 8>);
-    opt((const void *)k_sweep<T, true, 4>);
-    opt((const void *)k_sweep<T, false, 4>);
+    opt((const void *)k_sweep<T, true, 8, 1>);
+    opt((const void *)k_sweep<T, false, 8, 1>);
+    opt((const void *)k_sweep<T, true, 4, 1>);
+    opt((const void *)k_sweep<T, false, 4, 1>);
+    opt((const void *)k_sweep<T, true, 8, 2>);
+    opt((const void *)k_sweep<T, false, 8, 2>);
+    opt((const void *)k_sweep<T, true, 4, 2>);
+    opt((const void *)k_sweep<T, false, 4, 2>);
+    opt((const void *)k_sweep<T, true, 8, 4>);
+    opt((const void *)k_sweep<T, false, 8, 4>);
+    opt((const void *)k_sweep<T, true, 4, 4>);
+    opt((const void *)k_sweep<T, false, 4, 4>);
     return (int)e;
 }
 

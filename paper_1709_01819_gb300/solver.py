@@ -90,17 +90,27 @@ class Solver:
         return B.idg_iterate_profiled(self.ctx, self.stream)
 
     def set_tuning(self, **kw):
-        """sweep_tv=, sweep_stages=, macro_stages=, graph= (launch shapes only)."""
+        """sweep_tv=, sweep_vpt=, sweep_stages=, macro_stages=, graph= (launch shapes only)."""
         keys = {"sweep_tv": B.IDG_TUNE_SWEEP_TV, "sweep_stages": B.IDG_TUNE_SWEEP_STAGES,
-                "macro_stages": B.IDG_TUNE_MACRO_STAGES, "graph": B.IDG_TUNE_GRAPH}
-        for k, v in kw.items():
+                "macro_stages": B.IDG_TUNE_MACRO_STAGES, "graph": B.IDG_TUNE_GRAPH,
+                "sweep_vpt": B.IDG_TUNE_SWEEP_VPT}
+        cur = self.tuning()
+        # shrink shared-memory use first so that every intermediate shape fits
+        if any(k in kw for k in ("sweep_tv", "sweep_vpt", "sweep_stages", "macro_stages")):
+            for k in ("sweep_stages", "macro_stages"):
+                B.idg_set_tuning(self.ctx, keys[k], 4)
+            B.idg_set_tuning(self.ctx, keys["sweep_vpt"], 1)
+            B.idg_set_tuning(self.ctx, keys["sweep_tv"], 1)
+        for k in ("graph", "sweep_tv", "sweep_vpt", "sweep_stages", "macro_stages"):
+            v = kw.get(k, cur[k])
             B.idg_set_tuning(self.ctx, keys[k], int(v))
 
     def tuning(self) -> dict:
         return {"sweep_tv": B.idg_get_tuning(self.ctx, B.IDG_TUNE_SWEEP_TV),
                 "sweep_stages": B.idg_get_tuning(self.ctx, B.IDG_TUNE_SWEEP_STAGES),
                 "macro_stages": B.idg_get_tuning(self.ctx, B.IDG_TUNE_MACRO_STAGES),
-                "graph": B.idg_get_tuning(self.ctx, B.IDG_TUNE_GRAPH)}
+                "graph": B.idg_get_tuning(self.ctx, B.IDG_TUNE_GRAPH),
+                "sweep_vpt": B.idg_get_tuning(self.ctx, B.IDG_TUNE_SWEEP_VPT)}
 
     def moments(self) -> np.ndarray:
         return B.idg_get_moments(self.ctx, self.N, self.stream)
@@ -126,8 +136,13 @@ class BatchSolver:
         for s in self.solvers:
             s.init_uniform()
         if autotune:
+            # one batch shares the velocities-per-thread of its sweeps: tune
+            # the largest instance first and keep its choice for the rest
             tuner = Autotuner()
-            for s in self.solvers:
+            order = sorted(self.solvers, key=lambda s: -s.N * s.Nv)
+            vpt = tuner.tune(order[0])["sweep_vpt"]
+            tuner.candidates_vpt = (vpt,)
+            for s in order[1:]:
                 tuner.tune(s)
         self._make_batch()
 
@@ -164,8 +179,9 @@ class Autotuner:
     candidate on the problem itself; results are cached per (cells in i, in j,
     velocities, precision) so a batch of same-sized problems is timed once."""
 
-    def __init__(self, candidates_tv=(2, 4, 8, 16, 32), repeats: int = 3):
+    def __init__(self, candidates_tv=(2, 4, 8, 16), candidates_vpt=(1, 2, 4), repeats: int = 3):
         self.candidates_tv = candidates_tv
+        self.candidates_vpt = candidates_vpt
         self.repeats = repeats
         self.cache = {}
 
@@ -177,15 +193,17 @@ class Autotuner:
         G, H, W = solver.get_state()
         best, best_t = None, float("inf")
         for tv in self.candidates_tv:
-            for stages in (8, 4):
-                try:
-                    solver.set_tuning(sweep_tv=tv, sweep_stages=stages, macro_stages=stages)
-                except B.IdgError:
-                    continue
-                solver.iterate_profiled()  # warm-up
-                t = min(float(np.sum(solver.iterate_profiled())) for _ in range(self.repeats))
-                if t < best_t:
-                    best, best_t = dict(sweep_tv=tv, sweep_stages=stages, macro_stages=stages), t
+            for vpt in self.candidates_vpt:
+                for stages in (4, 8):
+                    try:
+                        solver.set_tuning(sweep_tv=tv, sweep_vpt=vpt, sweep_stages=stages, macro_stages=stages)
+                    except B.IdgError:
+                        continue
+                    solver.iterate_profiled()  # warm-up
+                    t = min(float(np.sum(solver.iterate_profiled())) for _ in range(self.repeats))
+                    if t < best_t:
+                        best = dict(sweep_tv=tv, sweep_vpt=vpt, sweep_stages=stages, macro_stages=stages)
+                        best_t = t
         solver.set_tuning(**best)
         solver.set_state(G, H, W)  # timing iterations leave no trace
         self.cache[key] = best

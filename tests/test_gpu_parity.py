@@ -149,10 +149,10 @@ def test_graph_replay_and_tuning_do_not_change_results():
     prob = I.cavity(12, Kn=0.075, U=0.15, nv=16, vmax=4.0)
     prob.nodes_x, prob.nodes_y = I.uniform_nodes(12, 10, 0, 1, 0, 0.9)
     out = []
-    for graph, tv, stages in ((1, 8, 8), (0, 8, 8), (1, 2, 4), (0, 4, 4)):
+    for graph, tv, stages, vpt in ((1, 8, 8, 1), (0, 8, 8, 2), (1, 2, 4, 4), (0, 4, 4, 1)):
         for prec in ("fp64", "mixed"):
             s = _solver(prob, prec)
-            s.set_tuning(graph=graph, sweep_tv=tv, sweep_stages=stages, macro_stages=stages)
+            s.set_tuning(graph=graph, sweep_tv=tv, sweep_stages=stages, macro_stages=stages, sweep_vpt=vpt)
             s.init_uniform()
             s.iterate(37)
             G, H, W = s.get_state()
