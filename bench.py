@@ -51,17 +51,20 @@ def workload(name: str) -> I.Problem:
 
 
 def algorithmic_bytes(prob: I.Problem, s: int, nf: int):
-    """Bytes each launch group must move (s = bytes per scalar of f).
-    cell_prep: read f~ twice (moments, fb+), write fb+ (2 scalars each per cell-velocity);
-    face_moments: read fb+ once;  face_flux: read fb+ once, write the face flux
-    (2 per face-velocity);  k_sweep_fwd: read the face fluxes once, read f~, write Delta*;
-    k_sweep_bwd: read Delta* and f~, write Delta and f~."""
+    """Compulsory bytes of each launch group (s = bytes per scalar of f; every
+    per-velocity array holds a G and an H scalar):
+    cell_prep: read f~ twice (moments, fb+), write fb+        6s per cell-velocity
+    face_moments: read fb+, write fb at the faces             2s per cell-velocity + 2s per face-velocity
+    face_flux: read fb, write the face flux                   4s per face-velocity
+    k_sweep_fwd: micro residual (read the fluxes and f~, write R), then the
+                 forward sweep (read R, write Delta*)         2s per face-velocity + 8s per cell-velocity
+    k_sweep_bwd: read Delta* and f~, write Delta and f~       8s per cell-velocity"""
     N, Nv = prob.ncells, prob.nvel
     return {
         "cell_prep": 6 * s * N * Nv,
-        "face_moments": 2 * s * N * Nv,
-        "face_flux": 2 * s * N * Nv + 2 * s * nf * Nv,
-        "k_sweep_fwd": 2 * s * nf * Nv + 4 * s * N * Nv,
+        "face_moments": 2 * s * N * Nv + 2 * s * nf * Nv,
+        "face_flux": 4 * s * nf * Nv,
+        "k_sweep_fwd": 2 * s * nf * Nv + 8 * s * N * Nv,
         "k_sweep_bwd": 8 * s * N * Nv,
     }
 

@@ -168,6 +168,12 @@ idg_status idg_get_residual_history(idg_ctx *ctx, double *out, int cap, int *n);
  * j-faces row by row; normal from the lower to the higher cell index side. */
 idg_status idg_get_face_flux_moments(idg_ctx *ctx, double *phi4, void *stream);
 
+/* Force (x, y) of the gas on the walls of the sides in side_mask (bit s =
+ * side s; each must be IDG_BC_WALL): the sum over their faces of the momentum
+ * components of Phi (Eq. 27) of the last iteration, oriented from the gas
+ * into the wall (the objective of idg_adjoint).  force2: host, 2 doubles. */
+idg_status idg_get_wall_force(idg_ctx *ctx, int side_mask, double *force2, void *stream);
+
 /* One iteration with a CUDA event recorded between its kernel launches on
  * the caller's stream (synchronises it).  kernel_ms[0..5] receives the
  * device time of: cell prep, interior faces, boundary faces, macroscopic
@@ -220,6 +226,67 @@ idg_status idg_batch_bind_workspace(idg_batch *b, void *dev_ptr, size_t bytes);
  * and an instance is left above it, IDG_ERR_NONFINITE if one diverged. */
 idg_status idg_batch_iterate(idg_batch *b, int max_iter, double tol, void *stream, int *iters_done,
                              double *max_residual, int *converged);
+
+/* ---------------------------------------------------------------------------
+ * Discrete adjoint of the steady solve.  The paper has no adjoint; this one
+ * differentiates the discrete iteration of Section 2.3 (Eq. 10-20, 23, 26-32,
+ * 34-35) in float64 at the state the context holds, which should be
+ * converged (the gradient is that of the steady state only to the extent
+ * that it is).  With u = (f~, W) and one iteration u -> u + P^-1 R(u) (macro
+ * predictor, then micro LU-SGS), the adjoint iterates the transposed
+ * fixed-point map lambda <- dJ/du + (I + P^-1 dR/du)^T lambda: the transposed
+ * micro sweeps, then the transposed macroscopic block sweeps (Euler flux
+ * Jacobians), then one vector-Jacobian product of the residual through the
+ * face fluxes, the reconstruction, the limiter and the cell equilibria.  It
+ * converges at the rate of the forward iteration.  At its fixed point
+ * dJ/dp = dJ/dp|_u + lambda^T d(iteration)/dp.
+ *
+ * Objective J: the x (IDG_OBJ_FORCE_X) or y (IDG_OBJ_FORCE_Y) force of the gas
+ * on the walls of the sides in side_mask (bit s = side s; each a wall): the sum
+ * over their faces of the momentum flux Phi (Eq. 27) through the face,
+ * oriented from the gas into the wall.  Lid shear force of a cavity, drag of
+ * a body.
+ *
+ * Parameters (params[i], one gradient each in grad[i]):
+ *   IDG_PARAM(IDG_PAR_KN, 0)            the Knudsen number of idg_set_gas
+ *   IDG_PARAM(IDG_PAR_WALL_T, mask)     temperature (units of T_ref) of the
+ *                                       walls of the sides in mask, together
+ *   IDG_PARAM(IDG_PAR_WALL_U, mask)     x velocity of those walls
+ *   IDG_PARAM(IDG_PAR_WALL_V, mask)     y velocity of those walls
+ *
+ * Closed domains (walls and periodic sides only): the mass residuals sum to
+ * zero identically, so the steady states form a one-parameter family indexed
+ * by the total mass M = sum_c Omega_c rho_c, and the iteration has a neutral
+ * mode.  There the adjoint also solves for the total mass as a second
+ * right-hand side and returns dJ/dp at fixed M (the mass of the context's
+ * state); both solves run together.  With a far-field side the steady state
+ * is unique and one solve is run.
+ *
+ * workspace: caller-owned device memory, 256-byte aligned, at least
+ * idg_adjoint_workspace_size bytes, used only during the call.  The context's
+ * own workspace and state are read, not changed.  Iterates until the norm of
+ * the update of lambda, relative to the first one, is <= tol, or max_iter
+ * (1 ... 65536) iterations.  J receives the objective at the context's state;
+ * residual the last relative update.  Returns IDG_ERR_ARG for an invalid
+ * objective, parameter or side (not a wall), or when numerics flags are set;
+ * IDG_ERR_NOT_CONVERGED (results still written) if tol > 0 was not reached;
+ * IDG_ERR_NONFINITE if the update overflowed.  Synchronises the stream.
+ * ------------------------------------------------------------------------- */
+enum { IDG_OBJ_FORCE_X = 0, IDG_OBJ_FORCE_Y = 1 };
+enum { IDG_PAR_KN = 0, IDG_PAR_WALL_T = 1, IDG_PAR_WALL_U = 2, IDG_PAR_WALL_V = 3 };
+#define IDG_PARAM(kind, side_mask) ((kind) | ((side_mask) << 8))
+idg_status idg_adjoint_workspace_size(idg_ctx *ctx, size_t *bytes);
+idg_status idg_adjoint(idg_ctx *ctx, int objective, int side_mask, const int *params, int nparam,
+                       void *workspace, size_t bytes, int max_iter, double tol, void *stream, double *J,
+                       double *grad, int *iters_done, double *residual);
+/* The adjoint variables lambda = (lambda_G, lambda_H [ncell][nvel], lambda_W
+ * [ncell][4]) left in the workspace by the last idg_adjoint call of this
+ * context.  which = 0: the adjoint of the returned gradient (for a closed
+ * domain, the fixed-mass combination of the two solves); 1: the solve seeded
+ * by the objective alone; 2: the one seeded by the total mass (closed domains
+ * only).  Host arrays; any may be NULL. */
+idg_status idg_adjoint_state(idg_ctx *ctx, const void *workspace, int which, double *lamG, double *lamH,
+                             double *lamW, void *stream);
 
 #ifdef __cplusplus
 }

@@ -20,6 +20,14 @@ IDG_NC_TRAP, IDG_NC_SIMPSON, IDG_GAUSS_HERMITE = 0, 1, 2
 IDG_IMIN, IDG_IMAX, IDG_JMIN, IDG_JMAX = 0, 1, 2, 3
 IDG_BGK, IDG_SHAKHOV = 0, 1
 IDG_TUNE_SWEEP_TV, IDG_TUNE_SWEEP_STAGES, IDG_TUNE_MACRO_STAGES, IDG_TUNE_GRAPH, IDG_TUNE_SWEEP_VPT = 1, 2, 3, 4, 5
+IDG_OBJ_FORCE_X, IDG_OBJ_FORCE_Y = 0, 1
+IDG_PAR_KN, IDG_PAR_WALL_T, IDG_PAR_WALL_U, IDG_PAR_WALL_V = 0, 1, 2, 3
+
+
+def IDG_PARAM(kind: int, side_mask: int = 0) -> int:
+    """Parameter id of idg_adjoint: a kind and, for wall parameters, a mask of sides."""
+    return kind | (side_mask << 8)
+
 
 _STATUS = {0: "IDG_OK", 1: "IDG_ERR_ARG", 2: "IDG_ERR_STATE", 3: "IDG_ERR_CUDA", 4: "IDG_ERR_OOM",
            5: "IDG_ERR_NONFINITE", 6: "IDG_ERR_TIMEOUT", 7: "IDG_ERR_NOT_CONVERGED"}
@@ -58,6 +66,10 @@ SIGNATURES = [
     ("idg_batch_workspace_size", _i, [_vp, _P(_sz)]),
     ("idg_batch_bind_workspace", _i, [_vp, _vp, _sz]),
     ("idg_batch_iterate", _i, [_vp, _i, _d, _vp, _P(_i), _P(_d), _P(_i)]),
+    ("idg_get_wall_force", _i, [_vp, _i, _P(_d), _vp]),
+    ("idg_adjoint_workspace_size", _i, [_vp, _P(_sz)]),
+    ("idg_adjoint_state", _i, [_vp, _vp, _i, _P(_d), _P(_d), _P(_d), _vp]),
+    ("idg_adjoint", _i, [_vp, _i, _i, _P(_i), _i, _vp, _sz, _i, _d, _vp, _P(_d), _P(_d), _P(_i), _P(_d)]),
 ]
 
 _lib = None
@@ -209,6 +221,38 @@ def idg_get_face_flux_moments(ctx, nf, stream=None):
     out = np.zeros((nf, 4))
     check(ctx, lib().idg_get_face_flux_moments(ctx, dptr(out), stream))
     return out
+
+
+def idg_get_wall_force(ctx, side_mask, stream=None):
+    out = np.zeros(2)
+    check(ctx, lib().idg_get_wall_force(ctx, side_mask, dptr(out), stream))
+    return out
+
+
+def idg_adjoint_workspace_size(ctx) -> int:
+    n = C.c_size_t()
+    check(ctx, lib().idg_adjoint_workspace_size(ctx, C.byref(n)))
+    return n.value
+
+
+def idg_adjoint(ctx, objective, side_mask, params, ws_ptr: int, ws_bytes: int, max_iter, tol, stream=None):
+    """Returns (status, J, grad[len(params)], iterations, relative update)."""
+    p = np.ascontiguousarray(params, dtype=np.int32)
+    g = np.zeros(max(len(p), 1))
+    J, r, n = C.c_double(), C.c_double(), C.c_int()
+    st = check(ctx, lib().idg_adjoint(ctx, objective, side_mask, p.ctypes.data_as(_P(_i)), len(p),
+                                      C.c_void_p(ws_ptr), ws_bytes, max_iter, tol, stream, C.byref(J),
+                                      dptr(g), C.byref(n), C.byref(r)),
+               allow=(IDG_ERR_NOT_CONVERGED,))
+    return st, J.value, g[: len(p)], n.value, r.value
+
+
+def idg_adjoint_state(ctx, ws_ptr: int, which, N, Nv, stream=None):
+    G = np.zeros((N, Nv))
+    H = np.zeros((N, Nv))
+    W = np.zeros((N, 4))
+    check(ctx, lib().idg_adjoint_state(ctx, C.c_void_p(ws_ptr), which, dptr(G), dptr(H), dptr(W), stream))
+    return G, H, W
 
 
 def idg_get_sizes(ctx):

@@ -1,6 +1,6 @@
 """Builds libidugks.so in-tree for sm_103a with nvcc (no cmake).
 
-The two translation units are compiled in parallel and linked into
+The translation units are compiled in parallel and linked into
 paper_1709_01819_gb300/lib/libidugks.so.
 """
 from __future__ import annotations
@@ -15,8 +15,9 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIBDIR = os.path.join(PKG, "lib")
 LIB = os.path.join(LIBDIR, "libidugks.so")
-SOURCES = ["idugks_host.cpp", "idugks_kernels.cu"]
-HEADERS = [os.path.join(ROOT, "include", "idugks.h"), os.path.join(CSRC, "idugks_internal.h")]
+SOURCES = ["idugks_host.cpp", "idugks_kernels.cu", "idugks_adjoint.cu"]
+HEADERS = [os.path.join(ROOT, "include", "idugks.h")] + [
+    os.path.join(CSRC, h) for h in ("idugks_internal.h", "idugks_adjoint.h", "adjoint_math.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 

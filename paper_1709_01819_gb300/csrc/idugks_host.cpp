@@ -3,6 +3,7 @@
 // workspace layout, state transfer and the iteration driver.
 #include "idugks.h"
 #include "idugks_internal.h"
+#include "idugks_adjoint.h"
 
 #include <cuda_runtime.h>
 
@@ -63,6 +64,9 @@ struct idg_ctx {
     long long host_iter = 0;   // iterations launched since bind
     long long start_iter = 0;  // iteration index of the last (re)start
     std::vector<double> hist;  // absolute residuals since the last (re)start
+    // last idg_adjoint: number of right-hand sides and the mass multiplier
+    int adj_nrhs = 0;
+    double adj_beta = 0.0;
 };
 
 namespace {
@@ -1145,6 +1149,28 @@ idg_status idg_get_face_flux_moments(idg_ctx *c, double *phi4, void *stream)
     return IDG_OK;
 }
 
+idg_status idg_get_wall_force(idg_ctx *c, int side_mask, double *force2, void *stream)
+{
+    idg_status s = check_ready(c);
+    if (s) return s;
+    if (!force2 || side_mask <= 0 || side_mask > 15) return fail(c, IDG_ERR_ARG, "invalid wall-force arguments");
+    for (int sd = 0; sd < 4; ++sd)
+        if (((side_mask >> sd) & 1) && c->bc_kind[sd] != IDG_BC_WALL)
+            return fail(c, IDG_ERR_ARG, "side %d is not a wall", sd);
+    std::vector<double> phi((size_t)4 * c->nf);
+    if ((s = idg_get_face_flux_moments(c, phi.data(), stream))) return s;
+    double fx = 0.0, fy = 0.0;
+    for (int f = 0; f < c->nf; ++f) {
+        if (c->fbc[f] != IDG_BC_WALL || !((side_mask >> c->fside[f]) & 1)) continue;
+        const double on = c->fL[f] >= 0 ? 1.0 : -1.0;  // from the gas into the wall
+        fx += on * phi[(size_t)4 * f + 1];
+        fy += on * phi[(size_t)4 * f + 2];
+    }
+    force2[0] = fx;
+    force2[1] = fy;
+    return IDG_OK;
+}
+
 }  // extern "C"
 
 // ===========================================================================
@@ -1433,6 +1459,239 @@ idg_status idg_batch_iterate(idg_batch *b, int max_iter, double tol, void *strea
     if (max_residual) *max_residual = worst;
     if (ret) return bfail(b, ret, "an instance became non-finite");
     if (tol > 0 && !all) return bfail(b, IDG_ERR_NOT_CONVERGED, "largest residual %.3e above tol %.3e", worst, tol);
+    return IDG_OK;
+}
+
+}  // extern "C"
+
+// -------------------------------------------------------------------------
+// discrete adjoint of the steady solve
+// -------------------------------------------------------------------------
+namespace {
+
+idg::AParams adjoint_shape(const idg_ctx *c)
+{
+    idg::AParams a{};
+    a.N = c->N; a.Nv = c->Nv; a.nf = c->nf; a.ni = c->ni; a.nj = c->nj;
+    return a;
+}
+
+// A domain bounded by walls and periodic sides only conserves mass in its
+// steady equations (the mass residuals sum to zero identically), so its
+// steady states form a one-parameter family indexed by the total mass.  The
+// adjoint then solves a second right-hand side, the total mass, and returns
+// gradients at fixed total mass.
+int adjoint_rhs(const idg_ctx *c)
+{
+    for (int sd = 0; sd < 4; ++sd)
+        if (c->bc_kind[sd] == IDG_BC_FARFIELD) return 1;
+    return 2;
+}
+
+}  // namespace
+
+extern "C" {
+
+idg_status idg_adjoint_workspace_size(idg_ctx *c, size_t *bytes)
+{
+    if (!c || !bytes) return IDG_ERR_ARG;
+    idg_status s = build(c);
+    if (s) return s;
+    *bytes = idg::adjoint_layout(adjoint_shape(c), adjoint_rhs(c), nullptr, nullptr);
+    return IDG_OK;
+}
+
+idg_status idg_adjoint(idg_ctx *c, int objective, int side_mask, const int *params, int nparam,
+                       void *workspace, size_t bytes, int max_iter, double tol, void *stream, double *J,
+                       double *grad, int *iters_done, double *residual)
+{
+    idg_status s = check_ready(c);
+    if (s) return s;
+    if (objective != IDG_OBJ_FORCE_X && objective != IDG_OBJ_FORCE_Y)
+        return fail(c, IDG_ERR_ARG, "unknown objective %d", objective);
+    if (side_mask <= 0 || side_mask > 15) return fail(c, IDG_ERR_ARG, "side mask %d out of range", side_mask);
+    for (int sd = 0; sd < 4; ++sd)
+        if (((side_mask >> sd) & 1) && c->bc_kind[sd] != IDG_BC_WALL)
+            return fail(c, IDG_ERR_ARG, "objective side %d is not a wall", sd);
+    if (nparam < 0 || (nparam > 0 && (!params || !grad))) return fail(c, IDG_ERR_ARG, "invalid parameter list");
+    for (int i = 0; i < nparam; ++i) {
+        int kind = params[i] & 0xff, mask = params[i] >> 8;
+        if (kind == IDG_PAR_KN) {
+            if (mask) return fail(c, IDG_ERR_ARG, "parameter %d: Kn takes no side mask", i);
+            continue;
+        }
+        if (kind < IDG_PAR_WALL_T || kind > IDG_PAR_WALL_V || mask <= 0 || mask > 15)
+            return fail(c, IDG_ERR_ARG, "parameter %d: invalid id 0x%x", i, params[i]);
+        for (int sd = 0; sd < 4; ++sd)
+            if (((mask >> sd) & 1) && c->bc_kind[sd] != IDG_BC_WALL)
+                return fail(c, IDG_ERR_ARG, "parameter %d: side %d is not a wall", i, sd);
+    }
+    if (c->flags) return fail(c, IDG_ERR_ARG, "the adjoint does not support numerics flags 0x%x", c->flags);
+    if (max_iter < 1 || max_iter > idg::kMaxHist) return fail(c, IDG_ERR_ARG, "max_iter out of [1, %d]", idg::kMaxHist);
+    if (!workspace) return fail(c, IDG_ERR_ARG, "null adjoint workspace");
+    if (((uintptr_t)workspace) & 255) return fail(c, IDG_ERR_ARG, "adjoint workspace must be 256-byte aligned");
+    const int nrhs = adjoint_rhs(c);
+    const size_t need = idg::adjoint_layout(adjoint_shape(c), nrhs, nullptr, nullptr);
+    if (bytes < need) return fail(c, IDG_ERR_OOM, "adjoint workspace of %zu bytes, need %zu", bytes, need);
+
+    idg::AParams base = adjoint_shape(c);
+    const KParams &k = c->kp;
+    base.K = c->K; base.shakhov = c->model == IDG_SHAKHOV; base.limiter = c->limiter;
+    base.dt = k.dt; base.h = k.h; base.mu_ref = k.mu_ref; base.RT_ref = k.RT_ref; base.omega = k.omega;
+    base.Pr = k.Pr; base.gam = k.gam; base.lusgs_omega = k.lusgs_omega;
+    base.kappa = base.shakhov ? (1.0 - c->Pr) / (c->K + 4) : 0.0;
+    base.area = k.area; base.dtimp = k.dtimp; base.fgeo = k.fgeo; base.ux = k.ux; base.uy = k.uy; base.w = k.w;
+    base.cface = k.cface; base.cnb = k.cnb; base.csign = k.csign; base.fL = k.fL; base.fR = k.fR;
+    base.fbc = k.fbc; base.fside = k.fside; base.W = k.W;
+    for (int sd = 0; sd < 4; ++sd) {
+        base.b_kind[sd] = c->bc_kind[sd];
+        base.b_rho[sd] = c->bc_kind[sd] == IDG_BC_WALL ? 1.0 : c->bc_rho[sd];
+        base.b_u[sd] = c->bc_u[sd];
+        base.b_v[sd] = c->bc_v[sd];
+        base.b_RT[sd] = c->bc_T[sd] * c->RT_ref;
+    }
+    base.obj_axis = objective == IDG_OBJ_FORCE_X ? 0 : 1;
+    base.obj_mask = side_mask;
+    idg::AParams A[2];
+    idg::adjoint_layout(base, nrhs, (char *)workspace, A);
+
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(A[0].lsw, c->clsg.data(), c->clsg.size() * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(A[0].crv, c->cr.data(), c->cr.size() * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return cuda_fail(c, e, "adjoint geometry upload");
+    int rc = idg::launch_from_dev(c->kp, c->precision == IDG_FP64, A[0].G, A[0].H, st);
+    if (!rc) rc = idg::launch_adjoint_setup(A[0], st);
+    for (int r = 0; r < nrhs && !rc; ++r) rc = idg::launch_adjoint_zero(A[r], st);
+    if (rc) return cuda_fail(c, (cudaError_t)rc, "adjoint setup");
+
+    // Transposed fixed-point iterations, checked every chunk.  With two
+    // right-hand sides both lambdas grow linearly along the neutral mode
+    // (whose lambda_f part is zero); the multiplier beta = -<dW_J, dW_m> /
+    // <dW_m, dW_m> of the lambda_W increments cancels the growth, and
+    // lambda_J + beta lambda_m is the fixed-mass adjoint.
+    const int chunk = 32;
+    const size_t N4 = (size_t)4 * c->N;
+    std::vector<double> buf[2], dW[2];
+    double first = -1.0, rel = NAN, beta = 0.0;
+    int done = 0;
+    bool converged = false;
+    while (done < max_iter) {
+        int n = std::min(chunk, max_iter - done);
+        for (int q = 0; q < n; ++q)
+            for (int r = 0; r < nrhs; ++r)
+                if ((rc = idg::launch_adjoint_iteration(A[r], done + q, st))) return cuda_fail(c, (cudaError_t)rc, "adjoint");
+        for (int r = 0; r < nrhs; ++r) {
+            buf[r].assign(n, 0.0);
+            dW[r].assign(N4, 0.0);
+            if ((e = cudaMemcpyAsync(buf[r].data(), A[r].res + done, n * 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+                (e = cudaMemcpyAsync(dW[r].data(), A[r].dlamW, N4 * 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+                return cuda_fail(c, e, "adjoint residual");
+        }
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(c, e, "adjoint iteration");
+        done += n;
+        double fnorm = buf[0][n - 1], w2 = 0.0, ww = 0.0, wm = 0.0;
+        bool finite = std::isfinite(fnorm);
+        if (nrhs == 2) {
+            for (size_t i = 0; i < N4; ++i) { ww += dW[1][i] * dW[1][i]; wm += dW[0][i] * dW[1][i]; }
+            beta = ww > 0 ? -wm / ww : 0.0;
+            fnorm += std::fabs(beta) * buf[1][n - 1];
+            finite = finite && std::isfinite(buf[1][n - 1]);
+        }
+        for (size_t i = 0; i < N4; ++i) {
+            double d = dW[0][i] + (nrhs == 2 ? beta * dW[1][i] : 0.0);
+            w2 += d * d;
+        }
+        const double upd = fnorm + std::sqrt(w2);
+        if (!finite || !std::isfinite(upd)) {
+            if (iters_done) *iters_done = done;
+            return fail(c, IDG_ERR_NONFINITE, "adjoint update became non-finite");
+        }
+        // relative to the lambda_f part of the first update, dJ/df
+        if (first < 0) first = buf[0][0] > 0 ? buf[0][0] : 1.0;
+        rel = upd / first;
+        if (tol > 0 && rel <= tol) { converged = true; break; }
+    }
+
+    // objective at the linearisation state and the parameter gradients of
+    // the last pass: sums in a fixed order on the host
+    std::vector<double> fpar((size_t)idg::kFP * c->nf), fpp[2], cpp[2];
+    if ((e = cudaMemcpyAsync(fpar.data(), A[0].fpar, fpar.size() * 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_fail(c, e, "adjoint results");
+    for (int r = 0; r < nrhs; ++r) {
+        fpp[r].assign((size_t)idg::kFPar * c->nf, 0.0);
+        cpp[r].assign((size_t)2 * c->N, 0.0);
+        if ((e = cudaMemcpyAsync(fpp[r].data(), A[r].fpp, fpp[r].size() * 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(cpp[r].data(), A[r].cpp, cpp[r].size() * 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+            return cuda_fail(c, e, "adjoint results");
+    }
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(c, e, "adjoint results");
+    double Jv = 0.0, knsum = 0.0, side_par[4][3] = {};
+    for (int f = 0; f < c->nf; ++f) {
+        const double *fp = &fpar[(size_t)idg::kFP * f];
+        const int sd = c->fside[f];
+        if (c->fbc[f] == IDG_BC_WALL && ((side_mask >> sd) & 1)) Jv += fp[idg::FP_ON] * fp[idg::FP_PHI1 + base.obj_axis];
+    }
+    for (int r = 0; r < nrhs; ++r) {
+        const double wr = r == 0 ? 1.0 : beta;
+        for (int f = 0; f < c->nf; ++f) {
+            knsum += wr * fpp[r][(size_t)idg::kFPar * f + 3];
+            if (c->fbc[f] == IDG_BC_WALL)
+                for (int q = 0; q < 3; ++q) side_par[c->fside[f]][q] += wr * fpp[r][(size_t)idg::kFPar * f + q];
+        }
+        for (int q = 0; q < c->N; ++q) knsum += wr * (cpp[r][2 * q] + cpp[r][2 * q + 1]);
+    }
+    for (int i = 0; i < nparam; ++i) {
+        int kind = params[i] & 0xff, mask = params[i] >> 8;
+        double g = 0.0;
+        if (kind == IDG_PAR_KN) g = knsum / c->Kn;
+        else
+            for (int sd = 0; sd < 4; ++sd) {
+                if (!((mask >> sd) & 1)) continue;
+                if (kind == IDG_PAR_WALL_U) g += side_par[sd][0];
+                else if (kind == IDG_PAR_WALL_V) g += side_par[sd][1];
+                else g += side_par[sd][2] * c->RT_ref;
+            }
+        grad[i] = g;
+    }
+    c->adj_beta = beta;
+    c->adj_nrhs = nrhs;
+    if (J) *J = Jv;
+    if (iters_done) *iters_done = done;
+    if (residual) *residual = rel;
+    if (tol > 0 && !converged) return fail(c, IDG_ERR_NOT_CONVERGED, "adjoint update %.3e above tol %.3e", rel, tol);
+    return IDG_OK;
+}
+
+idg_status idg_adjoint_state(idg_ctx *c, const void *workspace, int which, double *lamG, double *lamH,
+                             double *lamW, void *stream)
+{
+    idg_status s = check_ready(c);
+    if (s) return s;
+    if (!workspace || (((uintptr_t)workspace) & 255)) return fail(c, IDG_ERR_ARG, "invalid adjoint workspace");
+    if (c->adj_nrhs < 1) return fail(c, IDG_ERR_STATE, "no adjoint has been run");
+    if (which < 0 || which > c->adj_nrhs || (which == 2 && c->adj_nrhs < 2))
+        return fail(c, IDG_ERR_ARG, "adjoint solve %d not available", which);
+    const double wJ = which == 2 ? 0.0 : 1.0;
+    const double wm = which == 0 ? c->adj_beta : (which == 2 ? 1.0 : 0.0);
+    idg::AParams A[2];
+    idg::adjoint_layout(adjoint_shape(c), c->adj_nrhs, (char *)workspace, A);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t n = (size_t)c->N * c->Nv, n4 = (size_t)4 * c->N;
+    double *out[3] = {lamG, lamH, lamW};
+    const size_t cnt[3] = {n, n, n4};
+    for (int q = 0; q < 3; ++q) {
+        if (!out[q]) continue;
+        std::vector<double> v[2];
+        for (int r = 0; r < c->adj_nrhs; ++r) {
+            v[r].assign(cnt[q], 0.0);
+            const double *src = q == 0 ? A[r].lamG : (q == 1 ? A[r].lamH : A[r].lamW);
+            cudaError_t e = cudaMemcpyAsync(v[r].data(), src, cnt[q] * 8, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) return cuda_fail(c, e, "adjoint state");
+        }
+        for (size_t i = 0; i < cnt[q]; ++i) out[q][i] = wJ * v[0][i] + (c->adj_nrhs == 2 ? wm * v[1][i] : 0.0);
+    }
     return IDG_OK;
 }
 

@@ -26,6 +26,13 @@ import numpy as np
 BC_PERIODIC, BC_WALL, BC_FARFIELD = 0, 1, 2
 NC_TRAP, NC_SIMPSON, GAUSS_HERMITE = 0, 1, 2
 IMIN, IMAX, JMIN, JMAX = 0, 1, 2, 3
+# parameters of the steady solve that gradients are taken with respect to:
+# kind | (mask of sides << 8), the ids of idg_adjoint
+PAR_KN, PAR_WALL_T, PAR_WALL_U, PAR_WALL_V = 0, 1, 2, 3
+
+
+def param(kind: int, side_mask: int = 0) -> int:
+    return kind | (side_mask << 8)
 
 
 @dataclasses.dataclass
@@ -235,3 +242,23 @@ def random_state(prob: Problem, seed: int, amp: float = 0.05):
     W = np.stack([rho, rho * u, rho * v, 0.5 * rho * (u * u + v * v + 3.0 * RT[:, 0])], axis=1)
     return (np.ascontiguousarray(G.reshape(N, -1)), np.ascontiguousarray(H.reshape(N, -1)),
             np.ascontiguousarray(W))
+
+
+def with_params(prob: Problem, params, values) -> Problem:
+    """A copy of prob with the parameters (param() ids) set to values: the
+    Knudsen number, or the temperature / x / y velocity of the walls of the
+    sides in the id's mask."""
+    bc = [list(b) for b in prob.bc]
+    kn = prob.Kn
+    for pid, val in zip(params, values):
+        kind, mask = pid & 0xFF, pid >> 8
+        if kind == PAR_KN:
+            kn = float(val)
+            continue
+        slot = {PAR_WALL_T: 4, PAR_WALL_U: 2, PAR_WALL_V: 3}[kind]
+        for side in range(4):
+            if (mask >> side) & 1:
+                if bc[side][0] != BC_WALL:
+                    raise ValueError(f"side {side} is not a wall")
+                bc[side][slot] = float(val)
+    return dataclasses.replace(prob, bc=[tuple(b) for b in bc], Kn=kn)

@@ -8,7 +8,7 @@ from __future__ import annotations
 import numpy as np
 
 from . import binding as B
-from .inputs import Problem
+from .inputs import Problem, with_params
 
 
 def configure(ctx, prob: Problem):
@@ -120,6 +120,93 @@ class Solver:
 
     def face_flux_moments(self) -> np.ndarray:
         return B.idg_get_face_flux_moments(self.ctx, self.nf, self.stream)
+
+    def wall_force(self, side_mask: int) -> np.ndarray:
+        """(Fx, Fy) of the gas on the walls of the sides in side_mask, from the
+        face fluxes of the last iteration."""
+        return B.idg_get_wall_force(self.ctx, side_mask, self.stream)
+
+    def adjoint(self, objective: int, side_mask: int, params, max_iter: int = 20000, tol: float = 1e-10,
+                keep_state: bool = False):
+        """Discrete adjoint at the current state (idg_adjoint).  Returns
+        (converged, J, dJ/dparams, iterations, relative update); with
+        keep_state the adjoint variables stay readable by adjoint_state()."""
+        nbytes = B.idg_adjoint_workspace_size(self.ctx)
+        ws = self.torch.empty(nbytes + 256, dtype=self.torch.uint8, device=f"cuda:{self.device}")
+        aligned = (ws.data_ptr() + 255) & ~255
+        st, J, g, n, r = B.idg_adjoint(self.ctx, objective, side_mask, list(params), aligned, nbytes,
+                                       max_iter, tol, self.stream)
+        self._adj_ws = (ws, aligned) if keep_state else None
+        return st == B.IDG_OK, J, g, n, r
+
+    def adjoint_state(self, which: int = 0):
+        """(lambda_G, lambda_H, lambda_W) of the last adjoint(keep_state=True):
+        which = 0 the adjoint of the gradient, 1 the objective's solve, 2 the
+        total-mass solve of a closed domain."""
+        ws, aligned = self._adj_ws
+        return B.idg_adjoint_state(self.ctx, aligned, which, self.N, self.Nv, self.stream)
+
+
+def apply_params(prob: Problem, params, values) -> Problem:
+    """A copy of prob with the adjoint parameters (IDG_PARAM ids) set to values."""
+    return with_params(prob, params, values)
+
+
+class SteadySolve:
+    """Differentiable steady solve: theta -> J, the force of the gas on walls.
+
+    ``SteadySolve.apply(theta, spec)`` with theta a float64 tensor of the
+    parameter values (spec.params, IDG_PARAM ids: wall temperature, wall
+    velocity, Kn) converges the IDUGKS problem spec.problem with those values
+    and returns J (a 0-d float64 tensor).  Its backward runs the hand-written
+    discrete adjoint of libidugks (idg_adjoint) on the converged state; no
+    iteration history is stored.  Built lazily on torch.autograd.Function.
+    """
+
+    _fn = None
+
+    @classmethod
+    def apply(cls, theta, spec: "SteadySpec"):
+        if cls._fn is None:
+            cls._fn = _make_steady_fn()
+        return cls._fn.apply(theta, spec)
+
+
+class SteadySpec:
+    def __init__(self, problem: Problem, params, objective=B.IDG_OBJ_FORCE_X, side_mask=1 << B.IDG_JMAX,
+                 precision="fp64", max_iter=20000, tol=1e-12, adj_max_iter=20000, adj_tol=1e-10):
+        self.problem, self.params = problem, list(params)
+        self.objective, self.side_mask, self.precision = objective, side_mask, precision
+        self.max_iter, self.tol, self.adj_max_iter, self.adj_tol = max_iter, tol, adj_max_iter, adj_tol
+        self.last = None  # (solver, forward info, adjoint info) of the last call
+
+
+def _make_steady_fn():
+    import torch
+
+    class _SteadySolveFn(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, theta, spec):
+            vals = theta.detach().cpu().double().numpy()
+            solver = Solver(apply_params(spec.problem, spec.params, vals), spec.precision)
+            solver.init_uniform()
+            ok, n, r = solver.iterate(spec.max_iter, spec.tol)
+            force = solver.wall_force(spec.side_mask)
+            J = float(force[0 if spec.objective == B.IDG_OBJ_FORCE_X else 1])
+            ctx.solver, ctx.spec = solver, spec
+            spec.last = {"solver": solver, "converged": ok, "iterations": n, "residual": r}
+            return torch.tensor(J, dtype=torch.float64, device=theta.device)
+
+        @staticmethod
+        def backward(ctx, gJ):
+            spec = ctx.spec
+            ok, J, g, n, r = ctx.solver.adjoint(spec.objective, spec.side_mask, spec.params,
+                                                spec.adj_max_iter, spec.adj_tol)
+            spec.last.update({"adj_converged": ok, "adj_J": J, "adj_iterations": n, "adj_residual": r})
+            grad = torch.as_tensor(np.asarray(g), dtype=torch.float64, device=gJ.device)
+            return gJ * grad, None
+
+    return _SteadySolveFn
 
 
 class BatchSolver:

@@ -1,0 +1,164 @@
+"""Discrete adjoint of the steady solve (idg_adjoint) on the GPU.
+
+Gradients of the wall force with respect to Kn, the wall temperature and the
+wall speed are checked against central finite differences of the FP64 oracle
+(each side converged to a relative residual of 1e-12 or below).  The cavity
+and the Couette channel are closed domains, whose steady states are fixed
+only once the total mass is: the adjoint returns gradients at fixed total
+mass, and the finite differences hold the base solution's mass.  Dot-product
+tests check the first two transposed passes against finite differences of the
+GPU's own forward iteration, which localises an error to the face/cell chain
+(first pass) or to the transposed sweeps (second pass).
+"""
+import numpy as np
+import pytest
+
+from paper_1709_01819_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+LID = 1 << I.JMAX
+CAV = I.cavity(n=12, nv=12, Kn=0.075, name="cavity_12x12_v12")
+CAV_PARAMS = [I.param(I.PAR_KN), I.param(I.PAR_WALL_T, 0xF), I.param(I.PAR_WALL_U, LID)]
+COU = I.couette(ncell=16, nv=12, Kn=0.1, name="couette_16_v12")
+COU_PARAMS = [I.param(I.PAR_KN), I.param(I.PAR_WALL_T, (1 << I.JMIN) | LID), I.param(I.PAR_WALL_U, LID)]
+
+_fd_cache = {}
+
+
+def oracle_fd(prob, params, mask):
+    key = (prob.name, tuple(params), mask)
+    if key not in _fd_cache:
+        from oracle import fd
+
+        J = fd.objective(prob, mask, 0, tol=1e-13)
+        g = fd.fd_gradient(prob, params, mask, 0, rel_step=1e-4, tol=1e-13)
+        _fd_cache[key] = (J, g)
+    return _fd_cache[key]
+
+
+def converged(prob, precision="fp64", tol=1e-12):
+    from paper_1709_01819_gb300.solver import Solver
+
+    s = Solver(prob, precision)
+    s.init_uniform()
+    ok, n, r = s.iterate(40000, tol)
+    assert ok, (n, r)
+    return s
+
+
+@pytest.mark.parametrize("prob,params", [(CAV, CAV_PARAMS), (COU, COU_PARAMS)], ids=["cavity", "couette"])
+def test_adjoint_gradient_matches_oracle_central_differences(prob, params):
+    from paper_1709_01819_gb300 import binding as B
+
+    s = converged(prob)
+    ok, J, g, n, r = s.adjoint(B.IDG_OBJ_FORCE_X, LID, params, 40000, 1e-11)
+    assert ok, (n, r)
+    Jo, gfd = oracle_fd(prob, params, LID)
+    Jf = s.wall_force(LID)[0]
+    assert abs(J - Jo) <= 1e-9 * abs(Jo), (J, Jo)
+    assert abs(Jf - Jo) <= 1e-9 * abs(Jo), (Jf, Jo)
+    rel = np.abs(g - gfd) / np.abs(gfd)
+    print(prob.name, "adjoint", g, "fd", gfd, "rel", rel, "iterations", n)
+    assert np.all(rel <= 1e-4), rel
+
+
+def _perturbed(s, G, H, W, vG, vH, vW, eps):
+    s.set_state(G + eps * vG, H + eps * vH, W + eps * vW)
+
+
+def test_adjoint_first_two_passes_match_forward_differences():
+    from paper_1709_01819_gb300 import binding as B
+
+    s = converged(CAV)
+    G, H, W = s.get_state()
+    rng = np.random.default_rng(1709)
+    vG = G * rng.standard_normal(G.shape)
+    vH = H * rng.standard_normal(H.shape)
+    vW = W * rng.standard_normal(W.shape)
+    # lambda_1 = dJ/du, lambda_2 = dJ/du + M^T dJ/du
+    # (the objective's own solve: which = 1)
+    s.adjoint(B.IDG_OBJ_FORCE_X, LID, [], 1, 0.0, keep_state=True)
+    l1 = s.adjoint_state(1)
+    s.adjoint(B.IDG_OBJ_FORCE_X, LID, [], 2, 0.0, keep_state=True)
+    l2 = s.adjoint_state(1)
+    eps = 1e-5
+
+    def J_and_step(sign):
+        _perturbed(s, G, H, W, vG, vH, vW, sign * eps)
+        s.iterate(1)
+        J = s.wall_force(LID)[0]
+        return J, s.get_state()
+
+    Jp, up = J_and_step(+1)
+    Jm, um = J_and_step(-1)
+    dot = lambda lam, a, b, c: float(np.sum(lam[0] * a) + np.sum(lam[1] * b) + np.sum(lam[2] * c))
+    fd1 = (Jp - Jm) / (2 * eps)
+    ad1 = dot(l1, vG, vH, vW)
+    assert abs(ad1 - fd1) <= 1e-6 * abs(fd1), (ad1, fd1)
+    # g^T M v against g^T (Phi(u + eps v) - Phi(u - eps v)) / (2 eps)
+    fd2 = dot(l1, *[(a - b) / (2 * eps) for a, b in zip(up, um)])
+    ad2 = dot([a - b for a, b in zip(l2, l1)], vG, vH, vW)
+    assert abs(ad2 - fd2) <= 1e-5 * abs(fd2), (ad2, fd2)
+
+
+def test_adjoint_mixed_precision_state():
+    """The adjoint (float64) linearised at a float32 state converged to 1e-6."""
+    from paper_1709_01819_gb300 import binding as B
+
+    s = converged(CAV, "mixed", tol=1e-6)
+    ok, J, g, n, r = s.adjoint(B.IDG_OBJ_FORCE_X, LID, CAV_PARAMS, 40000, 1e-10)
+    assert ok
+    _, gfd = oracle_fd(CAV, CAV_PARAMS, LID)
+    rel = np.abs(g - gfd) / np.abs(gfd)
+    print("mixed-precision state: adjoint", g, "fd", gfd, "rel", rel)
+    assert np.all(rel <= 1e-3), rel
+
+
+# reduced hypersonic cylinder: Ma 5, Shakhov, VHS 0.81, limiter, far field
+CYL = I.cylinder(ntheta=24, nr=12, nv=41, vmax=12.0, cfl_imp=10.0, name="cylinder_24x12_ma5_v41")
+WALL = 1 << I.JMIN
+CYL_PARAMS = [I.param(I.PAR_KN), I.param(I.PAR_WALL_T, WALL)]
+
+
+def test_adjoint_drag_gradient_cylinder():
+    """Drag of a cylinder in a Ma 5 stream (one solve: the far field fixes the
+    mass).  The limiter is differentiated where it is smooth."""
+    from paper_1709_01819_gb300 import binding as B
+
+    s = converged(CYL)
+    ok, J, g, n, r = s.adjoint(B.IDG_OBJ_FORCE_X, WALL, CYL_PARAMS, 40000, 1e-11)
+    assert ok, (n, r)
+    Jo, gfd = oracle_fd(CYL, CYL_PARAMS, WALL)
+    assert abs(J - Jo) <= 1e-9 * abs(Jo), (J, Jo)
+    rel = np.abs(g - gfd) / np.abs(gfd)
+    print(CYL.name, "drag", J, "adjoint", g, "fd", gfd, "rel", rel, "iterations", n)
+    assert np.all(rel <= 1e-4), rel
+
+
+def test_steady_solve_autograd():
+    import torch
+
+    from paper_1709_01819_gb300 import binding as B
+    from paper_1709_01819_gb300.solver import SteadySolve, SteadySpec
+
+    spec = SteadySpec(CAV, CAV_PARAMS, B.IDG_OBJ_FORCE_X, LID, tol=1e-12, adj_tol=1e-11)
+    theta = torch.tensor([CAV.Kn, 1.0, CAV.bc[I.JMAX][2]], dtype=torch.float64, requires_grad=True)
+    J = SteadySolve.apply(theta, spec)
+    (2.0 * J).backward()
+    Jo, gfd = oracle_fd(CAV, CAV_PARAMS, LID)
+    assert abs(float(J) - Jo) <= 1e-9 * abs(Jo)
+    assert np.all(np.abs(theta.grad.numpy() - 2.0 * gfd) <= 1e-4 * np.abs(2.0 * gfd))
+    assert spec.last["adj_converged"]
+
+
+def test_adjoint_rejects_invalid_requests():
+    from paper_1709_01819_gb300 import binding as B
+
+    s = converged(COU, tol=1e-6)
+    with pytest.raises(B.IdgError):  # objective on a periodic side
+        s.adjoint(B.IDG_OBJ_FORCE_X, 1 << I.IMIN, [], 1, 0.0)
+    with pytest.raises(B.IdgError):  # wall parameter on a periodic side
+        s.adjoint(B.IDG_OBJ_FORCE_X, LID, [I.param(I.PAR_WALL_T, 1 << I.IMAX)], 1, 0.0)
+    with pytest.raises(B.IdgError):  # Kn with a side mask
+        s.adjoint(B.IDG_OBJ_FORCE_X, LID, [I.param(I.PAR_KN, 1)], 1, 0.0)
