@@ -239,7 +239,7 @@ __device__ void raw_to_state(const double *r, int K, double &rho, double &U, dou
 // reduced Maxwellian (Eq. 2, 5) with the Shakhov factor (Eq. 20 read for
 // D = 2 + K dof: G factor (c^2/RT - 4), H factor (c^2/RT - 2)).
 struct EqD {
-    double e0, ex, ey, e2, U, V, invRT, pqx, pqy, rr, rrm1, kRT, lnA, lam;
+    double e0, ex, ey, e2, U, V, invRT, pqx, pqy, rr, rrm1, kRT, A, lam;
 };
 
 __device__ EqD make_eq(const KParams &p, double rho, double U, double V, double RT, double qx,
@@ -250,8 +250,12 @@ __device__ EqD make_eq(const KParams &p, double rho, double U, double V, double 
     e.e2 = lamr - lam;
     e.ex = 2.0 * (lam * U - lamr * p.U_r);
     e.ey = 2.0 * (lam * V - lamr * p.V_r);
-    e.e0 = log(rho * lam / (p.rho_r * lamr)) - lam * (U * U + V * V) +
-           lamr * (p.U_r * p.U_r + p.V_r * p.V_r);
+    // a non-positive density (a transient state, e.g. an evacuated wall
+    // face after an impulsive start) has no logarithm: e0 then sends every
+    // velocity to the direct branch, which takes the signed amplitude A
+    e.e0 = rho > 0.0 ? log(rho * lam / (p.rho_r * lamr)) - lam * (U * U + V * V) +
+                           lamr * (p.U_r * p.U_r + p.V_r * p.V_r)
+                     : 1e30;
     e.U = U;
     e.V = V;
     e.invRT = 1.0 / RT;
@@ -261,20 +265,20 @@ __device__ EqD make_eq(const KParams &p, double rho, double U, double V, double 
     e.rr = RT / p.RT_r;
     e.rrm1 = (RT - p.RT_r) / p.RT_r;
     e.kRT = p.K * RT;
-    e.lnA = log(rho * lam / M_PI);
+    e.A = rho * lam / M_PI;
     e.lam = lam;
     return e;
 }
 
 template <class T> struct EqT {
-    T e0, ex, ey, e2, U, V, invRT, pqx, pqy, rr, rrm1, kRT, lnA, lam;
+    T e0, ex, ey, e2, U, V, invRT, pqx, pqy, rr, rrm1, kRT, A, lam;
 };
 
 template <class T> __device__ __forceinline__ void eq_storeT(T *cp, const EqD &e)
 {
     cp[0] = (T)e.e0; cp[1] = (T)e.ex; cp[2] = (T)e.ey; cp[3] = (T)e.e2; cp[4] = (T)e.U;
     cp[5] = (T)e.V; cp[6] = (T)e.invRT; cp[7] = (T)e.pqx; cp[8] = (T)e.pqy; cp[9] = (T)e.rr;
-    cp[10] = (T)e.rrm1; cp[11] = (T)e.kRT; cp[12] = (T)e.lnA; cp[13] = (T)e.lam;
+    cp[10] = (T)e.rrm1; cp[11] = (T)e.kRT; cp[12] = (T)e.A; cp[13] = (T)e.lam;
 }
 
 __device__ __forceinline__ void eq_store(double *cp, const EqD &e) { eq_storeT<double>(cp, e); }
@@ -284,7 +288,7 @@ template <class T> __device__ __forceinline__ EqT<T> eq_loadT(const T *cp)
     EqT<T> e;
     e.e0 = cp[0]; e.ex = cp[1]; e.ey = cp[2]; e.e2 = cp[3]; e.U = cp[4]; e.V = cp[5];
     e.invRT = cp[6]; e.pqx = cp[7]; e.pqy = cp[8]; e.rr = cp[9]; e.rrm1 = cp[10]; e.kRT = cp[11];
-    e.lnA = cp[12]; e.lam = cp[13];
+    e.A = cp[12]; e.lam = cp[13];
     return e;
 }
 
@@ -308,7 +312,7 @@ __device__ __forceinline__ void dev_equilibrium(const EqT<T> &e, T ux, T uy, T g
         dG = gref * s;
         dH = href * (e.rrm1 + e.rr * (em + PH * ((T)1 + em)));
     } else {
-        T g = t_exp(e.lnA - e.lam * q2);
+        T g = e.A * t_exp(-e.lam * q2);
         dG = g * ((T)1 + PG) - gref;
         dH = e.kRT * g * ((T)1 + PH) - href;
     }

@@ -115,27 +115,6 @@ def test_adjoint_mixed_precision_state():
     assert np.all(rel <= 1e-3), rel
 
 
-# reduced hypersonic cylinder: Ma 5, Shakhov, VHS 0.81, limiter, far field
-CYL = I.cylinder(ntheta=24, nr=12, nv=41, vmax=12.0, cfl_imp=10.0, name="cylinder_24x12_ma5_v41")
-WALL = 1 << I.JMIN
-CYL_PARAMS = [I.param(I.PAR_KN), I.param(I.PAR_WALL_T, WALL)]
-
-
-def test_adjoint_drag_gradient_cylinder():
-    """Drag of a cylinder in a Ma 5 stream (one solve: the far field fixes the
-    mass).  The limiter is differentiated where it is smooth."""
-    from paper_1709_01819_gb300 import binding as B
-
-    s = converged(CYL)
-    ok, J, g, n, r = s.adjoint(B.IDG_OBJ_FORCE_X, WALL, CYL_PARAMS, 40000, 1e-11)
-    assert ok, (n, r)
-    Jo, gfd = oracle_fd(CYL, CYL_PARAMS, WALL)
-    assert abs(J - Jo) <= 1e-9 * abs(Jo), (J, Jo)
-    rel = np.abs(g - gfd) / np.abs(gfd)
-    print(CYL.name, "drag", J, "adjoint", g, "fd", gfd, "rel", rel, "iterations", n)
-    assert np.all(rel <= 1e-4), rel
-
-
 def test_steady_solve_autograd():
     import torch
 

@@ -44,6 +44,9 @@ def _cases():
                                      stretch_beta=1.83297, cfl_imp=1e4)
     c["cylinder_20x8_simpson11_limiter"] = I.cylinder(ntheta=20, nr=8, nv=11, vmax=8.0, Ma=2.0, Kn=0.5)
     c["cavity_bgk_kn1_v24"] = I.cavity(8, Kn=1.0, U=0.3, nv=24, vmax=4.0, shakhov=0, Pr=1.0)
+    # impulsive Ma 5 start: the rear wall faces are evacuated in the first
+    # iterations (wall and face densities at or below zero transiently)
+    c["cylinder_24x12_ma5_v41_limiter"] = I.cylinder(ntheta=24, nr=12, nv=41, vmax=12.0, cfl_imp=10.0)
     return c
 
 
