@@ -251,6 +251,8 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ttr", action="store_true", help="skip the time-to-residual runs")
+    ap.add_argument("--tune", default="auto", choices=["auto", "default"],
+                    help="auto: pick the sweep kind, tiles and prefetch depths with the autotuner before timing")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.workload == "batch64":
@@ -282,6 +284,10 @@ def main():
 
     s = Solver(prob, args.precision, device=local)
     s.init_uniform()
+    if args.tune == "auto":
+        from paper_1709_01819_gb300.solver import Autotuner
+        Autotuner().tune(s)
+    tuning = s.tuning()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{local}")
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
@@ -374,7 +380,7 @@ def main():
             "dtype": "f32" if args.precision == "mixed" else "f64", "data": "synthetic",
             "config": {"workload": prob.name, "cells": prob.ncells, "velocities": prob.nvel,
                        "precision": args.precision, "l2": "flushed between timed steps (256 MB write)",
-                       "parallelism": "replicas" if ws > 1 else "single"},
+                       "parallelism": "replicas" if ws > 1 else "single", "tuning": tuning},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_source": "measured" if peaks else "fallback",

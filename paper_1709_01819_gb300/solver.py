@@ -227,8 +227,7 @@ class BatchSolver:
             # the largest instance first and keep its choice for the rest
             tuner = Autotuner()
             order = sorted(self.solvers, key=lambda s: -s.N * s.Nv)
-            vpt = tuner.tune(order[0])["sweep_vpt"]
-            tuner.candidates_vpt = (vpt,)
+            tuner.candidates_vpt = (tuner.tune(order[0])["sweep_vpt"],)
             for s in order[1:]:
                 tuner.tune(s)
         self._make_batch()
@@ -261,10 +260,11 @@ class BatchSolver:
 
 
 class Autotuner:
-    """Picks the micro-sweep tile (velocities per thread block) and the
-    prefetch depths of a Solver by timing one profiled iteration of each
-    candidate on the problem itself; results are cached per (cells in i, in j,
-    velocities, precision) so a batch of same-sized problems is timed once."""
+    """Picks the micro-sweep tile (velocities per thread block and per thread)
+    and the prefetch depths of a Solver by timing one profiled iteration of
+    each candidate on the problem itself; results are cached per (cells in i,
+    in j, velocities, precision) so a batch of same-sized problems is timed
+    once."""
 
     def __init__(self, candidates_tv=(2, 4, 8, 16), candidates_vpt=(1, 2, 4), repeats: int = 3):
         self.candidates_tv = candidates_tv
@@ -279,18 +279,18 @@ class Autotuner:
             return self.cache[key]
         G, H, W = solver.get_state()
         best, best_t = None, float("inf")
-        for tv in self.candidates_tv:
-            for vpt in self.candidates_vpt:
-                for stages in (4, 8):
-                    try:
-                        solver.set_tuning(sweep_tv=tv, sweep_vpt=vpt, sweep_stages=stages, macro_stages=stages)
-                    except B.IdgError:
-                        continue
-                    solver.iterate_profiled()  # warm-up
-                    t = min(float(np.sum(solver.iterate_profiled())) for _ in range(self.repeats))
-                    if t < best_t:
-                        best = dict(sweep_tv=tv, sweep_vpt=vpt, sweep_stages=stages, macro_stages=stages)
-                        best_t = t
+        cands = [dict(sweep_tv=tv, sweep_vpt=vpt, sweep_stages=st, macro_stages=st)
+                 for tv in self.candidates_tv for vpt in self.candidates_vpt for st in (4, 8)]
+        for cand in cands:
+            try:
+                solver.set_tuning(**cand)
+            except B.IdgError:
+                continue
+            solver.iterate_profiled()  # warm-up
+            t = min(float(np.sum(solver.iterate_profiled())) for _ in range(self.repeats))
+            if t < best_t:
+                best, best_t = dict(solver.tuning()), t
+        best.pop("graph", None)
         solver.set_tuning(**best)
         solver.set_state(G, H, W)  # timing iterations leave no trace
         self.cache[key] = best
