@@ -587,6 +587,17 @@ static double limiter_cell(const orc_state *s, int c, const double *val, size_t 
     return phi;
 }
 
+/* Venkatakrishnan limiter of a cell scalar field, Eq. (16)-(17), as applied
+ * inside the flux (LS gradient, then the minimum over the faces) */
+void orc_limiter(const orc_state *s, const double *phi, double *lim)
+{
+    for (int c = 0; c < s->N; ++c) {
+        double gx, gy;
+        ls_grad_cell(s, c, phi, 1, 0, &gx, &gy);
+        lim[c] = limiter_cell(s, c, phi, 1, 0, gx, gy);
+    }
+}
+
 /* ------------------------------------------------------------------------- */
 /* one DUGKS flux evaluation (Eq. 10-19): cell prep, gradients, faces          */
 /* ------------------------------------------------------------------------- */

@@ -78,6 +78,8 @@ void orc_equilibrium(const orc_state *s, double rho, double u, double v, double 
                      double qx, double qy, double *G, double *H);
 /* least-squares gradient of a scalar cell field, Eq. (14)-(15) */
 void orc_ls_gradient(const orc_state *s, const double *phi, double *grad2);
+/* Venkatakrishnan limiter value (Eq. 16-17) of a cell scalar field [N]. */
+void orc_limiter(const orc_state *s, const double *phi, double *lim);
 double orc_venkat_theta(double x);
 /* runs the cell-prep step (Eq. 10, 12) on the stored state and copies out
  * fb+ [N][Nv] (G and H), the cell heat flux q [N][2] and tau [N] */

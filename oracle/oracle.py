@@ -79,6 +79,7 @@ def lib():
         _lib.orc_velocity_grid.argtypes = [vp, P(d), P(d), P(d)]
         _lib.orc_equilibrium.argtypes = [vp, d, d, d, d, d, d, P(d), P(d)]
         _lib.orc_ls_gradient.argtypes = [vp, P(d), P(d)]
+        _lib.orc_limiter.argtypes = [vp, P(d), P(d)]
         _lib.orc_venkat_theta.restype = d
         _lib.orc_venkat_theta.argtypes = [d]
         _lib.orc_debug_cell_prep.argtypes = [vp, P(d), P(d), P(d), P(d)]
@@ -214,6 +215,12 @@ class Oracle:
         tau = np.zeros(self.N)
         lib().orc_debug_cell_prep(self._h, _dp(fbG), _dp(fbH), _dp(q), _dp(tau))
         return fbG, fbH, q, tau
+
+    def limiter(self, phi: np.ndarray) -> np.ndarray:
+        phi = np.ascontiguousarray(phi, dtype=np.float64)
+        out = np.zeros(self.N)
+        lib().orc_limiter(self._h, _dp(phi), _dp(out))
+        return out
 
     def ls_gradient(self, phi: np.ndarray) -> np.ndarray:
         phi = np.ascontiguousarray(phi, dtype=np.float64)

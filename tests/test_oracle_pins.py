@@ -211,6 +211,57 @@ def test_venkatakrishnan_theta():
     assert max(th(x) for x in np.linspace(2, 50, 500)) < 1.1  # mild overshoot, no cap in Eq. (17)
 
 
+def _uniform_block(n=12):
+    p = I.cavity(n, nv=4)
+    o = O.Oracle(p)
+    cx, cy, _ = o.geometry()
+    interior = np.array([(0 < c % n < n - 1) and (0 < c // n < n - 1) for c in range(n * n)])
+    return o, cx, cy, interior
+
+
+def test_limiter_leaves_linear_fields_unlimited():
+    """Eq. (16)-(17) on a uniform grid: for v = b x + c y the extrapolation to a
+    face is half the largest neighbour difference, ratio 2, theta(2) = 1."""
+    o, cx, cy, inner = _uniform_block()
+    for b, c in ((1.3, 0.4), (-0.7, 2.1), (0.0, -1.0)):
+        lim = o.limiter(0.2 + b * cx + c * cy)
+        assert np.all(np.abs(lim[inner] - 1.0) < 1e-12), (b, c)
+        assert np.all(lim <= 1.0 + 1e-12)
+
+
+def test_limiter_closed_form_on_a_parabola():
+    """v = x^2, spacing h: the central-difference slope 2 x0 gives the ratio
+    2 + h/x0 > 2 toward larger x (theta > 1, not binding) and 2 - h/x0 toward
+    smaller x, so phi = theta(2 - h/x0) at every interior cell."""
+    o, cx, cy, inner = _uniform_block()
+    h = 1.0 / 12
+    lim = o.limiter(cx ** 2)
+    expect = np.array([O.venkat_theta(2.0 - h / x0) for x0 in cx])
+    assert np.allclose(lim[inner], expect[inner], rtol=0, atol=1e-12)
+    assert np.all(expect[inner] < 1.0)
+
+
+def test_limiter_zero_at_a_strict_local_maximum():
+    """A cell above all its neighbours with a nonzero gradient: the face the
+    gradient points to has vmax - v0 = 0, theta(0) = 0, so phi = 0."""
+    o, cx, cy, inner = _uniform_block()
+    rng = np.random.default_rng(7)
+    v = rng.uniform(0.0, 0.3, cx.size)
+    c = 5 * 12 + 6
+    v[c] = 1.0
+    v[c + 1], v[c - 1] = 0.6, 0.1  # east above west: gradient toward east
+    lim = o.limiter(v)
+    assert lim[c] == 0.0
+
+
+def test_limiter_is_invariant_under_affine_maps():
+    o, cx, cy, _ = _uniform_block()
+    v = np.random.default_rng(3).normal(size=cx.size)
+    base = o.limiter(v)
+    for a, b in ((2.5, -1.0), (0.01, 7.0)):
+        assert np.allclose(o.limiter(a * v + b), base, rtol=0, atol=1e-12)
+
+
 def test_geometry_of_ogrid_is_closed_and_positive():
     p = I.cylinder(ntheta=40, nr=12, nv=5, vmax=4.0)
     o = O.Oracle(p)
