@@ -259,7 +259,7 @@ __device__ EqD make_eq(const KParams &p, double rho, double U, double V, double 
     e.U = U;
     e.V = V;
     e.invRT = 1.0 / RT;
-    double pc = p.shakhov ? (1.0 - p.Pr) / ((p.K + 4) * rho * RT * RT) : 0.0;
+    double pc = p.shakhov && rho != 0.0 ? (1.0 - p.Pr) / ((p.K + 4) * rho * RT * RT) : 0.0;
     e.pqx = pc * qx;
     e.pqy = pc * qy;
     e.rr = RT / p.RT_r;
@@ -597,9 +597,12 @@ __device__ __forceinline__ typename V2<T>::t face_fbar(const KParams &p, const F
     return fb;
 }
 
-// raw moments of fb - M_ref at every face (plus the wall density, Eq. 35)
+// raw moments of fb - M_ref at every face (plus the wall density, Eq. 35).
+// float32: four 256-thread blocks per SM (64 registers) hide the latency of
+// the stencil loads better than two blocks without spills (measured: -11% on
+// a 64^2 cavity, -20% on 128^2 with 28^2 velocities)
 template <class T, bool LIM>
-__global__ void __launch_bounds__(256) k_face_moments(Launch L)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 1) k_face_moments(Launch L)
 {
     IDG_LOCATE();
     using T2 = typename V2<T>::t;
@@ -665,11 +668,23 @@ __global__ void __launch_bounds__(32) k_face_params(Launch L)
     for (int q = 0; q < kRaw; ++q) r[q] = acc_load<T>(p.faceraw, (size_t)f * 12 + q) + p.mref_raw[q];
     double rho, U, V, RT, qbx, qby;
     raw_to_state(r, p.K, rho, U, V, RT, qbx, qby);
+    T *fA = (T *)p.faceA + kCellP * f;
+    // float32 storage keeps fb relative to the reference Maxwellian, so a
+    // face that an impulsive start evacuates (density ~1e-18 of the reference
+    // at the lee of a hypersonic body) is not resolved: its moments are
+    // rounding noise of the reference's.  Below 1e-6 of the reference density
+    // or temperature such a face takes the vacuum limit of Eq. (18):
+    // tau -> infinity, f = fb (free transport), no equilibrium part.
+    if (sizeof(T) == 4 && !(rho > 1e-6 * p.rho_r && RT > 1e-6 * p.RT_r)) {
+        eq_storeT<T>(fA, make_eq(p, 0.0, p.U_r, p.V_r, p.RT_r, 0.0, 0.0));
+        fA[14] = (T)1;
+        fA[15] = (T)0;
+        return;
+    }
     double tau = viscosity(p, RT) / (rho * RT);
     double Pr = p.shakhov ? p.Pr : 1.0;
     double qx = 2.0 * tau * qbx / (2.0 * tau + p.h * Pr);
     double qy = 2.0 * tau * qby / (2.0 * tau + p.h * Pr);
-    T *fA = (T *)p.faceA + kCellP * f;
     eq_storeT<T>(fA, make_eq(p, rho, U, V, RT, qx, qy));
     fA[14] = (T)(2.0 * tau / (2.0 * tau + p.h));
     fA[15] = (T)(p.h / (2.0 * tau + p.h));

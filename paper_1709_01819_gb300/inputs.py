@@ -186,7 +186,9 @@ def cylinder(ntheta: int = 121, nr: int = 81, Kn: float = 0.1, Ma: float = 5.0, 
 
 
 def cylinder_c5() -> Problem:
-    return cylinder(name="cylinder_121x81_ma5_kn0.1_v89")
+    # implicit CFL 30: from the impulsive uniform start 100 and above diverge,
+    # 10 converges more slowly (2384 against 1904 iterations to 1e-6)
+    return cylinder(cfl_imp=30.0, name="cylinder_121x81_ma5_kn0.1_v89")
 
 
 C4_SEED = 170901819
