@@ -55,6 +55,8 @@ def algorithmic_bytes(prob: I.Problem, s: int, nf: int):
     per-velocity array holds a G and an H scalar):
     cell_prep: read f~ twice (moments, fb+), write fb+        6s per cell-velocity
     face_moments: read fb+, write fb at the faces             2s per cell-velocity + 2s per face-velocity
+                  (limiter on: the gradient kernel also reads fb+ and writes the limited gradients,
+                  which the reconstruction reads back: +10s per cell-velocity)
     face_flux: read fb, write the face flux                   4s per face-velocity
     k_sweep_fwd: micro residual (read the fluxes and f~, write R), then the
                  forward sweep (read R, write Delta*)         2s per face-velocity + 8s per cell-velocity
@@ -62,7 +64,7 @@ def algorithmic_bytes(prob: I.Problem, s: int, nf: int):
     N, Nv = prob.ncells, prob.nvel
     return {
         "cell_prep": 6 * s * N * Nv,
-        "face_moments": 2 * s * N * Nv + 2 * s * nf * Nv,
+        "face_moments": (12 if prob.limiter else 2) * s * N * Nv + 2 * s * nf * Nv,
         "face_flux": 4 * s * nf * Nv,
         "k_sweep_fwd": 2 * s * nf * Nv + 8 * s * N * Nv,
         "k_sweep_bwd": 8 * s * N * Nv,

@@ -417,6 +417,7 @@ size_t layout(idg_ctx *c, char *base, KParams *kp)
     k.bdevH = L.take<char>(4 * ts * Nv);
     k.f = L.take<char>(t2 * N * Nv);
     k.fbp = L.take<char>(t2 * N * Nv);
+    k.grad = c->limiter ? L.take<char>(4 * ts * N * Nv) : nullptr;
     k.dst = L.take<char>(t2 * N * Nv);
     k.F = L.take<char>(t2 * nf * Nv);
     k.W = L.take<double>(32 * N);

@@ -53,6 +53,7 @@ struct KParams {
     // state and work (T2 = {G, H} deviation pairs of the storage type)
     void *f;        // [N][Nv] T2 state f~ - M_ref
     void *fbp;      // [N][Nv] T2 fb+ - M_ref
+    void *grad;     // [N][Nv][4] T limited gradients phi sigma of G and H (limiter on; else null)
     void *F;        // [nf][Nv] T2 flux of (f_face - M_ref)
     void *dst;      // [N][Nv] T2 Delta* then Delta
     double *W;      // [N][4]

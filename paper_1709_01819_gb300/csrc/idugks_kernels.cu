@@ -25,9 +25,11 @@
 //   k_cell_params    thread per cell: heat flux (q of Eq. 20), tau,
 //                    equilibrium at W^n, coefficients of fb+ (Eq. 10, 12)
 //   k_fbp            per (cell, velocity): fb+ = c1 f~ + c2 f^S
-//   k_face_moments   warp per face: least-squares gradient (Eq. 14-15),
-//                    limiter (Eq. 16-17), characteristic reconstruction of fb
-//                    at the half step (Eq. 11, 13), wall density (Eq. 35),
+//   k_cell_grad      (limiter on) per (cell, velocity): least-squares gradient
+//                    (Eq. 14-15) and limiter (Eq. 16-17), stored as phi sigma
+//   k_face_moments   warp per face: characteristic reconstruction of fb at the
+//                    half step (Eq. 11, 13) with the gradient (computed in
+//                    place when the limiter is off), wall density (Eq. 35),
 //                    raw moments of fb                                 [a2-a3]
 //   k_face_params    thread per face: face state, tau, q, equilibrium, and
 //                    the weights of Eq. (18)                              [a4]
@@ -494,6 +496,46 @@ __device__ __forceinline__ T limit_scalar(const SideRec<T> &r, T v0, T vmax, T v
     return phi;
 }
 
+// per (cell, velocity), limiter on: least-squares gradients of fb+ (Eq.
+// 14-15) and the Venkatakrishnan limiter (Eq. 16-17) of G and H, stored as
+// the limited gradients phi sigma for the reconstructions at the cell's faces
+template <class T>
+__global__ void __launch_bounds__(256) k_cell_grad(Launch L)
+{
+    IDG_LOCATE();
+    if (!p.limiter) return;
+    using T2 = typename V2<T>::t;
+    __shared__ SideRec<T> srec;
+    const int nvb = (p.Nv + 255) / 256;
+    const int c = blk / nvb;
+    const int k = (blk - c * nvb) * blockDim.x + threadIdx.x;
+    if (threadIdx.x == 0) load_side<T>(p, c, (T)0, (T)0, srec);
+    __syncthreads();
+    if (k >= p.Nv) return;
+    const SideRec<T> &r = srec;
+    const T2 *fb = (const T2 *)p.fbp;
+    const T2 f0 = fb[(size_t)c * p.Nv + k];
+    T sgx = 0, sgy = 0, shx = 0, shy = 0;
+    T gmax = f0.x, gmin = f0.x, hmax = f0.y, hmin = f0.y;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        if (r.nb[m] < 0) continue;
+        const T2 fn = fb[(size_t)r.nb[m] * p.Nv + k];
+        const T dg = fn.x - f0.x, dh = fn.y - f0.y;
+        sgx += r.gx[m] * dg; sgy += r.gy[m] * dg;
+        shx += r.gx[m] * dh; shy += r.gy[m] * dh;
+        gmax = fn.x > gmax ? fn.x : gmax; gmin = fn.x < gmin ? fn.x : gmin;
+        hmax = fn.y > hmax ? fn.y : hmax; hmin = fn.y < hmin ? fn.y : hmin;
+    }
+    const T pg = limit_scalar<T>(r, f0.x, gmax, gmin, sgx, sgy);
+    const T ph = limit_scalar<T>(r, f0.y, hmax, hmin, shx, shy);
+    T *g = (T *)p.grad + 4 * ((size_t)c * p.Nv + k);
+    g[0] = pg * sgx;
+    g[1] = pg * sgy;
+    g[2] = ph * shx;
+    g[3] = ph * shy;
+}
+
 // fb at the face from side r: fb+_c + phi sigma_c . (x_f - xi h - x_c).  The
 // limiter ratios only involve differences of fb+ between cells at one
 // velocity, so the M_ref offset cancels and deviations serve as is.
@@ -504,6 +546,16 @@ __device__ __forceinline__ typename V2<T>::t reconstruct(const KParams &p, const
     using T2 = typename V2<T>::t;
     const T2 *fb = (const T2 *)p.fbp;
     T2 f0 = fb[(size_t)r.c * p.Nv + k];
+    if (LIM && p.limiter) {
+        // limited gradients phi sigma of G and H, stored once per (cell,
+        // velocity) by k_cell_grad
+        const T *g = (const T *)p.grad + 4 * ((size_t)r.c * p.Nv + k);
+        const T ax = r.rx - ux * h, ay = r.ry - uy * h;
+        T2 o;
+        o.x = f0.x + (g[0] * ax + g[1] * ay);
+        o.y = f0.y + (g[2] * ax + g[3] * ay);
+        return o;
+    }
     T sgx = 0, sgy = 0, shx = 0, shy = 0;
     T gmax = f0.x, gmin = f0.x, hmax = f0.y, hmin = f0.y;
 #pragma unroll
@@ -1441,6 +1493,7 @@ static int iteration_t(const Plan &pl, cudaStream_t st, void **events)
     k_cell_params<T><<<nb[KT_CELL_PAR], 32, 0, st>>>(L(KT_CELL_PAR));
     k_fbp<T><<<nb[KT_FBP], 256, 0, st>>>(L(KT_FBP));
     mark(1);
+    if (pl.limiter_any) k_cell_grad<T><<<nb[KT_FBP], 256, 0, st>>>(L(KT_FBP));
     if (pl.limiter_any) k_face_moments<T, true><<<nb[KT_FACE_MOM], 256, 0, st>>>(L(KT_FACE_MOM));
     else k_face_moments<T, false><<<nb[KT_FACE_MOM], 256, 0, st>>>(L(KT_FACE_MOM));
     k_face_params<T><<<nb[KT_FACE_PAR], 32, 0, st>>>(L(KT_FACE_PAR));
