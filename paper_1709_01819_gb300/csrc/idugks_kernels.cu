@@ -479,7 +479,13 @@ __device__ __forceinline__ void load_side(const KParams &p, int c, T rx, T ry, S
     r.ry = ry;
 }
 
-template <class T> __device__ __forceinline__ T venkat(T x) { return (x * x + (T)2 * x) / (x * x + x + (T)2); }
+// Divisions of the limiter: exact in float64 (the oracle's rounding up to
+// order); in float32 storage the approximate quotient (2 ulp) of the fast
+// reciprocal path, the limiter being a smooth function of its ratios
+__device__ __forceinline__ float lim_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double lim_div(double a, double b) { return a / b; }
+
+template <class T> __device__ __forceinline__ T venkat(T x) { return lim_div(x * x + (T)2 * x, x * x + x + (T)2); }
 
 template <class T>
 __device__ __forceinline__ T limit_scalar(const SideRec<T> &r, T v0, T vmax, T vmin, T sx, T sy)
@@ -489,8 +495,8 @@ __device__ __forceinline__ T limit_scalar(const SideRec<T> &r, T v0, T vmax, T v
     for (int m = 0; m < 4; ++m) {
         T d = sx * r.frx[m] + sy * r.fry[m];
         T t = (T)1;
-        if (d > (T)0) t = venkat<T>((vmax - v0) / d);
-        else if (d < (T)0) t = venkat<T>((vmin - v0) / d);
+        if (d > (T)0) t = venkat<T>(lim_div(vmax - v0, d));
+        else if (d < (T)0) t = venkat<T>(lim_div(vmin - v0, d));
         phi = t < phi ? t : phi;
     }
     return phi;
@@ -556,8 +562,8 @@ __device__ __forceinline__ typename V2<T>::t reconstruct(const KParams &p, const
         o.y = f0.y + (g[2] * ax + g[3] * ay);
         return o;
     }
+    // limiter off: the unlimited least-squares gradient in place
     T sgx = 0, sgy = 0, shx = 0, shy = 0;
-    T gmax = f0.x, gmin = f0.x, hmax = f0.y, hmin = f0.y;
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
         if (r.nb[m] < 0) continue;
@@ -565,20 +571,11 @@ __device__ __forceinline__ typename V2<T>::t reconstruct(const KParams &p, const
         T dg = fn.x - f0.x, dh = fn.y - f0.y;
         sgx += r.gx[m] * dg; sgy += r.gy[m] * dg;
         shx += r.gx[m] * dh; shy += r.gy[m] * dh;
-        if (LIM) {
-            gmax = fn.x > gmax ? fn.x : gmax; gmin = fn.x < gmin ? fn.x : gmin;
-            hmax = fn.y > hmax ? fn.y : hmax; hmin = fn.y < hmin ? fn.y : hmin;
-        }
     }
     T ax = r.rx - ux * h, ay = r.ry - uy * h;
-    T pg = (T)1, ph = (T)1;
-    if (LIM && p.limiter) {
-        pg = limit_scalar<T>(r, f0.x, gmax, gmin, sgx, sgy);
-        ph = limit_scalar<T>(r, f0.y, hmax, hmin, shx, shy);
-    }
     T2 o;
-    o.x = f0.x + pg * (sgx * ax + sgy * ay);
-    o.y = f0.y + ph * (shx * ax + shy * ay);
+    o.x = f0.x + (sgx * ax + sgy * ay);
+    o.y = f0.y + (shx * ax + shy * ay);
     return o;
 }
 
