@@ -212,6 +212,20 @@ __device__ __forceinline__ double viscosity(const KParams &p, double RT)
     return p.mu_ref * pow(RT / p.RT_ref, p.omega);
 }
 
+// The power law of the viscosity for tau in the iteration's kernels: with
+// float32 storage tau only sets float32 coefficients (fb+ weights, Eq. 18
+// weights, the collision rate, the Shakhov factor) and the float32
+// preconditioner, so the power is taken in float32; float64 keeps float64.
+template <class T> __device__ __forceinline__ double viscosity_t(const KParams &p, double RT);
+template <> __device__ __forceinline__ double viscosity_t<double>(const KParams &p, double RT)
+{
+    return viscosity(p, RT);
+}
+template <> __device__ __forceinline__ double viscosity_t<float>(const KParams &p, double RT)
+{
+    return p.mu_ref * (double)powf((float)(RT / p.RT_ref), (float)p.omega);
+}
+
 // heat flux q = 1/2 sum w c (c^2 G + H) about (U, V) from raw moments
 // (G: 1,x,y,xx,xy,yy,x|xi|^2,y|xi|^2; H: 1,x,y), Eq. (4)-(5)
 __device__ __forceinline__ void raw_heat_flux(const double *r, double U, double V, double &qx,
@@ -413,7 +427,7 @@ __global__ void __launch_bounds__(32) k_cell_params(Launch L)
     const double *W = p.W + 4 * c;
     double rho = W[0], U = W[1] / rho, V = W[2] / rho;
     double RT = (2.0 * W[3] / rho - U * U - V * V) / (p.K + 2);
-    double tau = viscosity(p, RT) / (rho * RT);
+    double tau = viscosity_t<T>(p, RT) / (rho * RT);
     double qtx, qty;
     raw_heat_flux(r, U, V, qtx, qty);
     double Pr = p.shakhov ? p.Pr : 1.0;
@@ -730,7 +744,7 @@ __global__ void __launch_bounds__(32) k_face_params(Launch L)
         fA[15] = (T)0;
         return;
     }
-    double tau = viscosity(p, RT) / (rho * RT);
+    double tau = viscosity_t<T>(p, RT) / (rho * RT);
     double Pr = p.shakhov ? p.Pr : 1.0;
     double qx = 2.0 * tau * qbx / (2.0 * tau + p.h * Pr);
     double qy = 2.0 * tau * qby / (2.0 * tau + p.h * Pr);
@@ -834,6 +848,53 @@ __device__ __forceinline__ double face_lambda(const KParams &p, int fi)
     return (fabs(u * g[0] + v * g[1]) + cs) * g[2];
 }
 
+// Preconditioner coefficients of the macroscopic LU-SGS: in float32 storage
+// the spectral radius and the neighbours' base states only enter the float32
+// wavefront (R_W, the diagonal's sum and W^{n+1} stay float64), so they are
+// evaluated in float32; float64 storage evaluates them in float64.
+template <class T> __device__ __forceinline__ double face_lambda_t(const KParams &p, int fi);
+template <> __device__ __forceinline__ double face_lambda_t<double>(const KParams &p, int fi)
+{
+    return face_lambda(p, fi);
+}
+template <> __device__ __forceinline__ double face_lambda_t<float>(const KParams &p, int fi)
+{
+    const int L = p.fL[fi], R = p.fR[fi];
+    const double *g = p.fgeo + 7 * fi;
+    const float gam = (float)p.gam, k2 = 1.0f / (float)(p.K + 2);
+    float u = 0.f, v = 0.f, cs = 0.f;
+    int nc = 0;
+    for (int side = 0; side < 2; ++side) {
+        const int c = side ? R : L;
+        if (c < 0) continue;
+        const double *W = p.W + 4 * c;
+        const float rho = (float)W[0], ir = 1.0f / rho, uc = (float)W[1] * ir, vc = (float)W[2] * ir;
+        const float RT = (2.0f * (float)W[3] * ir - uc * uc - vc * vc) * k2;
+        u += uc; v += vc; cs += sqrtf(gam * RT);
+        ++nc;
+    }
+    if (nc == 2) { u *= 0.5f; v *= 0.5f; cs *= 0.5f; }
+    return (double)((fabsf(u * (float)g[0] + v * (float)g[1]) + cs) * (float)g[2]);
+}
+
+// base state (rho, m_x, m_y, u, v, E + p) of a neighbour for the flux increments
+template <class T> __device__ __forceinline__ void base_state(const KParams &p, const double *W, T *o);
+template <> __device__ __forceinline__ void base_state<double>(const KParams &p, const double *W, double *o)
+{
+    double rho = W[0], u = W[1] / rho, v = W[2] / rho;
+    double pr = (p.gam - 1.0) * (W[3] - 0.5 * rho * (u * u + v * v));
+    o[0] = rho; o[1] = W[1]; o[2] = W[2];
+    o[3] = u; o[4] = v; o[5] = W[3] + pr;
+}
+template <> __device__ __forceinline__ void base_state<float>(const KParams &p, const double *W, float *o)
+{
+    const float rho = (float)W[0], mx = (float)W[1], my = (float)W[2], E = (float)W[3];
+    const float ir = 1.0f / rho, u = mx * ir, v = my * ir;
+    const float pr = (float)(p.gam - 1.0) * (E - 0.5f * rho * (u * u + v * v));
+    o[0] = rho; o[1] = mx; o[2] = my;
+    o[3] = u; o[4] = v; o[5] = E + pr;
+}
+
 // cp.async helpers: asynchronous global -> shared copies used to prefetch
 // the next hyperplanes of a wavefront while the current one is computed
 __device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -884,7 +945,7 @@ __global__ void __launch_bounds__(32) k_macro_pre(Launch L)
         double d = p.area[c] / p.dtimp[c];
         for (int m = 0; m < 4; ++m) {
             int fi = p.cface[4 * c + m];
-            double lam = face_lambda(p, fi);
+            double lam = face_lambda_t<T>(p, fi);
             if (p.fL[fi] != p.fR[fi]) d += 0.5 * p.lusgs_omega * lam;
             double s = p.csign[4 * c + m];
             const double *g = p.fgeo + 7 * fi;
@@ -894,11 +955,7 @@ __global__ void __launch_bounds__(32) k_macro_pre(Launch L)
             o[2] = (T)(0.5 * p.lusgs_omega * lam);
             int nb = p.cnb[4 * c + m];
             if (nb >= 0) {
-                const double *W = p.W + 4 * nb;
-                double rho = W[0], u = W[1] / rho, v = W[2] / rho;
-                double pr = (p.gam - 1.0) * (W[3] - 0.5 * rho * (u * u + v * v));
-                o[3] = (T)rho; o[4] = (T)W[1]; o[5] = (T)W[2];
-                o[6] = (T)u; o[7] = (T)v; o[8] = (T)(W[3] + pr);
+                base_state<T>(p, p.W + 4 * nb, o + 3);
             } else {
                 for (int q = 3; q < 9; ++q) o[q] = (T)0;
             }
@@ -1047,7 +1104,7 @@ __global__ void __launch_bounds__(32) k_macro_post(Launch L)
     for (int q = 0; q < 4; ++q) W[q] += (double)dW[q];
     double rho = W[0], U = W[1] / rho, V = W[2] / rho;
     double RT = (2.0 * W[3] / rho - U * U - V * V) / (p.K + 2);
-    double taup = viscosity(p, RT) / (rho * RT);
+    double taup = viscosity_t<T>(p, RT) / (rho * RT);
     EqD e = make_eq(p, rho, U, V, RT, p.cellq[2 * c], p.cellq[2 * c + 1]);
     double *cp = p.cellp + kCellP * c;
     eq_store(cp, e);
@@ -1354,7 +1411,7 @@ __global__ void __launch_bounds__(256) k_moments_out(KParams p, double *out6)
     const double *W = p.W + 4 * c;
     double rho = W[0], U = W[1] / rho, V = W[2] / rho;
     double RT = (2.0 * W[3] / rho - U * U - V * V) / (p.K + 2);
-    double tau = viscosity(p, RT) / (rho * RT);
+    double tau = viscosity_t<T>(p, RT) / (rho * RT);
     double qtx, qty;
     raw_heat_flux(r, U, V, qtx, qty);
     double Pr = p.shakhov ? p.Pr : 1.0;
