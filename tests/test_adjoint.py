@@ -152,7 +152,7 @@ def test_steady_solve_autograd():
     J = SteadySolve.apply(theta, spec)
     (2.0 * J).backward()
     Jo, gfd = oracle_fd(CAV, CAV_PARAMS, LID)
-    assert abs(float(J) - Jo) <= 1e-9 * abs(Jo)
+    assert abs(float(J.detach()) - Jo) <= 1e-9 * abs(Jo)
     assert np.all(np.abs(theta.grad.numpy() - 2.0 * gfd) <= 1e-4 * np.abs(2.0 * gfd))
     assert spec.last["adj_converged"]
 
