@@ -433,7 +433,7 @@ size_t layout(idg_ctx *c, char *base, KParams *kp)
     k.phi = L.take<double>(32 * nf);
     k.rw = L.take<double>(32 * N);
     k.clink = L.take<int>(48 * N);
-    k.mrec = L.take<char>(44 * ts * N);
+    k.mrec = L.take<char>(24 * ts * N);
     k.mdW = L.take<char>(4 * ts * N);
     k.mpart = L.take<double>(8 * (N / 32 + 2));
     k.res = L.take<double>(8 * (size_t)idg::kMaxHist);

@@ -70,7 +70,7 @@ struct KParams {
     double *rw;     // [N][4]
     const int *clink;  // [N][12] per slot: neighbour, its i, its hyperplane i+j (-1 ghost)
     // macroscopic LU-SGS work (T = storage precision of the sweep)
-    void *mrec;     // [N][44] T: R, D, per slot (S/2) n_out, (omega/2) Lambda, neighbour base state
+    void *mrec;     // [N][24] T: R, 1/D, own base state, per slot (S/2) n_out, (omega/2) Lambda
     void *mdW;      // [N][4] T increments (Delta W* then Delta W)
     double *mpart;  // [ceil(N/256)] block partial sums of ||R/Omega||^2
     double *res;    // [kMaxHist] absolute residual per iteration

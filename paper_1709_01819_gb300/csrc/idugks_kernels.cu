@@ -917,10 +917,12 @@ template <> __device__ __forceinline__ void cp_async_b<16>(void *s, const void *
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N> __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-constexpr int kMRec = 44;    // macro sweep record: R[4], D, pad[3], 4 x (off[3], base[6])
+constexpr int kMRec = 24;  // macroscopic sweep record: R[4], 1/D, pad, own base[6], 4 x (n S/2 [2], omega Lambda/2)
+constexpr int kMRing = 12; // ring entry per cell: increment[4], base state[6], pad[2]
 
-// per cell: R_W, ||R_W/Omega||^2 partials, and the packed record of the
-// macroscopic sweep (diagonal, neighbour coefficients, neighbour base state)
+// per cell: R_W, ||R_W/Omega||^2 partials, and the record of the macroscopic
+// sweep (inverse diagonal, the cell's own base state for its neighbours'
+// flux increments, per-slot face coefficients)
 template <class T>
 __global__ void __launch_bounds__(32) k_macro_pre(Launch L)
 {
@@ -949,20 +951,14 @@ __global__ void __launch_bounds__(32) k_macro_pre(Launch L)
             if (p.fL[fi] != p.fR[fi]) d += 0.5 * p.lusgs_omega * lam;
             double s = p.csign[4 * c + m];
             const double *g = p.fgeo + 7 * fi;
-            T *o = rec + 8 + 9 * m;
+            T *o = rec + 12 + 3 * m;
             o[0] = (T)(0.5 * g[2] * s * g[0]);
             o[1] = (T)(0.5 * g[2] * s * g[1]);
             o[2] = (T)(0.5 * p.lusgs_omega * lam);
-            int nb = p.cnb[4 * c + m];
-            if (nb >= 0) {
-                base_state<T>(p, p.W + 4 * nb, o + 3);
-            } else {
-                for (int q = 3; q < 9; ++q) o[q] = (T)0;
-            }
         }
-        rec[4] = (T)d;
-        rec[5] = (T)(1.0 / d);
-        rec[6] = rec[7] = (T)0;
+        rec[4] = (T)(1.0 / d);
+        rec[5] = (T)0;
+        base_state<T>(p, p.W + 4 * c, rec + 6);
     }
     block_sum<1>(part, sm);
     if (threadIdx.x == 0) p.mpart[blk] = part[0];
@@ -988,12 +984,14 @@ __device__ __forceinline__ void euler_dflux(T gm1, const T *b, const T *dW, T nx
 
 // One CTA: forward then backward sweep over the i+j hyperplanes (the
 // lexicographic dependency order).  Four threads own one cell of the
-// hyperplane, thread m handling the neighbour across slot m; the four
-// off-diagonal terms 1/2 (dF S - omega Lambda dW_nb) are summed by a quad
-// shuffle and thread m then writes component m of the increment.  Records,
-// links and (backward) the cell's own dW* are prefetched kStages-1
-// hyperplanes ahead with cp.async; the previous hyperplane's increments sit
-// in a shared-memory ring.
+// hyperplane, thread m handling the neighbour across slot m (found from the
+// cell's (i, j) and the periodic flags); the four off-diagonal terms
+// 1/2 (dF S - omega Lambda dW_nb) are summed by a quad shuffle and thread m
+// then writes component m of the increment.  Records and (backward) the
+// cell's own dW* are prefetched kStages-1 hyperplanes ahead with cp.async;
+// the previous hyperplane's increments and base states sit in a
+// shared-memory ring indexed by the slot in the hyperplane; neighbours across
+// a periodic seam (earlier hyperplanes) come from global memory.
 template <class T, int kStages>
 __global__ void __launch_bounds__(1024) k_macro_sweep(Launch L)
 {
@@ -1002,10 +1000,10 @@ __global__ void __launch_bounds__(1024) k_macro_sweep(Launch L)
     const int tid = threadIdx.x, ncs = blockDim.x >> 2;  // cell slots
     const int cs = tid >> 2, m = tid & 3;
     const int ni = p.ni, nj = p.nj, nh = ni + nj - 1;
-    T *srec = (T *)smraw;                                     // [kStages][ncs][kMRec]
-    int *slnk = (int *)(srec + (size_t)kStages * ncs * kMRec);  // [kStages][ncs][12]
-    T *sdw = (T *)(slnk + (size_t)kStages * ncs * 12);        // [kStages][ncs][4] own dW* (backward)
-    T *ring = sdw + (size_t)kStages * ncs * 4;                // [2][ni][4]
+    const bool per_i = p.per_i, per_j = p.per_j;
+    T *srec = (T *)smraw;                               // [kStages][ncs][kMRec]
+    T *sdw = srec + (size_t)kStages * ncs * kMRec;      // [kStages][ncs][4] own dW* (backward)
+    T *ring = sdw + (size_t)kStages * ncs * 4;          // [2][ncs][kMRing]
     if (tid == 0) {
         double s = 0.0;
         int nb = (p.N + 31) / 32;
@@ -1018,24 +1016,21 @@ __global__ void __launch_bounds__(1024) k_macro_sweep(Launch L)
     const T gm1 = (T)(p.gam - 1.0);
     T *dWg = (T *)p.mdW;
     const T *mrec = (const T *)p.mrec;
-    const int *clink = p.clink;
     constexpr int RC = kMRec * sizeof(T) / 16;  // 16-byte chunks of one record
     constexpr int DC = 4 * sizeof(T) / 16;      // chunks of one dW
     for (int dir = 1; dir >= -1; dir -= 2) {
         auto step_d = [&](int s) { return dir > 0 ? s : nh - 1 - s; };
         auto issue = [&](int s) {
             if (s < nh) {
-                int d = step_d(s);
-                int ilo = max(0, d - (nj - 1)), ihi = min(ni - 1, d);
-                int i = ilo + cs;
-                if (i <= ihi) {
-                    int c = (d - i) * ni + i;
-                    size_t e = (size_t)(s & (kStages - 1)) * ncs + cs;
-                    const int nch = RC + 3 + (dir < 0 ? DC : 0);
+                const int d = step_d(s);
+                const int i = max(0, d - (nj - 1)) + cs;
+                if (i <= min(ni - 1, d)) {
+                    const int c = (d - i) * ni + i;
+                    const size_t e = (size_t)(s & (kStages - 1)) * ncs + cs;
+                    const int nch = RC + (dir < 0 ? DC : 0);
                     for (int q = m; q < nch; q += 4) {
                         if (q < RC) cp_async16((char *)(srec + e * kMRec) + 16 * q, (const char *)(mrec + (size_t)kMRec * c) + 16 * q);
-                        else if (q < RC + 3) cp_async16((char *)(slnk + e * 12) + 16 * (q - RC), (const char *)(clink + 12 * (size_t)c) + 16 * (q - RC));
-                        else cp_async16((char *)(sdw + e * 4) + 16 * (q - RC - 3), (const char *)(dWg + 4 * (size_t)c) + 16 * (q - RC - 3));
+                        else cp_async16((char *)(sdw + e * 4) + 16 * (q - RC), (const char *)(dWg + 4 * (size_t)c) + 16 * (q - RC));
                     }
                 }
             }
@@ -1048,26 +1043,41 @@ __global__ void __launch_bounds__(1024) k_macro_sweep(Launch L)
             issue(s + kStages - 1);
             const int d = step_d(s);
             const int ilo = max(0, d - (nj - 1)), ihi = min(ni - 1, d);
-            const int i = ilo + cs;
+            const int i = ilo + cs, j = d - i;
             const bool valid = i <= ihi;
-            const int c = (d - i) * ni + i;
+            const int c = j * ni + i;
             const size_t e = (size_t)(s & (kStages - 1)) * ncs + cs;
             const T *rec = srec + e * kMRec;
-            const int *lk = slnk + e * 12;
             T acc0 = 0, acc1 = 0, acc2 = 0, acc3 = 0;
             if (valid) {
-                int nb = lk[m];
-                if (nb >= 0 && (dir > 0 ? nb < c : nb > c)) {
-                    int nbi = lk[4 + m], nbd = lk[8 + m];
-                    const T *dWn = (nbd == d - dir) ? ring + 4 * (((d - dir) & 1) * ni + nbi) : dWg + 4 * (size_t)nb;
-                    T dn[4] = {dWn[0], dWn[1], dWn[2], dWn[3]};
-                    const T *o = rec + 8 + 9 * m;
+                // the neighbour across slot m (west, east, south, north)
+                int nbi = i, nbj = j;
+                bool ex = true;
+                if (m == 0) { nbi = i - 1; if (i == 0) { ex = per_i; nbi = ni - 1; } }
+                else if (m == 1) { nbi = i + 1; if (i == ni - 1) { ex = per_i; nbi = 0; } }
+                else if (m == 2) { nbj = j - 1; if (j == 0) { ex = per_j; nbj = nj - 1; } }
+                else { nbj = j + 1; if (j == nj - 1) { ex = per_j; nbj = 0; } }
+                const int nb = nbj * ni + nbi;
+                if (ex && (dir > 0 ? nb < c : nb > c)) {
+                    T dn[4];
+                    const T *base;
+                    if (nbi + nbj == d - dir) {
+                        const int ts = nbi - max(0, d - dir - (nj - 1));
+                        const T *x = ring + ((size_t)((s + 1) & 1) * ncs + ts) * kMRing;
+                        dn[0] = x[0]; dn[1] = x[1]; dn[2] = x[2]; dn[3] = x[3];
+                        base = x + 4;
+                    } else {
+                        const T *x = dWg + 4 * (size_t)nb;
+                        dn[0] = x[0]; dn[1] = x[1]; dn[2] = x[2]; dn[3] = x[3];
+                        base = mrec + (size_t)kMRec * nb + 6;
+                    }
+                    const T *cf = rec + 12 + 3 * m;
                     T dF[4];
-                    euler_dflux<T>(gm1, o + 3, dn, o[0], o[1], dF);
-                    acc0 = dF[0] - o[2] * dn[0];
-                    acc1 = dF[1] - o[2] * dn[1];
-                    acc2 = dF[2] - o[2] * dn[2];
-                    acc3 = dF[3] - o[2] * dn[3];
+                    euler_dflux<T>(gm1, base, dn, cf[0], cf[1], dF);
+                    acc0 = dF[0] - cf[2] * dn[0];
+                    acc1 = dF[1] - cf[2] * dn[1];
+                    acc2 = dF[2] - cf[2] * dn[2];
+                    acc3 = dF[3] - cf[2] * dn[3];
                 }
             }
             // sum over the four slots of the cell (fixed butterfly order)
@@ -1081,9 +1091,12 @@ __global__ void __launch_bounds__(1024) k_macro_sweep(Launch L)
             if (valid) {
                 // forward: dW*_c = (R_c - sum_lower) / D_c;  backward: dW_c = dW*_c - sum_upper / D_c
                 const T am = m == 0 ? acc0 : (m == 1 ? acc1 : (m == 2 ? acc2 : acc3));
-                const T iD = rec[5];
+                const T iD = rec[4];
                 const T x = dir > 0 ? (rec[m] - am) * iD : sdw[e * 4 + m] - am * iD;
-                ring[4 * ((d & 1) * ni + i) + m] = x;
+                T *r = ring + ((size_t)(s & 1) * ncs + cs) * kMRing;
+                r[m] = x;
+                r[4 + m] = rec[6 + m];
+                if (m < 2) r[8 + m] = rec[10 + m];
                 dWg[4 * (size_t)c + m] = x;
             }
         }
@@ -1432,7 +1445,7 @@ static int macro_threads(const KParams &p) { return std::min(1024, ((4 * std::mi
 
 template <class T> static size_t macro_smem_bytes(const KParams &p, int nt, int stages)
 {
-    return (size_t)stages * (nt / 4) * ((kMRec + 4) * sizeof(T) + 12 * sizeof(int)) + (size_t)2 * p.ni * 4 * sizeof(T);
+    return (size_t)stages * (nt / 4) * (kMRec + 4) * sizeof(T) + (size_t)2 * (nt / 4) * kMRing * sizeof(T);
 }
 
 template <class T, int S> static size_t sweep_bytes_s(const KParams &p, bool withF)
