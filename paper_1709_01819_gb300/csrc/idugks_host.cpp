@@ -397,7 +397,8 @@ size_t layout(idg_ctx *c, char *base, KParams *kp)
     k.csign = L.take<int>(16 * N);
     k.crT = L.take<char>(8 * ts * N);
     k.clsgT = L.take<char>(8 * ts * N);
-    k.cslotT = L.take<char>(16 * ts * N);
+    k.cslotT = L.take<char>(8 * ts * N);
+    k.scode = L.take<int>(32 * N);
     k.fL = L.take<int>(4 * nf);
     k.fR = L.take<int>(4 * nf);
     k.fgeo = L.take<double>(56 * nf);
@@ -432,7 +433,6 @@ size_t layout(idg_ctx *c, char *base, KParams *kp)
     k.phiraw = L.take<char>(32 * nf);
     k.phi = L.take<double>(32 * nf);
     k.rw = L.take<double>(32 * N);
-    k.clink = L.take<int>(48 * N);
     k.mrec = L.take<char>(24 * ts * N);
     k.mdW = L.take<char>(4 * ts * N);
     k.mpart = L.take<double>(8 * (N / 32 + 2));
@@ -841,32 +841,42 @@ idg_status idg_bind_workspace(idg_ctx *c, void *dev_ptr, size_t bytes)
     // uploads
     std::vector<float> uxf(c->ux.begin(), c->ux.end()), uyf(c->uy.begin(), c->uy.end()),
         wf(c->w.begin(), c->w.end());
-    std::vector<double> fgeo8((size_t)8 * c->nf, 0.0), cslot((size_t)16 * c->N, 0.0);
-    std::vector<int> clink((size_t)12 * c->N, -1);
-    for (int q = 0; q < c->N; ++q)
-        for (int m = 0; m < 4; ++m) {
-            int nb = c->cnb[4 * q + m];
-            if (nb < 0) continue;
-            clink[12 * q + m] = nb;
-            clink[12 * q + 4 + m] = nb % c->ni;
-            clink[12 * q + 8 + m] = nb % c->ni + nb / c->ni;
+    std::vector<double> fgeo8((size_t)8 * c->nf, 0.0), cslot((size_t)8 * c->N, 0.0);
+    // micro sweeps: the role of each slot's neighbour in the forward (dir +1)
+    // and backward (dir -1) sweep: its slot in the previous hyperplane (>= 0),
+    // -2 a ghost or not yet swept, -3 the cell itself, -4 - nb the neighbour
+    // nb across a periodic seam
+    std::vector<int> scode((size_t)8 * c->N, -2);
+    for (int dir = 1, o = 0; dir >= -1; dir -= 2, o += 4 * c->N)
+        for (int q = 0; q < c->N; ++q) {
+            const int d = q % c->ni + q / c->ni;
+            for (int m = 0; m < 4; ++m) {
+                const int nb = c->cnb[4 * q + m];
+                int code = -2;
+                if (nb == q) code = -3;
+                else if (nb >= 0 && (dir > 0 ? nb < q : nb > q)) {
+                    const int nbi = nb % c->ni, dp = d - dir;
+                    code = nbi + nb / c->ni == dp ? nbi - std::max(0, dp - (c->nj - 1)) : -4 - nb;
+                }
+                scode[o + 4 * q + m] = code;
+            }
         }
     for (int q = 0; q < c->nf; ++q)
         for (int m = 0; m < 7; ++m) fgeo8[(size_t)8 * q + m] = c->fgeo[(size_t)7 * q + m];
+    // micro sweeps: per slot the outward normal scaled by the face length
     for (int q = 0; q < c->N; ++q)
         for (int m = 0; m < 4; ++m) {
             int fi = c->cface[4 * q + m];
-            double s = c->csign[4 * q + m];
-            cslot[16 * q + 4 * m] = s * c->fgeo[(size_t)7 * fi];
-            cslot[16 * q + 4 * m + 1] = s * c->fgeo[(size_t)7 * fi + 1];
-            cslot[16 * q + 4 * m + 2] = c->fgeo[(size_t)7 * fi + 2];
+            double s = c->csign[4 * q + m], S = c->fgeo[(size_t)7 * fi + 2];
+            cslot[8 * q + 2 * m] = s * c->fgeo[(size_t)7 * fi] * S;
+            cslot[8 * q + 2 * m + 1] = s * c->fgeo[(size_t)7 * fi + 1] * S;
         }
     cudaError_t errs[] = {
         up((double *)k.area, c->area), up((double *)k.dtimp, c->dtimp), up((int *)k.cface, c->cface),
         up((int *)k.cnb, c->cnb), up((int *)k.csign, c->csign), up_storage(c, k.crT, c->cr),
-        up_storage(c, k.clsgT, c->clsg), up_storage(c, k.cslotT, cslot), up((int *)k.fL, c->fL),
+        up_storage(c, k.clsgT, c->clsg), up_storage(c, k.cslotT, cslot), up((int *)k.scode, scode), up((int *)k.fL, c->fL),
         up((int *)k.fR, c->fR), up((double *)k.fgeo, c->fgeo), up_storage(c, k.fgeoT, fgeo8),
-        up((int *)k.fbc, c->fbc), up((int *)k.fside, c->fside), up((int *)k.clink, clink),
+        up((int *)k.fbc, c->fbc), up((int *)k.fside, c->fside),
         up((double *)k.ux, c->ux), up((double *)k.uy, c->uy), up((double *)k.w, c->w),
         up((float *)k.uxf, uxf), up((float *)k.uyf, uyf), up((float *)k.wf, wf),
         cudaMemset(k.iter, 0, 256), cudaMemset(k.phi, 0, 32 * (size_t)c->nf)};

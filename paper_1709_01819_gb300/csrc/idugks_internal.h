@@ -31,7 +31,8 @@ struct KParams {
     const int *csign;      // [N][4] +1 if the cell is the L side of that face
     const void *crT;       // [N][8] T: face midpoint minus centroid, per slot
     const void *clsgT;     // [N][8] T: least-squares weight vector per slot
-    const void *cslotT;    // [N][4][4] T: sign*nx, sign*ny, S, 0 per slot
+    const void *cslotT;    // [N][4][2] T: sign*nx*S, sign*ny*S per slot (micro sweeps)
+    const int *scode;      // [2][N][4] forward, backward: role of each slot's neighbour in that micro sweep
     // faces
     const int *fL, *fR;    // [nf]
     const double *fgeo;    // [nf][7] nx, ny, S, rLx, rLy, rRx, rRy
@@ -68,7 +69,6 @@ struct KParams {
     void *phiraw;   // [nf][4] acc moments of the deviation flux
     double *phi;    // [nf][4]
     double *rw;     // [N][4]
-    const int *clink;  // [N][12] per slot: neighbour, its i, its hyperplane i+j (-1 ghost)
     // macroscopic LU-SGS work (T = storage precision of the sweep)
     void *mrec;     // [N][24] T: R, 1/D, own base state, per slot (S/2) n_out, (omega/2) Lambda
     void *mdW;      // [N][4] T increments (Delta W* then Delta W)

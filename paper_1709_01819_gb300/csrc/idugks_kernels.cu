@@ -1197,35 +1197,59 @@ template <> __device__ __forceinline__ void load16<double>(double (&r)[16], cons
     }
 }
 
+// Role of the neighbour across each slot of a cell in one micro sweep
+// (computed on the host): >= 0 its slot in the previous hyperplane's ring;
+// kOther a ghost or a neighbour not yet swept (outflow only adds to D); kSelf
+// the cell itself across a periodic direction one cell wide (no term at all);
+// <= kSeam the neighbour kSeam - code across a periodic seam (already swept,
+// read from global memory).
+constexpr int kOther = -2, kSelf = -3, kSeam = -4;
+
+// 8 storage scalars from 16-byte-aligned shared memory
+template <class T> __device__ __forceinline__ void load8(T (&r)[8], const T *s);
+template <> __device__ __forceinline__ void load8<float>(float (&r)[8], const float *s)
+{
+    const float4 a = ((const float4 *)s)[0], b = ((const float4 *)s)[1];
+    r[0] = a.x; r[1] = a.y; r[2] = a.z; r[3] = a.w; r[4] = b.x; r[5] = b.y; r[6] = b.z; r[7] = b.w;
+}
+template <> __device__ __forceinline__ void load8<double>(double (&r)[8], const double *s)
+{
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const double2 a = ((const double2 *)s)[u];
+        r[2 * u] = a.x; r[2 * u + 1] = a.y;
+    }
+}
+
 // shared-memory layout of the micro sweeps (VPT consecutive velocities per thread)
 template <class T, int kStages, int VPT> struct SweepSmem {
     using T2 = typename V2<T>::t;
     T2 *R;      // [kStages][pc][tv*VPT]  R (forward) / Delta* (backward)
     T2 *F;      // [kStages][pc][tv*VPT]  f~ (backward only)
-    T *geo;     // [kStages][pc][16]  sign*nx, sign*ny, S, 0 per slot
-    int *lnk;   // [kStages][pc][12]  neighbour, its i, its hyperplane
-    T2 *ring;   // [2][ni][tv*VPT]
+    T *geo;     // [kStages][pc][8]  per slot: sign*nx*S, sign*ny*S
+    int *code;  // [kStages][pc][4]  per slot: the neighbour's role in this sweep (sweep_codes)
+    T2 *ring;   // [2][pc][tv*VPT]  increments of the previous hyperplane, by slot
     T *D0;      // [kStages][pc]
-    __device__ SweepSmem(unsigned char *base, int pc, int tv, int ni, bool withF)
+    __device__ SweepSmem(unsigned char *base, int pc, int tv, bool withF)
     {
         size_t o = 0;
         const size_t w = (size_t)tv * VPT;
         R = (T2 *)(base + o); o += (size_t)kStages * pc * w * sizeof(T2);
         F = (T2 *)(base + o); if (withF) o += (size_t)kStages * pc * w * sizeof(T2);
-        geo = (T *)(base + o); o += (size_t)kStages * pc * 16 * sizeof(T);
-        lnk = (int *)(base + o); o += (size_t)kStages * pc * 12 * sizeof(int);
-        ring = (T2 *)(base + o); o += (size_t)2 * ni * w * sizeof(T2);
+        geo = (T *)(base + o); o += (size_t)kStages * pc * 8 * sizeof(T);
+        code = (int *)(base + o); o += (size_t)kStages * pc * 4 * sizeof(int);
+        ring = (T2 *)(base + o); o += (size_t)2 * pc * w * sizeof(T2);
         D0 = (T *)(base + o);
     }
 };
 
-template <class T, int kStages, int VPT> static size_t sweep_smem_bytes(int pc, int tv, int ni, bool withF)
+template <class T, int kStages, int VPT> static size_t sweep_smem_bytes(int pc, int tv, bool withF)
 {
     using T2 = typename V2<T>::t;
     const size_t w = (size_t)tv * VPT;
     size_t o = (size_t)kStages * pc * w * sizeof(T2) * (withF ? 2 : 1);
-    o += (size_t)kStages * pc * 16 * sizeof(T) + (size_t)kStages * pc * 12 * sizeof(int);
-    o += (size_t)2 * ni * w * sizeof(T2) + (size_t)kStages * pc * sizeof(T);
+    o += (size_t)kStages * pc * (8 * sizeof(T) + 4 * sizeof(int));
+    o += (size_t)2 * pc * w * sizeof(T2) + (size_t)kStages * pc * sizeof(T);
     return o;
 }
 
@@ -1234,12 +1258,12 @@ struct SweepArgs {
     int Nv, ni, nj, tv, pc;
     void *dst, *f;
     const void *cslotT, *cellpT;
-    const int *clink;
+    const int *codes;  // this sweep's [N][4] slot codes
 };
 
 // asynchronous copy of one step's data for the thread's cell: its VPT
-// consecutive velocities of R (or Delta*, f~), and the cell's geometry,
-// links and diagonal base spread over the cell's tv threads
+// consecutive velocities of R (or Delta*, f~), and the cell's slot geometry
+// and diagonal base spread over the cell's tv threads
 template <class T, int kStages, int VPT>
 __device__ __forceinline__ void sweep_issue(const SweepArgs &p, const SweepSmem<T, kStages, VPT> &sm, int s, int d,
                                             int slot, int t, int k0, bool act, bool withF)
@@ -1269,10 +1293,10 @@ __device__ __forceinline__ void sweep_issue(const SweepArgs &p, const SweepSmem<
                     for (int b = 0; b < B; b += CH) cp_async_b<CH>(sf + b, gf + b);
                 }
             }
-            constexpr int ng = 16 * sizeof(T) / 16;  // 16-byte chunks of the geometry record
-            for (int q = t; q < ng + 4; q += tv) {
-                if (q < ng) cp_async16((char *)(sm.geo + e * 16) + 16 * q, (const char *)((const T *)p.cslotT + 16 * (size_t)c) + 16 * q);
-                else if (q < ng + 3) cp_async16((char *)(sm.lnk + e * 12) + 16 * (q - ng), (const char *)(p.clink + 12 * (size_t)c) + 16 * (q - ng));
+            constexpr int ng = 8 * sizeof(T) / 16;  // 16-byte chunks of the slot geometry
+            for (int q = t; q < ng + 2; q += tv) {
+                if (q < ng) cp_async16((char *)(sm.geo + e * 8) + 16 * q, (const char *)((const T *)p.cslotT + 8 * (size_t)c) + 16 * q);
+                else if (q == ng) cp_async16(sm.code + e * 4, p.codes + 4 * (size_t)c);
                 else cp_async_b<sizeof(T)>(sm.D0 + e, (const T *)p.cellpT + kCellP * (size_t)c + 15);
             }
         }
@@ -1286,9 +1310,10 @@ __global__ void __launch_bounds__(512) k_sweep(Launch L)
     IDG_LOCATE();
     using T2 = typename V2<T>::t;
     extern __shared__ __align__(16) unsigned char smraw[];
-    const SweepArgs a{p.Nv, p.ni, p.nj, p.sweep_tv, p.sweep_pc, p.dst, p.f, p.cslotT, p.cellpT, p.clink};
+    const SweepArgs a{p.Nv, p.ni, p.nj, p.sweep_tv, p.sweep_pc, p.dst, p.f, p.cslotT, p.cellpT,
+                      p.scode + (FWD ? 0 : 4 * (size_t)p.N)};
     const int tv = a.tv, pc = a.pc, ni = a.ni, nj = a.nj, Nv = a.Nv;
-    const SweepSmem<T, kStages, VPT> sm(smraw, pc, tv, ni, !FWD);
+    const SweepSmem<T, kStages, VPT> sm(smraw, pc, tv, !FWD);
     const int t = threadIdx.x % tv, slot = threadIdx.x / tv;
     const int k0 = (blk * tv + t) * VPT;  // Nv is a multiple of VPT
     const bool act = k0 < Nv;
@@ -1312,45 +1337,38 @@ __global__ void __launch_bounds__(512) k_sweep(Launch L)
         sweep_issue<T, kStages, VPT>(a, sm, s + kStages - 1, step_d(s + kStages - 1), slot, t, k0, act, !FWD);
         const int d = step_d(s);
         const int ilo = max(0, d - (nj - 1)), ihi = min(ni - 1, d);
-        const int i = ilo + slot;
+        const int i = ilo + slot, j = d - i;
         if (i > ihi || !act) continue;
-        const int c = (d - i) * ni + i;
+        const int c = j * ni + i;
         const size_t e = (size_t)(s & (kStages - 1)) * pc + slot;
-        // the whole cell record at once (vector shared-memory loads)
-        T g[16];
-        load16<T>(g, sm.geo + e * 16);
-        const int4 lnb = *(const int4 *)(sm.lnk + e * 12);
-        const int4 lni = *(const int4 *)(sm.lnk + e * 12 + 4);
-        const int4 lnd = *(const int4 *)(sm.lnk + e * 12 + 8);
-        const int nbv[4] = {lnb.x, lnb.y, lnb.z, lnb.w};
-        const int niv[4] = {lni.x, lni.y, lni.z, lni.w};
-        const int ndv[4] = {lnd.x, lnd.y, lnd.z, lnd.w};
+        T g[8];
+        load8<T>(g, sm.geo + e * 8);
+        const int4 cd = *(const int4 *)(sm.code + e * 4);
+        const int code[4] = {cd.x, cd.y, cd.z, cd.w};
         const T D0 = sm.D0[e];
         const size_t ck = (size_t)c * Nv + k0;
         const size_t rbase = e * w + (size_t)t * VPT;
-        const size_t rprev = (size_t)(((d - dir) & 1) * ni) * w + (size_t)t * VPT;
+        const size_t rprev = (size_t)((s + 1) & 1) * pc * w + (size_t)t * VPT;
 #pragma unroll
         for (int v = 0; v < VPT; ++v) {
-            // slot terms, branch-free: outflow adds to D, inflow from the
-            // already-swept side adds |xi.n| S Delta_nb
+            // slot terms, branch-free: outflow adds (xi.n) S to D, inflow from
+            // the already-swept side adds |xi.n| S Delta_nb
             T D = D0;
             T aS[4];
             bool in[4];
 #pragma unroll
             for (int m = 0; m < 4; ++m) {
-                const bool self = nbv[m] == c;
-                const T so = xi_dot_n<T>(ux[v], uy[v], g[4 * m], g[4 * m + 1]);
-                aS[m] = so * g[4 * m + 2];
-                D += (so > (T)0 && !self) ? aS[m] : (T)0;
-                in[m] = so < (T)0 && !self && nbv[m] >= 0 && (FWD ? nbv[m] < c : nbv[m] > c);
+                aS[m] = add_rn(mul_rn(ux[v], g[2 * m]), mul_rn(uy[v], g[2 * m + 1]));
+                D += (aS[m] > (T)0 && code[m] != kSelf) ? aS[m] : (T)0;
+                in[m] = aS[m] < (T)0 && (code[m] >= 0 || code[m] <= kSeam);
             }
             T2 dn[4];
 #pragma unroll
             for (int m = 0; m < 4; ++m) {
                 dn[m].x = (T)0;
                 dn[m].y = (T)0;
-                if (in[m]) dn[m] = (ndv[m] == d - dir) ? sm.ring[rprev + (size_t)niv[m] * w + v]
-                                                       : ds[(size_t)nbv[m] * Nv + k0 + v];
+                if (in[m]) dn[m] = code[m] >= 0 ? sm.ring[rprev + (size_t)code[m] * w + v]
+                                                : ds[(size_t)(kSeam - code[m]) * Nv + k0 + v];
             }
             T ag = 0, ah = 0;
 #pragma unroll
@@ -1373,7 +1391,7 @@ __global__ void __launch_bounds__(512) k_sweep(Launch L)
                 f[ck + v] = fv;
             }
             ds[ck + v] = o;
-            sm.ring[((d & 1) * ni + i) * w + (size_t)t * VPT + v] = o;
+            sm.ring[((size_t)(s & 1) * pc + slot) * w + (size_t)t * VPT + v] = o;
         }
     }
     cp_wait<0>();
@@ -1451,9 +1469,9 @@ template <class T> static size_t macro_smem_bytes(const KParams &p, int nt, int 
 template <class T, int S> static size_t sweep_bytes_s(const KParams &p, bool withF)
 {
     switch (p.sweep_vpt) {
-    case 4: return sweep_smem_bytes<T, S, 4>(p.sweep_pc, p.sweep_tv, p.ni, withF);
-    case 2: return sweep_smem_bytes<T, S, 2>(p.sweep_pc, p.sweep_tv, p.ni, withF);
-    default: return sweep_smem_bytes<T, S, 1>(p.sweep_pc, p.sweep_tv, p.ni, withF);
+    case 4: return sweep_smem_bytes<T, S, 4>(p.sweep_pc, p.sweep_tv, withF);
+    case 2: return sweep_smem_bytes<T, S, 2>(p.sweep_pc, p.sweep_tv, withF);
+    default: return sweep_smem_bytes<T, S, 1>(p.sweep_pc, p.sweep_tv, withF);
     }
 }
 
