@@ -44,6 +44,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <type_traits>
 
 namespace idg {
 
@@ -1349,50 +1350,62 @@ __global__ void __launch_bounds__(512) k_sweep(Launch L)
         const size_t ck = (size_t)c * Nv + k0;
         const size_t rbase = e * w + (size_t)t * VPT;
         const size_t rprev = (size_t)((s + 1) & 1) * pc * w + (size_t)t * VPT;
+        // the step of one cell; SEAM: some neighbour lies across a periodic
+        // seam (read from global memory), otherwise every inflow comes from
+        // the ring
+        auto cell_step = [&](auto seam_tag) {
+            constexpr bool SEAM = decltype(seam_tag)::value;
 #pragma unroll
-        for (int v = 0; v < VPT; ++v) {
-            // slot terms, branch-free: outflow adds (xi.n) S to D, inflow from
-            // the already-swept side adds |xi.n| S Delta_nb
-            T D = D0;
-            T aS[4];
-            bool in[4];
+            for (int v = 0; v < VPT; ++v) {
+                // slot terms, branch-free: outflow adds (xi.n) S to D, inflow
+                // from the already-swept side adds |xi.n| S Delta_nb
+                T D = D0;
+                T aS[4];
+                bool in[4];
 #pragma unroll
-            for (int m = 0; m < 4; ++m) {
-                aS[m] = add_rn(mul_rn(ux[v], g[2 * m]), mul_rn(uy[v], g[2 * m + 1]));
-                D += (aS[m] > (T)0 && code[m] != kSelf) ? aS[m] : (T)0;
-                in[m] = aS[m] < (T)0 && (code[m] >= 0 || code[m] <= kSeam);
-            }
-            T2 dn[4];
+                for (int m = 0; m < 4; ++m) {
+                    aS[m] = add_rn(mul_rn(ux[v], g[2 * m]), mul_rn(uy[v], g[2 * m + 1]));
+                    D += (aS[m] > (T)0 && code[m] != kSelf) ? aS[m] : (T)0;
+                    in[m] = aS[m] < (T)0 && (code[m] >= 0 || (SEAM && code[m] <= kSeam));
+                }
+                T2 dn[4];
 #pragma unroll
-            for (int m = 0; m < 4; ++m) {
-                dn[m].x = (T)0;
-                dn[m].y = (T)0;
-                if (in[m]) dn[m] = code[m] >= 0 ? sm.ring[rprev + (size_t)code[m] * w + v]
-                                                : ds[(size_t)(kSeam - code[m]) * Nv + k0 + v];
-            }
-            T ag = 0, ah = 0;
+                for (int m = 0; m < 4; ++m) {
+                    dn[m].x = (T)0;
+                    dn[m].y = (T)0;
+                    if (in[m]) {
+                        if (!SEAM || code[m] >= 0) dn[m] = sm.ring[rprev + (size_t)code[m] * w + v];
+                        else dn[m] = ds[(size_t)(kSeam - code[m]) * Nv + k0 + v];
+                    }
+                }
+                T ag = 0, ah = 0;
 #pragma unroll
-            for (int m = 0; m < 4; ++m) {
-                ag -= aS[m] * dn[m].x;
-                ah -= aS[m] * dn[m].y;
+                for (int m = 0; m < 4; ++m) {
+                    ag -= aS[m] * dn[m].x;
+                    ah -= aS[m] * dn[m].y;
+                }
+                const T2 r = sm.R[rbase + v];
+                const T iD = (T)1 / D;
+                T2 o;
+                if (FWD) {
+                    o.x = (r.x + ag) * iD;
+                    o.y = (r.y + ah) * iD;
+                } else {
+                    o.x = r.x + ag * iD;
+                    o.y = r.y + ah * iD;
+                    T2 fv = sm.F[rbase + v];
+                    fv.x += o.x;
+                    fv.y += o.y;
+                    f[ck + v] = fv;
+                }
+                ds[ck + v] = o;
+                sm.ring[((size_t)(s & 1) * pc + slot) * w + (size_t)t * VPT + v] = o;
             }
-            const T2 r = sm.R[rbase + v];
-            const T iD = (T)1 / D;
-            T2 o;
-            if (FWD) {
-                o.x = (r.x + ag) * iD;
-                o.y = (r.y + ah) * iD;
-            } else {
-                o.x = r.x + ag * iD;
-                o.y = r.y + ah * iD;
-                T2 fv = sm.F[rbase + v];
-                fv.x += o.x;
-                fv.y += o.y;
-                f[ck + v] = fv;
-            }
-            ds[ck + v] = o;
-            sm.ring[((size_t)(s & 1) * pc + slot) * w + (size_t)t * VPT + v] = o;
-        }
+        };
+        if (code[0] <= kSeam || code[1] <= kSeam || code[2] <= kSeam || code[3] <= kSeam)
+            cell_step(std::true_type{});
+        else
+            cell_step(std::false_type{});
     }
     cp_wait<0>();
 }
