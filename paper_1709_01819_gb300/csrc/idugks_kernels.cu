@@ -984,22 +984,25 @@ __device__ __forceinline__ void euler_dflux(T gm1, const T *b, const T *dW, T nx
 }
 
 // One CTA: forward then backward sweep over the i+j hyperplanes (the
-// lexicographic dependency order).  Four threads own one cell of the
-// hyperplane, thread m handling the neighbour across slot m (found from the
-// cell's (i, j) and the periodic flags); the four off-diagonal terms
-// 1/2 (dF S - omega Lambda dW_nb) are summed by a quad shuffle and thread m
-// then writes component m of the increment.  Records and (backward) the
-// cell's own dW* are prefetched kStages-1 hyperplanes ahead with cp.async;
-// the previous hyperplane's increments and base states sit in a
-// shared-memory ring indexed by the slot in the hyperplane; neighbours across
-// a periodic seam (earlier hyperplanes) come from global memory.
+// lexicographic dependency order).  Two threads own one cell of the
+// hyperplane: thread h handles the slot pair (west, east) for h = 0 and
+// (south, north) for h = 1 -- of each pair at most one neighbour is on the
+// already-swept side away from a periodic seam, so each thread usually
+// evaluates one flux increment 1/2 (dF S - omega Lambda dW_nb).  The two
+// partial sums meet in one pair shuffle and thread h writes components 2h and
+// 2h+1 of the increment.  Neighbours are found from the cell's (i, j) and the
+// periodic flags.  Records and (backward) the cell's own dW* are prefetched
+// kStages-1 hyperplanes ahead with cp.async; the previous hyperplane's
+// increments and base states sit in a shared-memory ring indexed by the slot
+// in the hyperplane; neighbours across a periodic seam (earlier hyperplanes)
+// come from global memory.
 template <class T, int kStages>
-__global__ void __launch_bounds__(1024) k_macro_sweep(Launch L)
+__global__ void __launch_bounds__(512) k_macro_sweep(Launch L)
 {
     IDG_LOCATE();
     extern __shared__ __align__(16) unsigned char smraw[];
-    const int tid = threadIdx.x, ncs = blockDim.x >> 2;  // cell slots
-    const int cs = tid >> 2, m = tid & 3;
+    const int tid = threadIdx.x, ncs = blockDim.x >> 1;  // cell slots
+    const int cs = tid >> 1, h = tid & 1;
     const int ni = p.ni, nj = p.nj, nh = ni + nj - 1;
     const bool per_i = p.per_i, per_j = p.per_j;
     T *srec = (T *)smraw;                               // [kStages][ncs][kMRec]
@@ -1029,7 +1032,7 @@ __global__ void __launch_bounds__(1024) k_macro_sweep(Launch L)
                     const int c = (d - i) * ni + i;
                     const size_t e = (size_t)(s & (kStages - 1)) * ncs + cs;
                     const int nch = RC + (dir < 0 ? DC : 0);
-                    for (int q = m; q < nch; q += 4) {
+                    for (int q = h; q < nch; q += 2) {
                         if (q < RC) cp_async16((char *)(srec + e * kMRec) + 16 * q, (const char *)(mrec + (size_t)kMRec * c) + 16 * q);
                         else cp_async16((char *)(sdw + e * 4) + 16 * (q - RC), (const char *)(dWg + 4 * (size_t)c) + 16 * (q - RC));
                     }
@@ -1051,15 +1054,21 @@ __global__ void __launch_bounds__(1024) k_macro_sweep(Launch L)
             const T *rec = srec + e * kMRec;
             T acc0 = 0, acc1 = 0, acc2 = 0, acc3 = 0;
             if (valid) {
-                // the neighbour across slot m (west, east, south, north)
-                int nbi = i, nbj = j;
-                bool ex = true;
-                if (m == 0) { nbi = i - 1; if (i == 0) { ex = per_i; nbi = ni - 1; } }
-                else if (m == 1) { nbi = i + 1; if (i == ni - 1) { ex = per_i; nbi = 0; } }
-                else if (m == 2) { nbj = j - 1; if (j == 0) { ex = per_j; nbj = nj - 1; } }
-                else { nbj = j + 1; if (j == nj - 1) { ex = per_j; nbj = 0; } }
-                const int nb = nbj * ni + nbi;
-                if (ex && (dir > 0 ? nb < c : nb > c)) {
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    // slot m = 2h + u: west, east (h = 0); south, north (h = 1)
+                    const int m = 2 * h + u;
+                    int nbi = i, nbj = j;
+                    bool ex = true;
+                    if (h == 0) {
+                        nbi = u ? i + 1 : i - 1;
+                        if (u ? i == ni - 1 : i == 0) { ex = per_i; nbi = u ? 0 : ni - 1; }
+                    } else {
+                        nbj = u ? j + 1 : j - 1;
+                        if (u ? j == nj - 1 : j == 0) { ex = per_j; nbj = u ? 0 : nj - 1; }
+                    }
+                    const int nb = nbj * ni + nbi;
+                    if (!ex || !(dir > 0 ? nb < c : nb > c)) continue;
                     T dn[4];
                     const T *base;
                     if (nbi + nbj == d - dir) {
@@ -1075,30 +1084,38 @@ __global__ void __launch_bounds__(1024) k_macro_sweep(Launch L)
                     const T *cf = rec + 12 + 3 * m;
                     T dF[4];
                     euler_dflux<T>(gm1, base, dn, cf[0], cf[1], dF);
-                    acc0 = dF[0] - cf[2] * dn[0];
-                    acc1 = dF[1] - cf[2] * dn[1];
-                    acc2 = dF[2] - cf[2] * dn[2];
-                    acc3 = dF[3] - cf[2] * dn[3];
+                    acc0 += dF[0] - cf[2] * dn[0];
+                    acc1 += dF[1] - cf[2] * dn[1];
+                    acc2 += dF[2] - cf[2] * dn[2];
+                    acc3 += dF[3] - cf[2] * dn[3];
                 }
             }
-            // sum over the four slots of the cell (fixed butterfly order)
-#pragma unroll
-            for (int o = 1; o <= 2; o <<= 1) {
-                acc0 += __shfl_xor_sync(0xffffffffu, acc0, o);
-                acc1 += __shfl_xor_sync(0xffffffffu, acc1, o);
-                acc2 += __shfl_xor_sync(0xffffffffu, acc2, o);
-                acc3 += __shfl_xor_sync(0xffffffffu, acc3, o);
-            }
+            // sum over the two slot pairs of the cell
+            acc0 += __shfl_xor_sync(0xffffffffu, acc0, 1);
+            acc1 += __shfl_xor_sync(0xffffffffu, acc1, 1);
+            acc2 += __shfl_xor_sync(0xffffffffu, acc2, 1);
+            acc3 += __shfl_xor_sync(0xffffffffu, acc3, 1);
             if (valid) {
                 // forward: dW*_c = (R_c - sum_lower) / D_c;  backward: dW_c = dW*_c - sum_upper / D_c
-                const T am = m == 0 ? acc0 : (m == 1 ? acc1 : (m == 2 ? acc2 : acc3));
                 const T iD = rec[4];
-                const T x = dir > 0 ? (rec[m] - am) * iD : sdw[e * 4 + m] - am * iD;
+                const T a0 = h ? acc2 : acc0, a1 = h ? acc3 : acc1;
+                const int q0 = 2 * h;
+                T x0, x1;
+                if (dir > 0) {
+                    x0 = (rec[q0] - a0) * iD;
+                    x1 = (rec[q0 + 1] - a1) * iD;
+                } else {
+                    x0 = sdw[e * 4 + q0] - a0 * iD;
+                    x1 = sdw[e * 4 + q0 + 1] - a1 * iD;
+                }
                 T *r = ring + ((size_t)(s & 1) * ncs + cs) * kMRing;
-                r[m] = x;
-                r[4 + m] = rec[6 + m];
-                if (m < 2) r[8 + m] = rec[10 + m];
-                dWg[4 * (size_t)c + m] = x;
+                r[q0] = x0;
+                r[q0 + 1] = x1;
+                r[4 + 3 * h] = rec[6 + 3 * h];
+                r[5 + 3 * h] = rec[7 + 3 * h];
+                r[6 + 3 * h] = rec[8 + 3 * h];
+                dWg[4 * (size_t)c + q0] = x0;
+                dWg[4 * (size_t)c + q0 + 1] = x1;
             }
         }
         cp_wait<0>();
@@ -1472,11 +1489,11 @@ __global__ void __launch_bounds__(256) k_moments_out(KParams p, double *out6)
 // ---------------------------------------------------------------------------
 static inline int nblk(int n, int per) { return (n + per - 1) / per; }
 
-static int macro_threads(const KParams &p) { return std::min(1024, ((4 * std::min(p.ni, p.nj) + 31) / 32) * 32); }
+static int macro_threads(const KParams &p) { return std::min(512, ((2 * std::min(p.ni, p.nj) + 31) / 32) * 32); }
 
 template <class T> static size_t macro_smem_bytes(const KParams &p, int nt, int stages)
 {
-    return (size_t)stages * (nt / 4) * (kMRec + 4) * sizeof(T) + (size_t)2 * (nt / 4) * kMRing * sizeof(T);
+    return (size_t)stages * (nt / 2) * (kMRec + 4) * sizeof(T) + (size_t)2 * (nt / 2) * kMRing * sizeof(T);
 }
 
 template <class T, int S> static size_t sweep_bytes_s(const KParams &p, bool withF)
