@@ -253,6 +253,8 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ttr", action="store_true", help="skip the time-to-residual runs")
+    ap.add_argument("--explicit-ttr", action="store_true",
+                    help="also time explicit DUGKS (Eq. 21, same precision) to the residual 1e-6 (tens of seconds)")
     ap.add_argument("--tune", default="auto", choices=["auto", "default"],
                     help="auto: pick the sweep kind, tiles and prefetch depths with the autotuner before timing")
     args = ap.parse_args()
@@ -373,6 +375,17 @@ def main():
             torch.cuda.synchronize()
             ttr[prec] = {"seconds": time.perf_counter() - t0, "iterations": n, "residual": r, "converged": ok}
             del s2
+        if args.explicit_ttr:
+            # explicit DUGKS: physical step dt, residual ||(W^{n+1} - W^n)/dt||
+            s2 = Solver(prob, args.precision, device=local, explicit=True)
+            s2.init_uniform()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ok, n, r = s2.iterate(1000000, 1e-6)
+            torch.cuda.synchronize()
+            ttr["explicit_" + args.precision] = {"seconds": time.perf_counter() - t0, "iterations": n,
+                                                 "residual": r, "converged": ok}
+            del s2
 
     if rank == 0:
         line = {
@@ -392,7 +405,10 @@ def main():
             "e2e": e2e,
             "time_to_residual_1e-6": ttr,
             "clocks": clk.summary(),
-            "gpu_launches": 6 * args.steps if s.nf else 5 * args.steps,
+            # per iteration: cell moments, cell params, fb+, [limited gradients],
+            # face moments, face params, face flux, Phi, macro pre / sweep /
+            # post, micro residual, forward and backward sweeps
+            "gpu_launches": (13 + (1 if prob.limiter else 0)) * args.steps,
         }
         print(json.dumps(line), flush=True)
     if dist:

@@ -103,7 +103,18 @@ idg_status idg_set_boundary(idg_ctx *ctx, int side, int kind, double rho, double
  * xi_max of Eq. (26) and (30); cfl_phys the physical DUGKS step dt = cfl_phys
  * h_min / xi_max of Eq. (8); limiter 0 (phi = 1) or 1 (Eq. 16-17);
  * lusgs_omega the relaxation of the macroscopic LU-SGS (2 reproduces Eq. 30);
- * flags must be 0. */
+ * flags 0 or IDG_NUM_EXPLICIT.
+ * IDG_NUM_EXPLICIT: idg_iterate and idg_iterate_profiled advance explicit
+ * DUGKS time steps instead of IDUGKS iterations: the cell and face stages of
+ * the iteration (Eq. 10-20, flux with the physical step dt) followed by the
+ * update of Eq. (21), f~ <- (2tau-dt)/(2tau+dt) f~ + 2dt/(2tau+dt) f^S -
+ * dt/Omega sum_faces F, tau and f^S at the moments of f~.  W is the moment
+ * set of f~ (recomputed before the first step of every call and after each
+ * step); cfl_imp and lusgs_omega are unused.  The residual of a step is
+ * ||(W^{n+1} - W^n)/dt||_2 (at the fixed point of the march R_W balances the
+ * moments of the discrete collision term and does not vanish).  Such a
+ * context can neither join a batch nor run idg_adjoint (IDG_ERR_ARG). */
+enum { IDG_NUM_EXPLICIT = 1 };
 idg_status idg_set_numerics(idg_ctx *ctx, double cfl_imp, double cfl_phys, int limiter,
                             double lusgs_omega, int flags);
 
@@ -129,6 +140,7 @@ idg_status idg_set_state(idg_ctx *ctx, const double *G, const double *H, const d
 idg_status idg_get_state(idg_ctx *ctx, double *G, double *H, double *W, void *stream);
 
 /* Run IDUGKS iterations (Section 2.2) until the residual ||R_W/Omega||_2
+ * (explicit DUGKS: ||(W^{n+1} - W^n)/dt||_2, see IDG_NUM_EXPLICIT)
  * divided by that of the first iteration after the last (re)start is <= tol,
  * or max_iter iterations ran.  tol <= 0 runs exactly max_iter iterations.
  * iters_done and residual (relative) may be NULL.  Returns

@@ -22,6 +22,7 @@ IDG_BGK, IDG_SHAKHOV = 0, 1
 IDG_TUNE_SWEEP_TV, IDG_TUNE_SWEEP_STAGES, IDG_TUNE_MACRO_STAGES, IDG_TUNE_GRAPH, IDG_TUNE_SWEEP_VPT = 1, 2, 3, 4, 5
 IDG_OBJ_FORCE_X, IDG_OBJ_FORCE_Y = 0, 1
 IDG_PAR_KN, IDG_PAR_WALL_T, IDG_PAR_WALL_U, IDG_PAR_WALL_V = 0, 1, 2, 3
+IDG_NUM_EXPLICIT = 1
 
 
 def IDG_PARAM(kind: int, side_mask: int = 0) -> int:

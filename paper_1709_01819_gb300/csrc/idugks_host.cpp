@@ -628,6 +628,7 @@ idg_status refresh_plan(idg_ctx *c)
         return fail(c, IDG_ERR_ARG, "launch shape does not fit in shared memory");
     c->kp.macro_stages = pl.macro_stages;
     c->kp.sweep_stages = pl.sweep_stages;
+    pl.explicit_dugks = (c->flags & IDG_NUM_EXPLICIT) ? 1 : 0;
     cudaError_t e;
     if (c->gstream && (e = cudaStreamSynchronize(c->gstream)) != cudaSuccess) return cuda_fail(c, e, "sync");
     if ((e = cudaMemcpy(c->kp_dev, &c->kp, sizeof(KParams), cudaMemcpyHostToDevice)) != cudaSuccess)
@@ -747,7 +748,7 @@ idg_status idg_set_numerics(idg_ctx *c, double cfl_imp, double cfl_phys, int lim
     if (!c) return IDG_ERR_ARG;
     if (c->bound) return fail(c, IDG_ERR_STATE, "setters are closed after idg_bind_workspace");
     if (!(cfl_imp > 0) || !(cfl_phys > 0) || (limiter != 0 && limiter != 1) || !(lusgs_omega >= 1.0) ||
-        flags != 0)
+        (flags & ~IDG_NUM_EXPLICIT) != 0)
         return fail(c, IDG_ERR_ARG, "invalid numerics");
     c->cfl_imp = cfl_imp; c->cfl_phys = cfl_phys; c->limiter = limiter;
     c->lusgs_omega = lusgs_omega; c->flags = flags;
@@ -976,6 +977,10 @@ idg_status idg_iterate(idg_ctx *c, int max_iter, double tol, void *stream, int *
     cudaStream_t st = (cudaStream_t)stream;
     const bool fp64 = c->precision == IDG_FP64;
     const int chunk = kGraphChunk;
+    if (c->plan.explicit_dugks && max_iter > 0) {
+        int rc = idg::launch_explicit_prologue(c->plan, fp64, st);
+        if (rc) return cuda_fail(c, (cudaError_t)rc, "launch");
+    }
     int done = 0;
     double rel = NAN;
     std::vector<double> buf(chunk);
@@ -1033,7 +1038,8 @@ idg_status idg_iterate_profiled(idg_ctx *c, void *stream, double *kernel_ms)
             return cuda_fail(c, e, "cudaEventCreate");
         }
     }
-    int rc = idg::launch_iteration(c->plan, c->precision == IDG_FP64, st, (void **)ev);
+    int rc = c->plan.explicit_dugks ? idg::launch_explicit_prologue(c->plan, c->precision == IDG_FP64, st) : 0;
+    if (!rc) rc = idg::launch_iteration(c->plan, c->precision == IDG_FP64, st, (void **)ev);
     cudaError_t e = rc ? (cudaError_t)rc : cudaStreamSynchronize(st);
     double r = 0.0;
     if (e == cudaSuccess) {
@@ -1337,6 +1343,7 @@ idg_status idg_batch_create(idg_batch **out, idg_ctx *const *ctxs, int n)
     for (int i = 0; i < n; ++i) {
         if (!ctxs[i] || !ctxs[i]->bound) return IDG_ERR_STATE;
         if (ctxs[i]->precision != ctxs[0]->precision || ctxs[i]->device != ctxs[0]->device) return IDG_ERR_ARG;
+        if (ctxs[i]->flags & IDG_NUM_EXPLICIT) return IDG_ERR_ARG;  // batches run IDUGKS iterations
         for (int j = 0; j < i; ++j)
             if (ctxs[j] == ctxs[i]) return IDG_ERR_ARG;
     }

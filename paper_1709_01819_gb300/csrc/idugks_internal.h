@@ -101,6 +101,7 @@ struct Plan {
     int macro_threads, sweep_threads;
     size_t macro_smem, fwd_smem, bwd_smem;
     int macro_stages, sweep_stages, limiter_any, sweep_vpt;
+    int explicit_dugks;  // 1: launch_iteration runs one explicit DUGKS step (Eq. 21)
 };
 
 // kernel launchers (idugks_kernels.cu)
@@ -110,6 +111,8 @@ int plan_shapes(const KParams *hp, int n, bool fp64, Plan &plan);
 constexpr int kProfiled = 6;  // timed groups in launch_iteration(events)
 int launch_iteration(const Plan &plan, bool fp64, void *stream, void **events = nullptr);
 int launch_cell_moments(const KParams &p, bool fp64, double *out6_dev, void *stream);
+// explicit DUGKS: W and the raw moments of the current f~ before the first step
+int launch_explicit_prologue(const Plan &plan, bool fp64, void *stream);
 // idg_get_moments_noalloc: raw moments in a static device array (no workspace)
 int launch_cell_moments_noalloc(const KParams &p, bool fp64, int device, double *out6_dev, void *stream);
 int launch_to_dev(const KParams &p, bool fp64, const double *G, const double *H, void *stream);

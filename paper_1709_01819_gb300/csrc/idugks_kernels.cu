@@ -965,6 +965,19 @@ __global__ void __launch_bounds__(32) k_macro_pre(Launch L)
     if (threadIdx.x == 0) p.mpart[blk] = part[0];
 }
 
+// ||R_W/Omega||_2 of this iteration from k_macro_pre's partials (fixed
+// order) into the residual ring; a non-finite value raises the status word
+__device__ __forceinline__ void record_residual(const KParams &p)
+{
+    double s = 0.0;
+    const int nb = (p.N + 31) / 32;
+    for (int q = 0; q < nb; ++q) s += p.mpart[q];
+    const int it = *p.iter;
+    const double r = sqrt(s);
+    p.res[it & (kMaxHist - 1)] = r;
+    if (!isfinite(r)) *p.status = 5;
+}
+
 // Exact increment F_n(W + dW) - F_n(W) of the Euler flux, written so that no
 // two O(1) quantities are subtracted (every term is an increment times a
 // base quantity); n is pre-scaled by S/2.  b = rho, m_x, m_y, u, v, E+p.
@@ -1008,15 +1021,7 @@ __global__ void __launch_bounds__(512) k_macro_sweep(Launch L)
     T *srec = (T *)smraw;                               // [kStages][ncs][kMRec]
     T *sdw = srec + (size_t)kStages * ncs * kMRec;      // [kStages][ncs][4] own dW* (backward)
     T *ring = sdw + (size_t)kStages * ncs * 4;          // [2][ncs][kMRing]
-    if (tid == 0) {
-        double s = 0.0;
-        int nb = (p.N + 31) / 32;
-        for (int q = 0; q < nb; ++q) s += p.mpart[q];
-        int it = *p.iter;
-        double r = sqrt(s);
-        p.res[it & (kMaxHist - 1)] = r;
-        if (!isfinite(r)) *p.status = 5;
-    }
+    if (tid == 0) record_residual(p);
     const T gm1 = (T)(p.gam - 1.0);
     T *dWg = (T *)p.mdW;
     const T *mrec = (const T *)p.mrec;
@@ -1144,6 +1149,88 @@ __global__ void __launch_bounds__(32) k_macro_post(Launch L)
     cp[15] = p.area[c] / p.dtimp[c] + cq;
     T *ct = (T *)p.cellpT + kCellP * c;
     for (int q = 0; q < kCellP; ++q) ct[q] = (T)cp[q];
+}
+
+// ---------------------------------------------------------------------------
+// explicit DUGKS (Eq. 10, 21): the cell and face kernels of the implicit
+// iteration build the face fluxes with the physical step dt, then
+//   k_explicit_update  per (cell, velocity):
+//                      f~ <- (2tau-dt)/(2tau+dt) f~ + 2dt/(2tau+dt) f^S - dt/Omega sum F
+//   k_cell_moments, k_explicit_w: W = moments of the new f~ (the collision
+//                      conserves them, so f~ and f share them), which the
+//                      next step's cell prep reads, and partial sums of
+//                      ||(W^{n+1} - W^n)/dt||^2
+//   k_explicit_norm    one thread per instance: the step's residual
+//                      ||(W^{n+1} - W^n)/dt||_2 into the residual ring.
+// At the fixed point of the march R_W = -sum Phi does not vanish: it balances
+// the moments of the discrete collision term (the quadrature error of the
+// discrete equilibrium), so the march is measured by its rate of change.
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void __launch_bounds__(32) k_explicit_norm(Launch L)
+{
+    IDG_LOCATE();
+    (void)blk;
+    if (threadIdx.x == 0) {
+        record_residual(p);
+        *p.iter += 1;
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_explicit_update(Launch L)
+{
+    IDG_LOCATE();
+    using T2 = typename V2<T>::t;
+    const int nvb = (p.Nv + 255) / 256;
+    const int c = blk / nvb;
+    const int k = (blk - c * nvb) * blockDim.x + threadIdx.x;
+    if (k >= p.Nv) return;
+    const T *cA = (const T *)p.cellA + kCellP * c;
+    const EqT<T> e = eq_loadT<T>(cA);
+    // k_cell_params stores c2 = 3h/(2tau+dt) = (3/4) 2dt/(2tau+dt) (h = dt/2)
+    const T b = cA[15] * (T)(4.0 / 3.0), a = (T)1 - b;
+    const T dto = (T)(p.dt / p.area[c]);
+    const T ux = vx<T>(p, k), uy = vy<T>(p, k);
+    T dG, dH;
+    dev_equilibrium<T>(e, ux, uy, vgref<T>(p, k), (T)(p.K * p.RT_r), dG, dH);
+    const T2 *F = (const T2 *)p.F;
+    T sg_ = 0, sh_ = 0;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const T2 Fv = F[(size_t)p.cface[4 * c + m] * p.Nv + k];
+        const T sg = (T)p.csign[4 * c + m];
+        sg_ += sg * Fv.x;
+        sh_ += sg * Fv.y;
+    }
+    const size_t ck = (size_t)c * p.Nv + k;
+    T2 v = ((const T2 *)p.f)[ck];
+    v.x = a * v.x + b * dG - dto * sg_;
+    v.y = a * v.y + b * dH - dto * sh_;
+    ((T2 *)p.f)[ck] = v;
+}
+
+// W = (rho, rho U, rho V, rho E) of f~ from its raw moments (Eq. 4), and
+// block partials of ||(W_new - W_old)/dt||^2 (fixed order)
+template <class T>
+__global__ void __launch_bounds__(32) k_explicit_w(Launch L)
+{
+    IDG_LOCATE();
+    __shared__ double sm[32];
+    const int c = blk * blockDim.x + threadIdx.x;
+    double part[1] = {0.0};
+    if (c < p.N) {
+        auto r = [&](int q) { return acc_load<T>(p.cellraw, (size_t)c * kRaw + q) + p.mref_raw[q]; };
+        double *W = p.W + 4 * c;
+        const double Wn[4] = {r(0), r(1), r(2), 0.5 * (r(3) + r(5) + r(8))};
+        for (int q = 0; q < 4; ++q) {
+            const double d = (Wn[q] - W[q]) / p.dt;
+            part[0] += d * d;
+            W[q] = Wn[q];
+        }
+    }
+    block_sum<1>(part, sm);
+    if (threadIdx.x == 0) p.mpart[blk] = part[0];
 }
 
 // ---------------------------------------------------------------------------
@@ -1603,6 +1690,30 @@ static int iteration_t(const Plan &pl, cudaStream_t st, void **events)
     };
     auto L = [&](int kt) { return launch_of<T>(pl, kt); };
     const int *nb = pl.nblocks;
+    if (pl.explicit_dugks) {
+        // W^n and the raw moments of f~^n are left by the previous step (or
+        // by launch_explicit_prologue)
+        mark(0);
+        k_cell_params<T><<<nb[KT_CELL_PAR], 32, 0, st>>>(L(KT_CELL_PAR));
+        k_fbp<T><<<nb[KT_FBP], 256, 0, st>>>(L(KT_FBP));
+        mark(1);
+        if (pl.limiter_any) k_cell_grad<T><<<nb[KT_FBP], 256, 0, st>>>(L(KT_FBP));
+        if (pl.limiter_any) k_face_moments<T, true><<<nb[KT_FACE_MOM], 256, 0, st>>>(L(KT_FACE_MOM));
+        else k_face_moments<T, false><<<nb[KT_FACE_MOM], 256, 0, st>>>(L(KT_FACE_MOM));
+        k_face_params<T><<<nb[KT_FACE_PAR], 32, 0, st>>>(L(KT_FACE_PAR));
+        mark(2);
+        k_face_flux<T><<<nb[KT_FACE_FLUX], 256, 0, st>>>(L(KT_FACE_FLUX));
+        k_face_phi<T><<<nb[KT_FACE_PHI], 64, 0, st>>>(L(KT_FACE_PHI));
+        mark(3);
+        mark(4);
+        k_explicit_update<T><<<nb[KT_MICRO_RES], 256, 0, st>>>(L(KT_MICRO_RES));
+        k_cell_moments<T><<<nb[KT_CELL_MOM], 256, 0, st>>>(L(KT_CELL_MOM));
+        k_explicit_w<T><<<nb[KT_CELL_PAR], 32, 0, st>>>(L(KT_CELL_PAR));
+        k_explicit_norm<T><<<nb[KT_MACRO_SWEEP], 32, 0, st>>>(L(KT_MACRO_SWEEP));
+        mark(5);
+        mark(6);
+        return (int)cudaGetLastError();
+    }
     mark(0);
     k_cell_moments<T><<<nb[KT_CELL_MOM], 256, 0, st>>>(L(KT_CELL_MOM));
     k_cell_params<T><<<nb[KT_CELL_PAR], 32, 0, st>>>(L(KT_CELL_PAR));
@@ -1662,6 +1773,20 @@ int launch_iteration(const Plan &pl, bool fp64, void *stream, void **events)
 {
     cudaStream_t st = (cudaStream_t)stream;
     return fp64 ? iteration_t<double>(pl, st, events) : iteration_t<float>(pl, st, events);
+}
+
+template <class T> static int explicit_prologue_t(const Plan &pl, cudaStream_t st)
+{
+    auto L = [&](int kt) { return launch_of<T>(pl, kt); };
+    k_cell_moments<T><<<pl.nblocks[KT_CELL_MOM], 256, 0, st>>>(L(KT_CELL_MOM));
+    k_explicit_w<T><<<pl.nblocks[KT_CELL_PAR], 32, 0, st>>>(L(KT_CELL_PAR));
+    return (int)cudaGetLastError();
+}
+
+int launch_explicit_prologue(const Plan &pl, bool fp64, void *stream)
+{
+    cudaStream_t st = (cudaStream_t)stream;
+    return fp64 ? explicit_prologue_t<double>(pl, st) : explicit_prologue_t<float>(pl, st);
 }
 
 int launch_cell_moments(const KParams &p, bool fp64, double *out6_dev, void *stream)

@@ -11,8 +11,11 @@ from . import binding as B
 from .inputs import Problem, with_params
 
 
-def configure(ctx, prob: Problem):
-    """Pass a Problem description to a fresh context (setters of include/idugks.h)."""
+def configure(ctx, prob: Problem, explicit: bool = False):
+    """Pass a Problem description to a fresh context (setters of include/idugks.h).
+    explicit: the context advances explicit DUGKS steps (IDG_NUM_EXPLICIT)."""
+    if prob.flags:
+        raise ValueError("Problem.flags selects oracle-only options; the library takes none")
     B.idg_set_mesh_structured(ctx, prob.nodes_x, prob.nodes_y)
     x0, x1, y0, y1 = prob.vrange
     B.idg_set_velocity_grid(ctx, prob.vrule, prob.nvx, prob.nvy, x0, x1, y0, y1)
@@ -21,7 +24,8 @@ def configure(ctx, prob: Problem):
     for side in range(4):
         kind, rho, u, v, T = prob.bc[side]
         B.idg_set_boundary(ctx, side, kind, rho, u, v, T)
-    B.idg_set_numerics(ctx, prob.cfl_imp, prob.cfl_phys, prob.limiter, prob.lusgs_omega, prob.flags)
+    B.idg_set_numerics(ctx, prob.cfl_imp, prob.cfl_phys, prob.limiter, prob.lusgs_omega,
+                       B.IDG_NUM_EXPLICIT if explicit else 0)
 
 
 class Solver:
@@ -29,9 +33,12 @@ class Solver:
 
     precision: "fp64" (f in float64) or "mixed" (f in float32, moments,
     macroscopic predictor and residual in float64).
+    explicit: iterate() advances explicit DUGKS time steps (Eq. 21) instead of
+    IDUGKS iterations.
     """
 
-    def __init__(self, prob: Problem, precision: str = "fp64", device: int = 0, stream=None):
+    def __init__(self, prob: Problem, precision: str = "fp64", device: int = 0, stream=None,
+                 explicit: bool = False):
         import torch
 
         self.prob = prob
@@ -40,7 +47,8 @@ class Solver:
         p = B.IDG_FP64 if precision == "fp64" else B.IDG_MIXED
         self.precision = precision
         self.ctx = B.idg_create(p, device)
-        configure(self.ctx, prob)
+        self.explicit = explicit
+        configure(self.ctx, prob, explicit)
         self.N, self.Nv, self.nf = B.idg_get_sizes(self.ctx)
         nbytes = B.idg_workspace_size(self.ctx)
         self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=f"cuda:{device}")
