@@ -255,8 +255,10 @@ def main():
     ap.add_argument("--no-ttr", action="store_true", help="skip the time-to-residual runs")
     ap.add_argument("--explicit-ttr", action="store_true",
                     help="also time explicit DUGKS (Eq. 21, same precision) to the residual 1e-6 (tens of seconds)")
-    ap.add_argument("--tune", default="auto", choices=["auto", "default"],
-                    help="auto: pick the sweep kind, tiles and prefetch depths with the autotuner before timing")
+    ap.add_argument("--tune", default="auto",
+                    help="auto: pick the sweep tiles and prefetch depths with the autotuner before timing; "
+                         "default: the library's default shape; or an explicit shape such as "
+                         "sweep_tv=4,sweep_vpt=2 (keys of Solver.set_tuning)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.workload == "batch64":
@@ -288,7 +290,9 @@ def main():
 
     s = Solver(prob, args.precision, device=local)
     s.init_uniform()
-    if args.tune == "auto":
+    if args.tune not in ("auto", "default"):
+        s.set_tuning(**{k: int(v) for k, v in (kv.split("=") for kv in args.tune.split(","))})
+    elif args.tune == "auto":
         from paper_1709_01819_gb300.solver import Autotuner
         Autotuner().tune(s)
     tuning = s.tuning()
