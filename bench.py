@@ -47,6 +47,10 @@ def workload(name: str) -> I.Problem:
         return I.cavity_c3()
     if name == "cylinder":
         return I.cylinder_c5()
+    if name == "cylinder61x41":
+        # the cylinder at a quarter of the cells (same velocities, f 158 MB):
+        # the size for full ncu captures of its kernels
+        return I.cylinder(ntheta=61, nr=41, cfl_imp=30.0, name="cylinder_61x41_ma5_kn0.1_v89")
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -195,7 +199,7 @@ def _cpu_worker(name, budget_s, q):
 
 
 def workload_by_name(name):
-    for w in ("cavity64", "couette64", "cavity128", "cylinder"):
+    for w in ("cavity64", "couette64", "cavity128", "cylinder", "cylinder61x41"):
         p = workload(w)
         if p.name == name:
             return p

@@ -199,8 +199,10 @@ idg_status idg_iterate_profiled(idg_ctx *ctx, void *stream, double *kernel_ms);
  * prefetched ahead by the micro / macroscopic sweeps (4 or 8).  Returns
  * IDG_ERR_ARG for a value that is invalid or does not fit in shared memory.
  * IDG_TUNE_SWEEP_VPT: consecutive velocities per thread of the micro sweeps
- * (1, 2 or 4; must divide the number of velocities; all instances of a
- * batch must agree).
+ * (1, 2 or 4; all instances of a batch must agree).  Any velocity count takes
+ * all three: the library stores each cell's velocities rounded up to a
+ * multiple of 4, the extra ones being ghost velocities of zero weight at
+ * xi = 0 that enter no moment and no flux and never reach the caller.
  * IDG_TUNE_GRAPH (1 default, 0 off): idg_iterate replays chunks of 16
  * iterations (and single iterations) as captured CUDA graphs on a
  * library-owned stream that is ordered after, and before, the caller's

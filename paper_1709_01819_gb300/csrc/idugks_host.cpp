@@ -36,7 +36,11 @@ struct idg_ctx {
     int limiter = 0, flags = 0;
     // derived on the host
     bool built = false;
-    int N = 0, Nv = 0, nf = 0;
+    // Nvu: discrete velocities of the caller's grid; Nv: velocities stored per
+    // cell and face, Nvu rounded up to a multiple of 4 with ghost velocities
+    // of zero weight at xi = 0 (they enter no moment and no flux, and let every
+    // row start on a 16-byte boundary for the vectorised sweeps)
+    int N = 0, Nv = 0, Nvu = 0, nf = 0;
     std::vector<double> area, cxc, cyc, hcell, dtimp, cr, clsg, fgeo;
     std::vector<int> cface, cnb, csign, fL, fR, fbc, fside;
     std::vector<double> ux, uy, w;
@@ -222,10 +226,11 @@ idg_status build(idg_ctx *c)
     if (!rule_1d(c->vrule, c->nvx, c->vx0, c->vx1, unit, x1, w1) ||
         !rule_1d(c->vrule, c->nvy, c->vy0, c->vy1, unit, y1, v1))
         return fail(c, IDG_ERR_ARG, "invalid velocity quadrature (rule %d, %d x %d)", c->vrule, c->nvx, c->nvy);
-    c->Nv = c->nvx * c->nvy;
-    c->ux.resize(c->Nv);
-    c->uy.resize(c->Nv);
-    c->w.resize(c->Nv);
+    c->Nvu = c->nvx * c->nvy;
+    c->Nv = (c->Nvu + 3) & ~3;
+    c->ux.assign(c->Nv, 0.0);
+    c->uy.assign(c->Nv, 0.0);
+    c->w.assign(c->Nv, 0.0);
     c->xi_max = 0;
     for (int ky = 0; ky < c->nvy; ++ky)
         for (int kx = 0; kx < c->nvx; ++kx) {
@@ -772,7 +777,7 @@ idg_status idg_get_sizes(const idg_ctx *cc, int *ncell, int *nvel, int *nface)
     idg_status s = build(c);
     if (s) return s;
     if (ncell) *ncell = c->N;
-    if (nvel) *nvel = c->Nv;
+    if (nvel) *nvel = c->Nvu;
     if (nface) *nface = c->nf;
     return IDG_OK;
 }
@@ -793,9 +798,9 @@ idg_status idg_velocity_grid(const idg_ctx *cc, double *ux, double *uy, double *
     if (!c) return IDG_ERR_ARG;
     idg_status s = build(c);
     if (s) return s;
-    if (ux) std::memcpy(ux, c->ux.data(), c->Nv * sizeof(double));
-    if (uy) std::memcpy(uy, c->uy.data(), c->Nv * sizeof(double));
-    if (w) std::memcpy(w, c->w.data(), c->Nv * sizeof(double));
+    if (ux) std::memcpy(ux, c->ux.data(), c->Nvu * sizeof(double));
+    if (uy) std::memcpy(uy, c->uy.data(), c->Nvu * sizeof(double));
+    if (w) std::memcpy(w, c->w.data(), c->Nvu * sizeof(double));
     return IDG_OK;
 }
 
@@ -932,7 +937,7 @@ idg_status idg_set_state(idg_ctx *c, const double *G, const double *H, const dou
     if (s) return s;
     if (!G || !H || !W) return fail(c, IDG_ERR_ARG, "null state array");
     cudaStream_t st = (cudaStream_t)stream;
-    size_t n = (size_t)c->N * c->Nv;
+    size_t n = (size_t)c->N * c->Nvu;
     cudaError_t e;
     // stage G and H as float64 in the face-flux buffer (large enough: nf >= 2N)
     double *dG = c->stage, *dH = c->stage + n;
@@ -941,7 +946,7 @@ idg_status idg_set_state(idg_ctx *c, const double *G, const double *H, const dou
     if ((e = cudaMemcpyAsync(dH, H, n * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess) return cuda_fail(c, e, "H2D H");
     if ((e = cudaMemcpyAsync(c->kp.W, W, (size_t)c->N * 32, cudaMemcpyHostToDevice, st)) != cudaSuccess)
         return cuda_fail(c, e, "H2D W");
-    int rc = idg::launch_to_dev(c->kp, c->precision == IDG_FP64, dG, dH, st);
+    int rc = idg::launch_to_dev(c->kp, c->precision == IDG_FP64, dG, dH, c->Nvu, st);
     if (rc) return cuda_fail(c, (cudaError_t)rc, "to_dev");
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(c, e, "sync");
     restart(c);
@@ -953,11 +958,11 @@ idg_status idg_get_state(idg_ctx *c, double *G, double *H, double *W, void *stre
     idg_status s = check_ready(c);
     if (s) return s;
     cudaStream_t st = (cudaStream_t)stream;
-    size_t n = (size_t)c->N * c->Nv;
+    size_t n = (size_t)c->N * c->Nvu;
     cudaError_t e;
     double *dG = c->stage, *dH = c->stage + n;
     if (G || H) {
-        int rc = idg::launch_from_dev(c->kp, c->precision == IDG_FP64, dG, dH, st);
+        int rc = idg::launch_from_dev(c->kp, c->precision == IDG_FP64, dG, dH, c->Nvu, st);
         if (rc) return cuda_fail(c, (cudaError_t)rc, "from_dev");
         if (G && (e = cudaMemcpyAsync(G, dG, n * 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return cuda_fail(c, e, "D2H G");
         if (H && (e = cudaMemcpyAsync(H, dH, n * 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return cuda_fail(c, e, "D2H H");
@@ -1578,7 +1583,7 @@ idg_status idg_adjoint(idg_ctx *c, int objective, int side_mask, const int *para
     if ((e = cudaMemcpyAsync(A[0].lsw, c->clsg.data(), c->clsg.size() * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
         (e = cudaMemcpyAsync(A[0].crv, c->cr.data(), c->cr.size() * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess)
         return cuda_fail(c, e, "adjoint geometry upload");
-    int rc = idg::launch_from_dev(c->kp, c->precision == IDG_FP64, A[0].G, A[0].H, st);
+    int rc = idg::launch_from_dev(c->kp, c->precision == IDG_FP64, A[0].G, A[0].H, c->Nv, st);
     if (!rc) rc = idg::launch_adjoint_setup(A[0], st);
     for (int r = 0; r < nrhs && !rc; ++r) rc = idg::launch_adjoint_zero(A[r], st);
     if (rc) return cuda_fail(c, (cudaError_t)rc, "adjoint setup");
@@ -1698,6 +1703,13 @@ idg_status idg_adjoint_state(idg_ctx *c, const void *workspace, int which, doubl
     const size_t n = (size_t)c->N * c->Nv, n4 = (size_t)4 * c->N;
     double *out[3] = {lamG, lamH, lamW};
     const size_t cnt[3] = {n, n, n4};
+    // per-velocity multipliers are stored with the ghost velocities; the
+    // caller's arrays have Nvu entries per cell
+    auto dst = [&](int q, size_t i) -> double * {
+        if (q == 2) return out[q] + i;
+        const size_t cc = i / c->Nv, k = i % c->Nv;
+        return k < (size_t)c->Nvu ? out[q] + cc * c->Nvu + k : nullptr;
+    };
     for (int q = 0; q < 3; ++q) {
         if (!out[q]) continue;
         std::vector<double> v[2];
@@ -1708,7 +1720,8 @@ idg_status idg_adjoint_state(idg_ctx *c, const void *workspace, int which, doubl
             if (e == cudaSuccess) e = cudaStreamSynchronize(st);
             if (e != cudaSuccess) return cuda_fail(c, e, "adjoint state");
         }
-        for (size_t i = 0; i < cnt[q]; ++i) out[q][i] = wJ * v[0][i] + (c->adj_nrhs == 2 ? wm * v[1][i] : 0.0);
+        for (size_t i = 0; i < cnt[q]; ++i)
+            if (double *o = dst(q, i)) *o = wJ * v[0][i] + (c->adj_nrhs == 2 ? wm * v[1][i] : 0.0);
     }
     return IDG_OK;
 }

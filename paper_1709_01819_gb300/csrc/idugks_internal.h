@@ -115,7 +115,9 @@ int launch_cell_moments(const KParams &p, bool fp64, double *out6_dev, void *str
 int launch_explicit_prologue(const Plan &plan, bool fp64, void *stream);
 // idg_get_moments_noalloc: raw moments in a static device array (no workspace)
 int launch_cell_moments_noalloc(const KParams &p, bool fp64, int device, double *out6_dev, void *stream);
-int launch_to_dev(const KParams &p, bool fp64, const double *G, const double *H, void *stream);
-int launch_from_dev(const KParams &p, bool fp64, double *G, double *H, void *stream);
+// absolute float64 G, H of [N][nvu] (the first nvu stored velocities of each
+// cell) to / from the storage; to_dev sets the ghost velocities beyond nvu to M_ref
+int launch_to_dev(const KParams &p, bool fp64, const double *G, const double *H, int nvu, void *stream);
+int launch_from_dev(const KParams &p, bool fp64, double *G, double *H, int nvu, void *stream);
 
 }  // namespace idg

@@ -376,6 +376,41 @@ __device__ __forceinline__ void vel_loop(int Nv, int lane, Acc<T> (&acc)[NA], Bo
     }
 }
 
+// The same loop with each thread's float-float accumulators held in shared
+// memory (sacc[q * blockDim.x + threadIdx.x]) between chunks: the arithmetic is
+// that of vel_loop, while the registers of a 64-register thread stay free for
+// the loads in flight.  Float storage only; the float64 path keeps vel_loop.
+template <int NA, class Body>
+__device__ __forceinline__ void vel_loop_sm(int Nv, int lane, FF *sacc, Body body)
+{
+    const int t = threadIdx.x, nt = blockDim.x;
+#pragma unroll
+    for (int q = 0; q < NA; ++q) sacc[q * nt + t] = FF{0.f, 0.f};
+    auto fold = [&](const float(&a)[NA]) {
+#pragma unroll
+        for (int q = 0; q < NA; ++q) sacc[q * nt + t] = ff_add(sacc[q * nt + t], FF{a[q], 0.f});
+    };
+    int k0 = 0;
+    for (; k0 + 256 <= Nv; k0 += 256) {
+        float a[NA];
+#pragma unroll
+        for (int q = 0; q < NA; ++q) a[q] = 0.f;
+#pragma unroll 4
+        for (int u = 0; u < 8; ++u) body(k0 + 32 * u + lane, a);
+        fold(a);
+    }
+    if (k0 < Nv) {
+        float a[NA];
+#pragma unroll
+        for (int q = 0; q < NA; ++q) a[q] = 0.f;
+        for (int u = 0; u < 8; ++u) {
+            int k = k0 + 32 * u + lane;
+            if (k < Nv) body(k, a);
+        }
+        fold(a);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // cell moments and cell prep (Eq. 10, 12)                                [a1]
 // ---------------------------------------------------------------------------
@@ -502,59 +537,112 @@ __device__ __forceinline__ double lim_div(double a, double b) { return a / b; }
 
 template <class T> __device__ __forceinline__ T venkat(T x) { return lim_div(x * x + (T)2 * x, x * x + x + (T)2); }
 
+// G and H of two consecutive velocities k, k + 1 (k even: 16-byte aligned
+// because the stored velocity count is a multiple of 4)
+template <class T> __device__ __forceinline__ void load_pair(const void *base, size_t i, T (&g)[2], T (&h)[2]);
+template <> __device__ __forceinline__ void load_pair<float>(const void *base, size_t i, float (&g)[2], float (&h)[2])
+{
+    const float4 a = ((const float4 *)base)[i >> 1];
+    g[0] = a.x; h[0] = a.y; g[1] = a.z; h[1] = a.w;
+}
+template <> __device__ __forceinline__ void load_pair<double>(const void *base, size_t i, double (&g)[2], double (&h)[2])
+{
+    const double2 a = ((const double2 *)base)[i], b = ((const double2 *)base)[i + 1];
+    g[0] = a.x; h[0] = a.y; g[1] = b.x; h[1] = b.y;
+}
+
+// four storage scalars (one velocity's limited gradients), 16- or 32-byte aligned
+template <class T> __device__ __forceinline__ void store4(T *d, T a, T b, T c, T e);
+template <> __device__ __forceinline__ void store4<float>(float *d, float a, float b, float c, float e)
+{
+    *(float4 *)d = make_float4(a, b, c, e);
+}
+template <> __device__ __forceinline__ void store4<double>(double *d, double a, double b, double c, double e)
+{
+    ((double2 *)d)[0] = make_double2(a, b);
+    ((double2 *)d)[1] = make_double2(c, e);
+}
+template <class T> __device__ __forceinline__ void load4(const T *s, T &a, T &b, T &c, T &e);
+template <> __device__ __forceinline__ void load4<float>(const float *s, float &a, float &b, float &c, float &e)
+{
+    const float4 v = *(const float4 *)s;
+    a = v.x; b = v.y; c = v.z; e = v.w;
+}
+template <> __device__ __forceinline__ void load4<double>(const double *s, double &a, double &b, double &c, double &e)
+{
+    const double2 v = ((const double2 *)s)[0], w = ((const double2 *)s)[1];
+    a = v.x; b = v.y; c = w.x; e = w.y;
+}
+
+// limiter of one scalar (Eq. 16-17): phi = min over the faces of
+// theta((v_max - v0)/d) where the extrapolated increment d to the face is
+// positive, theta((v_min - v0)/d) where it is negative; a face with d = 0
+// leaves phi unchanged.  Selects instead of branches: the sign of d differs
+// between neighbouring velocities.
 template <class T>
-__device__ __forceinline__ T limit_scalar(const SideRec<T> &r, T v0, T vmax, T vmin, T sx, T sy)
+__device__ __forceinline__ T limit_scalar_sel(const T (&frx)[4], const T (&fry)[4], T v0, T vmax, T vmin, T sx, T sy)
 {
     T phi = (T)1;
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
-        T d = sx * r.frx[m] + sy * r.fry[m];
-        T t = (T)1;
-        if (d > (T)0) t = venkat<T>(lim_div(vmax - v0, d));
-        else if (d < (T)0) t = venkat<T>(lim_div(vmin - v0, d));
-        phi = t < phi ? t : phi;
+        const T d = sx * frx[m] + sy * fry[m];
+        const T t = venkat<T>(lim_div((d > (T)0 ? vmax : vmin) - v0, d));
+        phi = (d != (T)0 && t < phi) ? t : phi;
     }
     return phi;
 }
 
-// per (cell, velocity), limiter on: least-squares gradients of fb+ (Eq.
-// 14-15) and the Venkatakrishnan limiter (Eq. 16-17) of G and H, stored as
-// the limited gradients phi sigma for the reconstructions at the cell's faces
+// per (cell, pair of velocities), limiter on: least-squares gradients of fb+
+// (Eq. 14-15) and the Venkatakrishnan limiter (Eq. 16-17) of G and H, stored
+// as the limited gradients phi sigma for the reconstructions at the cell's
+// faces.  128-thread blocks, each over 256 velocities of one cell; the cell's
+// stencil record is read by every thread (one broadcast per load).
 template <class T>
-__global__ void __launch_bounds__(256) k_cell_grad(Launch L)
+__global__ void __launch_bounds__(128) k_cell_grad(Launch L)
 {
     IDG_LOCATE();
     if (!p.limiter) return;
-    using T2 = typename V2<T>::t;
-    __shared__ SideRec<T> srec;
     const int nvb = (p.Nv + 255) / 256;
     const int c = blk / nvb;
-    const int k = (blk - c * nvb) * blockDim.x + threadIdx.x;
-    if (threadIdx.x == 0) load_side<T>(p, c, (T)0, (T)0, srec);
-    __syncthreads();
+    const int k = 2 * ((blk - c * nvb) * 128 + threadIdx.x);
     if (k >= p.Nv) return;
-    const SideRec<T> &r = srec;
-    const T2 *fb = (const T2 *)p.fbp;
-    const T2 f0 = fb[(size_t)c * p.Nv + k];
-    T sgx = 0, sgy = 0, shx = 0, shy = 0;
-    T gmax = f0.x, gmin = f0.x, hmax = f0.y, hmin = f0.y;
+    int nb[4];
+    T gx[4], gy[4], frx[4], fry[4];
+    {
+        const int4 n4 = *(const int4 *)(p.cnb + 4 * c);
+        nb[0] = n4.x; nb[1] = n4.y; nb[2] = n4.z; nb[3] = n4.w;
+        const T *g = (const T *)p.clsgT + 8 * c;
+        const T *o = (const T *)p.crT + 8 * c;
+        load4<T>(g, gx[0], gy[0], gx[1], gy[1]);
+        load4<T>(g + 4, gx[2], gy[2], gx[3], gy[3]);
+        load4<T>(o, frx[0], fry[0], frx[1], fry[1]);
+        load4<T>(o + 4, frx[2], fry[2], frx[3], fry[3]);
+    }
+    T g0[2], h0[2];
+    load_pair<T>(p.fbp, (size_t)c * p.Nv + k, g0, h0);
+    T sgx[2] = {0, 0}, sgy[2] = {0, 0}, shx[2] = {0, 0}, shy[2] = {0, 0};
+    T gmax[2] = {g0[0], g0[1]}, gmin[2] = {g0[0], g0[1]}, hmax[2] = {h0[0], h0[1]}, hmin[2] = {h0[0], h0[1]};
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
-        if (r.nb[m] < 0) continue;
-        const T2 fn = fb[(size_t)r.nb[m] * p.Nv + k];
-        const T dg = fn.x - f0.x, dh = fn.y - f0.y;
-        sgx += r.gx[m] * dg; sgy += r.gy[m] * dg;
-        shx += r.gx[m] * dh; shy += r.gy[m] * dh;
-        gmax = fn.x > gmax ? fn.x : gmax; gmin = fn.x < gmin ? fn.x : gmin;
-        hmax = fn.y > hmax ? fn.y : hmax; hmin = fn.y < hmin ? fn.y : hmin;
+        if (nb[m] < 0) continue;
+        T gn[2], hn[2];
+        load_pair<T>(p.fbp, (size_t)nb[m] * p.Nv + k, gn, hn);
+#pragma unroll
+        for (int v = 0; v < 2; ++v) {
+            const T dg = gn[v] - g0[v], dh = hn[v] - h0[v];
+            sgx[v] += gx[m] * dg; sgy[v] += gy[m] * dg;
+            shx[v] += gx[m] * dh; shy[v] += gy[m] * dh;
+            gmax[v] = gn[v] > gmax[v] ? gn[v] : gmax[v]; gmin[v] = gn[v] < gmin[v] ? gn[v] : gmin[v];
+            hmax[v] = hn[v] > hmax[v] ? hn[v] : hmax[v]; hmin[v] = hn[v] < hmin[v] ? hn[v] : hmin[v];
+        }
     }
-    const T pg = limit_scalar<T>(r, f0.x, gmax, gmin, sgx, sgy);
-    const T ph = limit_scalar<T>(r, f0.y, hmax, hmin, shx, shy);
-    T *g = (T *)p.grad + 4 * ((size_t)c * p.Nv + k);
-    g[0] = pg * sgx;
-    g[1] = pg * sgy;
-    g[2] = ph * shx;
-    g[3] = ph * shy;
+    T *gout = (T *)p.grad + 4 * ((size_t)c * p.Nv + k);
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+        const T pg = limit_scalar_sel<T>(frx, fry, g0[v], gmax[v], gmin[v], sgx[v], sgy[v]);
+        const T ph = limit_scalar_sel<T>(frx, fry, h0[v], hmax[v], hmin[v], shx[v], shy[v]);
+        store4<T>(gout + 4 * v, pg * sgx[v], pg * sgy[v], ph * shx[v], ph * shy[v]);
+    }
 }
 
 // fb at the face from side r: fb+_c + phi sigma_c . (x_f - xi h - x_c).  The
@@ -570,11 +658,12 @@ __device__ __forceinline__ typename V2<T>::t reconstruct(const KParams &p, const
     if (LIM && p.limiter) {
         // limited gradients phi sigma of G and H, stored once per (cell,
         // velocity) by k_cell_grad
-        const T *g = (const T *)p.grad + 4 * ((size_t)r.c * p.Nv + k);
+        T g0, g1, g2, g3;
+        load4<T>((const T *)p.grad + 4 * ((size_t)r.c * p.Nv + k), g0, g1, g2, g3);
         const T ax = r.rx - ux * h, ay = r.ry - uy * h;
         T2 o;
-        o.x = f0.x + (g[0] * ax + g[1] * ay);
-        o.y = f0.y + (g[2] * ax + g[3] * ay);
+        o.x = f0.x + (g0 * ax + g1 * ay);
+        o.y = f0.y + (g2 * ax + g3 * ay);
         return o;
     }
     // limiter off: the unlimited least-squares gradient in place
@@ -662,11 +751,13 @@ __device__ __forceinline__ typename V2<T>::t face_fbar(const KParams &p, const F
 }
 
 // raw moments of fb - M_ref at every face (plus the wall density, Eq. 35).
-// float32: four 256-thread blocks per SM (64 registers) hide the latency of
-// the stencil loads better than two blocks without spills (measured: -11% on
-// a 64^2 cavity, -20% on 128^2 with 28^2 velocities)
+// float32: the kernel is bound by the latency of its stencil loads, so
+// occupancy decides: four 256-thread blocks per SM (64 registers, the lanes'
+// float-float accumulators in shared memory) with the in-place gradient, five
+// (48 registers) when it reads the stored limited gradients; three or two
+// blocks without spills, or six and eight with more, were slower
 template <class T, bool LIM>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 1) k_face_moments(Launch L)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? (LIM ? 5 : 4) : 1) k_face_moments(Launch L)
 {
     IDG_LOCATE();
     using T2 = typename V2<T>::t;
@@ -701,15 +792,23 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 1) k_face_moments(La
     // fb - M_ref is kept in the face-flux buffer for k_face_flux
     T2 *Fo = (T2 *)p.F + (size_t)f * p.Nv;
     Acc<T> acc[kRaw];
-#pragma unroll
-    for (int q = 0; q < kRaw; ++q) acc[q].zero();
-    vel_loop<kRaw, T>(p.Nv, lane, acc, [&](int k, T(&a)[kRaw]) {
+    auto body = [&](int k, T(&a)[kRaw]) {
         T ux = vx<T>(p, k), uy = vy<T>(p, k);
         T s = xi_dot_n<T>(ux, uy, fc.nx, fc.ny);
         T2 fb = face_fbar<T, LIM>(p, fc, k, ux, uy, s, rhow, rwm1);
         Fo[k] = fb;
         raw_terms<T>(a, vw<T>(p, k), ux, uy, fb.x, fb.y);
-    });
+    };
+    if constexpr (sizeof(T) == 4) {
+        __shared__ FF sacc[kRaw * 256];
+        vel_loop_sm<kRaw>(p.Nv, lane, sacc, body);
+#pragma unroll
+        for (int q = 0; q < kRaw; ++q) acc[q].v = sacc[q * blockDim.x + threadIdx.x];
+    } else {
+#pragma unroll
+        for (int q = 0; q < kRaw; ++q) acc[q].zero();
+        vel_loop<kRaw, T>(p.Nv, lane, acc, body);
+    }
 #pragma unroll
     for (int q = 0; q < kRaw; ++q) acc[q].warp_sum();
     if (lane == 0) {
@@ -1518,33 +1617,42 @@ __global__ void __launch_bounds__(512) k_sweep(Launch L)
 // state conversion and diagnostics
 // ---------------------------------------------------------------------------
 template <class T>
-__global__ void k_to_dev(KParams p, const double *G, const double *H)
+__global__ void k_to_dev(KParams p, const double *G, const double *H, int nvu)
 {
     using T2 = typename V2<T>::t;
     size_t n = (size_t)p.N * p.Nv;
     double kRTr = p.K * p.RT_r;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
          i += (size_t)gridDim.x * blockDim.x) {
-        int k = (int)(i % p.Nv);
+        const size_t c = i / p.Nv;
+        const int k = (int)(i - c * p.Nv);
         T2 o;
-        o.x = (T)(G[i] - p.gref[k]);
-        o.y = (T)(H[i] - kRTr * p.gref[k]);
+        o.x = (T)0;
+        o.y = (T)0;
+        if (k < nvu) {
+            const size_t j = c * nvu + k;
+            o.x = (T)(G[j] - p.gref[k]);
+            o.y = (T)(H[j] - kRTr * p.gref[k]);
+        }
         ((T2 *)p.f)[i] = o;
     }
 }
 
 template <class T>
-__global__ void k_from_dev(KParams p, double *G, double *H)
+__global__ void k_from_dev(KParams p, double *G, double *H, int nvu)
 {
     using T2 = typename V2<T>::t;
     size_t n = (size_t)p.N * p.Nv;
     double kRTr = p.K * p.RT_r;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
          i += (size_t)gridDim.x * blockDim.x) {
-        int k = (int)(i % p.Nv);
+        const size_t c = i / p.Nv;
+        const int k = (int)(i - c * p.Nv);
+        if (k >= nvu) continue;
+        const size_t j = c * nvu + k;
         T2 v = ((const T2 *)p.f)[i];
-        G[i] = p.gref[k] + (double)v.x;
-        H[i] = kRTr * p.gref[k] + (double)v.y;
+        G[j] = p.gref[k] + (double)v.x;
+        H[j] = kRTr * p.gref[k] + (double)v.y;
     }
 }
 
@@ -1697,7 +1805,7 @@ static int iteration_t(const Plan &pl, cudaStream_t st, void **events)
         k_cell_params<T><<<nb[KT_CELL_PAR], 32, 0, st>>>(L(KT_CELL_PAR));
         k_fbp<T><<<nb[KT_FBP], 256, 0, st>>>(L(KT_FBP));
         mark(1);
-        if (pl.limiter_any) k_cell_grad<T><<<nb[KT_FBP], 256, 0, st>>>(L(KT_FBP));
+        if (pl.limiter_any) k_cell_grad<T><<<nb[KT_FBP], 128, 0, st>>>(L(KT_FBP));
         if (pl.limiter_any) k_face_moments<T, true><<<nb[KT_FACE_MOM], 256, 0, st>>>(L(KT_FACE_MOM));
         else k_face_moments<T, false><<<nb[KT_FACE_MOM], 256, 0, st>>>(L(KT_FACE_MOM));
         k_face_params<T><<<nb[KT_FACE_PAR], 32, 0, st>>>(L(KT_FACE_PAR));
@@ -1719,7 +1827,7 @@ static int iteration_t(const Plan &pl, cudaStream_t st, void **events)
     k_cell_params<T><<<nb[KT_CELL_PAR], 32, 0, st>>>(L(KT_CELL_PAR));
     k_fbp<T><<<nb[KT_FBP], 256, 0, st>>>(L(KT_FBP));
     mark(1);
-    if (pl.limiter_any) k_cell_grad<T><<<nb[KT_FBP], 256, 0, st>>>(L(KT_FBP));
+    if (pl.limiter_any) k_cell_grad<T><<<nb[KT_FBP], 128, 0, st>>>(L(KT_FBP));
     if (pl.limiter_any) k_face_moments<T, true><<<nb[KT_FACE_MOM], 256, 0, st>>>(L(KT_FACE_MOM));
     else k_face_moments<T, false><<<nb[KT_FACE_MOM], 256, 0, st>>>(L(KT_FACE_MOM));
     k_face_params<T><<<nb[KT_FACE_PAR], 32, 0, st>>>(L(KT_FACE_PAR));
@@ -1871,19 +1979,19 @@ int launch_batch_gather(const KParams *dparams, int n, int last, double *dres, i
     return (int)cudaGetLastError();
 }
 
-int launch_to_dev(const KParams &p, bool fp64, const double *G, const double *H, void *stream)
+int launch_to_dev(const KParams &p, bool fp64, const double *G, const double *H, int nvu, void *stream)
 {
     cudaStream_t st = (cudaStream_t)stream;
-    if (fp64) k_to_dev<double><<<1024, 256, 0, st>>>(p, G, H);
-    else k_to_dev<float><<<1024, 256, 0, st>>>(p, G, H);
+    if (fp64) k_to_dev<double><<<1024, 256, 0, st>>>(p, G, H, nvu);
+    else k_to_dev<float><<<1024, 256, 0, st>>>(p, G, H, nvu);
     return (int)cudaGetLastError();
 }
 
-int launch_from_dev(const KParams &p, bool fp64, double *G, double *H, void *stream)
+int launch_from_dev(const KParams &p, bool fp64, double *G, double *H, int nvu, void *stream)
 {
     cudaStream_t st = (cudaStream_t)stream;
-    if (fp64) k_from_dev<double><<<1024, 256, 0, st>>>(p, G, H);
-    else k_from_dev<float><<<1024, 256, 0, st>>>(p, G, H);
+    if (fp64) k_from_dev<double><<<1024, 256, 0, st>>>(p, G, H, nvu);
+    else k_from_dev<float><<<1024, 256, 0, st>>>(p, G, H, nvu);
     return (int)cudaGetLastError();
 }
 

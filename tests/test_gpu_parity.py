@@ -167,6 +167,32 @@ def test_graph_replay_and_tuning_do_not_change_results():
             assert np.array_equal(o[3], ref[0][3])
 
 
+def test_odd_velocity_count_takes_every_sweep_shape():
+    """15 x 15 = 225 velocities are stored as 228 (three ghost velocities of
+    zero weight at xi = 0): every velocities-per-thread shape is accepted, gives
+    the same bits, matches the oracle, and the state round-trips exactly."""
+    prob = I.cavity(10, Kn=0.075, U=0.15, nv=15, vmax=4.0)
+    o = O.Oracle(prob)
+    o.init_uniform()
+    o.iterate(6)
+    Go, Ho, Wo = o.get_state()
+    out = []
+    for vpt in (1, 2, 4):
+        s = _solver(prob, "fp64")
+        assert s.Nv == 225
+        s.set_tuning(sweep_vpt=vpt)
+        s.init_uniform()
+        s.iterate(6)
+        G, H, W = s.get_state()
+        assert _rel(G, Go) < 1e-12 and _rel(H, Ho) < 1e-12 and _rel(W, Wo) < 1e-12
+        out.append((G, H, W))
+        s.set_state(G, H, W)
+        G2, H2, W2 = s.get_state()
+        assert np.array_equal(G2, G) and np.array_equal(H2, H) and np.array_equal(W2, W)
+    for G, H, W in out[1:]:
+        assert np.array_equal(G, out[0][0]) and np.array_equal(H, out[0][1]) and np.array_equal(W, out[0][2])
+
+
 def test_batched_instances_match_individual_runs_bitwise():
     """One launch per kernel over uneven instances gives each instance exactly
     the result of running it alone; converged instances stop."""
