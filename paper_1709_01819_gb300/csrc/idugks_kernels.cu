@@ -376,6 +376,64 @@ __device__ __forceinline__ void vel_loop(int Nv, int lane, Acc<T> (&acc)[NA], Bo
     }
 }
 
+template <class T> __device__ __forceinline__ void load_pair(const void *base, size_t i, T (&g)[2], T (&h)[2]);
+
+// Pair loop over the discrete velocities: lane l takes the two velocities
+// k, k + 1 with k = k0 + 64u + 2l, u < 4, for chunks of 256 velocities (the
+// stored velocity count is a multiple of 4, so pairs are whole and start on
+// 16-byte boundaries); each chunk's per-lane partial sums (at most 8 terms)
+// are folded into the accumulators as in vel_loop.
+template <int NA, class T, class Body>
+__device__ __forceinline__ void vel_loop2(int Nv, int lane, Acc<T> (&acc)[NA], Body body)
+{
+    int k0 = 0;
+    for (; k0 + 256 <= Nv; k0 += 256) {
+        T a[NA];
+#pragma unroll
+        for (int q = 0; q < NA; ++q) a[q] = (T)0;
+#pragma unroll 2
+        for (int u = 0; u < 4; ++u) body(k0 + 64 * u + 2 * lane, a);
+#pragma unroll
+        for (int q = 0; q < NA; ++q) acc[q].add(a[q]);
+    }
+    if (k0 < Nv) {
+        T a[NA];
+#pragma unroll
+        for (int q = 0; q < NA; ++q) a[q] = (T)0;
+        for (int u = 0; u < 4; ++u) {
+            int k = k0 + 64 * u + 2 * lane;
+            if (k < Nv) body(k, a);
+        }
+#pragma unroll
+        for (int q = 0; q < NA; ++q) acc[q].add(a[q]);
+    }
+}
+
+// store of two consecutive velocities' {G, H} (see load_pair)
+template <class T> __device__ __forceinline__ void store_pair(void *base, size_t i, const T (&g)[2], const T (&h)[2]);
+template <> __device__ __forceinline__ void store_pair<float>(void *base, size_t i, const float (&g)[2], const float (&h)[2])
+{
+    ((float4 *)base)[i >> 1] = make_float4(g[0], h[0], g[1], h[1]);
+}
+template <> __device__ __forceinline__ void store_pair<double>(void *base, size_t i, const double (&g)[2], const double (&h)[2])
+{
+    ((double2 *)base)[i] = make_double2(g[0], h[0]);
+    ((double2 *)base)[i + 1] = make_double2(g[1], h[1]);
+}
+
+// velocity table entries k, k + 1 (k even)
+template <class T> __device__ __forceinline__ void vtab2(const float *tf, const double *td, int k, T (&o)[2]);
+template <> __device__ __forceinline__ void vtab2<float>(const float *tf, const double *, int k, float (&o)[2])
+{
+    const float2 v = ((const float2 *)tf)[k >> 1];
+    o[0] = v.x; o[1] = v.y;
+}
+template <> __device__ __forceinline__ void vtab2<double>(const float *, const double *td, int k, double (&o)[2])
+{
+    const double2 v = ((const double2 *)td)[k >> 1];
+    o[0] = v.x; o[1] = v.y;
+}
+
 // The same loop with each thread's float-float accumulators held in shared
 // memory (sacc[q * blockDim.x + threadIdx.x]) between chunks: the arithmetic is
 // that of vel_loop, while the registers of a 64-register thread stay free for
@@ -411,6 +469,38 @@ __device__ __forceinline__ void vel_loop_sm(int Nv, int lane, FF *sacc, Body bod
     }
 }
 
+// vel_loop2 with the accumulators of vel_loop_sm
+template <int NA, class Body>
+__device__ __forceinline__ void vel_loop2_sm(int Nv, int lane, FF *sacc, Body body)
+{
+    const int t = threadIdx.x, nt = blockDim.x;
+#pragma unroll
+    for (int q = 0; q < NA; ++q) sacc[q * nt + t] = FF{0.f, 0.f};
+    auto fold = [&](const float(&a)[NA]) {
+#pragma unroll
+        for (int q = 0; q < NA; ++q) sacc[q * nt + t] = ff_add(sacc[q * nt + t], FF{a[q], 0.f});
+    };
+    int k0 = 0;
+    for (; k0 + 256 <= Nv; k0 += 256) {
+        float a[NA];
+#pragma unroll
+        for (int q = 0; q < NA; ++q) a[q] = 0.f;
+#pragma unroll 2
+        for (int u = 0; u < 4; ++u) body(k0 + 64 * u + 2 * lane, a);
+        fold(a);
+    }
+    if (k0 < Nv) {
+        float a[NA];
+#pragma unroll
+        for (int q = 0; q < NA; ++q) a[q] = 0.f;
+        for (int u = 0; u < 4; ++u) {
+            int k = k0 + 64 * u + 2 * lane;
+            if (k < Nv) body(k, a);
+        }
+        fold(a);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // cell moments and cell prep (Eq. 10, 12)                                [a1]
 // ---------------------------------------------------------------------------
@@ -425,9 +515,14 @@ __device__ __forceinline__ void cell_moments_body(const KParams &__restrict__ p,
     Acc<T> acc[kRaw];
 #pragma unroll
     for (int q = 0; q < kRaw; ++q) acc[q].zero();
-    vel_loop<kRaw, T>(p.Nv, lane, acc, [&](int k, T(&a)[kRaw]) {
-        T2 v = f[k];
-        raw_terms<T>(a, vw<T>(p, k), vx<T>(p, k), vy<T>(p, k), v.x, v.y);
+    vel_loop2<kRaw, T>(p.Nv, lane, acc, [&](int k, T(&a)[kRaw]) {
+        T ux[2], uy[2], w[2], g[2], h[2];
+        vtab2<T>(p.uxf, p.ux, k, ux);
+        vtab2<T>(p.uyf, p.uy, k, uy);
+        vtab2<T>(p.wf, p.w, k, w);
+        load_pair<T>(f, k, g, h);
+        raw_terms<T>(a, w[0], ux[0], uy[0], g[0], h[0]);
+        raw_terms<T>(a, w[1], ux[1], uy[1], g[1], h[1]);
     });
 #pragma unroll
     for (int q = 0; q < kRaw; ++q) acc[q].warp_sum();
@@ -477,26 +572,33 @@ __global__ void __launch_bounds__(32) k_cell_params(Launch L)
     cA[15] = (T)(3.0 * p.h / (2.0 * tau + p.dt));
 }
 
+// per (cell, pair of velocities): fb+ = c1 f~ + c2 f^S; 128-thread blocks,
+// each over 256 velocities of one cell
 template <class T>
-__global__ void __launch_bounds__(256) k_fbp(Launch L)
+__global__ void __launch_bounds__(128) k_fbp(Launch L)
 {
     IDG_LOCATE();
-    using T2 = typename V2<T>::t;
     const int nvb = (p.Nv + 255) / 256;
     const int c = blk / nvb;
-    const int k = (blk - c * nvb) * blockDim.x + threadIdx.x;
+    const int k = 2 * ((blk - c * nvb) * 128 + threadIdx.x);
     if (k >= p.Nv) return;
     const T *cA = (const T *)p.cellA + kCellP * c;
-    EqT<T> e = eq_loadT<T>(cA);
-    T c1 = cA[14], c2 = cA[15];
-    size_t ck = (size_t)c * p.Nv + k;
-    T2 v = ((const T2 *)p.f)[ck];
-    T dG, dH;
-    dev_equilibrium<T>(e, vx<T>(p, k), vy<T>(p, k), vgref<T>(p, k), (T)(p.K * p.RT_r), dG, dH);
-    T2 o;
-    o.x = c1 * v.x + c2 * dG;
-    o.y = c1 * v.y + c2 * dH;
-    ((T2 *)p.fbp)[ck] = o;
+    const EqT<T> e = eq_loadT<T>(cA);
+    const T c1 = cA[14], c2 = cA[15], kRTr = (T)(p.K * p.RT_r);
+    const size_t ck = (size_t)c * p.Nv + k;
+    T ux[2], uy[2], gr[2], g[2], h[2];
+    vtab2<T>(p.uxf, p.ux, k, ux);
+    vtab2<T>(p.uyf, p.uy, k, uy);
+    vtab2<T>(p.greff, p.gref, k, gr);
+    load_pair<T>(p.f, ck, g, h);
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+        T dG, dH;
+        dev_equilibrium<T>(e, ux[v], uy[v], gr[v], kRTr, dG, dH);
+        g[v] = c1 * g[v] + c2 * dG;
+        h[v] = c1 * h[v] + c2 * dH;
+    }
+    store_pair<T>(p.fbp, ck, g, h);
 }
 
 // ---------------------------------------------------------------------------
@@ -683,6 +785,46 @@ __device__ __forceinline__ typename V2<T>::t reconstruct(const KParams &p, const
     return o;
 }
 
+// reconstruct for the velocity pair k, k + 1 from one side
+template <class T, bool LIM>
+__device__ __forceinline__ void reconstruct2(const KParams &p, const SideRec<T> &r, int k, const T (&ux)[2],
+                                             const T (&uy)[2], T h, T (&og)[2], T (&oh)[2])
+{
+    T g0[2], h0[2];
+    load_pair<T>(p.fbp, (size_t)r.c * p.Nv + k, g0, h0);
+    if (LIM) {
+        const T *gp = (const T *)p.grad + 4 * ((size_t)r.c * p.Nv + k);
+#pragma unroll
+        for (int v = 0; v < 2; ++v) {
+            T a0, a1, a2, a3;
+            load4<T>(gp + 4 * v, a0, a1, a2, a3);
+            const T ax = r.rx - ux[v] * h, ay = r.ry - uy[v] * h;
+            og[v] = g0[v] + (a0 * ax + a1 * ay);
+            oh[v] = h0[v] + (a2 * ax + a3 * ay);
+        }
+        return;
+    }
+    T sgx[2] = {0, 0}, sgy[2] = {0, 0}, shx[2] = {0, 0}, shy[2] = {0, 0};
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        if (r.nb[m] < 0) continue;
+        T gn[2], hn[2];
+        load_pair<T>(p.fbp, (size_t)r.nb[m] * p.Nv + k, gn, hn);
+#pragma unroll
+        for (int v = 0; v < 2; ++v) {
+            const T dg = gn[v] - g0[v], dh = hn[v] - h0[v];
+            sgx[v] += r.gx[m] * dg; sgy[v] += r.gy[m] * dg;
+            shx[v] += r.gx[m] * dh; shy[v] += r.gy[m] * dh;
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+        const T ax = r.rx - ux[v] * h, ay = r.ry - uy[v] * h;
+        og[v] = g0[v] + (sgx[v] * ax + sgy[v] * ay);
+        oh[v] = h0[v] + (shx[v] * ax + shy[v] * ay);
+    }
+}
+
 // The two side records live in shared memory (one pair per warp) so the
 // per-lane choice of the upwind side is an indexed shared-memory read.
 template <class T> struct FaceCtx {
@@ -753,11 +895,10 @@ __device__ __forceinline__ typename V2<T>::t face_fbar(const KParams &p, const F
 // raw moments of fb - M_ref at every face (plus the wall density, Eq. 35).
 // float32: the kernel is bound by the latency of its stencil loads, so
 // occupancy decides: four 256-thread blocks per SM (64 registers, the lanes'
-// float-float accumulators in shared memory) with the in-place gradient, five
-// (48 registers) when it reads the stored limited gradients; three or two
-// blocks without spills, or six and eight with more, were slower
+// float-float accumulators in shared memory, two velocities per lane); three
+// or two blocks without spills, or five, six and eight with more, were slower
 template <class T, bool LIM>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? (LIM ? 5 : 4) : 1) k_face_moments(Launch L)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 1) k_face_moments(Launch L)
 {
     IDG_LOCATE();
     using T2 = typename V2<T>::t;
@@ -799,9 +940,33 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? (LIM ? 5 : 4) : 1) k_fac
         Fo[k] = fb;
         raw_terms<T>(a, vw<T>(p, k), ux, uy, fb.x, fb.y);
     };
+    // velocity pairs: at an interior face whose two velocities are upwind
+    // from the same side (no tie) one pair reconstruction; else per velocity
+    auto body2 = [&](int k, T(&a)[kRaw]) {
+        T ux[2], uy[2], w[2], s[2], g[2], hh[2];
+        vtab2<T>(p.uxf, p.ux, k, ux);
+        vtab2<T>(p.uyf, p.uy, k, uy);
+        vtab2<T>(p.wf, p.w, k, w);
+        s[0] = xi_dot_n<T>(ux[0], uy[0], fc.nx, fc.ny);
+        s[1] = xi_dot_n<T>(ux[1], uy[1], fc.nx, fc.ny);
+        const bool up0 = s[0] > (T)0, up1 = s[1] > (T)0;
+        if (fc.kind < 0 && up0 == up1 && s[0] != (T)0 && s[1] != (T)0) {
+            reconstruct2<T, LIM>(p, fc.rec[up0 ? 0 : 1], k, ux, uy, h, g, hh);
+        } else {
+#pragma unroll
+            for (int v = 0; v < 2; ++v) {
+                const T2 fb = face_fbar<T, LIM>(p, fc, k + v, ux[v], uy[v], s[v], rhow, rwm1);
+                g[v] = fb.x;
+                hh[v] = fb.y;
+            }
+        }
+        store_pair<T>(Fo, k, g, hh);
+        raw_terms<T>(a, w[0], ux[0], uy[0], g[0], hh[0]);
+        raw_terms<T>(a, w[1], ux[1], uy[1], g[1], hh[1]);
+    };
     if constexpr (sizeof(T) == 4) {
         __shared__ FF sacc[kRaw * 256];
-        vel_loop_sm<kRaw>(p.Nv, lane, sacc, body);
+        vel_loop2_sm<kRaw>(p.Nv, lane, sacc, body2);
 #pragma unroll
         for (int q = 0; q < kRaw; ++q) acc[q].v = sacc[q * blockDim.x + threadIdx.x];
     } else {
@@ -872,22 +1037,28 @@ __global__ void __launch_bounds__(256) k_face_flux(Launch L)
     Acc<T> acc[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) acc[q].zero();
-    vel_loop<4, T>(p.Nv, lane, acc, [&](int k, T(&a)[4]) {
-        T ux = vx<T>(p, k), uy = vy<T>(p, k);
-        T s = xi_dot_n<T>(ux, uy, nx, ny);
-        T2 fb = Fo[k];
-        T dG, dH;
-        dev_equilibrium<T>(e, ux, uy, vgref<T>(p, k), kRTr, dG, dH);
-        T sS = s * S;
-        T2 Fk;
-        Fk.x = sS * (wa * fb.x + wb * dG);
-        Fk.y = sS * (wa * fb.y + wb * dH);
-        Fo[k] = Fk;
-        T w = vw<T>(p, k), wg = w * Fk.x;
-        a[0] += wg;
-        a[1] += wg * ux;
-        a[2] += wg * uy;
-        a[3] += (T)0.5 * w * ((ux * ux + uy * uy) * Fk.x + Fk.y);
+    vel_loop2<4, T>(p.Nv, lane, acc, [&](int k, T(&a)[4]) {
+        T ux[2], uy[2], w[2], gr[2], fg[2], fh[2];
+        vtab2<T>(p.uxf, p.ux, k, ux);
+        vtab2<T>(p.uyf, p.uy, k, uy);
+        vtab2<T>(p.wf, p.w, k, w);
+        vtab2<T>(p.greff, p.gref, k, gr);
+        load_pair<T>(Fo, k, fg, fh);
+#pragma unroll
+        for (int v = 0; v < 2; ++v) {
+            T s = xi_dot_n<T>(ux[v], uy[v], nx, ny);
+            T dG, dH;
+            dev_equilibrium<T>(e, ux[v], uy[v], gr[v], kRTr, dG, dH);
+            T sS = s * S;
+            fg[v] = sS * (wa * fg[v] + wb * dG);
+            fh[v] = sS * (wa * fh[v] + wb * dH);
+            T wg = w[v] * fg[v];
+            a[0] += wg;
+            a[1] += wg * ux[v];
+            a[2] += wg * uy[v];
+            a[3] += (T)0.5 * w[v] * ((ux[v] * ux[v] + uy[v] * uy[v]) * fg[v] + fh[v]);
+        }
+        store_pair<T>(Fo, k, fg, fh);
     });
 #pragma unroll
     for (int q = 0; q < 4; ++q) acc[q].warp_sum();
@@ -1277,36 +1448,45 @@ __global__ void __launch_bounds__(32) k_explicit_norm(Launch L)
 }
 
 template <class T>
-__global__ void __launch_bounds__(256) k_explicit_update(Launch L)
+__global__ void __launch_bounds__(128) k_explicit_update(Launch L)
 {
     IDG_LOCATE();
-    using T2 = typename V2<T>::t;
     const int nvb = (p.Nv + 255) / 256;
     const int c = blk / nvb;
-    const int k = (blk - c * nvb) * blockDim.x + threadIdx.x;
+    const int k = 2 * ((blk - c * nvb) * 128 + threadIdx.x);
     if (k >= p.Nv) return;
     const T *cA = (const T *)p.cellA + kCellP * c;
     const EqT<T> e = eq_loadT<T>(cA);
     // k_cell_params stores c2 = 3h/(2tau+dt) = (3/4) 2dt/(2tau+dt) (h = dt/2)
     const T b = cA[15] * (T)(4.0 / 3.0), a = (T)1 - b;
-    const T dto = (T)(p.dt / p.area[c]);
-    const T ux = vx<T>(p, k), uy = vy<T>(p, k);
-    T dG, dH;
-    dev_equilibrium<T>(e, ux, uy, vgref<T>(p, k), (T)(p.K * p.RT_r), dG, dH);
-    const T2 *F = (const T2 *)p.F;
-    T sg_ = 0, sh_ = 0;
+    const T dto = (T)(p.dt / p.area[c]), kRTr = (T)(p.K * p.RT_r);
+    T ux[2], uy[2], gr[2];
+    vtab2<T>(p.uxf, p.ux, k, ux);
+    vtab2<T>(p.uyf, p.uy, k, uy);
+    vtab2<T>(p.greff, p.gref, k, gr);
+    T sg_[2] = {0, 0}, sh_[2] = {0, 0};
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
-        const T2 Fv = F[(size_t)p.cface[4 * c + m] * p.Nv + k];
+        T fg[2], fh[2];
+        load_pair<T>(p.F, (size_t)p.cface[4 * c + m] * p.Nv + k, fg, fh);
         const T sg = (T)p.csign[4 * c + m];
-        sg_ += sg * Fv.x;
-        sh_ += sg * Fv.y;
+#pragma unroll
+        for (int v = 0; v < 2; ++v) {
+            sg_[v] += sg * fg[v];
+            sh_[v] += sg * fh[v];
+        }
     }
     const size_t ck = (size_t)c * p.Nv + k;
-    T2 v = ((const T2 *)p.f)[ck];
-    v.x = a * v.x + b * dG - dto * sg_;
-    v.y = a * v.y + b * dH - dto * sh_;
-    ((T2 *)p.f)[ck] = v;
+    T g[2], h[2];
+    load_pair<T>(p.f, ck, g, h);
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+        T dG, dH;
+        dev_equilibrium<T>(e, ux[v], uy[v], gr[v], kRTr, dG, dH);
+        g[v] = a * g[v] + b * dG - dto * sg_[v];
+        h[v] = a * h[v] + b * dH - dto * sh_[v];
+    }
+    store_pair<T>(p.f, ck, g, h);
 }
 
 // W = (rho, rho U, rho V, rho E) of f~ from its raw moments (Eq. 4), and
@@ -1349,35 +1529,42 @@ __global__ void __launch_bounds__(32) k_explicit_w(Launch L)
 // a periodic seam (earlier hyperplanes) are read back from global memory.
 // ---------------------------------------------------------------------------
 template <class T>
-__global__ void __launch_bounds__(256) k_micro_residual(Launch L)
+__global__ void __launch_bounds__(128) k_micro_residual(Launch L)
 {
     IDG_LOCATE();
-    using T2 = typename V2<T>::t;
     const int nvb = (p.Nv + 255) / 256;
     const int c = blk / nvb;
-    const int k = (blk - c * nvb) * blockDim.x + threadIdx.x;
+    const int k = 2 * ((blk - c * nvb) * 128 + threadIdx.x);
     if (k >= p.Nv) return;
     const T *cp = (const T *)p.cellpT + kCellP * c;
     const EqT<T> e = eq_loadT<T>(cp);
-    const T cq = cp[14];
-    T dG, dH;
-    const T ux = vx<T>(p, k), uy = vy<T>(p, k);
-    dev_equilibrium<T>(e, ux, uy, vgref<T>(p, k), (T)(p.K * p.RT_r), dG, dH);
+    const T cq = cp[14], kRTr = (T)(p.K * p.RT_r);
+    T ux[2], uy[2], gr[2];
+    vtab2<T>(p.uxf, p.ux, k, ux);
+    vtab2<T>(p.uyf, p.uy, k, uy);
+    vtab2<T>(p.greff, p.gref, k, gr);
     const size_t ck = (size_t)c * p.Nv + k;
-    const T2 fv = ((const T2 *)p.f)[ck];
-    T rg = -cq * (fv.x - dG), rh = -cq * (fv.y - dH);
-    const T2 *F = (const T2 *)p.F;
+    T rg[2], rh[2];
+    load_pair<T>(p.f, ck, rg, rh);
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+        T dG, dH;
+        dev_equilibrium<T>(e, ux[v], uy[v], gr[v], kRTr, dG, dH);
+        rg[v] = -cq * (rg[v] - dG);
+        rh[v] = -cq * (rh[v] - dH);
+    }
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
-        T2 Fv = F[(size_t)p.cface[4 * c + m] * p.Nv + k];
-        T sg = (T)p.csign[4 * c + m];
-        rg -= sg * Fv.x;
-        rh -= sg * Fv.y;
+        T fg[2], fh[2];
+        load_pair<T>(p.F, (size_t)p.cface[4 * c + m] * p.Nv + k, fg, fh);
+        const T sg = (T)p.csign[4 * c + m];
+#pragma unroll
+        for (int v = 0; v < 2; ++v) {
+            rg[v] -= sg * fg[v];
+            rh[v] -= sg * fh[v];
+        }
     }
-    T2 o;
-    o.x = rg;
-    o.y = rh;
-    ((T2 *)p.dst)[ck] = o;
+    store_pair<T>(p.dst, ck, rg, rh);
 }
 
 // 16 storage scalars from 16-byte-aligned shared memory
@@ -1803,7 +1990,7 @@ static int iteration_t(const Plan &pl, cudaStream_t st, void **events)
         // by launch_explicit_prologue)
         mark(0);
         k_cell_params<T><<<nb[KT_CELL_PAR], 32, 0, st>>>(L(KT_CELL_PAR));
-        k_fbp<T><<<nb[KT_FBP], 256, 0, st>>>(L(KT_FBP));
+        k_fbp<T><<<nb[KT_FBP], 128, 0, st>>>(L(KT_FBP));
         mark(1);
         if (pl.limiter_any) k_cell_grad<T><<<nb[KT_FBP], 128, 0, st>>>(L(KT_FBP));
         if (pl.limiter_any) k_face_moments<T, true><<<nb[KT_FACE_MOM], 256, 0, st>>>(L(KT_FACE_MOM));
@@ -1814,7 +2001,7 @@ static int iteration_t(const Plan &pl, cudaStream_t st, void **events)
         k_face_phi<T><<<nb[KT_FACE_PHI], 64, 0, st>>>(L(KT_FACE_PHI));
         mark(3);
         mark(4);
-        k_explicit_update<T><<<nb[KT_MICRO_RES], 256, 0, st>>>(L(KT_MICRO_RES));
+        k_explicit_update<T><<<nb[KT_MICRO_RES], 128, 0, st>>>(L(KT_MICRO_RES));
         k_cell_moments<T><<<nb[KT_CELL_MOM], 256, 0, st>>>(L(KT_CELL_MOM));
         k_explicit_w<T><<<nb[KT_CELL_PAR], 32, 0, st>>>(L(KT_CELL_PAR));
         k_explicit_norm<T><<<nb[KT_MACRO_SWEEP], 32, 0, st>>>(L(KT_MACRO_SWEEP));
@@ -1825,7 +2012,7 @@ static int iteration_t(const Plan &pl, cudaStream_t st, void **events)
     mark(0);
     k_cell_moments<T><<<nb[KT_CELL_MOM], 256, 0, st>>>(L(KT_CELL_MOM));
     k_cell_params<T><<<nb[KT_CELL_PAR], 32, 0, st>>>(L(KT_CELL_PAR));
-    k_fbp<T><<<nb[KT_FBP], 256, 0, st>>>(L(KT_FBP));
+    k_fbp<T><<<nb[KT_FBP], 128, 0, st>>>(L(KT_FBP));
     mark(1);
     if (pl.limiter_any) k_cell_grad<T><<<nb[KT_FBP], 128, 0, st>>>(L(KT_FBP));
     if (pl.limiter_any) k_face_moments<T, true><<<nb[KT_FACE_MOM], 256, 0, st>>>(L(KT_FACE_MOM));
@@ -1842,7 +2029,7 @@ static int iteration_t(const Plan &pl, cudaStream_t st, void **events)
         k_macro_sweep<T, 4><<<nb[KT_MACRO_SWEEP], pl.macro_threads, pl.macro_smem, st>>>(L(KT_MACRO_SWEEP));
     k_macro_post<T><<<nb[KT_MACRO_POST], 32, 0, st>>>(L(KT_MACRO_POST));
     mark(4);
-    k_micro_residual<T><<<nb[KT_MICRO_RES], 256, 0, st>>>(L(KT_MICRO_RES));
+    k_micro_residual<T><<<nb[KT_MICRO_RES], 128, 0, st>>>(L(KT_MICRO_RES));
     launch_sweep<T, true>(pl, st, L(KT_SWEEP));
     mark(5);
     launch_sweep<T, false>(pl, st, L(KT_SWEEP));
