@@ -118,6 +118,20 @@ enum { IDG_NUM_EXPLICIT = 1 };
 idg_status idg_set_numerics(idg_ctx *ctx, double cfl_imp, double cfl_phys, int limiter,
                             double lusgs_omega, int flags);
 
+/* Macroscopic predictor of the implicit iteration (Eq. 28-31).  relax_sweeps
+ * 0 (default): the LU-SGS forward and backward sweeps of Eq. (30).
+ * relax_sweeps n in 1..64: point relaxation of the same predictor equations,
+ * the other predictor the paper's conclusions name:
+ *     D dW_c + sum_nb 1/2 (dF_nb S - omega Lambda dW_nb) = R_c,
+ * solved by n Jacobi sweeps from dW = 0 (n = 1: dW = R / D), every cell in
+ * parallel from the previous sweep.  Either predictor leaves the fixed point
+ * (R_W = 0) unchanged; they differ in convergence per iteration and in cost
+ * (LU-SGS is a dependent wavefront of 2(ni+nj-1) steps on one SM, each
+ * relaxation sweep one grid-wide kernel).  A context with n > 0 cannot run
+ * idg_adjoint, and the instances of a batch must share n (IDG_ERR_ARG).
+ * Before idg_bind_workspace. */
+idg_status idg_set_predictor(idg_ctx *ctx, int relax_sweeps);
+
 /* Bytes of device workspace the configured problem needs (>= 0; host only). */
 idg_status idg_workspace_size(idg_ctx *ctx, size_t *bytes);
 

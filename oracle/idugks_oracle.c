@@ -22,6 +22,9 @@
  *  - Eq. (22)-(23): the collision residual is -(2 Omega/(2 tau + dt)) (f~ - f^S);
  *  - Eq. (30): matrix-free LU-SGS with off-diagonal 1/2 (dF S - w Lambda dW),
  *    w = 2 by default, Lambda = (|V.n| + c) S at the face average;
+ *  - the point relaxation the conclusions name as the other predictor (no
+ *    equation printed): Jacobi sweeps on the same predictor equations
+ *    D dW_c + sum_nb 1/2 (dF_nb S - w Lambda dW_nb) = R_c, from dW = 0;
  *  - diffuse wall (Eq. 34-35 in non-delta form) on f-bar with zero net mass
  *    flux; the mass component of the wall flux moment is set to zero;
  *  - ghost increments are zero in both sweeps (end of Section 2.3).
@@ -780,6 +783,49 @@ static double face_lambda(const orc_state *s, const orc_face *F)
     return (fabs(u * F->nx + v * F->ny) + c) * F->S;
 }
 
+/* off-diagonal term of the predictor equations between cell c and the
+ * neighbour across slot m with increment dn: 1/2 (dF S - w Lambda dn), dF the
+ * change of the Euler flux of the neighbour's state along c's outward normal;
+ * 0 (returns 0) when the slot has no neighbour cell or wraps c onto itself */
+static int offdiag(const orc_state *s, const double *lam, int c, int m, const double *dnW, double *o)
+{
+    int fi = s->cell_face[4 * c + m];
+    const orc_face *F = &s->face[fi];
+    if (F->L < 0 || F->R < 0 || F->L == F->R) return 0;
+    int sg = s->cell_sign[4 * c + m];
+    int nb = sg > 0 ? F->R : F->L;
+    double nx = sg * F->nx, ny = sg * F->ny;
+    double Wn[4], F1[4], F0[4];
+    for (int q = 0; q < 4; ++q) Wn[q] = s->W[4 * nb + q] + dnW[4 * nb + q];
+    euler_flux(s, Wn, nx, ny, F1);
+    euler_flux(s, s->W + 4 * nb, nx, ny, F0);
+    for (int q = 0; q < 4; ++q) o[q] = 0.5 * ((F1[q] - F0[q]) * F->S - s->p.lusgs_omega * lam[fi] * dnW[4 * nb + q]);
+    return 1;
+}
+
+/* point relaxation: n Jacobi sweeps, every cell from the previous sweep's
+ * increments of all its neighbours, starting from dW = 0 (one sweep gives
+ * dW = R / D) */
+static void point_relaxation(orc_state *s, const double *Dd, const double *lam, int n)
+{
+    const int N = s->N;
+    double *prev = dalloc(4 * N), *next = dalloc(4 * N);
+    for (int k = 0; k < n; ++k) {
+        for (int c = 0; c < N; ++c) {
+            double acc[4] = {s->rw[4 * c], s->rw[4 * c + 1], s->rw[4 * c + 2], s->rw[4 * c + 3]};
+            for (int m = 0; m < 4; ++m) {
+                double o[4];
+                if (!offdiag(s, lam, c, m, prev, o)) continue;
+                for (int q = 0; q < 4; ++q) acc[q] -= o[q];
+            }
+            for (int q = 0; q < 4; ++q) next[4 * c + q] = acc[q] / Dd[c];
+        }
+        double *t = prev; prev = next; next = t;
+    }
+    memcpy(s->dW, prev, 4 * (size_t)N * sizeof(double));
+    free(prev); free(next);
+}
+
 static void macro_predictor(orc_state *s)
 {
     const int N = s->N;
@@ -795,6 +841,11 @@ static void macro_predictor(orc_state *s)
             d += 0.5 * om * lam[s->cell_face[4 * c + m]];
         }
         Dd[c] = d;
+    }
+    if (s->p.relax_sweeps > 0) {
+        point_relaxation(s, Dd, lam, s->p.relax_sweeps);
+        free(Dd); free(lam);
+        return;
     }
     /* forward sweep, lexicographic order idx = j*ni + i */
     for (int c = 0; c < N; ++c) {
@@ -985,6 +1036,29 @@ void orc_explicit_step(orc_state *s, int n)
     }
     for (int c = 0; c < N; ++c)
         moments_W(s, s->G + (size_t)c * Nv, s->H + (size_t)c * Nv, s->W + 4 * c);
+}
+
+/* the macroscopic residual R_W (Eq. 27) of the current state and the
+ * predictor's increment dW (Eq. 28-31, LU-SGS or point relaxation as
+ * configured); the state itself is not advanced */
+void orc_debug_predictor(orc_state *s, double *rw, double *dW)
+{
+    const int N = s->N;
+    cell_prep(s);
+    gradients(s);
+    face_fluxes(s);
+    for (int c = 0; c < N; ++c) {
+        double acc[4] = {0, 0, 0, 0};
+        for (int m = 0; m < 4; ++m) {
+            int fi = s->cell_face[4 * c + m];
+            double sg = s->cell_sign[4 * c + m];
+            for (int q = 0; q < 4; ++q) acc[q] -= sg * s->phi[4 * fi + q];
+        }
+        for (int q = 0; q < 4; ++q) s->rw[4 * c + q] = acc[q];
+    }
+    macro_predictor(s);
+    memcpy(rw, s->rw, 4 * (size_t)N * sizeof(double));
+    memcpy(dW, s->dW, 4 * (size_t)N * sizeof(double));
 }
 
 void orc_debug_cell_prep(orc_state *s, double *fbG, double *fbH, double *q, double *tau)

@@ -41,6 +41,8 @@ typedef struct {
     int limiter;                /* 0: phi = 1; 1: Venkatakrishnan, Eq. (16)-(17)      */
     int flags;
     double lusgs_omega;         /* macro LU-SGS relaxation; 2 is the Eq. (30) form    */
+    int relax_sweeps;           /* 0: LU-SGS predictor; n >= 1: point relaxation of   */
+                                /* the same equations, n Jacobi sweeps from dW = 0     */
 } orc_problem;
 
 typedef struct orc_state orc_state;
@@ -60,6 +62,8 @@ void orc_get_state(const orc_state *s, double *G, double *H, double *W);
 void orc_iterate(orc_state *s, int n, double *res_abs);
 /* n explicit DUGKS steps, Eq. (21). */
 void orc_explicit_step(orc_state *s, int n);
+/* R_W of the current state and the predictor's dW, without advancing it. */
+void orc_debug_predictor(orc_state *s, double *rw, double *dW);
 
 /* per cell: rho, u, v, T/T_ref, qx, qy (q from the stored state) */
 void orc_get_moments(orc_state *s, double *out6);

@@ -44,6 +44,7 @@ class _Problem(C.Structure):
         ("cfl_imp", C.c_double), ("cfl_phys", C.c_double),
         ("limiter", C.c_int), ("flags", C.c_int),
         ("lusgs_omega", C.c_double),
+        ("relax_sweeps", C.c_int),
     ]
 
 
@@ -83,6 +84,7 @@ def lib():
         _lib.orc_venkat_theta.restype = d
         _lib.orc_venkat_theta.argtypes = [d]
         _lib.orc_debug_cell_prep.argtypes = [vp, P(d), P(d), P(d), P(d)]
+        _lib.orc_debug_predictor.argtypes = [vp, P(d), P(d)]
     return _lib
 
 
@@ -128,6 +130,7 @@ class Oracle:
         p.shakhov = prob.shakhov
         p.cfl_imp, p.cfl_phys = prob.cfl_imp, prob.cfl_phys
         p.limiter, p.flags, p.lusgs_omega = prob.limiter, prob.flags, prob.lusgs_omega
+        p.relax_sweeps = prob.relax_sweeps
         self._p = p
         self._h = L.orc_create(C.byref(p))
         if not self._h:
@@ -169,6 +172,13 @@ class Oracle:
 
     def explicit(self, n: int):
         lib().orc_explicit_step(self._h, n)
+
+    def predictor(self):
+        """(R_W, dW) of the current state: the macroscopic residual and the
+        predictor's increment (the state is not advanced)."""
+        rw, dW = np.zeros((self.N, 4)), np.zeros((self.N, 4))
+        lib().orc_debug_predictor(self._h, _dp(rw), _dp(dW))
+        return rw, dW
 
     def moments(self) -> np.ndarray:
         out = np.zeros((self.N, 6))

@@ -45,6 +45,7 @@ SIGNATURES = [
     ("idg_set_gas", _i, [_vp, _i, _d, _d, _d, _d, _i]),
     ("idg_set_boundary", _i, [_vp, _i, _i, _d, _d, _d, _d]),
     ("idg_set_numerics", _i, [_vp, _d, _d, _i, _d, _i]),
+    ("idg_set_predictor", _i, [_vp, _i]),
     ("idg_workspace_size", _i, [_vp, _P(_sz)]),
     ("idg_bind_workspace", _i, [_vp, _vp, _sz]),
     ("idg_init_uniform", _i, [_vp, _d, _d, _d, _d, _vp]),
@@ -146,6 +147,10 @@ def idg_set_boundary(ctx, side, kind, rho, u, v, T):
 
 def idg_set_numerics(ctx, cfl_imp, cfl_phys, limiter, lusgs_omega, flags=0):
     return check(ctx, lib().idg_set_numerics(ctx, cfl_imp, cfl_phys, limiter, lusgs_omega, flags))
+
+
+def idg_set_predictor(ctx, relax_sweeps):
+    return check(ctx, lib().idg_set_predictor(ctx, relax_sweeps))
 
 
 def idg_workspace_size(ctx) -> int:

@@ -34,6 +34,7 @@ struct idg_ctx {
            bc_T[4] = {0, 0, 0, 0};
     double cfl_imp = 100.0, cfl_phys = 0.5, lusgs_omega = 2.0;
     int limiter = 0, flags = 0;
+    int relax_sweeps = 0;  // macroscopic predictor: 0 LU-SGS, n point-relaxation sweeps
     // derived on the host
     bool built = false;
     // Nvu: discrete velocities of the caller's grid; Nv: velocities stored per
@@ -440,6 +441,7 @@ size_t layout(idg_ctx *c, char *base, KParams *kp)
     k.rw = L.take<double>(32 * N);
     k.mrec = L.take<char>(24 * ts * N);
     k.mdW = L.take<char>(4 * ts * N);
+    k.mdW2 = c->relax_sweeps > 0 ? L.take<char>(4 * ts * N) : nullptr;
     k.mpart = L.take<double>(8 * (N / 32 + 2));
     k.res = L.take<double>(8 * (size_t)idg::kMaxHist);
     k.iter = L.take<int>(256);
@@ -761,6 +763,16 @@ idg_status idg_set_numerics(idg_ctx *c, double cfl_imp, double cfl_phys, int lim
     return IDG_OK;
 }
 
+idg_status idg_set_predictor(idg_ctx *c, int relax_sweeps)
+{
+    if (!c) return IDG_ERR_ARG;
+    if (c->bound) return fail(c, IDG_ERR_STATE, "setters are closed after idg_bind_workspace");
+    if (relax_sweeps < 0 || relax_sweeps > 64) return fail(c, IDG_ERR_ARG, "relax_sweeps %d outside 0..64", relax_sweeps);
+    c->relax_sweeps = relax_sweeps;
+    c->built = false;
+    return IDG_OK;
+}
+
 idg_status idg_workspace_size(idg_ctx *c, size_t *bytes)
 {
     if (!c || !bytes) return IDG_ERR_ARG;
@@ -830,6 +842,7 @@ idg_status idg_bind_workspace(idg_ctx *c, void *dev_ptr, size_t bytes)
     k.per_j = c->bc_kind[IDG_JMIN] == IDG_BC_PERIODIC;
     k.dt = c->dt; k.h = 0.5 * c->dt; k.mu_ref = c->mu_ref; k.RT_ref = c->RT_ref; k.omega = c->omega;
     k.Pr = c->Pr; k.gam = (double)(c->K + 4) / (double)(c->K + 2); k.lusgs_omega = c->lusgs_omega;
+    k.relax_sweeps = c->relax_sweeps;
     // sweep launch shape: cell slots cover the longest hyperplane up to 64
     // micro sweeps: one thread per cell of the longest hyperplane and tv
     // velocities per CTA (8 by default, more on very narrow blocks)
@@ -1349,6 +1362,7 @@ idg_status idg_batch_create(idg_batch **out, idg_ctx *const *ctxs, int n)
         if (!ctxs[i] || !ctxs[i]->bound) return IDG_ERR_STATE;
         if (ctxs[i]->precision != ctxs[0]->precision || ctxs[i]->device != ctxs[0]->device) return IDG_ERR_ARG;
         if (ctxs[i]->flags & IDG_NUM_EXPLICIT) return IDG_ERR_ARG;  // batches run IDUGKS iterations
+        if (ctxs[i]->relax_sweeps != ctxs[0]->relax_sweeps) return IDG_ERR_ARG;  // one predictor per batch
         for (int j = 0; j < i; ++j)
             if (ctxs[j] == ctxs[i]) return IDG_ERR_ARG;
     }
@@ -1550,6 +1564,7 @@ idg_status idg_adjoint(idg_ctx *c, int objective, int side_mask, const int *para
                 return fail(c, IDG_ERR_ARG, "parameter %d: side %d is not a wall", i, sd);
     }
     if (c->flags) return fail(c, IDG_ERR_ARG, "the adjoint does not support numerics flags 0x%x", c->flags);
+    if (c->relax_sweeps) return fail(c, IDG_ERR_ARG, "the adjoint transposes the LU-SGS predictor only");
     if (max_iter < 1 || max_iter > idg::kMaxHist) return fail(c, IDG_ERR_ARG, "max_iter out of [1, %d]", idg::kMaxHist);
     if (!workspace) return fail(c, IDG_ERR_ARG, "null adjoint workspace");
     if (((uintptr_t)workspace) & 255) return fail(c, IDG_ERR_ARG, "adjoint workspace must be 256-byte aligned");

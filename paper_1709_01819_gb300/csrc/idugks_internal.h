@@ -72,6 +72,7 @@ struct KParams {
     // macroscopic LU-SGS work (T = storage precision of the sweep)
     void *mrec;     // [N][24] T: R, 1/D, own base state, per slot (S/2) n_out, (omega/2) Lambda
     void *mdW;      // [N][4] T increments (Delta W* then Delta W)
+    void *mdW2;     // [N][4] T second increment buffer of the point relaxation (else null)
     double *mpart;  // [ceil(N/256)] block partial sums of ||R/Omega||^2
     double *res;    // [kMaxHist] absolute residual per iteration
     int *iter;      // [1] device iteration counter
@@ -80,6 +81,7 @@ struct KParams {
     // slots of the micro sweeps, prefetch depths (hyperplanes; 4 or 8)
     int sweep_tv, sweep_pc, sweep_stages, macro_stages;
     int sweep_vpt;  // consecutive velocities per thread in the micro sweeps (1, 2, 4)
+    int relax_sweeps;  // macroscopic predictor: 0 LU-SGS, n >= 1 n point-relaxation sweeps
 };
 
 // kernels of one iteration, in launch order
@@ -102,6 +104,7 @@ struct Plan {
     size_t macro_smem, fwd_smem, bwd_smem;
     int macro_stages, sweep_stages, limiter_any, sweep_vpt;
     int explicit_dugks;  // 1: launch_iteration runs one explicit DUGKS step (Eq. 21)
+    int relax_sweeps;    // macroscopic predictor of every instance (KParams::relax_sweeps)
 };
 
 // kernel launchers (idugks_kernels.cu)

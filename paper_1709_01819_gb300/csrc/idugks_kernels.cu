@@ -1421,6 +1421,46 @@ __global__ void __launch_bounds__(32) k_macro_post(Launch L)
     for (int q = 0; q < kCellP; ++q) ct[q] = (T)cp[q];
 }
 
+// Point relaxation of the predictor equations (the alternative to LU-SGS the
+// conclusions name): D dW_c + sum_nb 1/2 (dF_nb S - omega Lambda dW_nb) = R_c
+// solved by Jacobi sweeps from dW = 0, every cell at once from the previous
+// sweep's increments of all its neighbours -- no wavefront, every SM busy.
+// Sweep k of n (1-based) writes mdW when n - k is even, mdW2 when odd, so the
+// last one leaves dW in mdW for k_macro_post; sweep 1 gives dW = R / D.  The
+// record of k_macro_pre holds R, 1/D, the cell's base state and per slot
+// (S/2) n_out and (omega/2) Lambda, as for the sweeps.
+template <class T>
+__global__ void __launch_bounds__(32) k_macro_relax(Launch L, int sweep, int nsweeps)
+{
+    IDG_LOCATE();
+    const int c = blk * blockDim.x + threadIdx.x;
+    if (c >= p.N) return;
+    const bool odd = (nsweeps - sweep) & 1;
+    T *dst = (T *)(odd ? p.mdW2 : p.mdW);
+    const T *src = (const T *)(odd ? p.mdW : p.mdW2);
+    const T *mrec = (const T *)p.mrec;
+    const T *rec = mrec + (size_t)kMRec * c;
+    const T gm1 = (T)(p.gam - 1.0);
+    T acc[4] = {0, 0, 0, 0};
+    if (sweep > 1) {
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int nb = p.cnb[4 * c + m];
+            if (nb < 0 || nb == c) continue;  // ghost, or a cell wrapped onto itself
+            const T *x = src + 4 * (size_t)nb;
+            const T dn[4] = {x[0], x[1], x[2], x[3]};
+            const T *cf = rec + 12 + 3 * m;
+            T dF[4];
+            euler_dflux<T>(gm1, mrec + (size_t)kMRec * nb + 6, dn, cf[0], cf[1], dF);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[q] += dF[q] - cf[2] * dn[q];
+        }
+    }
+    const T iD = rec[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) dst[4 * (size_t)c + q] = (rec[q] - acc[q]) * iD;
+}
+
 // ---------------------------------------------------------------------------
 // explicit DUGKS (Eq. 10, 21): the cell and face kernels of the implicit
 // iteration build the face fluxes with the physical step dt, then
@@ -1430,14 +1470,16 @@ __global__ void __launch_bounds__(32) k_macro_post(Launch L)
 //                      conserves them, so f~ and f share them), which the
 //                      next step's cell prep reads, and partial sums of
 //                      ||(W^{n+1} - W^n)/dt||^2
-//   k_explicit_norm    one thread per instance: the step's residual
-//                      ||(W^{n+1} - W^n)/dt||_2 into the residual ring.
+//   k_record_residual  the step's residual ||(W^{n+1} - W^n)/dt||_2.
 // At the fixed point of the march R_W = -sum Phi does not vanish: it balances
 // the moments of the discrete collision term (the quadrature error of the
 // discrete equilibrium), so the march is measured by its rate of change.
 // ---------------------------------------------------------------------------
+
+// one thread per instance: the residual of this iteration from the block
+// partials of the kernel before it into the ring, and the iteration count
 template <class T>
-__global__ void __launch_bounds__(32) k_explicit_norm(Launch L)
+__global__ void __launch_bounds__(32) k_record_residual(Launch L)
 {
     IDG_LOCATE();
     (void)blk;
@@ -1917,7 +1959,9 @@ int plan_shapes(const KParams *hp, int n, bool fp64, Plan &pl)
     pl.macro_threads = pl.sweep_threads = 0;
     pl.limiter_any = 0;
     pl.sweep_vpt = hp[0].sweep_vpt;
+    pl.relax_sweeps = hp[0].relax_sweeps;
     for (int i = 0; i < n; ++i) {
+        if (hp[i].relax_sweeps != pl.relax_sweeps) return (int)cudaErrorInvalidValue;
         pl.macro_threads = std::max(pl.macro_threads, macro_threads(hp[i]));
         pl.sweep_threads = std::max(pl.sweep_threads, hp[i].sweep_tv * hp[i].sweep_pc);
         pl.limiter_any |= hp[i].limiter;
@@ -2004,7 +2048,7 @@ static int iteration_t(const Plan &pl, cudaStream_t st, void **events)
         k_explicit_update<T><<<nb[KT_MICRO_RES], 128, 0, st>>>(L(KT_MICRO_RES));
         k_cell_moments<T><<<nb[KT_CELL_MOM], 256, 0, st>>>(L(KT_CELL_MOM));
         k_explicit_w<T><<<nb[KT_CELL_PAR], 32, 0, st>>>(L(KT_CELL_PAR));
-        k_explicit_norm<T><<<nb[KT_MACRO_SWEEP], 32, 0, st>>>(L(KT_MACRO_SWEEP));
+        k_record_residual<T><<<nb[KT_MACRO_SWEEP], 32, 0, st>>>(L(KT_MACRO_SWEEP));
         mark(5);
         mark(6);
         return (int)cudaGetLastError();
@@ -2023,7 +2067,11 @@ static int iteration_t(const Plan &pl, cudaStream_t st, void **events)
     k_face_phi<T><<<nb[KT_FACE_PHI], 64, 0, st>>>(L(KT_FACE_PHI));
     mark(3);
     k_macro_pre<T><<<nb[KT_MACRO_PRE], 32, 0, st>>>(L(KT_MACRO_PRE));
-    if (pl.macro_stages == 8)
+    if (pl.relax_sweeps > 0) {
+        k_record_residual<T><<<nb[KT_MACRO_SWEEP], 32, 0, st>>>(L(KT_MACRO_SWEEP));
+        for (int k = 1; k <= pl.relax_sweeps; ++k)
+            k_macro_relax<T><<<nb[KT_MACRO_PRE], 32, 0, st>>>(L(KT_MACRO_PRE), k, pl.relax_sweeps);
+    } else if (pl.macro_stages == 8)
         k_macro_sweep<T, 8><<<nb[KT_MACRO_SWEEP], pl.macro_threads, pl.macro_smem, st>>>(L(KT_MACRO_SWEEP));
     else
         k_macro_sweep<T, 4><<<nb[KT_MACRO_SWEEP], pl.macro_threads, pl.macro_smem, st>>>(L(KT_MACRO_SWEEP));

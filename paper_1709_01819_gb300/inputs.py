@@ -57,6 +57,7 @@ class Problem:
     limiter: int = 0
     flags: int = 0
     lusgs_omega: float = 2.0
+    relax_sweeps: int = 0          # macroscopic predictor: 0 LU-SGS, n >= 1 n point-relaxation sweeps
     init: Tuple[float, float, float, float] = (1.0, 0.0, 0.0, 1.0)  # rho, u, v, T
     name: str = ""
 

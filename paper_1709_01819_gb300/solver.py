@@ -26,6 +26,8 @@ def configure(ctx, prob: Problem, explicit: bool = False):
         B.idg_set_boundary(ctx, side, kind, rho, u, v, T)
     B.idg_set_numerics(ctx, prob.cfl_imp, prob.cfl_phys, prob.limiter, prob.lusgs_omega,
                        B.IDG_NUM_EXPLICIT if explicit else 0)
+    if prob.relax_sweeps:
+        B.idg_set_predictor(ctx, prob.relax_sweeps)
 
 
 class Solver:

@@ -408,3 +408,65 @@ def test_explicit_and_implicit_reach_the_same_steady_state():
     T_i, T_e = mi[:, 3], me[:, 3]
     assert np.linalg.norm(u_i - u_e) / np.linalg.norm(u_i) < 1e-9
     assert np.linalg.norm(T_i - T_e) / np.linalg.norm(T_i) < 1e-9
+
+
+# ---------------------------------------------------------------------------
+# point-relaxation predictor (the other predictor the conclusions name)
+# ---------------------------------------------------------------------------
+def _predictor(prob, n, seed=3):
+    import dataclasses
+
+    p = dataclasses.replace(prob, relax_sweeps=n)
+    o = O.Oracle(p)
+    o.init_uniform()
+    o.iterate(3)
+    G, H, W = I.random_state(p, seed=seed)
+    o.set_state(G, H, W)
+    return o.predictor()
+
+
+def test_point_relaxation_one_sweep_is_the_diagonal_predictor():
+    """From dW = 0 one Jacobi sweep leaves only the diagonal: dW = R / D, one
+    scalar D per cell, so dW / R is the same for the four components."""
+    prob = I.cavity(10, Kn=0.075, U=0.15, nv=12, vmax=4.0, cfl_imp=1000.0)
+    rw, dW = _predictor(prob, 1)
+    ratio = dW / rw
+    assert np.all(ratio > 0)
+    assert np.abs(ratio - ratio[:, :1]).max() <= 1e-13 * np.abs(ratio).max()
+
+
+def test_point_relaxation_solves_the_lusgs_predictor_system():
+    """At a small pseudo step (CFL_imp 0.25) the off-diagonal coupling is weak
+    (one sweep against two differ by 6%): Jacobi converges (sweeps 40 and 41
+    agree to round-off) and its limit agrees with the LU-SGS increment to
+    second order in the coupling (0.2%; an off-diagonal term of the wrong
+    sign would put them ~10% apart)."""
+    prob = I.cavity(10, Kn=0.075, U=0.15, nv=12, vmax=4.0, cfl_imp=0.25)
+    d40 = _predictor(prob, 40)[1]
+    d41 = _predictor(prob, 41)[1]
+    d2, d1 = _predictor(prob, 2)[1], _predictor(prob, 1)[1]
+    lu = _predictor(prob, 0)[1]
+    scale = np.abs(lu).max()
+    assert np.abs(d41 - d40).max() <= 1e-12 * scale
+    assert np.abs(d2 - d1).max() >= 0.03 * scale
+    assert np.abs(d40 - lu).max() <= 0.01 * scale
+
+
+def test_point_relaxation_keeps_the_fixed_point():
+    """The predictor only preconditions the iteration: a cylinder in a Ma 0.5
+    stream (the far field fixes the mass; a closed domain would land on a
+    steady state of slightly different total mass, its LU-SGS not being
+    conservative per iteration) converged with five relaxation sweeps equals
+    the LU-SGS steady state to round-off."""
+    import dataclasses
+
+    out = []
+    for n in (0, 5):
+        p = I.cylinder(ntheta=16, nr=8, nv=12, vmax=6.0, Ma=0.5, Kn=0.5, cfl_imp=100.0, limiter=0)
+        o = O.Oracle(dataclasses.replace(p, relax_sweeps=n))
+        o.init_uniform()
+        r = o.iterate(600)
+        assert r[-1] < 1e-13 * r[0]
+        out.append(o.get_state())
+    for a, b in zip(out[0], out[1]):
+        assert np.abs(a - b).max() <= 1e-12 * np.abs(a).max()
