@@ -70,14 +70,15 @@ def algorithmic_bytes(prob: I.Problem, s: int, nf: int):
     face_flux: read fb, write the face flux                   4s per face-velocity
     k_sweep_fwd: micro residual (read the fluxes and f~, write R), then the
                  forward sweep (read R, write Delta*)         2s per face-velocity + 8s per cell-velocity
-    k_sweep_bwd: read Delta* and f~, write Delta and f~       8s per cell-velocity"""
+    k_sweep_bwd: read Delta* and f~, write f~                 6s per cell-velocity
+                 (Delta itself is kept only across a periodic seam)"""
     N, Nv = prob.ncells, prob.nvel
     return {
         "cell_prep": 6 * s * N * Nv,
         "face_moments": (12 if prob.limiter else 2) * s * N * Nv + 2 * s * nf * Nv,
         "face_flux": 4 * s * nf * Nv,
         "k_sweep_fwd": 2 * s * nf * Nv + 8 * s * N * Nv,
-        "k_sweep_bwd": 8 * s * N * Nv,
+        "k_sweep_bwd": 6 * s * N * Nv,
     }
 
 

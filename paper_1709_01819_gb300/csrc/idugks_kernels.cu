@@ -1749,6 +1749,7 @@ __global__ void __launch_bounds__(512) k_sweep(Launch L)
     const SweepArgs a{p.Nv, p.ni, p.nj, p.sweep_tv, p.sweep_pc, p.dst, p.f, p.cslotT, p.cellpT,
                       p.scode + (FWD ? 0 : 4 * (size_t)p.N)};
     const int tv = a.tv, pc = a.pc, ni = a.ni, nj = a.nj, Nv = a.Nv;
+    const bool per_i = p.per_i, per_j = p.per_j;
     const SweepSmem<T, kStages, VPT> sm(smraw, pc, tv, !FWD);
     const int t = threadIdx.x % tv, slot = threadIdx.x / tv;
     const int k0 = (blk * tv + t) * VPT;  // Nv is a multiple of VPT
@@ -1785,6 +1786,10 @@ __global__ void __launch_bounds__(512) k_sweep(Launch L)
         const size_t ck = (size_t)c * Nv + k0;
         const size_t rbase = e * w + (size_t)t * VPT;
         const size_t rprev = (size_t)((s + 1) & 1) * pc * w + (size_t)t * VPT;
+        // the backward sweep's increments are read back from global memory
+        // only across a periodic seam (the first and last cells of a periodic
+        // direction); elsewhere only f and the ring take them
+        const bool keep = FWD || (per_i && (i == 0 || i == ni - 1)) || (per_j && (j == 0 || j == nj - 1));
         // the step of one cell; SEAM: some neighbour lies across a periodic
         // seam (read from global memory), otherwise every inflow comes from
         // the ring
@@ -1833,7 +1838,7 @@ __global__ void __launch_bounds__(512) k_sweep(Launch L)
                     fv.y += o.y;
                     f[ck + v] = fv;
                 }
-                ds[ck + v] = o;
+                if (keep) ds[ck + v] = o;
                 sm.ring[((size_t)(s & 1) * pc + slot) * w + (size_t)t * VPT + v] = o;
             }
         };
