@@ -54,7 +54,9 @@ struct orc_state {
     /* geometry */
     double *cx, *cy, *area, *hcell, *dtimp;
     orc_face *face;
-    int *cell_face;     /* [N][4]: west, east, south, north face index */
+    int *cell_face;     /* [N][4]: west, east, south, north face index (structured);
+                           unstructured: the edges node m -> m+1 */
+    int *nslot;         /* [N] faces of the cell (4; 3 for a triangle) */
     int *cell_sign;     /* [N][4]: +1 if the cell is L of that face, -1 if R */
     double *lsinv;      /* [N][4] inverse of the 2x2 least-squares matrix (row-major) */
     /* velocity space */
@@ -282,9 +284,12 @@ static int jface_index(const orc_state *s, int i, int j) { return s->p.nj * nfi_
 static double NX(const orc_state *s, int i, int j) { return s->nodes_x[j * (s->p.ni + 1) + i]; }
 static double NY(const orc_state *s, int i, int j) { return s->nodes_y[j * (s->p.ni + 1) + i]; }
 
+static void finish_geometry(orc_state *s);
+
 static void build_geometry(orc_state *s)
 {
     const int ni = s->p.ni, nj = s->p.nj;
+    for (int c = 0; c < s->N; ++c) s->nslot[c] = 4;
     const int per_i = s->p.bc_kind[ORC_IMIN] == ORC_BC_PERIODIC;
     const int per_j = s->p.bc_kind[ORC_JMIN] == ORC_BC_PERIODIC;
     /* cells: area by the polygon (shoelace) formula, centroid of the polygon */
@@ -375,12 +380,135 @@ static void build_geometry(orc_state *s)
             s->cell_face[4 * c + 3] = jface_index(s, i, per_j ? (j + 1) % nj : j + 1);
             s->cell_sign[4 * c + 3] = +1;
         }
-    /* cell size, pseudo time step, least-squares matrices (Eq. 15) */
+    finish_geometry(s);
+}
+
+/* node pair of a cell edge, for matching the two cells of an interior edge */
+typedef struct {
+    int a, b, cell, slot;
+} orc_edge;
+
+static int edge_cmp(const void *x, const void *y)
+{
+    const orc_edge *p = (const orc_edge *)x, *q = (const orc_edge *)y;
+    if (p->a != q->a) return p->a < q->a ? -1 : 1;
+    if (p->b != q->b) return p->b < q->b ? -1 : 1;
+    if (p->cell != q->cell) return p->cell < q->cell ? -1 : 1;
+    return p->slot - q->slot;
+}
+
+/* Unstructured block of triangles and quadrilaterals (nodes counter-clockwise).
+ * Face f between the two cells sharing an edge; L is the cell that runs along
+ * the edge counter-clockwise first in cell order (its outward normal is the
+ * face normal), R the other one or -1 on the boundary.  Slot m of a cell is
+ * its edge node m -> m+1.  Faces are numbered in order of first appearance
+ * (cell by cell, slot by slot).  Returns 0, or -1 for a malformed mesh (an edge
+ * shared by more than two cells or twice in one direction, a cell of
+ * non-positive area, a boundary group out of range or periodic). */
+static int build_geometry_unstructured(orc_state *s)
+{
+    const orc_problem *p = &s->p;
+    const int N = p->n_ucells;
+    int ne = 0;
+    for (int c = 0; c < N; ++c) {
+        int k = p->ucell_nodes[4 * c + 3] < 0 ? 3 : 4;
+        s->nslot[c] = k;
+        double a = 0, gx = 0, gy = 0;
+        for (int m = 0; m < k; ++m) {
+            int n0 = p->ucell_nodes[4 * c + m], n1 = p->ucell_nodes[4 * c + (m + 1) % k];
+            if (n0 < 0 || n1 < 0 || n0 >= p->n_unodes || n1 >= p->n_unodes || n0 == n1) return -1;
+            double cr = s->nodes_x[n0] * s->nodes_y[n1] - s->nodes_x[n1] * s->nodes_y[n0];
+            a += 0.5 * cr;
+            gx += (s->nodes_x[n0] + s->nodes_x[n1]) * cr;
+            gy += (s->nodes_y[n0] + s->nodes_y[n1]) * cr;
+        }
+        if (!(a > 0)) return -1;
+        s->area[c] = a;
+        s->cx[c] = gx / (6.0 * a);
+        s->cy[c] = gy / (6.0 * a);
+        ne += k;
+    }
+    orc_edge *E = (orc_edge *)malloc(sizeof(orc_edge) * (size_t)ne);
+    int q = 0;
+    for (int c = 0; c < N; ++c)
+        for (int m = 0; m < s->nslot[c]; ++m) {
+            int n0 = p->ucell_nodes[4 * c + m], n1 = p->ucell_nodes[4 * c + (m + 1) % s->nslot[c]];
+            E[q].a = n0 < n1 ? n0 : n1;
+            E[q].b = n0 < n1 ? n1 : n0;
+            E[q].cell = c;
+            E[q].slot = m;
+            ++q;
+        }
+    qsort(E, (size_t)ne, sizeof(orc_edge), edge_cmp);
+    /* partner of each cell slot (-1: boundary) */
+    int *partner = (int *)malloc(sizeof(int) * 4 * (size_t)N);
+    for (int i = 0; i < 4 * N; ++i) partner[i] = -1;
+    for (int i = 0; i < ne;) {
+        int j = i + 1;
+        while (j < ne && E[j].a == E[i].a && E[j].b == E[i].b) ++j;
+        if (j - i > 2) { free(E); free(partner); return -1; }
+        if (j - i == 2) {
+            partner[4 * E[i].cell + E[i].slot] = 4 * E[i + 1].cell + E[i + 1].slot;
+            partner[4 * E[i + 1].cell + E[i + 1].slot] = 4 * E[i].cell + E[i].slot;
+        }
+        i = j;
+    }
+    free(E);
+    int nf = 0;
+    for (int i = 0; i < 4 * N; ++i) s->cell_face[i] = -1;
+    for (int c = 0; c < N; ++c)
+        for (int m = 0; m < s->nslot[c]; ++m) {
+            if (s->cell_face[4 * c + m] >= 0) continue; /* the partner created it */
+            int k = s->nslot[c];
+            int n0 = p->ucell_nodes[4 * c + m], n1 = p->ucell_nodes[4 * c + (m + 1) % k];
+            orc_face *F = &s->face[nf];
+            double x0 = s->nodes_x[n0], y0 = s->nodes_y[n0], x1 = s->nodes_x[n1], y1 = s->nodes_y[n1];
+            double tx = x1 - x0, ty = y1 - y0, S = sqrt(tx * tx + ty * ty);
+            double mx = 0.5 * (x0 + x1), my = 0.5 * (y0 + y1);
+            F->S = S; F->nx = ty / S; F->ny = -tx / S; /* outward of c (counter-clockwise) */
+            F->L = c;
+            F->rLx = mx - s->cx[c]; F->rLy = my - s->cy[c];
+            F->bc = -1; F->side = -1;
+            s->cell_face[4 * c + m] = nf;
+            s->cell_sign[4 * c + m] = +1;
+            int pr = partner[4 * c + m];
+            if (pr >= 0) {
+                int c2 = pr / 4, m2 = pr % 4, k2 = s->nslot[c2];
+                /* the neighbour must run along the edge the other way */
+                if (p->ucell_nodes[4 * c2 + m2] != n1 || p->ucell_nodes[4 * c2 + (m2 + 1) % k2] != n0) {
+                    free(partner); return -1;
+                }
+                F->R = c2;
+                F->rRx = mx - s->cx[c2]; F->rRy = my - s->cy[c2];
+                s->cell_face[pr] = nf;
+                s->cell_sign[pr] = -1;
+            } else {
+                int side = p->uedge_side[4 * c + m];
+                if (side < 0 || side > 3 || p->bc_kind[side] == ORC_BC_PERIODIC) { free(partner); return -1; }
+                F->R = -1;
+                F->rRx = F->rRy = 0;
+                F->bc = p->bc_kind[side];
+                F->side = side;
+            }
+            ++nf;
+        }
+    free(partner);
+    s->nf = nf;
+    /* a triangle's unused slot 3 keeps a valid face index; nslot excludes it */
+    for (int c = 0; c < N; ++c)
+        if (s->nslot[c] == 3) { s->cell_face[4 * c + 3] = s->cell_face[4 * c]; s->cell_sign[4 * c + 3] = 0; }
+    finish_geometry(s);
+    return 0;
+}
+
+/* cell size, pseudo time step, least-squares matrices (Eq. 15) */
+static void finish_geometry(orc_state *s)
+{
     double hmin = 1e300;
     for (int c = 0; c < s->N; ++c) {
         double smax = 0;
         double a11 = 0, a12 = 0, a22 = 0;
-        for (int m = 0; m < 4; ++m) {
+        for (int m = 0; m < s->nslot[c]; ++m) {
             const orc_face *F = &s->face[s->cell_face[4 * c + m]];
             if (F->S > smax) smax = F->S;
             if (F->L < 0 || F->R < 0) continue; /* one-sided at boundaries */
@@ -390,10 +518,16 @@ static void build_geometry(orc_state *s)
             a11 += dx * dx; a12 += dx * dy; a22 += dy * dy;
         }
         double det = a11 * a22 - a12 * a12;
-        s->lsinv[4 * c + 0] = a22 / det;
-        s->lsinv[4 * c + 1] = -a12 / det;
-        s->lsinv[4 * c + 2] = -a12 / det;
-        s->lsinv[4 * c + 3] = a11 / det;
+        if (!(det > 1e-10 * (a11 + a22) * (a11 + a22))) {
+            /* fewer than two neighbours in independent directions (a mesh
+             * corner of triangles): no gradient, first-order reconstruction */
+            for (int q = 0; q < 4; ++q) s->lsinv[4 * c + q] = 0.0;
+        } else {
+            s->lsinv[4 * c + 0] = a22 / det;
+            s->lsinv[4 * c + 1] = -a12 / det;
+            s->lsinv[4 * c + 2] = -a12 / det;
+            s->lsinv[4 * c + 3] = a11 / det;
+        }
         s->hcell[c] = s->area[c] / smax;
         if (s->hcell[c] < hmin) hmin = s->hcell[c];
     }
@@ -408,17 +542,23 @@ static double *dalloc(size_t n) { return (double *)calloc(n ? n : 1, sizeof(doub
 
 orc_state *orc_create(const orc_problem *p)
 {
-    if (p->ni < 1 || p->nj < 1) return NULL;
-    if ((p->bc_kind[ORC_IMIN] == ORC_BC_PERIODIC) != (p->bc_kind[ORC_IMAX] == ORC_BC_PERIODIC)) return NULL;
-    if ((p->bc_kind[ORC_JMIN] == ORC_BC_PERIODIC) != (p->bc_kind[ORC_JMAX] == ORC_BC_PERIODIC)) return NULL;
+    const int unstructured = p->n_ucells > 0;
+    if (unstructured) {
+        if (p->n_unodes < 3 || !p->ucell_nodes || !p->uedge_side) return NULL;
+    } else {
+        if (p->ni < 1 || p->nj < 1) return NULL;
+        if ((p->bc_kind[ORC_IMIN] == ORC_BC_PERIODIC) != (p->bc_kind[ORC_IMAX] == ORC_BC_PERIODIC)) return NULL;
+        if ((p->bc_kind[ORC_JMIN] == ORC_BC_PERIODIC) != (p->bc_kind[ORC_JMAX] == ORC_BC_PERIODIC)) return NULL;
+    }
     orc_state *s = (orc_state *)calloc(1, sizeof(orc_state));
     s->p = *p;
-    size_t nn = (size_t)(p->ni + 1) * (p->nj + 1);
+    size_t nn = unstructured ? (size_t)p->n_unodes : (size_t)(p->ni + 1) * (p->nj + 1);
     s->nodes_x = dalloc(nn); s->nodes_y = dalloc(nn);
     memcpy(s->nodes_x, p->nodes_x, nn * sizeof(double));
     memcpy(s->nodes_y, p->nodes_y, nn * sizeof(double));
     s->p.nodes_x = s->nodes_x; s->p.nodes_y = s->nodes_y;
-    s->N = p->ni * p->nj;
+    s->p.ucell_nodes = NULL; s->p.uedge_side = NULL; /* read during creation only */
+    s->N = unstructured ? p->n_ucells : p->ni * p->nj;
     /* velocity grid: tensor product, k = ky * nvx + kx */
     double *x1 = dalloc(p->nvx), *w1 = dalloc(p->nvx), *y1 = dalloc(p->nvy), *v1 = dalloc(p->nvy);
     double unit = sqrt(2.0 * p->RT_ref);
@@ -440,17 +580,36 @@ orc_state *orc_create(const orc_problem *p)
     double om = p->omega;
     s->mu_ref = 15.0 * sqrt(2.0 * M_PI * p->RT_ref) * p->Kn / (2.0 * (5.0 - 2.0 * om) * (7.0 - 2.0 * om));
     s->gam = (double)(p->K + 4) / (double)(p->K + 2);
-    /* faces */
-    int nfi = (p->bc_kind[ORC_IMIN] == ORC_BC_PERIODIC ? p->ni : p->ni + 1) * p->nj;
-    int nfj = (p->bc_kind[ORC_JMIN] == ORC_BC_PERIODIC ? p->nj : p->nj + 1) * p->ni;
-    s->nf = nfi + nfj;
-    size_t N = s->N, Nv = s->Nv, NNv = N * Nv, nf = s->nf;
+    /* faces (unstructured: at most 4 per cell, the count is known after the build) */
+    if (unstructured) {
+        s->nf = 4 * s->N;
+    } else {
+        int nfi = (p->bc_kind[ORC_IMIN] == ORC_BC_PERIODIC ? p->ni : p->ni + 1) * p->nj;
+        int nfj = (p->bc_kind[ORC_JMIN] == ORC_BC_PERIODIC ? p->nj : p->nj + 1) * p->ni;
+        s->nf = nfi + nfj;
+    }
+    size_t N = s->N, Nv = s->Nv, NNv = N * Nv;
     s->cx = dalloc(N); s->cy = dalloc(N); s->area = dalloc(N); s->hcell = dalloc(N); s->dtimp = dalloc(N);
-    s->face = (orc_face *)calloc(nf, sizeof(orc_face));
+    s->face = (orc_face *)calloc((size_t)s->nf, sizeof(orc_face));
     s->cell_face = (int *)calloc(4 * N, sizeof(int));
     s->cell_sign = (int *)calloc(4 * N, sizeof(int));
+    s->nslot = (int *)calloc(N, sizeof(int));
     s->lsinv = dalloc(4 * N);
-    build_geometry(s);
+    if (unstructured) {
+        s->p.ucell_nodes = p->ucell_nodes; s->p.uedge_side = p->uedge_side;
+        int bad = build_geometry_unstructured(s);
+        s->p.ucell_nodes = NULL; s->p.uedge_side = NULL;
+        if (bad) {
+            free(s->nodes_x); free(s->nodes_y); free(s->ux); free(s->uy); free(s->w);
+            free(s->cx); free(s->cy); free(s->area); free(s->hcell); free(s->dtimp);
+            free(s->face); free(s->cell_face); free(s->cell_sign); free(s->nslot); free(s->lsinv);
+            free(s);
+            return NULL;
+        }
+    } else {
+        build_geometry(s);
+    }
+    size_t nf = s->nf;
     s->G = dalloc(NNv); s->H = dalloc(NNv); s->W = dalloc(4 * N);
     s->fbG = dalloc(NNv); s->fbH = dalloc(NNv);
     s->grG = dalloc(2 * NNv); s->grH = dalloc(2 * NNv);
@@ -471,7 +630,7 @@ void orc_destroy(orc_state *s)
                       s->limG, s->limH, s->FG, s->FH, s->phi, s->rw, s->qcell, s->tau, s->RG,
                       s->RH, s->Dm, s->dG, s->dH, s->dW, s->eqG, s->eqH};
     for (size_t i = 0; i < sizeof(arrs) / sizeof(arrs[0]); ++i) free(arrs[i]);
-    free(s->face); free(s->cell_face); free(s->cell_sign);
+    free(s->face); free(s->cell_face); free(s->cell_sign); free(s->nslot);
     free(s);
 }
 
@@ -540,7 +699,7 @@ static void ls_grad_cell(const orc_state *s, int c, const double *val, size_t st
 {
     double bx = 0, by = 0;
     double v0 = val[(size_t)c * stride + off];
-    for (int m = 0; m < 4; ++m) {
+    for (int m = 0; m < s->nslot[c]; ++m) {
         const orc_face *F = &s->face[s->cell_face[4 * c + m]];
         if (F->L < 0 || F->R < 0) continue;
         int sg = s->cell_sign[4 * c + m];
@@ -568,7 +727,7 @@ static double limiter_cell(const orc_state *s, int c, const double *val, size_t 
                            double gx, double gy)
 {
     double v0 = val[(size_t)c * stride + off], vmax = v0, vmin = v0;
-    for (int m = 0; m < 4; ++m) {
+    for (int m = 0; m < s->nslot[c]; ++m) {
         const orc_face *F = &s->face[s->cell_face[4 * c + m]];
         if (F->L < 0 || F->R < 0) continue;
         int nb = s->cell_sign[4 * c + m] > 0 ? F->R : F->L;
@@ -577,7 +736,7 @@ static double limiter_cell(const orc_state *s, int c, const double *val, size_t 
         if (v < vmin) vmin = v;
     }
     double phi = 1.0;
-    for (int m = 0; m < 4; ++m) {
+    for (int m = 0; m < s->nslot[c]; ++m) {
         const orc_face *F = &s->face[s->cell_face[4 * c + m]];
         int sg = s->cell_sign[4 * c + m];
         double rx = sg > 0 ? F->rLx : F->rRx, ry = sg > 0 ? F->rLy : F->rRy;
@@ -813,7 +972,7 @@ static void point_relaxation(orc_state *s, const double *Dd, const double *lam, 
     for (int k = 0; k < n; ++k) {
         for (int c = 0; c < N; ++c) {
             double acc[4] = {s->rw[4 * c], s->rw[4 * c + 1], s->rw[4 * c + 2], s->rw[4 * c + 3]};
-            for (int m = 0; m < 4; ++m) {
+            for (int m = 0; m < s->nslot[c]; ++m) {
                 double o[4];
                 if (!offdiag(s, lam, c, m, prev, o)) continue;
                 for (int q = 0; q < 4; ++q) acc[q] -= o[q];
@@ -835,7 +994,7 @@ static void macro_predictor(orc_state *s)
     for (int f = 0; f < s->nf; ++f) lam[f] = face_lambda(s, &s->face[f]);
     for (int c = 0; c < N; ++c) {
         double d = s->area[c] / s->dtimp[c];
-        for (int m = 0; m < 4; ++m) {
+        for (int m = 0; m < s->nslot[c]; ++m) {
             const orc_face *F = &s->face[s->cell_face[4 * c + m]];
             if (F->L == F->R) continue; /* a cell wrapped onto itself: no net term */
             d += 0.5 * om * lam[s->cell_face[4 * c + m]];
@@ -850,7 +1009,7 @@ static void macro_predictor(orc_state *s)
     /* forward sweep, lexicographic order idx = j*ni + i */
     for (int c = 0; c < N; ++c) {
         double acc[4] = {s->rw[4 * c], s->rw[4 * c + 1], s->rw[4 * c + 2], s->rw[4 * c + 3]};
-        for (int m = 0; m < 4; ++m) {
+        for (int m = 0; m < s->nslot[c]; ++m) {
             int fi = s->cell_face[4 * c + m];
             const orc_face *F = &s->face[fi];
             if (F->L < 0 || F->R < 0 || F->L == F->R) continue;
@@ -870,7 +1029,7 @@ static void macro_predictor(orc_state *s)
     /* backward sweep */
     for (int c = N - 1; c >= 0; --c) {
         double acc[4] = {0, 0, 0, 0};
-        for (int m = 0; m < 4; ++m) {
+        for (int m = 0; m < s->nslot[c]; ++m) {
             int fi = s->cell_face[4 * c + m];
             const orc_face *F = &s->face[fi];
             if (F->L < 0 || F->R < 0 || F->L == F->R) continue;
@@ -906,7 +1065,7 @@ static double idugks_iteration(orc_state *s)
     double r2 = 0.0;
     for (int c = 0; c < N; ++c) {
         double acc[4] = {0, 0, 0, 0};
-        for (int m = 0; m < 4; ++m) {
+        for (int m = 0; m < s->nslot[c]; ++m) {
             int fi = s->cell_face[4 * c + m];
             double sg = s->cell_sign[4 * c + m];
             for (int q = 0; q < 4; ++q) acc[q] -= sg * s->phi[4 * fi + q];
@@ -935,7 +1094,7 @@ static double idugks_iteration(orc_state *s)
         for (int k = 0; k < Nv; ++k) {
             size_t ck = (size_t)c * Nv + k;
             double mg = 0, mh = 0, dd = d0;
-            for (int m = 0; m < 4; ++m) {
+            for (int m = 0; m < s->nslot[c]; ++m) {
                 int fi = s->cell_face[4 * c + m];
                 const orc_face *F = &s->face[fi];
                 double sg = s->cell_sign[4 * c + m];
@@ -956,7 +1115,7 @@ static double idugks_iteration(orc_state *s)
         for (int c = 0; c < N; ++c) {
             size_t ck = (size_t)c * Nv + k;
             double ag = s->RG[ck], ah = s->RH[ck];
-            for (int m = 0; m < 4; ++m) {
+            for (int m = 0; m < s->nslot[c]; ++m) {
                 const orc_face *F = &s->face[s->cell_face[4 * c + m]];
                 if (F->L < 0 || F->R < 0 || F->L == F->R) continue;
                 int sg = s->cell_sign[4 * c + m];
@@ -974,7 +1133,7 @@ static double idugks_iteration(orc_state *s)
         for (int c = N - 1; c >= 0; --c) {
             size_t ck = (size_t)c * Nv + k;
             double ag = 0, ah = 0;
-            for (int m = 0; m < 4; ++m) {
+            for (int m = 0; m < s->nslot[c]; ++m) {
                 const orc_face *F = &s->face[s->cell_face[4 * c + m]];
                 if (F->L < 0 || F->R < 0 || F->L == F->R) continue;
                 int sg = s->cell_sign[4 * c + m];
@@ -1023,7 +1182,7 @@ void orc_explicit_step(orc_state *s, int n)
             for (int k = 0; k < Nv; ++k) {
                 size_t ck = (size_t)c * Nv + k;
                 double mg = 0, mh = 0;
-                for (int m = 0; m < 4; ++m) {
+                for (int m = 0; m < s->nslot[c]; ++m) {
                     int fi = s->cell_face[4 * c + m];
                     double sg = s->cell_sign[4 * c + m];
                     mg += sg * s->FG[(size_t)fi * Nv + k];
@@ -1049,7 +1208,7 @@ void orc_debug_predictor(orc_state *s, double *rw, double *dW)
     face_fluxes(s);
     for (int c = 0; c < N; ++c) {
         double acc[4] = {0, 0, 0, 0};
-        for (int m = 0; m < 4; ++m) {
+        for (int m = 0; m < s->nslot[c]; ++m) {
             int fi = s->cell_face[4 * c + m];
             double sg = s->cell_sign[4 * c + m];
             for (int q = 0; q < 4; ++q) acc[q] -= sg * s->phi[4 * fi + q];

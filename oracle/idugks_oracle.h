@@ -43,6 +43,12 @@ typedef struct {
     double lusgs_omega;         /* macro LU-SGS relaxation; 2 is the Eq. (30) form    */
     int relax_sweeps;           /* 0: LU-SGS predictor; n >= 1: point relaxation of   */
                                 /* the same equations, n Jacobi sweeps from dW = 0     */
+    /* unstructured mesh (used when n_ucells > 0; ni, nj are then ignored):      */
+    int n_ucells, n_unodes;     /* cells (triangles or quadrilaterals), nodes         */
+    const int *ucell_nodes;     /* [n_ucells][4] node indices counter-clockwise, -1   */
+                                /* as the 4th of a triangle; nodes_x/y hold n_unodes  */
+    const int *uedge_side;      /* [n_ucells][4] boundary group (0..3, the bc_* slot)  */
+                                /* of edge m (node m -> m+1) where it has no neighbour */
 } orc_problem;
 
 typedef struct orc_state orc_state;

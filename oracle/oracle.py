@@ -45,6 +45,8 @@ class _Problem(C.Structure):
         ("limiter", C.c_int), ("flags", C.c_int),
         ("lusgs_omega", C.c_double),
         ("relax_sweeps", C.c_int),
+        ("n_ucells", C.c_int), ("n_unodes", C.c_int),
+        ("ucell_nodes", C.POINTER(C.c_int)), ("uedge_side", C.POINTER(C.c_int)),
     ]
 
 
@@ -131,6 +133,11 @@ class Oracle:
         p.cfl_imp, p.cfl_phys = prob.cfl_imp, prob.cfl_phys
         p.limiter, p.flags, p.lusgs_omega = prob.limiter, prob.flags, prob.lusgs_omega
         p.relax_sweeps = prob.relax_sweeps
+        if getattr(prob, "cell_nodes", None) is not None:
+            self._cn = np.ascontiguousarray(prob.cell_nodes, dtype=np.int32)
+            self._es = np.ascontiguousarray(prob.edge_side, dtype=np.int32)
+            p.n_ucells, p.n_unodes = len(self._cn), len(self._nx)
+            p.ucell_nodes, p.uedge_side = _ip(self._cn), _ip(self._es)
         self._p = p
         self._h = L.orc_create(C.byref(p))
         if not self._h:

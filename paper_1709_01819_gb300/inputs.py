@@ -58,16 +58,26 @@ class Problem:
     flags: int = 0
     lusgs_omega: float = 2.0
     relax_sweeps: int = 0          # macroscopic predictor: 0 LU-SGS, n >= 1 n point-relaxation sweeps
+    # unstructured mesh (triangles and quadrilaterals): nodes_x, nodes_y are
+    # then flat node arrays, cell_nodes [ncells][4] int (counter-clockwise, -1
+    # as the 4th node of a triangle), edge_side [ncells][4] int: boundary group
+    # (0..3, the bc entry) of edge m (node m -> m+1) where it has no neighbour
+    cell_nodes: Optional[np.ndarray] = None
+    edge_side: Optional[np.ndarray] = None
     init: Tuple[float, float, float, float] = (1.0, 0.0, 0.0, 1.0)  # rho, u, v, T
     name: str = ""
 
     @property
+    def unstructured(self) -> bool:
+        return self.cell_nodes is not None
+
+    @property
     def ni(self) -> int:
-        return self.nodes_x.shape[1] - 1
+        return len(self.cell_nodes) if self.unstructured else self.nodes_x.shape[1] - 1
 
     @property
     def nj(self) -> int:
-        return self.nodes_x.shape[0] - 1
+        return 1 if self.unstructured else self.nodes_x.shape[0] - 1
 
     @property
     def ncells(self) -> int:
@@ -121,6 +131,70 @@ def ogrid_nodes(ntheta: int, nr: int, q: float = 1.05, rmax: float = 15.0):
     X = r[:, None] * cos_t[None, :]
     Y = r[:, None] * sin_t[None, :]
     return np.ascontiguousarray(X), np.ascontiguousarray(Y)
+
+
+def quads_to_unstructured(X: np.ndarray, Y: np.ndarray, tri=None, wrap_i: bool = False):
+    """Cells of a structured node block (X, Y: (nj+1, ni+1)) as an unstructured
+    mesh: nodes flattened (node (i, j) -> j (ni+1) + i; with wrap_i, column ni
+    is column 0 and i runs periodically), cell (i, j) the quad (i,j), (i+1,j),
+    (i+1,j+1), (i,j+1), or -- where tri(i, j) is true -- the two triangles
+    split along the diagonal (i,j)-(i+1,j+1).  Cells are numbered row by row
+    (quad or first triangle, then second).  Boundary edges: j = 0 -> side 2
+    (JMIN), j = nj -> 3 (JMAX), i = 0 -> 0 (IMIN), i = ni -> 1 (IMAX)."""
+    nj, ni = X.shape[0] - 1, X.shape[1] - 1
+    nc = ni if wrap_i else ni + 1
+    if wrap_i:
+        nx, ny = X[:, :ni].ravel(), Y[:, :ni].ravel()
+    else:
+        nx, ny = X.ravel(), Y.ravel()
+    node = lambda i, j: j * nc + (i % ni if wrap_i else i)
+    cells, sides = [], []
+    for j in range(nj):
+        for i in range(ni):
+            a, b, c, d = node(i, j), node(i + 1, j), node(i + 1, j + 1), node(i, j + 1)
+            south = JMIN if j == 0 else -1
+            north = JMAX if j == nj - 1 else -1
+            west = IMIN if (i == 0 and not wrap_i) else -1
+            east = IMAX if (i == ni - 1 and not wrap_i) else -1
+            if tri is not None and tri(i, j):
+                cells += [[a, b, c, -1], [a, c, d, -1]]
+                sides += [[south, east, -1, -1], [-1, north, west, -1]]
+            else:
+                cells.append([a, b, c, d])
+                sides.append([south, east, north, west])
+    return (np.ascontiguousarray(nx, dtype=np.float64), np.ascontiguousarray(ny, dtype=np.float64),
+            np.ascontiguousarray(np.array(cells, dtype=np.int32)), np.ascontiguousarray(np.array(sides, dtype=np.int32)))
+
+
+def as_unstructured(prob: Problem, tri=None, wrap_i: bool = False, name: Optional[str] = None) -> Problem:
+    """The same problem on the unstructured description of its block (see
+    quads_to_unstructured); with wrap_i the periodic i-direction becomes plain
+    connectivity and sides IMIN/IMAX are unused."""
+    import dataclasses
+
+    nx, ny, cells, sides = quads_to_unstructured(prob.nodes_x, prob.nodes_y, tri, wrap_i)
+    bc = list(prob.bc)
+    if wrap_i:
+        bc[IMIN] = bc[IMAX] = (BC_WALL, 1.0, 0.0, 0.0, 1.0)  # unused
+    return dataclasses.replace(prob, nodes_x=nx, nodes_y=ny, bc=bc, cell_nodes=cells, edge_side=sides,
+                               name=name or (prob.name + "_unstructured"))
+
+
+def tri_cavity(n: int = 16, **kw) -> Problem:
+    """The lid-driven cavity on n x n squares each split into two triangles
+    along the diagonal from its lower left to its upper right corner (2 n^2
+    cells)."""
+    prob = cavity(n, **kw)
+    return as_unstructured(prob, tri=lambda i, j: True, name=f"cavity_tri_{n}x{n}")
+
+
+def hybrid_cylinder(ntheta: int = 24, nr: int = 12, nr_quad: int = 4, **kw) -> Problem:
+    """The cylinder O-grid as a hybrid unstructured mesh: quadrilaterals in the
+    nr_quad rings next to the wall, triangles outside, the ring closed by
+    connectivity (no periodic boundary)."""
+    prob = cylinder(ntheta=ntheta, nr=nr, **kw)
+    return as_unstructured(prob, tri=lambda i, j: j >= nr_quad, wrap_i=True,
+                           name=f"cylinder_hybrid_{ntheta}x{nr}_q{nr_quad}")
 
 
 # --------------------------------------------------------------------------
@@ -221,11 +295,23 @@ def random_state(prob: Problem, seed: int, amp: float = 0.05):
     reproducible, physically sized input.
     """
     rng = np.random.default_rng(seed)
-    ni, nj = prob.ni, prob.nj
-    N = ni * nj
-    jj, ii = np.meshgrid(np.arange(nj), np.arange(ni), indexing="ij")
-    s = (ii.ravel() + 0.5) / ni
-    t = (jj.ravel() + 0.5) / nj
+    N = prob.ncells
+    if prob.unstructured:
+        # smooth in space: from the cells' node means, scaled to [0, 1]
+        cn = np.asarray(prob.cell_nodes)
+        tri = cn[:, 3] < 0
+        idx = np.where(cn < 0, cn[:, :1], cn)  # a triangle's 4th entry repeats node 0
+        Xn, Yn = np.asarray(prob.nodes_x)[idx], np.asarray(prob.nodes_y)[idx]
+        cnt = np.where(tri, 3.0, 4.0)
+        cx = (Xn.sum(axis=1) - np.where(tri, Xn[:, 3], 0.0)) / cnt
+        cy = (Yn.sum(axis=1) - np.where(tri, Yn[:, 3], 0.0)) / cnt
+        s = (cx - cx.min()) / max(np.ptp(cx), 1e-300)
+        t = (cy - cy.min()) / max(np.ptp(cy), 1e-300)
+    else:
+        ni, nj = prob.ni, prob.nj
+        jj, ii = np.meshgrid(np.arange(nj), np.arange(ni), indexing="ij")
+        s = (ii.ravel() + 0.5) / ni
+        t = (jj.ravel() + 0.5) / nj
     rho = 1.0 + 0.1 * np.sin(2 * np.pi * s) * np.cos(np.pi * t)
     u = 0.05 * np.cos(np.pi * t) + prob.init[1]
     v = 0.03 * np.sin(2 * np.pi * s)
