@@ -78,6 +78,27 @@ const char *idg_last_error(const idg_ctx *ctx);
 idg_status idg_set_mesh_structured(idg_ctx *ctx, int ni, int nj, const double *nodes_x,
                                    const double *nodes_y);
 
+/* Unstructured mesh of triangles and quadrilaterals (the hybrid meshes of
+ * Section 3), in place of a structured block.
+ *  - x, y: nnodes host float64 node coordinates.
+ *  - cell_nodes: host [ncells][4] node indices, counter-clockwise (positive
+ *    area); -1 as the 4th entry of a triangle.  Slot m of a cell is its edge
+ *    from node m to node m+1; two cells sharing an edge must run along it in
+ *    opposite directions.
+ *  - edge_side: host [ncells][4]: for a slot whose edge has no neighbour, the
+ *    boundary group 0..3 whose idg_set_boundary condition applies (a wall or
+ *    the far field; periodic is refused: close a ring by sharing its nodes);
+ *    ignored elsewhere (-1 allowed).
+ * The cell numbering is the LU-SGS order (Eq. 26, 30: lower neighbours are
+ * those of smaller index); the sweeps run level by level through it.  A cell
+ * without two neighbours in independent directions gets no least-squares
+ * gradient (first-order reconstruction).  Faces are numbered in order of first
+ * appearance (cell by cell, slot by slot).  Malformed meshes are refused at
+ * idg_bind_workspace (IDG_ERR_ARG).  Such a context cannot run idg_adjoint or
+ * join a batch (IDG_ERR_ARG).  At most 2^24 cells. */
+idg_status idg_set_mesh_unstructured(idg_ctx *ctx, int nnodes, const double *x, const double *y, int ncells,
+                                     const int *cell_nodes, const int *edge_side);
+
 /* Tensor-product discrete velocity grid (Section 2.2, closing paragraph).
  * IDG_NC_TRAP: composite trapezoid (closed 2-point Newton-Cotes) on
  * [xmin,xmax] x [ymin,ymax], any n >= 2.  IDG_NC_SIMPSON: composite Simpson,

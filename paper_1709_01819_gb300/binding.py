@@ -46,6 +46,7 @@ SIGNATURES = [
     ("idg_set_boundary", _i, [_vp, _i, _i, _d, _d, _d, _d]),
     ("idg_set_numerics", _i, [_vp, _d, _d, _i, _d, _i]),
     ("idg_set_predictor", _i, [_vp, _i]),
+    ("idg_set_mesh_unstructured", _i, [_vp, _i, _P(_d), _P(_d), _i, _P(_i), _P(_i)]),
     ("idg_workspace_size", _i, [_vp, _P(_sz)]),
     ("idg_bind_workspace", _i, [_vp, _vp, _sz]),
     ("idg_init_uniform", _i, [_vp, _d, _d, _d, _d, _vp]),
@@ -151,6 +152,16 @@ def idg_set_numerics(ctx, cfl_imp, cfl_phys, limiter, lusgs_omega, flags=0):
 
 def idg_set_predictor(ctx, relax_sweeps):
     return check(ctx, lib().idg_set_predictor(ctx, relax_sweeps))
+
+
+def idg_set_mesh_unstructured(ctx, x, y, cell_nodes, edge_side):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    cn = np.ascontiguousarray(cell_nodes, dtype=np.int32)
+    es = np.ascontiguousarray(edge_side, dtype=np.int32)
+    return check(ctx, lib().idg_set_mesh_unstructured(
+        ctx, len(x), x.ctypes.data_as(C.POINTER(C.c_double)), y.ctypes.data_as(C.POINTER(C.c_double)),
+        len(cn), cn.ctypes.data_as(C.POINTER(C.c_int)), es.ctypes.data_as(C.POINTER(C.c_int))))
 
 
 def idg_workspace_size(ctx) -> int:

@@ -24,6 +24,11 @@ struct idg_ctx {
     // problem description
     int ni = 0, nj = 0;
     std::vector<double> nodes_x, nodes_y;
+    // unstructured mesh (idg_set_mesh_unstructured): ni = cells, nj = 1
+    bool unstr = false;
+    std::vector<int> ucell, uside;                 // [N][4] nodes, boundary groups
+    std::vector<int> sched, sptr;                  // sweep schedules (see KParams)
+    int nsteps_f = 0, nsteps_b = 0, sched_pc = 0;  // steps, cells per step at most
     int vrule = -1, nvx = 0, nvy = 0;
     double vx0 = 0, vx1 = 0, vy0 = 0, vy1 = 0;
     bool gas_set = false;
@@ -205,6 +210,180 @@ bool rule_1d(int rule, int n, double a, double b, double unit, std::vector<doubl
 }
 
 // -------------------------------------------------------------------------
+// unstructured mesh of triangles and quadrilaterals
+// -------------------------------------------------------------------------
+// Faces are the edges: the first cell (in cell order) running along an edge
+// counter-clockwise is its L side (the face normal is L's outward normal),
+// the other cell R, or none on the boundary (the boundary group of that slot
+// gives the condition).  Slot m of a cell is its edge node m -> m+1; a
+// triangle's slot 3 is unused (sign 0, no neighbour, no geometry, the face
+// index of its slot 0).  Least squares over the face neighbours; a cell
+// without two neighbours in independent directions has no gradient.  The
+// sweep schedules group the cells by level in the graph of lower (forward:
+// smaller index) or upper (backward) neighbours -- the dependency order of
+// the lexicographic sweeps -- in steps of at most sched_pc cells.
+idg_status build_unstructured(idg_ctx *c, double &hmin)
+{
+    const int N = c->N;
+    const std::vector<double> &X = c->nodes_x, &Y = c->nodes_y;
+    std::vector<int> ns(N);
+    c->area.assign(N, 0);
+    c->cxc.assign(N, 0);
+    c->cyc.assign(N, 0);
+    for (int q = 0; q < N; ++q) {
+        const int *cn = &c->ucell[4 * (size_t)q];
+        ns[q] = cn[3] < 0 ? 3 : 4;
+        double a2 = 0, sx = 0, sy = 0;
+        for (int m = 0; m < ns[q]; ++m) {
+            const int a = cn[m], b = cn[(m + 1) % ns[q]];
+            if (a == b) return fail(c, IDG_ERR_ARG, "cell %d repeats node %d", q, a);
+            const double cr = X[a] * Y[b] - X[b] * Y[a];
+            a2 += cr;
+            sx += (X[a] + X[b]) * cr;
+            sy += (Y[a] + Y[b]) * cr;
+        }
+        if (!(a2 > 0)) return fail(c, IDG_ERR_ARG, "cell %d has non-positive area (nodes must run counter-clockwise)", q);
+        c->area[q] = 0.5 * a2;
+        c->cxc[q] = sx / (3.0 * a2);
+        c->cyc[q] = sy / (3.0 * a2);
+    }
+    // match the two slots of every interior edge by its sorted node pair
+    struct Edge {
+        int a, b, slot;  // slot = 4 cell + m
+    };
+    std::vector<Edge> E;
+    E.reserve(4 * (size_t)N);
+    for (int q = 0; q < N; ++q)
+        for (int m = 0; m < ns[q]; ++m) {
+            const int a = c->ucell[4 * q + m], b = c->ucell[4 * q + (m + 1) % ns[q]];
+            E.push_back({std::min(a, b), std::max(a, b), 4 * q + m});
+        }
+    std::sort(E.begin(), E.end(), [](const Edge &u, const Edge &v) {
+        return u.a != v.a ? u.a < v.a : (u.b != v.b ? u.b < v.b : u.slot < v.slot);
+    });
+    std::vector<int> partner(4 * (size_t)N, -1);
+    for (size_t i = 0; i < E.size();) {
+        size_t j = i + 1;
+        while (j < E.size() && E[j].a == E[i].a && E[j].b == E[i].b) ++j;
+        if (j - i > 2) return fail(c, IDG_ERR_ARG, "edge (%d,%d) is shared by %d cells", E[i].a, E[i].b, (int)(j - i));
+        if (j - i == 2) {
+            partner[E[i].slot] = E[i + 1].slot;
+            partner[E[i + 1].slot] = E[i].slot;
+        }
+        i = j;
+    }
+    c->cface.assign(4 * N, -1);
+    c->cnb.assign(4 * N, -1);
+    c->csign.assign(4 * N, 0);
+    c->cr.assign((size_t)8 * N, 0.0);
+    c->clsg.assign((size_t)8 * N, 0.0);
+    c->fL.clear(); c->fR.clear(); c->fbc.clear(); c->fside.clear(); c->fgeo.clear();
+    int nf = 0;
+    for (int q = 0; q < N; ++q)
+        for (int m = 0; m < ns[q]; ++m) {
+            const int sl = 4 * q + m;
+            if (c->cface[sl] >= 0) continue;
+            const int a = c->ucell[sl], b = c->ucell[4 * q + (m + 1) % ns[q]];
+            const double tx = X[b] - X[a], ty = Y[b] - Y[a], S = std::sqrt(tx * tx + ty * ty);
+            const double mx = 0.5 * (X[a] + X[b]), my = 0.5 * (Y[a] + Y[b]);
+            double g[7] = {ty / S, -tx / S, S, mx - c->cxc[q], my - c->cyc[q], 0.0, 0.0};
+            int R = -1, bc = -1, side = -1;
+            const int pr = partner[sl];
+            if (pr >= 0) {
+                const int q2 = pr / 4, m2 = pr % 4;
+                if (c->ucell[pr] != b || c->ucell[4 * q2 + (m2 + 1) % ns[q2]] != a)
+                    return fail(c, IDG_ERR_ARG, "cells %d and %d run along edge (%d,%d) the same way", q, q2, a, b);
+                R = q2;
+                g[5] = mx - c->cxc[q2];
+                g[6] = my - c->cyc[q2];
+                c->cface[pr] = nf;
+                c->csign[pr] = -1;
+                c->cnb[pr] = q;
+                c->cnb[sl] = q2;
+            } else {
+                side = c->uside[sl];
+                if (side < 0 || c->bc_kind[side] == IDG_BC_PERIODIC)
+                    return fail(c, IDG_ERR_ARG, "boundary edge (%d,%d) of cell %d needs a wall or far-field group, has %d", a, b, q, side);
+                bc = c->bc_kind[side];
+            }
+            c->cface[sl] = nf;
+            c->csign[sl] = +1;
+            c->fL.push_back(q);
+            c->fR.push_back(R);
+            c->fbc.push_back(bc);
+            c->fside.push_back(side);
+            c->fgeo.insert(c->fgeo.end(), g, g + 7);
+            ++nf;
+        }
+    c->nf = nf;
+    c->hcell.assign(N, 0.0);
+    c->dtimp.assign(N, 0.0);
+    for (int q = 0; q < N; ++q) {
+        if (ns[q] == 3) c->cface[4 * q + 3] = c->cface[4 * q];
+        double smax = 0, a11 = 0, a12 = 0, a22 = 0, d[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+        for (int m = 0; m < ns[q]; ++m) {
+            const int fi = c->cface[4 * q + m];
+            const double *g = &c->fgeo[(size_t)7 * fi];
+            const bool own_L = c->csign[4 * q + m] > 0;
+            c->cr[8 * q + 2 * m] = own_L ? g[3] : g[5];
+            c->cr[8 * q + 2 * m + 1] = own_L ? g[4] : g[6];
+            smax = std::max(smax, g[2]);
+            if (c->cnb[4 * q + m] < 0) continue;
+            d[m][0] = own_L ? g[3] - g[5] : g[5] - g[3];
+            d[m][1] = own_L ? g[4] - g[6] : g[6] - g[4];
+            a11 += d[m][0] * d[m][0];
+            a12 += d[m][0] * d[m][1];
+            a22 += d[m][1] * d[m][1];
+        }
+        const double det = a11 * a22 - a12 * a12;
+        if (det > 1e-10 * (a11 + a22) * (a11 + a22))
+            for (int m = 0; m < ns[q]; ++m) {
+                if (c->cnb[4 * q + m] < 0) continue;
+                c->clsg[8 * q + 2 * m] = (a22 * d[m][0] - a12 * d[m][1]) / det;
+                c->clsg[8 * q + 2 * m + 1] = (-a12 * d[m][0] + a11 * d[m][1]) / det;
+            }
+        c->hcell[q] = c->area[q] / smax;
+        hmin = std::min(hmin, c->hcell[q]);
+    }
+    // sweep schedules
+    std::vector<int> lev(N);
+    int maxlevel = 0;
+    std::vector<std::vector<int>> levels[2];
+    for (int dir = 0; dir < 2; ++dir) {
+        int nl = 0;
+        for (int k = 0; k < N; ++k) {
+            const int q = dir == 0 ? k : N - 1 - k;
+            int l = 0;
+            for (int m = 0; m < 4; ++m) {
+                const int nb = c->cnb[4 * q + m];
+                if (nb >= 0 && nb != q && (dir == 0 ? nb < q : nb > q)) l = std::max(l, lev[nb] + 1);
+            }
+            lev[q] = l;
+            nl = std::max(nl, l + 1);
+        }
+        levels[dir].assign(nl, {});
+        for (int q = 0; q < N; ++q) levels[dir][lev[q]].push_back(q);
+        for (auto &lv : levels[dir]) maxlevel = std::max(maxlevel, (int)lv.size());
+    }
+    c->sched_pc = std::min(maxlevel, 128);
+    c->sched.clear();
+    c->sptr.clear();
+    for (int dir = 0; dir < 2; ++dir) {
+        int steps = 0;
+        c->sptr.push_back(0);
+        const int base = (int)c->sched.size();
+        for (auto &lv : levels[dir])
+            for (size_t o = 0; o < lv.size(); o += c->sched_pc) {
+                for (size_t x = o; x < std::min(lv.size(), o + c->sched_pc); ++x) c->sched.push_back(lv[x]);
+                c->sptr.push_back((int)c->sched.size() - base);
+                ++steps;
+            }
+        (dir == 0 ? c->nsteps_f : c->nsteps_b) = steps;
+    }
+    return IDG_OK;
+}
+
+// -------------------------------------------------------------------------
 // structured block geometry (Fig. 1, Section 2.3)
 // -------------------------------------------------------------------------
 idg_status build(idg_ctx *c)
@@ -215,9 +394,9 @@ idg_status build(idg_ctx *c)
     if (!c->gas_set) return fail(c, IDG_ERR_STATE, "gas not set");
     for (int s = 0; s < 4; ++s)
         if (c->bc_kind[s] < 0) return fail(c, IDG_ERR_STATE, "boundary of side %d not set", s);
-    const bool per_i = c->bc_kind[IDG_IMIN] == IDG_BC_PERIODIC;
-    const bool per_j = c->bc_kind[IDG_JMIN] == IDG_BC_PERIODIC;
-    if (per_i != (c->bc_kind[IDG_IMAX] == IDG_BC_PERIODIC) || per_j != (c->bc_kind[IDG_JMAX] == IDG_BC_PERIODIC))
+    const bool per_i = !c->unstr && c->bc_kind[IDG_IMIN] == IDG_BC_PERIODIC;
+    const bool per_j = !c->unstr && c->bc_kind[IDG_JMIN] == IDG_BC_PERIODIC;
+    if (!c->unstr && (per_i != (c->bc_kind[IDG_IMAX] == IDG_BC_PERIODIC) || per_j != (c->bc_kind[IDG_JMAX] == IDG_BC_PERIODIC)))
         return fail(c, IDG_ERR_ARG, "a periodic direction needs IDG_BC_PERIODIC on both sides");
     const int ni = c->ni, nj = c->nj;
     c->N = ni * nj;
@@ -241,6 +420,11 @@ idg_status build(idg_ctx *c)
             c->w[k] = w1[kx] * v1[ky];
             c->xi_max = std::max(c->xi_max, std::sqrt(x1[kx] * x1[kx] + y1[ky] * y1[ky]));
         }
+    double hmin = 1e300;
+    if (c->unstr) {
+        idg_status su = build_unstructured(c, hmin);
+        if (su) return su;
+    } else {
     auto X = [&](int i, int j) { return c->nodes_x[(size_t)j * (ni + 1) + i]; };
     auto Y = [&](int i, int j) { return c->nodes_y[(size_t)j * (ni + 1) + i]; };
     // cells: shoelace area and polygon centroid
@@ -326,7 +510,6 @@ idg_status build(idg_ctx *c)
     c->clsg.assign((size_t)8 * c->N, 0.0);
     c->hcell.assign(c->N, 0.0);
     c->dtimp.assign(c->N, 0.0);
-    double hmin = 1e300;
     for (int j = 0; j < nj; ++j)
         for (int i = 0; i < ni; ++i) {
             int cc = j * ni + i;
@@ -365,6 +548,7 @@ idg_status build(idg_ctx *c)
             c->hcell[cc] = c->area[cc] / smax;
             hmin = std::min(hmin, c->hcell[cc]);
         }
+    }
     c->dt = c->cfl_phys * hmin / c->xi_max;
     for (int q = 0; q < c->N; ++q) c->dtimp[q] = c->cfl_imp * c->hcell[q] / c->xi_max;
     const double om = c->omega;
@@ -405,6 +589,8 @@ size_t layout(idg_ctx *c, char *base, KParams *kp)
     k.clsgT = L.take<char>(8 * ts * N);
     k.cslotT = L.take<char>(8 * ts * N);
     k.scode = L.take<int>(32 * N);
+    k.sched = c->unstr ? L.take<int>(4 * c->sched.size()) : nullptr;
+    k.sptr = c->unstr ? L.take<int>(4 * c->sptr.size()) : nullptr;
     k.fL = L.take<int>(4 * nf);
     k.fR = L.take<int>(4 * nf);
     k.fgeo = L.take<double>(56 * nf);
@@ -696,8 +882,40 @@ idg_status idg_set_mesh_structured(idg_ctx *c, int ni, int nj, const double *nod
             return fail(c, IDG_ERR_ARG, "non-finite node coordinate at %zu", q);
     c->ni = ni;
     c->nj = nj;
+    c->unstr = false;
+    c->ucell.clear();
+    c->uside.clear();
     c->nodes_x.assign(nodes_x, nodes_x + nn);
     c->nodes_y.assign(nodes_y, nodes_y + nn);
+    c->built = false;
+    return IDG_OK;
+}
+
+idg_status idg_set_mesh_unstructured(idg_ctx *c, int nnodes, const double *x, const double *y, int ncells,
+                                     const int *cell_nodes, const int *edge_side)
+{
+    if (!c) return IDG_ERR_ARG;
+    if (c->bound) return fail(c, IDG_ERR_STATE, "setters are closed after idg_bind_workspace");
+    if (nnodes < 3 || ncells < 1 || ncells > (1 << 24) || !x || !y || !cell_nodes || !edge_side)
+        return fail(c, IDG_ERR_ARG, "invalid unstructured mesh sizes (%d nodes, %d cells) or null arrays", nnodes, ncells);
+    for (int q = 0; q < nnodes; ++q)
+        if (!std::isfinite(x[q]) || !std::isfinite(y[q])) return fail(c, IDG_ERR_ARG, "non-finite node coordinate at %d", q);
+    for (int q = 0; q < ncells; ++q) {
+        for (int m = 0; m < 4; ++m) {
+            const int nd = cell_nodes[4 * q + m];
+            if (nd >= nnodes || (nd < 0 && m < 3) || (nd < 0 && nd != -1))
+                return fail(c, IDG_ERR_ARG, "cell %d: node %d of slot %d invalid", q, nd, m);
+            const int sd = edge_side[4 * q + m];
+            if (sd < -1 || sd > 3) return fail(c, IDG_ERR_ARG, "cell %d: boundary group %d of slot %d invalid", q, sd, m);
+        }
+    }
+    c->unstr = true;
+    c->ni = ncells;
+    c->nj = 1;
+    c->nodes_x.assign(x, x + nnodes);
+    c->nodes_y.assign(y, y + nnodes);
+    c->ucell.assign(cell_nodes, cell_nodes + 4 * (size_t)ncells);
+    c->uside.assign(edge_side, edge_side + 4 * (size_t)ncells);
     c->built = false;
     return IDG_OK;
 }
@@ -843,10 +1061,16 @@ idg_status idg_bind_workspace(idg_ctx *c, void *dev_ptr, size_t bytes)
     k.dt = c->dt; k.h = 0.5 * c->dt; k.mu_ref = c->mu_ref; k.RT_ref = c->RT_ref; k.omega = c->omega;
     k.Pr = c->Pr; k.gam = (double)(c->K + 4) / (double)(c->K + 2); k.lusgs_omega = c->lusgs_omega;
     k.relax_sweeps = c->relax_sweeps;
+    if (c->unstr) {
+        k.per_i = k.per_j = 0;
+        k.nsteps_f = c->nsteps_f;
+        k.nsteps_b = c->nsteps_b;
+    }
     // sweep launch shape: cell slots cover the longest hyperplane up to 64
-    // micro sweeps: one thread per cell of the longest hyperplane and tv
-    // velocities per CTA (8 by default, more on very narrow blocks)
-    int maxlen = std::min(c->ni, c->nj);
+    // micro sweeps: one thread per cell of the longest hyperplane (of the
+    // longest schedule step on an unstructured mesh) and tv velocities per
+    // CTA (8 by default, more on very narrow blocks)
+    int maxlen = c->unstr ? c->sched_pc : std::min(c->ni, c->nj);
     if (maxlen > 256) return fail(c, IDG_ERR_ARG, "min(ni, nj) = %d exceeds 256", maxlen);
     k.sweep_pc = maxlen;
     k.sweep_vpt = 1;
@@ -874,8 +1098,12 @@ idg_status idg_bind_workspace(idg_ctx *c, void *dev_ptr, size_t bytes)
                 int code = -2;
                 if (nb == q) code = -3;
                 else if (nb >= 0 && (dir > 0 ? nb < q : nb > q)) {
-                    const int nbi = nb % c->ni, dp = d - dir;
-                    code = nbi + nb / c->ni == dp ? nbi - std::max(0, dp - (c->nj - 1)) : -4 - nb;
+                    if (c->unstr) {
+                        code = -4 - nb;  // scheduled sweeps read every neighbour from global memory
+                    } else {
+                        const int nbi = nb % c->ni, dp = d - dir;
+                        code = nbi + nb / c->ni == dp ? nbi - std::max(0, dp - (c->nj - 1)) : -4 - nb;
+                    }
                 }
                 scode[o + 4 * q + m] = code;
             }
@@ -898,7 +1126,8 @@ idg_status idg_bind_workspace(idg_ctx *c, void *dev_ptr, size_t bytes)
         up((int *)k.fbc, c->fbc), up((int *)k.fside, c->fside),
         up((double *)k.ux, c->ux), up((double *)k.uy, c->uy), up((double *)k.w, c->w),
         up((float *)k.uxf, uxf), up((float *)k.uyf, uyf), up((float *)k.wf, wf),
-        cudaMemset(k.iter, 0, 256), cudaMemset(k.phi, 0, 32 * (size_t)c->nf)};
+        cudaMemset(k.iter, 0, 256), cudaMemset(k.phi, 0, 32 * (size_t)c->nf),
+        c->unstr ? up((int *)k.sched, c->sched) : cudaSuccess, c->unstr ? up((int *)k.sptr, c->sptr) : cudaSuccess};
     for (cudaError_t x : errs)
         if (x != cudaSuccess) return cuda_fail(c, x, "workspace upload");
     int rcfg = idg::configure_kernels(c->precision == IDG_FP64);
@@ -1363,6 +1592,7 @@ idg_status idg_batch_create(idg_batch **out, idg_ctx *const *ctxs, int n)
         if (ctxs[i]->precision != ctxs[0]->precision || ctxs[i]->device != ctxs[0]->device) return IDG_ERR_ARG;
         if (ctxs[i]->flags & IDG_NUM_EXPLICIT) return IDG_ERR_ARG;  // batches run IDUGKS iterations
         if (ctxs[i]->relax_sweeps != ctxs[0]->relax_sweeps) return IDG_ERR_ARG;  // one predictor per batch
+        if (ctxs[i]->unstr) return IDG_ERR_ARG;  // batches hold structured blocks
         for (int j = 0; j < i; ++j)
             if (ctxs[j] == ctxs[i]) return IDG_ERR_ARG;
     }
@@ -1565,6 +1795,7 @@ idg_status idg_adjoint(idg_ctx *c, int objective, int side_mask, const int *para
     }
     if (c->flags) return fail(c, IDG_ERR_ARG, "the adjoint does not support numerics flags 0x%x", c->flags);
     if (c->relax_sweeps) return fail(c, IDG_ERR_ARG, "the adjoint transposes the LU-SGS predictor only");
+    if (c->unstr) return fail(c, IDG_ERR_ARG, "the adjoint runs on structured blocks only");
     if (max_iter < 1 || max_iter > idg::kMaxHist) return fail(c, IDG_ERR_ARG, "max_iter out of [1, %d]", idg::kMaxHist);
     if (!workspace) return fail(c, IDG_ERR_ARG, "null adjoint workspace");
     if (((uintptr_t)workspace) & 255) return fail(c, IDG_ERR_ARG, "adjoint workspace must be 256-byte aligned");

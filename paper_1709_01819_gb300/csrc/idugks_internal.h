@@ -82,6 +82,13 @@ struct KParams {
     int sweep_tv, sweep_pc, sweep_stages, macro_stages;
     int sweep_vpt;  // consecutive velocities per thread in the micro sweeps (1, 2, 4)
     int relax_sweeps;  // macroscopic predictor: 0 LU-SGS, n >= 1 n point-relaxation sweeps
+    // unstructured meshes: the sweeps' schedule (null on a structured block,
+    // whose sweeps walk the i+j hyperplanes): sched [2][N] cells in processing
+    // order for the forward then the backward sweep, sptr the step offsets
+    // into each ([nsteps_f + 1] then [nsteps_b + 1]); the cells of one step
+    // depend on none of each other
+    const int *sched, *sptr;
+    int nsteps_f, nsteps_b;
 };
 
 // kernels of one iteration, in launch order
@@ -105,6 +112,7 @@ struct Plan {
     int macro_stages, sweep_stages, limiter_any, sweep_vpt;
     int explicit_dugks;  // 1: launch_iteration runs one explicit DUGKS step (Eq. 21)
     int relax_sweeps;    // macroscopic predictor of every instance (KParams::relax_sweeps)
+    int sched;           // 1: the instances are unstructured (scheduled sweeps)
 };
 
 // kernel launchers (idugks_kernels.cu)

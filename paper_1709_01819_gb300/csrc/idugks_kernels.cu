@@ -1222,8 +1222,8 @@ __global__ void __launch_bounds__(32) k_macro_pre(Launch L)
         for (int m = 0; m < 4; ++m) {
             int fi = p.cface[4 * c + m];
             double lam = face_lambda_t<T>(p, fi);
-            if (p.fL[fi] != p.fR[fi]) d += 0.5 * p.lusgs_omega * lam;
-            double s = p.csign[4 * c + m];
+            double s = p.csign[4 * c + m];  // 0: a triangle's unused slot
+            if (s != 0.0 && p.fL[fi] != p.fR[fi]) d += 0.5 * p.lusgs_omega * lam;
             const double *g = p.fgeo + 7 * fi;
             T *o = rec + 12 + 3 * m;
             o[0] = (T)(0.5 * g[2] * s * g[0]);
@@ -1400,6 +1400,55 @@ __global__ void __launch_bounds__(512) k_macro_sweep(Launch L)
         __syncthreads();
     }
     if (tid == 0) *p.iter += 1;
+}
+
+// The macroscopic LU-SGS sweeps on an unstructured mesh: one CTA walks the
+// steps of the forward, then the backward schedule (the lower- and
+// upper-neighbour levels of the cell numbering), a thread per cell of a step,
+// every neighbour's increment and base state read from global memory (the
+// block barrier between steps orders them); the same equations and cell
+// order as k_macro_sweep.
+template <class T>
+__global__ void __launch_bounds__(256) k_macro_sweep_sched(Launch L)
+{
+    IDG_LOCATE();
+    (void)blk;
+    if (threadIdx.x == 0) record_residual(p);
+    const T gm1 = (T)(p.gam - 1.0);
+    T *dWg = (T *)p.mdW;
+    const T *mrec = (const T *)p.mrec;
+    for (int dir = 1; dir >= -1; dir -= 2) {
+        const int *sc = p.sched + (dir > 0 ? 0 : (size_t)p.N);
+        const int *sp = p.sptr + (dir > 0 ? 0 : p.nsteps_f + 1);
+        const int ns = dir > 0 ? p.nsteps_f : p.nsteps_b;
+        for (int st = 0; st < ns; ++st) {
+            __syncthreads();
+            for (int x = sp[st] + threadIdx.x; x < sp[st + 1]; x += blockDim.x) {
+                const int c = sc[x];
+                const T *rec = mrec + (size_t)kMRec * c;
+                T acc[4] = {0, 0, 0, 0};
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    const int nb = p.cnb[4 * c + m];
+                    if (nb < 0 || nb == c || !(dir > 0 ? nb < c : nb > c)) continue;
+                    const T *x4 = dWg + 4 * (size_t)nb;
+                    const T dn[4] = {x4[0], x4[1], x4[2], x4[3]};
+                    const T *cf = rec + 12 + 3 * m;
+                    T dF[4];
+                    euler_dflux<T>(gm1, mrec + (size_t)kMRec * nb + 6, dn, cf[0], cf[1], dF);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc[q] += dF[q] - cf[2] * dn[q];
+                }
+                // forward: dW*_c = (R_c - sum_lower) / D_c;  backward: dW_c = dW*_c - sum_upper / D_c
+                const T iD = rec[4];
+                T *o = dWg + 4 * (size_t)c;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) o[q] = dir > 0 ? (rec[q] - acc[q]) * iD : o[q] - acc[q] * iD;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *p.iter += 1;
 }
 
 template <class T>
@@ -1695,7 +1744,21 @@ struct SweepArgs {
     void *dst, *f;
     const void *cslotT, *cellpT;
     const int *codes;  // this sweep's [N][4] slot codes
+    const int *sched, *sptr;  // this sweep's schedule (unstructured) or null
+    int nsteps;               // steps of the sweep
 };
+
+// the cell of slot `slot` at step d (a hyperplane i + j = d on a structured
+// block, the d-th step of the schedule otherwise), -1 past the step's end
+__device__ __forceinline__ int sweep_cell(const SweepArgs &p, int d, int slot)
+{
+    if (p.sched) {
+        const int b = p.sptr[d];
+        return slot < p.sptr[d + 1] - b ? p.sched[b + slot] : -1;
+    }
+    const int ilo = max(0, d - (p.nj - 1)), ihi = min(p.ni - 1, d), i = ilo + slot;
+    return i <= ihi ? (d - i) * p.ni + i : -1;
+}
 
 // asynchronous copy of one step's data for the thread's cell: its VPT
 // consecutive velocities of R (or Delta*, f~), and the cell's slot geometry
@@ -1705,13 +1768,10 @@ __device__ __forceinline__ void sweep_issue(const SweepArgs &p, const SweepSmem<
                                             int slot, int t, int k0, bool act, bool withF)
 {
     using T2 = typename V2<T>::t;
-    const int ni = p.ni, nj = p.nj, tv = p.tv, pc = p.pc;
-    const int nh = ni + nj - 1;
-    if (s < nh) {
-        int ilo = max(0, d - (nj - 1)), ihi = min(ni - 1, d);
-        int i = ilo + slot;
-        if (i <= ihi) {
-            int c = (d - i) * ni + i;
+    const int tv = p.tv, pc = p.pc;
+    if (s < p.nsteps) {
+        const int c = sweep_cell(p, d, slot);
+        if (c >= 0) {
             int st = s & (kStages - 1);
             size_t e = ((size_t)st * pc + slot);
             if (act) {
@@ -1747,7 +1807,10 @@ __global__ void __launch_bounds__(512) k_sweep(Launch L)
     using T2 = typename V2<T>::t;
     extern __shared__ __align__(16) unsigned char smraw[];
     const SweepArgs a{p.Nv, p.ni, p.nj, p.sweep_tv, p.sweep_pc, p.dst, p.f, p.cslotT, p.cellpT,
-                      p.scode + (FWD ? 0 : 4 * (size_t)p.N)};
+                      p.scode + (FWD ? 0 : 4 * (size_t)p.N),
+                      p.sched ? p.sched + (FWD ? 0 : (size_t)p.N) : nullptr,
+                      p.sched ? p.sptr + (FWD ? 0 : p.nsteps_f + 1) : nullptr,
+                      p.sched ? (FWD ? p.nsteps_f : p.nsteps_b) : p.ni + p.nj - 1};
     const int tv = a.tv, pc = a.pc, ni = a.ni, nj = a.nj, Nv = a.Nv;
     const bool per_i = p.per_i, per_j = p.per_j;
     const SweepSmem<T, kStages, VPT> sm(smraw, pc, tv, !FWD);
@@ -1763,20 +1826,18 @@ __global__ void __launch_bounds__(512) k_sweep(Launch L)
     }
     T2 *ds = (T2 *)a.dst;
     T2 *f = (T2 *)a.f;
-    const int nh = ni + nj - 1;
-    const int dir = FWD ? 1 : -1;
+    const int nh = a.nsteps;
     const size_t w = (size_t)tv * VPT;
-    auto step_d = [&](int s) { return FWD ? s : nh - 1 - s; };
+    // a schedule lists the backward sweep's steps in processing order
+    auto step_d = [&](int s) { return (FWD || a.sched) ? s : nh - 1 - s; };
     for (int s = 0; s < kStages - 1; ++s) sweep_issue<T, kStages, VPT>(a, sm, s, step_d(s), slot, t, k0, act, !FWD);
     for (int s = 0; s < nh; ++s) {
         cp_wait<kStages - 2>();
         __syncthreads();
         sweep_issue<T, kStages, VPT>(a, sm, s + kStages - 1, step_d(s + kStages - 1), slot, t, k0, act, !FWD);
-        const int d = step_d(s);
-        const int ilo = max(0, d - (nj - 1)), ihi = min(ni - 1, d);
-        const int i = ilo + slot, j = d - i;
-        if (i > ihi || !act) continue;
-        const int c = j * ni + i;
+        const int c = sweep_cell(a, step_d(s), slot);
+        if (c < 0 || !act) continue;
+        const int i = c % ni, j = c / ni;
         const size_t e = (size_t)(s & (kStages - 1)) * pc + slot;
         T g[8];
         load8<T>(g, sm.geo + e * 8);
@@ -1789,7 +1850,7 @@ __global__ void __launch_bounds__(512) k_sweep(Launch L)
         // the backward sweep's increments are read back from global memory
         // only across a periodic seam (the first and last cells of a periodic
         // direction); elsewhere only f and the ring take them
-        const bool keep = FWD || (per_i && (i == 0 || i == ni - 1)) || (per_j && (j == 0 || j == nj - 1));
+        const bool keep = FWD || a.sched || (per_i && (i == 0 || i == ni - 1)) || (per_j && (j == 0 || j == nj - 1));
         // the step of one cell; SEAM: some neighbour lies across a periodic
         // seam (read from global memory), otherwise every inflow comes from
         // the ring
@@ -1968,7 +2029,9 @@ int plan_shapes(const KParams *hp, int n, bool fp64, Plan &pl)
     pl.limiter_any = 0;
     pl.sweep_vpt = hp[0].sweep_vpt;
     pl.relax_sweeps = hp[0].relax_sweeps;
+    pl.sched = hp[0].sched != nullptr;
     for (int i = 0; i < n; ++i) {
+        if ((hp[i].sched != nullptr) != (pl.sched != 0)) return (int)cudaErrorInvalidValue;
         if (hp[i].relax_sweeps != pl.relax_sweeps) return (int)cudaErrorInvalidValue;
         pl.macro_threads = std::max(pl.macro_threads, macro_threads(hp[i]));
         pl.sweep_threads = std::max(pl.sweep_threads, hp[i].sweep_tv * hp[i].sweep_pc);
@@ -2079,7 +2142,9 @@ static int iteration_t(const Plan &pl, cudaStream_t st, void **events)
         k_record_residual<T><<<nb[KT_MACRO_SWEEP], 32, 0, st>>>(L(KT_MACRO_SWEEP));
         for (int k = 1; k <= pl.relax_sweeps; ++k)
             k_macro_relax<T><<<nb[KT_MACRO_PRE], 32, 0, st>>>(L(KT_MACRO_PRE), k, pl.relax_sweeps);
-    } else if (pl.macro_stages == 8)
+    } else if (pl.sched)
+        k_macro_sweep_sched<T><<<nb[KT_MACRO_SWEEP], 256, 0, st>>>(L(KT_MACRO_SWEEP));
+    else if (pl.macro_stages == 8)
         k_macro_sweep<T, 8><<<nb[KT_MACRO_SWEEP], pl.macro_threads, pl.macro_smem, st>>>(L(KT_MACRO_SWEEP));
     else
         k_macro_sweep<T, 4><<<nb[KT_MACRO_SWEEP], pl.macro_threads, pl.macro_smem, st>>>(L(KT_MACRO_SWEEP));

@@ -16,7 +16,10 @@ def configure(ctx, prob: Problem, explicit: bool = False):
     explicit: the context advances explicit DUGKS steps (IDG_NUM_EXPLICIT)."""
     if prob.flags:
         raise ValueError("Problem.flags selects oracle-only options; the library takes none")
-    B.idg_set_mesh_structured(ctx, prob.nodes_x, prob.nodes_y)
+    if prob.unstructured:
+        B.idg_set_mesh_unstructured(ctx, prob.nodes_x, prob.nodes_y, prob.cell_nodes, prob.edge_side)
+    else:
+        B.idg_set_mesh_structured(ctx, prob.nodes_x, prob.nodes_y)
     x0, x1, y0, y1 = prob.vrange
     B.idg_set_velocity_grid(ctx, prob.vrule, prob.nvx, prob.nvy, x0, x1, y0, y1)
     B.idg_set_gas(ctx, prob.K, prob.Pr, prob.omega, prob.Kn, prob.RT_ref,

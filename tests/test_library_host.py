@@ -131,3 +131,37 @@ def test_host_setup_agrees_with_oracle(case):
     assert abs(B.idg_get_dt(ctx) - o.dt) <= 1e-14 * o.dt
     assert B.idg_workspace_size(ctx) > 0
     B.idg_destroy(ctx)
+
+
+def test_unstructured_mesh_host_checks_and_sizes():
+    """Host-side: the setter refuses bad indices; the builder (run by
+    idg_workspace_size) refuses a clockwise cell and an edge shared three
+    times, and finds the oracle's face count on a triangle mesh."""
+    import dataclasses
+
+    from oracle import oracle as O
+    from paper_1709_01819_gb300 import binding as B
+    from paper_1709_01819_gb300 import inputs as I
+    from paper_1709_01819_gb300.solver import configure
+
+    prob = I.tri_cavity(5, nv=4)
+
+    def sizes(p):
+        ctx = B.idg_create(B.IDG_MIXED, 0)
+        try:
+            configure(ctx, p)
+            B.idg_workspace_size(ctx)
+            return B.idg_get_sizes(ctx)
+        finally:
+            B.idg_destroy(ctx)
+
+    N, Nv, nf = sizes(prob)
+    assert (N, nf) == (O.Oracle(prob).N, O.Oracle(prob).nf) == (50, 85)
+    bad = prob.cell_nodes.copy()
+    bad[3, :3] = bad[3, 2::-1]
+    with pytest.raises(B.IdgError):
+        sizes(dataclasses.replace(prob, cell_nodes=bad))
+    bad = prob.cell_nodes.copy()
+    bad[0, 1] = 10_000
+    with pytest.raises(B.IdgError):
+        sizes(dataclasses.replace(prob, cell_nodes=bad))
