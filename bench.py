@@ -53,6 +53,15 @@ def workload(name: str) -> I.Problem:
         return I.cavity_c3()
     if name == "cylinder":
         return I.cylinder_c5()
+    if name == "cavity64_tri":
+        # the 64x64 cavity with every square split into two triangles (8192 cells);
+        # implicit CFL 10: on these triangles the iteration diverges at 30 and
+        # above (the oracle's as the library's)
+        return I.tri_cavity(64, Kn=0.075, U=0.15, nv=32, vmax=4.0, cfl_imp=10.0)
+    if name == "cylinder_hybrid":
+        # the 121x81 cylinder as a hybrid mesh: quadrilaterals in the 41 rings next
+        # to the wall, triangles outside (14641 cells), the ring closed by connectivity
+        return I.hybrid_cylinder(ntheta=121, nr=81, nr_quad=41, cfl_imp=30.0)
     if name == "cylinder61x41":
         # the cylinder at a quarter of the cells (same velocities, f 158 MB):
         # the size for full ncu captures of its kernels
@@ -206,7 +215,7 @@ def _cpu_worker(name, budget_s, q):
 
 
 def workload_by_name(name):
-    for w in ("cavity64", "couette64", "cavity128", "cylinder", "cylinder61x41"):
+    for w in ("cavity64", "couette64", "cavity128", "cylinder", "cylinder61x41", "cavity64_tri", "cylinder_hybrid"):
         p = workload(w)
         if p.name == name:
             return p

@@ -612,7 +612,10 @@ size_t layout(idg_ctx *c, char *base, KParams *kp)
     k.fbp = L.take<char>(t2 * N * Nv);
     k.grad = c->limiter ? L.take<char>(4 * ts * N * Nv) : nullptr;
     k.dst = L.take<char>(t2 * N * Nv);
-    k.F = L.take<char>(t2 * nf * Nv);
+    // the face-flux buffer doubles as the float64 staging area of
+    // idg_set_state / idg_get_state (G and H of every cell): on an unstructured
+    // mesh (about 1.5 faces per cell for triangles) that can be the larger need
+    k.F = L.take<char>(std::max(t2 * nf * Nv, 16 * N * Nv));
     k.W = L.take<double>(32 * N);
     k.cellraw = L.take<char>(8 * idg::kRaw * N);
     k.cellA = L.take<char>(ts * idg::kCellP * N);
@@ -1133,7 +1136,7 @@ idg_status idg_bind_workspace(idg_ctx *c, void *dev_ptr, size_t bytes)
     int rcfg = idg::configure_kernels(c->precision == IDG_FP64);
     if (rcfg) return cuda_fail(c, (cudaError_t)rcfg, "configure kernels");
     c->stage = (double *)k.F;
-    c->stage_bytes = (c->precision == IDG_FP64 ? 16 : 8) * (size_t)c->nf * c->Nv;
+    c->stage_bytes = std::max((c->precision == IDG_FP64 ? 16 : 8) * (size_t)c->nf * c->Nv, 16 * (size_t)c->N * c->Nv);
     c->bound = true;
     idg_status st = upload_reference(c);
     if (!st) st = refresh_plan(c);
@@ -1203,6 +1206,7 @@ idg_status idg_get_state(idg_ctx *c, double *G, double *H, double *W, void *stre
     size_t n = (size_t)c->N * c->Nvu;
     cudaError_t e;
     double *dG = c->stage, *dH = c->stage + n;
+    if (2 * n * sizeof(double) > c->stage_bytes) return fail(c, IDG_ERR_STATE, "staging buffer too small");
     if (G || H) {
         int rc = idg::launch_from_dev(c->kp, c->precision == IDG_FP64, dG, dH, c->Nvu, st);
         if (rc) return cuda_fail(c, (cudaError_t)rc, "from_dev");
