@@ -37,7 +37,16 @@
 //                    flux moments
 //   k_face_phi       thread per face: Phi_f = sum_k w psi F_k (Eq. 27)
 //   k_macro_pre, k_macro_sweep, k_macro_post: macroscopic LU-SGS          [a5]
-//   k_sweep_fwd, k_sweep_bwd: micro LU-SGS sweeps and update           [a6-a7]
+//                    (k_macro_sweep_sched on an unstructured mesh; with the
+//                    point-relaxation predictor k_record_residual and n
+//                    launches of k_macro_relax in place of the sweep)
+//   k_micro_residual, k_sweep_fwd, k_sweep_bwd: micro LU-SGS sweeps and
+//                    update (hyperplanes on a structured block, level
+//                    schedules on an unstructured mesh)              [a6-a7]
+// Explicit DUGKS (Eq. 21) runs the cell and face kernels, then
+// k_explicit_update, k_cell_moments, k_explicit_w and k_record_residual.
+// Data are laid out per cell in four face slots (a triangle's fourth slot is
+// unused: sign 0, no neighbour, no geometry).
 #include "idugks_internal.h"
 
 #include <cuda_runtime.h>
