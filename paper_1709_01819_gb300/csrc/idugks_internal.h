@@ -113,6 +113,7 @@ struct Plan {
     int explicit_dugks;  // 1: launch_iteration runs one explicit DUGKS step (Eq. 21)
     int relax_sweeps;    // macroscopic predictor of every instance (KParams::relax_sweeps)
     int sched;           // 1: the instances are unstructured (scheduled sweeps)
+    size_t sched_smem;   // shared memory of the scheduled macroscopic sweep (0: increments in global memory)
 };
 
 // kernel launchers (idugks_kernels.cu)

@@ -1413,50 +1413,88 @@ __global__ void __launch_bounds__(512) k_macro_sweep(Launch L)
 
 // The macroscopic LU-SGS sweeps on an unstructured mesh: one CTA walks the
 // steps of the forward, then the backward schedule (the lower- and
-// upper-neighbour levels of the cell numbering), a thread per cell of a step,
-// every neighbour's increment and base state read from global memory (the
-// block barrier between steps orders them); the same equations and cell
-// order as k_macro_sweep.
+// upper-neighbour levels of the cell numbering), a thread per cell of a step
+// (a step holds at most blockDim.x cells); the same equations and cell order
+// as k_macro_sweep.  Everything of a step that the sweep does not change --
+// the cell, its neighbours, its record, their base states -- is loaded into
+// registers before the barrier that opens the step, so after it only the
+// neighbours' increments are read.  SMEM: the increments of all cells live in
+// shared memory for the two sweeps and go to global memory at the end;
+// otherwise they are read from global memory.
+template <class T> struct MacroCell {
+    int c, nb[4];
+    T r[4], iD, cf[12], base[4][6];
+};
+
 template <class T>
+__device__ __forceinline__ void macro_cell_load(const KParams &p, const int *sc, const int *sp, int st, int ns,
+                                                int dir, MacroCell<T> &x)
+{
+    x.c = -1;
+    if (st >= ns || (int)threadIdx.x >= sp[st + 1] - sp[st]) return;
+    const int c = sc[sp[st] + threadIdx.x];
+    const T *mrec = (const T *)p.mrec;
+    const T *rec = mrec + (size_t)kMRec * c;
+    x.c = c;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) x.r[q] = rec[q];
+    x.iD = rec[4];
+#pragma unroll
+    for (int q = 0; q < 12; ++q) x.cf[q] = rec[12 + q];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        int nb = p.cnb[4 * c + m];
+        if (nb < 0 || nb == c || !(dir > 0 ? nb < c : nb > c)) nb = -1;
+        x.nb[m] = nb;
+        if (nb >= 0)
+#pragma unroll
+            for (int q = 0; q < 6; ++q) x.base[m][q] = mrec[(size_t)kMRec * nb + 6 + q];
+    }
+}
+
+template <class T, bool SMEM>
 __global__ void __launch_bounds__(256) k_macro_sweep_sched(Launch L)
 {
     IDG_LOCATE();
     (void)blk;
+    extern __shared__ __align__(16) unsigned char smraw[];
     if (threadIdx.x == 0) record_residual(p);
     const T gm1 = (T)(p.gam - 1.0);
     T *dWg = (T *)p.mdW;
-    const T *mrec = (const T *)p.mrec;
+    T *dw = SMEM ? (T *)smraw : dWg;  // [N][4]
     for (int dir = 1; dir >= -1; dir -= 2) {
         const int *sc = p.sched + (dir > 0 ? 0 : (size_t)p.N);
         const int *sp = p.sptr + (dir > 0 ? 0 : p.nsteps_f + 1);
         const int ns = dir > 0 ? p.nsteps_f : p.nsteps_b;
+        MacroCell<T> cur;
+        macro_cell_load<T>(p, sc, sp, 0, ns, dir, cur);
         for (int st = 0; st < ns; ++st) {
+            MacroCell<T> nxt;
+            macro_cell_load<T>(p, sc, sp, st + 1, ns, dir, nxt);
             __syncthreads();
-            for (int x = sp[st] + threadIdx.x; x < sp[st + 1]; x += blockDim.x) {
-                const int c = sc[x];
-                const T *rec = mrec + (size_t)kMRec * c;
+            if (cur.c >= 0) {
                 T acc[4] = {0, 0, 0, 0};
 #pragma unroll
                 for (int m = 0; m < 4; ++m) {
-                    const int nb = p.cnb[4 * c + m];
-                    if (nb < 0 || nb == c || !(dir > 0 ? nb < c : nb > c)) continue;
-                    const T *x4 = dWg + 4 * (size_t)nb;
+                    if (cur.nb[m] < 0) continue;
+                    const T *x4 = dw + 4 * (size_t)cur.nb[m];
                     const T dn[4] = {x4[0], x4[1], x4[2], x4[3]};
-                    const T *cf = rec + 12 + 3 * m;
                     T dF[4];
-                    euler_dflux<T>(gm1, mrec + (size_t)kMRec * nb + 6, dn, cf[0], cf[1], dF);
+                    euler_dflux<T>(gm1, cur.base[m], dn, cur.cf[3 * m], cur.cf[3 * m + 1], dF);
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) acc[q] += dF[q] - cf[2] * dn[q];
+                    for (int q = 0; q < 4; ++q) acc[q] += dF[q] - cur.cf[3 * m + 2] * dn[q];
                 }
                 // forward: dW*_c = (R_c - sum_lower) / D_c;  backward: dW_c = dW*_c - sum_upper / D_c
-                const T iD = rec[4];
-                T *o = dWg + 4 * (size_t)c;
+                T *o = dw + 4 * (size_t)cur.c;
 #pragma unroll
-                for (int q = 0; q < 4; ++q) o[q] = dir > 0 ? (rec[q] - acc[q]) * iD : o[q] - acc[q] * iD;
+                for (int q = 0; q < 4; ++q) o[q] = dir > 0 ? (cur.r[q] - acc[q]) * cur.iD : o[q] - acc[q] * cur.iD;
             }
+            cur = nxt;
         }
         __syncthreads();
     }
+    if (SMEM)
+        for (int q = threadIdx.x; q < 4 * p.N; q += blockDim.x) dWg[q] = dw[q];
     if (threadIdx.x == 0) *p.iter += 1;
 }
 
@@ -2039,14 +2077,17 @@ int plan_shapes(const KParams *hp, int n, bool fp64, Plan &pl)
     pl.sweep_vpt = hp[0].sweep_vpt;
     pl.relax_sweeps = hp[0].relax_sweeps;
     pl.sched = hp[0].sched != nullptr;
+    pl.sched_smem = 0;
     for (int i = 0; i < n; ++i) {
         if ((hp[i].sched != nullptr) != (pl.sched != 0)) return (int)cudaErrorInvalidValue;
+        pl.sched_smem = std::max(pl.sched_smem, (size_t)hp[i].N * 4 * (fp64 ? 8 : 4));
         if (hp[i].relax_sweeps != pl.relax_sweeps) return (int)cudaErrorInvalidValue;
         pl.macro_threads = std::max(pl.macro_threads, macro_threads(hp[i]));
         pl.sweep_threads = std::max(pl.sweep_threads, hp[i].sweep_tv * hp[i].sweep_pc);
         pl.limiter_any |= hp[i].limiter;
         if (hp[i].sweep_vpt != pl.sweep_vpt) return (int)cudaErrorInvalidValue;
     }
+    if (!pl.sched || pl.sched_smem > 200 * 1024) pl.sched_smem = 0;
     for (int stages : {std::min(hp[0].macro_stages, 8), 4}) {
         size_t m = 0;
         for (int i = 0; i < n; ++i)
@@ -2151,9 +2192,12 @@ static int iteration_t(const Plan &pl, cudaStream_t st, void **events)
         k_record_residual<T><<<nb[KT_MACRO_SWEEP], 32, 0, st>>>(L(KT_MACRO_SWEEP));
         for (int k = 1; k <= pl.relax_sweeps; ++k)
             k_macro_relax<T><<<nb[KT_MACRO_PRE], 32, 0, st>>>(L(KT_MACRO_PRE), k, pl.relax_sweeps);
-    } else if (pl.sched)
-        k_macro_sweep_sched<T><<<nb[KT_MACRO_SWEEP], 256, 0, st>>>(L(KT_MACRO_SWEEP));
-    else if (pl.macro_stages == 8)
+    } else if (pl.sched) {
+        if (pl.sched_smem)
+            k_macro_sweep_sched<T, true><<<nb[KT_MACRO_SWEEP], 256, pl.sched_smem, st>>>(L(KT_MACRO_SWEEP));
+        else
+            k_macro_sweep_sched<T, false><<<nb[KT_MACRO_SWEEP], 256, 0, st>>>(L(KT_MACRO_SWEEP));
+    } else if (pl.macro_stages == 8)
         k_macro_sweep<T, 8><<<nb[KT_MACRO_SWEEP], pl.macro_threads, pl.macro_smem, st>>>(L(KT_MACRO_SWEEP));
     else
         k_macro_sweep<T, 4><<<nb[KT_MACRO_SWEEP], pl.macro_threads, pl.macro_smem, st>>>(L(KT_MACRO_SWEEP));
@@ -2175,6 +2219,7 @@ template <class T> static int configure_t()
     auto opt = [&](const void *fn) {
         if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     };
+    opt((const void *)k_macro_sweep_sched<T, true>);
     opt((const void *)k_macro_sweep<T, 8>);
     opt((const void *)k_macro_sweep<T, 4>);
     opt((const void *)k_sweep<T, true, 8, 1>);
