@@ -1796,28 +1796,33 @@ struct SweepArgs {
 };
 
 // the cell of slot `slot` at step d (a hyperplane i + j = d on a structured
-// block, the d-th step of the schedule otherwise), -1 past the step's end
-__device__ __forceinline__ int sweep_cell(const SweepArgs &p, int d, int slot)
+// block, with its (i, j); the d-th step of the schedule otherwise), -1 past
+// the step's end
+template <bool SCHED> __device__ __forceinline__ int sweep_cell(const SweepArgs &p, int d, int slot, int &i, int &j)
 {
-    if (p.sched) {
+    if (SCHED) {
         const int b = p.sptr[d];
+        i = j = 0;
         return slot < p.sptr[d + 1] - b ? p.sched[b + slot] : -1;
     }
-    const int ilo = max(0, d - (p.nj - 1)), ihi = min(p.ni - 1, d), i = ilo + slot;
-    return i <= ihi ? (d - i) * p.ni + i : -1;
+    const int ilo = max(0, d - (p.nj - 1)), ihi = min(p.ni - 1, d);
+    i = ilo + slot;
+    j = d - i;
+    return i <= ihi ? j * p.ni + i : -1;
 }
 
 // asynchronous copy of one step's data for the thread's cell: its VPT
 // consecutive velocities of R (or Delta*, f~), and the cell's slot geometry
 // and diagonal base spread over the cell's tv threads
-template <class T, int kStages, int VPT>
+template <class T, int kStages, int VPT, bool SCHED>
 __device__ __forceinline__ void sweep_issue(const SweepArgs &p, const SweepSmem<T, kStages, VPT> &sm, int s, int d,
                                             int slot, int t, int k0, bool act, bool withF)
 {
     using T2 = typename V2<T>::t;
     const int tv = p.tv, pc = p.pc;
     if (s < p.nsteps) {
-        const int c = sweep_cell(p, d, slot);
+        int ci, cj;
+        const int c = sweep_cell<SCHED>(p, d, slot, ci, cj);
         if (c >= 0) {
             int st = s & (kStages - 1);
             size_t e = ((size_t)st * pc + slot);
@@ -1847,17 +1852,19 @@ __device__ __forceinline__ void sweep_issue(const SweepArgs &p, const SweepSmem<
     cp_commit();
 }
 
-template <class T, bool FWD, int kStages, int VPT>
+template <class T, bool FWD, int kStages, int VPT, bool SCHED = false>
 __global__ void __launch_bounds__(512) k_sweep(Launch L)
 {
     IDG_LOCATE();
     using T2 = typename V2<T>::t;
     extern __shared__ __align__(16) unsigned char smraw[];
+    // SCHED (unstructured mesh): the steps of the schedule; otherwise the i+j
+    // hyperplanes, compiled without any schedule state
     const SweepArgs a{p.Nv, p.ni, p.nj, p.sweep_tv, p.sweep_pc, p.dst, p.f, p.cslotT, p.cellpT,
                       p.scode + (FWD ? 0 : 4 * (size_t)p.N),
-                      p.sched ? p.sched + (FWD ? 0 : (size_t)p.N) : nullptr,
-                      p.sched ? p.sptr + (FWD ? 0 : p.nsteps_f + 1) : nullptr,
-                      p.sched ? (FWD ? p.nsteps_f : p.nsteps_b) : p.ni + p.nj - 1};
+                      SCHED ? p.sched + (FWD ? 0 : (size_t)p.N) : nullptr,
+                      SCHED ? p.sptr + (FWD ? 0 : p.nsteps_f + 1) : nullptr,
+                      SCHED ? (FWD ? p.nsteps_f : p.nsteps_b) : p.ni + p.nj - 1};
     const int tv = a.tv, pc = a.pc, ni = a.ni, nj = a.nj, Nv = a.Nv;
     const bool per_i = p.per_i, per_j = p.per_j;
     const SweepSmem<T, kStages, VPT> sm(smraw, pc, tv, !FWD);
@@ -1876,15 +1883,15 @@ __global__ void __launch_bounds__(512) k_sweep(Launch L)
     const int nh = a.nsteps;
     const size_t w = (size_t)tv * VPT;
     // a schedule lists the backward sweep's steps in processing order
-    auto step_d = [&](int s) { return (FWD || a.sched) ? s : nh - 1 - s; };
-    for (int s = 0; s < kStages - 1; ++s) sweep_issue<T, kStages, VPT>(a, sm, s, step_d(s), slot, t, k0, act, !FWD);
+    auto step_d = [&](int s) { return (FWD || SCHED) ? s : nh - 1 - s; };
+    for (int s = 0; s < kStages - 1; ++s) sweep_issue<T, kStages, VPT, SCHED>(a, sm, s, step_d(s), slot, t, k0, act, !FWD);
     for (int s = 0; s < nh; ++s) {
         cp_wait<kStages - 2>();
         __syncthreads();
-        sweep_issue<T, kStages, VPT>(a, sm, s + kStages - 1, step_d(s + kStages - 1), slot, t, k0, act, !FWD);
-        const int c = sweep_cell(a, step_d(s), slot);
+        sweep_issue<T, kStages, VPT, SCHED>(a, sm, s + kStages - 1, step_d(s + kStages - 1), slot, t, k0, act, !FWD);
+        int i, j;
+        const int c = sweep_cell<SCHED>(a, step_d(s), slot, i, j);
         if (c < 0 || !act) continue;
-        const int i = c % ni, j = c / ni;
         const size_t e = (size_t)(s & (kStages - 1)) * pc + slot;
         T g[8];
         load8<T>(g, sm.geo + e * 8);
@@ -1897,7 +1904,7 @@ __global__ void __launch_bounds__(512) k_sweep(Launch L)
         // the backward sweep's increments are read back from global memory
         // only across a periodic seam (the first and last cells of a periodic
         // direction); elsewhere only f and the ring take them
-        const bool keep = FWD || a.sched || (per_i && (i == 0 || i == ni - 1)) || (per_j && (j == 0 || j == nj - 1));
+        const bool keep = FWD || SCHED || (per_i && (i == 0 || i == ni - 1)) || (per_j && (j == 0 || j == nj - 1));
         // the step of one cell; SEAM: some neighbour lies across a periodic
         // seam (read from global memory), otherwise every inflow comes from
         // the ring
@@ -2097,7 +2104,7 @@ int plan_shapes(const KParams *hp, int n, bool fp64, Plan &pl)
         pl.macro_smem = m;
         if (m <= lim) break;
     }
-    for (int stages : {std::min(hp[0].sweep_stages, 8), 4}) {
+    for (int stages : {pl.sched ? 4 : std::min(hp[0].sweep_stages, 8), 4}) {
         size_t f = 0, b = 0;
         for (int i = 0; i < n; ++i) {
             f = std::max(f, fp64 ? sweep_bytes<double>(hp[i], false, stages) : sweep_bytes<float>(hp[i], false, stages));
@@ -2124,9 +2131,23 @@ static void launch_sweep_s(const Plan &pl, cudaStream_t st, const Launch &L)
     }
 }
 
+// unstructured meshes: the scheduled sweeps (always a 4-step prefetch)
+template <class T, bool FWD>
+static void launch_sweep_sched(const Plan &pl, cudaStream_t st, const Launch &L)
+{
+    const size_t sm = FWD ? pl.fwd_smem : pl.bwd_smem;
+    const int nb = pl.nblocks[KT_SWEEP], nt = pl.sweep_threads;
+    switch (pl.sweep_vpt) {
+    case 4: k_sweep<T, FWD, 4, 4, true><<<nb, nt, sm, st>>>(L); break;
+    case 2: k_sweep<T, FWD, 4, 2, true><<<nb, nt, sm, st>>>(L); break;
+    default: k_sweep<T, FWD, 4, 1, true><<<nb, nt, sm, st>>>(L); break;
+    }
+}
+
 template <class T, bool FWD> static void launch_sweep(const Plan &pl, cudaStream_t st, const Launch &L)
 {
-    if (pl.sweep_stages == 8) launch_sweep_s<T, FWD, 8>(pl, st, L);
+    if (pl.sched) launch_sweep_sched<T, FWD>(pl, st, L);
+    else if (pl.sweep_stages == 8) launch_sweep_s<T, FWD, 8>(pl, st, L);
     else launch_sweep_s<T, FWD, 4>(pl, st, L);
 }
 
@@ -2222,6 +2243,12 @@ template <class T> static int configure_t()
     opt((const void *)k_macro_sweep_sched<T, true>);
     opt((const void *)k_macro_sweep<T, 8>);
     opt((const void *)k_macro_sweep<T, 4>);
+    opt((const void *)k_sweep<T, true, 4, 1, true>);
+    opt((const void *)k_sweep<T, false, 4, 1, true>);
+    opt((const void *)k_sweep<T, true, 4, 2, true>);
+    opt((const void *)k_sweep<T, false, 4, 2, true>);
+    opt((const void *)k_sweep<T, true, 4, 4, true>);
+    opt((const void *)k_sweep<T, false, 4, 4, true>);
     opt((const void *)k_sweep<T, true, 8, 1>);
     opt((const void *)k_sweep<T, false, 8, 1>);
     opt((const void *)k_sweep<T, true, 4, 1>);
