@@ -27,7 +27,9 @@
  *    D dW_c + sum_nb 1/2 (dF_nb S - w Lambda dW_nb) = R_c, from dW = 0;
  *  - diffuse wall (Eq. 34-35 in non-delta form) on f-bar with zero net mass
  *    flux; the mass component of the wall flux moment is set to zero;
- *  - ghost increments are zero in both sweeps (end of Section 2.3).
+ *  - ghost increments are zero in both sweeps (end of Section 2.3), or, with
+ *    implicit_wall, the wall ghost of Eq. (34)-(35) built from the inner
+ *    cell's increment of the previous iteration (zero after a restart).
  */
 #include "idugks_oracle.h"
 
@@ -662,6 +664,14 @@ void orc_get_faces(const orc_state *s, int *L, int *R, int *bc, int *side, doubl
     }
 }
 
+/* a (re)start has no last increment: the wall ghost terms start from zero */
+static void clear_increments(orc_state *s)
+{
+    size_t NNv = (size_t)s->N * s->Nv;
+    memset(s->dG, 0, NNv * sizeof(double));
+    memset(s->dH, 0, NNv * sizeof(double));
+}
+
 void orc_init_uniform(orc_state *s, double rho, double u, double v, double T)
 {
     /* W0 = exact continuous moments of the uniform Maxwellian; f~0 = f^eq(W0) */
@@ -672,6 +682,7 @@ void orc_init_uniform(orc_state *s, double rho, double u, double v, double T)
         W[3] = 0.5 * rho * (u * u + v * v + (s->p.K + 2) * RT);
         equilibrium(s, rho, u, v, RT, 0.0, 0.0, s->G + (size_t)c * s->Nv, s->H + (size_t)c * s->Nv);
     }
+    clear_increments(s);
 }
 
 void orc_set_state(orc_state *s, const double *G, const double *H, const double *W)
@@ -680,6 +691,7 @@ void orc_set_state(orc_state *s, const double *G, const double *H, const double 
     memcpy(s->G, G, NNv * sizeof(double));
     memcpy(s->H, H, NNv * sizeof(double));
     memcpy(s->W, W, 4 * s->N * sizeof(double));
+    clear_increments(s);
 }
 
 void orc_get_state(const orc_state *s, double *G, double *H, double *W)
@@ -1053,17 +1065,12 @@ static void macro_predictor(orc_state *s)
 /* one IDUGKS iteration                                                        */
 /* ------------------------------------------------------------------------- */
 
-static double idugks_iteration(orc_state *s)
+/* macroscopic residual M_W = -sum_k int psi F_k (Eq. 27) per cell from the
+ * last face fluxes; returns ||R_W / Omega||_2 */
+static double macro_residual(orc_state *s)
 {
-    const int N = s->N, Nv = s->Nv;
-    const double dt = s->dt;
-    /* DUGKS flux at the half step from f~^n and W^n */
-    cell_prep(s);
-    gradients(s);
-    face_fluxes(s);
-    /* macroscopic residual M_W = -sum_k int psi F_k (Eq. 27) and its norm */
     double r2 = 0.0;
-    for (int c = 0; c < N; ++c) {
+    for (int c = 0; c < s->N; ++c) {
         double acc[4] = {0, 0, 0, 0};
         for (int m = 0; m < s->nslot[c]; ++m) {
             int fi = s->cell_face[4 * c + m];
@@ -1076,10 +1083,15 @@ static double idugks_iteration(orc_state *s)
             r2 += r * r;
         }
     }
-    /* macroscopic predictor -> W^{n+1} */
-    macro_predictor(s);
-    /* micro residual M + Q (Eq. 23 with the Omega/dt factor) and LU-SGS
-     * diagonal (Eq. 26), equilibrium at the predicted W^{n+1} */
+    return sqrt(r2);
+}
+
+/* micro residual M + Q (Eq. 23 with the Omega/dt factor) and LU-SGS
+ * diagonal (Eq. 26), equilibrium at the predicted W^{n+1} = W + dW */
+static void micro_residual(orc_state *s)
+{
+    const int N = s->N, Nv = s->Nv;
+    const double dt = s->dt;
 #pragma omp parallel for schedule(static)
     for (int c = 0; c < N; ++c) {
         double Wn[4];
@@ -1109,7 +1121,60 @@ static double idugks_iteration(orc_state *s)
             s->Dm[ck] = dd;
         }
     }
-    /* LU-SGS sweeps for f~, each velocity independent; ghost increments are 0 */
+}
+
+/* Linearised diffuse wall in the micro sweeps (Eq. 33-35).  The ghost cell
+ * behind a wall face takes, in each velocity coming into the domain, the
+ * increment drho_g M_w (Eq. 34: M_w the unit-density wall Maxwellian, with
+ * the wall's velocity and temperature), drho_g fixed by Eq. (35): the ghost
+ * increment carries back the mass flux of the inner cell's outgoing
+ * increments.  The inner increments are the last iteration's (dG still holds
+ * them; zero after a restart, the start the end of Section 2.3 prescribes),
+ * so the ghost term is known before the sweeps and enters both of them as
+ * the upwind neighbour term |xi.n| S Delta_ghost, i.e. on the right-hand side. */
+static void wall_ghost_terms(orc_state *s)
+{
+    const int Nv = s->Nv;
+    double *gw = dalloc(Nv), *hw = dalloc(Nv);
+    for (int f = 0; f < s->nf; ++f) {
+        const orc_face *F = &s->face[f];
+        if (F->bc != ORC_BC_WALL) continue;
+        const int c = F->L >= 0 ? F->L : F->R, sd = F->side;
+        const double on = F->L >= 0 ? 1.0 : -1.0;
+        equilibrium(s, 1.0, s->p.bc_u[sd], s->p.bc_v[sd], s->p.bc_T[sd] * s->p.RT_ref, 0, 0, gw, hw);
+        double out = 0, in = 0;
+        for (int k = 0; k < Nv; ++k) {
+            double so = on * (s->ux[k] * F->nx + s->uy[k] * F->ny);
+            if (so > 0) out += s->w[k] * so * s->dG[(size_t)c * Nv + k];
+            else if (so < 0) in += s->w[k] * (-so) * gw[k];
+        }
+        const double drho = out / in;
+        for (int k = 0; k < Nv; ++k) {
+            double so = on * (s->ux[k] * F->nx + s->uy[k] * F->ny);
+            if (so < 0) {
+                size_t ck = (size_t)c * Nv + k;
+                s->RG[ck] += -so * F->S * drho * gw[k];
+                s->RH[ck] += -so * F->S * drho * hw[k];
+            }
+        }
+    }
+    free(gw); free(hw);
+}
+
+static double idugks_iteration(orc_state *s)
+{
+    const int N = s->N, Nv = s->Nv;
+    /* DUGKS flux at the half step from f~^n and W^n */
+    cell_prep(s);
+    gradients(s);
+    face_fluxes(s);
+    double res = macro_residual(s);
+    /* macroscopic predictor -> W^{n+1} */
+    macro_predictor(s);
+    micro_residual(s);
+    if (s->p.implicit_wall) wall_ghost_terms(s);
+    /* LU-SGS sweeps for f~, each velocity independent; the ghost increments
+     * are zero here (their wall part, if any, is on the right-hand side) */
 #pragma omp parallel for schedule(static)
     for (int k = 0; k < Nv; ++k) {
         for (int c = 0; c < N; ++c) {
@@ -1153,7 +1218,7 @@ static double idugks_iteration(orc_state *s)
     size_t NNv = (size_t)N * Nv;
     for (size_t i = 0; i < NNv; ++i) { s->G[i] += s->dG[i]; s->H[i] += s->dH[i]; }
     for (int i = 0; i < 4 * N; ++i) s->W[i] += s->dW[i];
-    return sqrt(r2);
+    return res;
 }
 
 void orc_iterate(orc_state *s, int n, double *res_abs)
@@ -1195,6 +1260,7 @@ void orc_explicit_step(orc_state *s, int n)
     }
     for (int c = 0; c < N; ++c)
         moments_W(s, s->G + (size_t)c * Nv, s->H + (size_t)c * Nv, s->W + 4 * c);
+    clear_increments(s);
 }
 
 /* the macroscopic residual R_W (Eq. 27) of the current state and the
@@ -1206,18 +1272,26 @@ void orc_debug_predictor(orc_state *s, double *rw, double *dW)
     cell_prep(s);
     gradients(s);
     face_fluxes(s);
-    for (int c = 0; c < N; ++c) {
-        double acc[4] = {0, 0, 0, 0};
-        for (int m = 0; m < s->nslot[c]; ++m) {
-            int fi = s->cell_face[4 * c + m];
-            double sg = s->cell_sign[4 * c + m];
-            for (int q = 0; q < 4; ++q) acc[q] -= sg * s->phi[4 * fi + q];
-        }
-        for (int q = 0; q < 4; ++q) s->rw[4 * c + q] = acc[q];
-    }
+    macro_residual(s);
     macro_predictor(s);
     memcpy(rw, s->rw, 4 * (size_t)N * sizeof(double));
     memcpy(dW, s->dW, 4 * (size_t)N * sizeof(double));
+}
+
+/* the right-hand side of the micro sweeps of the current state (the steps
+ * of one iteration up to the sweeps); the state is not advanced */
+void orc_debug_micro_residual(orc_state *s, double *RG, double *RH)
+{
+    size_t NNv = (size_t)s->N * s->Nv;
+    cell_prep(s);
+    gradients(s);
+    face_fluxes(s);
+    macro_residual(s);
+    macro_predictor(s);
+    micro_residual(s);
+    if (s->p.implicit_wall) wall_ghost_terms(s);
+    memcpy(RG, s->RG, NNv * sizeof(double));
+    memcpy(RH, s->RH, NNv * sizeof(double));
 }
 
 void orc_debug_cell_prep(orc_state *s, double *fbG, double *fbH, double *q, double *tau)

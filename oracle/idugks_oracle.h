@@ -49,6 +49,10 @@ typedef struct {
                                 /* as the 4th of a triangle; nodes_x/y hold n_unodes  */
     const int *uedge_side;      /* [n_ucells][4] boundary group (0..3, the bc_* slot)  */
                                 /* of edge m (node m -> m+1) where it has no neighbour */
+    int implicit_wall;          /* 1: the ghost cell of a wall face takes the          */
+                                /* linearised diffuse-reflection increment of Eq.     */
+                                /* (34)-(35) from the inner cell's last increment;    */
+                                /* 0: ghost increments are zero (end of Section 2.3)  */
 } orc_problem;
 
 typedef struct orc_state orc_state;
@@ -70,6 +74,10 @@ void orc_iterate(orc_state *s, int n, double *res_abs);
 void orc_explicit_step(orc_state *s, int n);
 /* R_W of the current state and the predictor's dW, without advancing it. */
 void orc_debug_predictor(orc_state *s, double *rw, double *dW);
+/* right-hand side of the micro sweeps (Eq. 23 with the Omega/dt factor, plus
+ * the wall ghost term when implicit_wall is set) of the current state, G and
+ * H [N][Nv], without advancing it. */
+void orc_debug_micro_residual(orc_state *s, double *RG, double *RH);
 
 /* per cell: rho, u, v, T/T_ref, qx, qy (q from the stored state) */
 void orc_get_moments(orc_state *s, double *out6);

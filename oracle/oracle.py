@@ -47,6 +47,7 @@ class _Problem(C.Structure):
         ("relax_sweeps", C.c_int),
         ("n_ucells", C.c_int), ("n_unodes", C.c_int),
         ("ucell_nodes", C.POINTER(C.c_int)), ("uedge_side", C.POINTER(C.c_int)),
+        ("implicit_wall", C.c_int),
     ]
 
 
@@ -87,6 +88,7 @@ def lib():
         _lib.orc_venkat_theta.argtypes = [d]
         _lib.orc_debug_cell_prep.argtypes = [vp, P(d), P(d), P(d), P(d)]
         _lib.orc_debug_predictor.argtypes = [vp, P(d), P(d)]
+        _lib.orc_debug_micro_residual.argtypes = [vp, P(d), P(d)]
     return _lib
 
 
@@ -133,6 +135,7 @@ class Oracle:
         p.cfl_imp, p.cfl_phys = prob.cfl_imp, prob.cfl_phys
         p.limiter, p.flags, p.lusgs_omega = prob.limiter, prob.flags, prob.lusgs_omega
         p.relax_sweeps = prob.relax_sweeps
+        p.implicit_wall = int(getattr(prob, "implicit_wall", 0))
         if getattr(prob, "cell_nodes", None) is not None:
             self._cn = np.ascontiguousarray(prob.cell_nodes, dtype=np.int32)
             self._es = np.ascontiguousarray(prob.edge_side, dtype=np.int32)
@@ -186,6 +189,14 @@ class Oracle:
         rw, dW = np.zeros((self.N, 4)), np.zeros((self.N, 4))
         lib().orc_debug_predictor(self._h, _dp(rw), _dp(dW))
         return rw, dW
+
+    def micro_residual(self):
+        """(R_G, R_H) [N][Nv]: the right-hand side of the micro sweeps of the
+        current state (with the wall ghost term under implicit_wall); the
+        state is not advanced."""
+        RG, RH = np.zeros((self.N, self.Nv)), np.zeros((self.N, self.Nv))
+        lib().orc_debug_micro_residual(self._h, _dp(RG), _dp(RH))
+        return RG, RH
 
     def moments(self) -> np.ndarray:
         out = np.zeros((self.N, 6))

@@ -58,6 +58,7 @@ class Problem:
     flags: int = 0
     lusgs_omega: float = 2.0
     relax_sweeps: int = 0          # macroscopic predictor: 0 LU-SGS, n >= 1 n point-relaxation sweeps
+    implicit_wall: int = 0         # 1: linearised diffuse-wall ghost increments in the micro sweeps (Eq. 34-35)
     # unstructured mesh (triangles and quadrilaterals): nodes_x, nodes_y are
     # then flat node arrays, cell_nodes [ncells][4] int (counter-clockwise, -1
     # as the 4th node of a triangle), edge_side [ncells][4] int: boundary group

@@ -548,3 +548,114 @@ def test_malformed_unstructured_meshes_are_rejected():
     side[side >= 0] = 7  # boundary group out of range
     with pytest.raises(ValueError):
         O.Oracle(dataclasses.replace(good, edge_side=side))
+
+
+# ---------------------------------------------------------------------------
+# linearised diffuse wall in the micro sweeps (Section 2.3, Eq. 33-35)
+# ---------------------------------------------------------------------------
+def _wall_pair(prob, n_before=4):
+    """Oracle with the implicit wall iterated n_before times, the increment
+    of its last iteration (from two stored states), and the micro right-hand
+    sides of that state with and without the wall ghost term."""
+    import dataclasses
+
+    a = O.Oracle(dataclasses.replace(prob, implicit_wall=1))
+    a.init_uniform()
+    a.iterate(n_before - 1)
+    G0 = a.get_state()[0]
+    a.iterate(1)
+    G, H, W = a.get_state()
+    b = O.Oracle(dataclasses.replace(prob, implicit_wall=0))
+    b.set_state(G, H, W)
+    return a, b, G - G0, a.micro_residual(), b.micro_residual()
+
+
+def test_implicit_wall_ghost_increment_is_the_diffuse_reflection_of_the_outgoing_one():
+    """Couette (walls at y = 0 moving with -U and y = 1 with +U, one wall face
+    per wall cell).  The wall term changes only the incoming velocities of
+    the wall cells; there it is |xi.n| S drho M_w with M_w the closed-form
+    Maxwellian of the wall (its velocity and temperature, unit density;
+    H = K RT_w G), and drho returns through the wall exactly the mass flux
+    that the inner cell's last outgoing increments sent into it (Eq. 35)."""
+    U, n, Tw = 0.1, 16, 1.0
+    prob = I.couette(n, U=U, Kn=0.1, nv=12, vmax=4.0, Tw=Tw)
+    a, b, dprev, (RGa, RHa), (RGb, RHb) = _wall_pair(prob)
+    ux, uy, w = a.velocity_grid()
+    dG, dH = RGa - RGb, RHa - RHb
+    S = 1.0 / n  # wall face length: the cells are 1/n wide
+    RTw = Tw * prob.RT_ref
+    assert np.all(dG[1:n - 1] == 0) and np.all(dH[1:n - 1] == 0)
+    for c, ny, Uw in ((0, -1.0, -U), (n - 1, 1.0, U)):
+        so = uy * ny  # xi . n_out at the wall face of cell c
+        out, inc = so > 0, so < 0
+        assert np.all(dG[c, ~inc] == 0) and np.all(dH[c, ~inc] == 0)
+        Mw = np.exp(-((ux - Uw) ** 2 + uy ** 2) / (2 * RTw)) / (2 * np.pi * RTw)
+        ghost = dG[c, inc] / (-so[inc] * S)
+        drho = ghost / Mw[inc]
+        assert np.abs(drho - drho.mean()).max() <= 1e-11 * abs(drho.mean())
+        assert abs(drho.mean()) > 1e-8  # a live term, not a vacuous pass
+        back = np.sum(w[inc] * -so[inc] * ghost)
+        sent = np.sum(w[out] * so[out] * dprev[c, out])
+        assert abs(back - sent) <= 1e-9 * abs(sent)
+        assert np.abs(dH[c, inc] - prob.K * RTw * dG[c, inc]).max() <= 1e-13 * np.abs(dG[c, inc]).max()
+
+
+def test_implicit_wall_term_is_zero_after_a_restart():
+    """A restart has no last increment (the sweeps start from zero ghost
+    increments, end of Section 2.3): the first right-hand side after
+    set_state is the one without the wall term."""
+    prob = I.cavity(8, Kn=0.075, U=0.15, nv=10, vmax=4.0)
+    a, b, _, _, (RGb, RHb) = _wall_pair(prob)
+    a.set_state(*b.get_state())
+    RGa, RHa = a.micro_residual()
+    assert np.array_equal(RGa, RGb) and np.array_equal(RHa, RHb)
+
+
+def test_implicit_wall_keeps_the_fixed_point():
+    """The ghost term is a preconditioner term that vanishes with the
+    increments: a cylinder in a Ma 0.5 stream (the far field fixes the mass)
+    converged with it equals the steady state without it to round-off; the
+    uniform Maxwellian at rest stays an exact fixed point."""
+    import dataclasses
+
+    out = []
+    for iw in (0, 1):
+        p = I.cylinder(ntheta=16, nr=8, nv=12, vmax=6.0, Ma=0.5, Kn=0.5, cfl_imp=100.0, limiter=0)
+        o = O.Oracle(dataclasses.replace(p, implicit_wall=iw))
+        o.init_uniform()
+        r = o.iterate(600)
+        assert r[-1] < 1e-13 * r[0]
+        out.append(o.get_state())
+    for x, y in zip(out[0], out[1]):
+        assert np.abs(x - y).max() <= 1e-12 * np.abs(x).max()
+    prob = I.cavity(8, Kn=0.075, U=0.0, nv=10, vmax=4.0)
+    o = O.Oracle(dataclasses.replace(prob, implicit_wall=1))
+    o.init_uniform()
+    G0, H0, W0 = o.get_state()
+    o.iterate(20)
+    G1, H1, W1 = o.get_state()
+    assert np.abs(G1 - G0).max() <= 1e-14 * np.abs(G0).max()
+    assert np.abs(W1 - W0).max() <= 1e-14 * np.abs(W0).max()
+
+
+@pytest.mark.parametrize("case", ["couette", "cavity"])
+def test_implicit_wall_closed_box_differs_only_in_its_mass(case):
+    """In a closed box the steady states form a family labelled by the total
+    mass, which the non-conservative predictor drifts along on the way; with
+    and without the wall term the converged states differ by no more than
+    their (relative) total masses do."""
+    import dataclasses
+
+    prob = (I.couette(16, U=0.1, Kn=0.1, nv=12, vmax=4.0) if case == "couette"
+            else I.cavity(8, Kn=0.075, U=0.15, nv=10, vmax=4.0, cfl_imp=1000.0))
+    out = []
+    for iw in (0, 1):
+        o = O.Oracle(dataclasses.replace(prob, implicit_wall=iw))
+        o.init_uniform()
+        r = o.iterate(1500)
+        assert r[-1] < 1e-13 * r[0], (case, iw, r[-1] / r[0])
+        area = o.geometry()[2]
+        out.append((o.get_state()[2], np.sum(o.get_state()[2][:, 0] * area)))
+    (W0, m0), (W1, m1) = out
+    dm = abs(m1 - m0) / m0
+    assert np.abs(W1 - W0).max() <= 1.5 * dm * np.abs(W0).max() + 1e-13
