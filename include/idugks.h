@@ -153,6 +153,24 @@ idg_status idg_set_numerics(idg_ctx *ctx, double cfl_imp, double cfl_phys, int l
  * Before idg_bind_workspace. */
 idg_status idg_set_predictor(idg_ctx *ctx, int relax_sweeps);
 
+/* Linearised diffuse wall in the micro sweeps (Section 2.3, Eq. 33-35).
+ * on = 0 (default): ghost increments are zero in both sweeps, the start the
+ * paper prescribes.  on = 1: the ghost cell of each wall face takes, in the
+ * velocities coming into the domain, the increment drho_g M_w (Eq. 34; M_w
+ * the wall's unit-density Maxwellian with the wall's velocity and
+ * temperature, H part K RT_w G), with drho_g (Eq. 35) returning through the
+ * wall the mass flux of the inner cell's outgoing increments of the previous
+ * iteration (zero for the first iteration after idg_init_uniform or
+ * idg_set_state).  The known ghost increment enters both sweeps as the
+ * upwind neighbour term |xi.n| S Delta_ghost on the wall cells' right-hand
+ * side; the face flux moments and R_W (the residual) exclude it, and the
+ * fixed point is unchanged.  Far-field ghosts and the macroscopic predictor
+ * keep zero ghost increments.  Call before idg_bind_workspace (else
+ * IDG_ERR_STATE); on outside {0, 1}: IDG_ERR_ARG.  Such a context can join no
+ * batch and run no idg_adjoint, and binding it with IDG_NUM_EXPLICIT set
+ * fails (IDG_ERR_ARG). */
+idg_status idg_set_implicit_wall(idg_ctx *ctx, int on);
+
 /* Bytes of device workspace the configured problem needs (>= 0; host only). */
 idg_status idg_workspace_size(idg_ctx *ctx, size_t *bytes);
 

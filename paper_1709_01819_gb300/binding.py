@@ -46,6 +46,7 @@ SIGNATURES = [
     ("idg_set_boundary", _i, [_vp, _i, _i, _d, _d, _d, _d]),
     ("idg_set_numerics", _i, [_vp, _d, _d, _i, _d, _i]),
     ("idg_set_predictor", _i, [_vp, _i]),
+    ("idg_set_implicit_wall", _i, [_vp, _i]),
     ("idg_set_mesh_unstructured", _i, [_vp, _i, _P(_d), _P(_d), _i, _P(_i), _P(_i)]),
     ("idg_workspace_size", _i, [_vp, _P(_sz)]),
     ("idg_bind_workspace", _i, [_vp, _vp, _sz]),
@@ -152,6 +153,10 @@ def idg_set_numerics(ctx, cfl_imp, cfl_phys, limiter, lusgs_omega, flags=0):
 
 def idg_set_predictor(ctx, relax_sweeps):
     return check(ctx, lib().idg_set_predictor(ctx, relax_sweeps))
+
+
+def idg_set_implicit_wall(ctx, on):
+    return check(ctx, lib().idg_set_implicit_wall(ctx, on))
 
 
 def idg_set_mesh_unstructured(ctx, x, y, cell_nodes, edge_side):

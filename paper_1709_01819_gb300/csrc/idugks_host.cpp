@@ -40,6 +40,7 @@ struct idg_ctx {
     double cfl_imp = 100.0, cfl_phys = 0.5, lusgs_omega = 2.0;
     int limiter = 0, flags = 0;
     int relax_sweeps = 0;  // macroscopic predictor: 0 LU-SGS, n point-relaxation sweeps
+    int implicit_wall = 0; // 1: linearised diffuse-wall ghost increments in the micro sweeps (Eq. 33-35)
     // derived on the host
     bool built = false;
     // Nvu: discrete velocities of the caller's grid; Nv: velocities stored per
@@ -631,10 +632,13 @@ size_t layout(idg_ctx *c, char *base, KParams *kp)
     k.mrec = L.take<char>(24 * ts * N);
     k.mdW = L.take<char>(4 * ts * N);
     k.mdW2 = c->relax_sweeps > 0 ? L.take<char>(4 * ts * N) : nullptr;
+    k.wallS = c->implicit_wall ? L.take<double>(8 * nf) : nullptr;
+    k.walldrg = c->implicit_wall ? L.take<double>(8 * nf) : nullptr;
     k.mpart = L.take<double>(8 * (N / 32 + 2));
     k.res = L.take<double>(8 * (size_t)idg::kMaxHist);
     k.iter = L.take<int>(256);
     k.status = k.iter + 1;
+    k.wallok = k.iter + 2;
     double *mom = L.take<double>(48 * N);
     KParams *kdev = L.take<KParams>(sizeof(KParams));
     if (kp) {
@@ -994,6 +998,16 @@ idg_status idg_set_predictor(idg_ctx *c, int relax_sweeps)
     return IDG_OK;
 }
 
+idg_status idg_set_implicit_wall(idg_ctx *c, int on)
+{
+    if (!c) return IDG_ERR_ARG;
+    if (c->bound) return fail(c, IDG_ERR_STATE, "setters are closed after idg_bind_workspace");
+    if (on != 0 && on != 1) return fail(c, IDG_ERR_ARG, "implicit_wall %d is not 0 or 1", on);
+    c->implicit_wall = on;
+    c->built = false;
+    return IDG_OK;
+}
+
 idg_status idg_workspace_size(idg_ctx *c, size_t *bytes)
 {
     if (!c || !bytes) return IDG_ERR_ARG;
@@ -1040,6 +1054,8 @@ idg_status idg_velocity_grid(const idg_ctx *cc, double *ux, double *uy, double *
 idg_status idg_bind_workspace(idg_ctx *c, void *dev_ptr, size_t bytes)
 {
     if (!c || !dev_ptr) return IDG_ERR_ARG;
+    if (c->implicit_wall && (c->flags & IDG_NUM_EXPLICIT))
+        return fail(c, IDG_ERR_ARG, "the linearised wall belongs to the implicit sweeps, not to explicit DUGKS");
     idg_status s = build(c);
     if (s) return s;
     size_t need = layout(c, nullptr, nullptr);
@@ -1064,6 +1080,7 @@ idg_status idg_bind_workspace(idg_ctx *c, void *dev_ptr, size_t bytes)
     k.dt = c->dt; k.h = 0.5 * c->dt; k.mu_ref = c->mu_ref; k.RT_ref = c->RT_ref; k.omega = c->omega;
     k.Pr = c->Pr; k.gam = (double)(c->K + 4) / (double)(c->K + 2); k.lusgs_omega = c->lusgs_omega;
     k.relax_sweeps = c->relax_sweeps;
+    k.implicit_wall = c->implicit_wall;
     if (c->unstr) {
         k.per_i = k.per_j = 0;
         k.nsteps_f = c->nsteps_f;
@@ -1171,6 +1188,8 @@ idg_status idg_init_uniform(idg_ctx *c, double rho, double u, double v, double T
     if ((e = cudaMemcpyAsync(c->kp.W, W.data(), W.size() * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess)
         return cuda_fail(c, e, "upload W");
     if ((e = cudaMemsetAsync(c->kp.status, 0, sizeof(int), st)) != cudaSuccess) return cuda_fail(c, e, "status");
+    // a restart has no last increment: the wall ghost terms start from zero
+    if ((e = cudaMemsetAsync(c->kp.wallok, 0, sizeof(int), st)) != cudaSuccess) return cuda_fail(c, e, "wallok");
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(c, e, "sync");
     restart(c);
     return IDG_OK;
@@ -1193,6 +1212,7 @@ idg_status idg_set_state(idg_ctx *c, const double *G, const double *H, const dou
         return cuda_fail(c, e, "H2D W");
     int rc = idg::launch_to_dev(c->kp, c->precision == IDG_FP64, dG, dH, c->Nvu, st);
     if (rc) return cuda_fail(c, (cudaError_t)rc, "to_dev");
+    if ((e = cudaMemsetAsync(c->kp.wallok, 0, sizeof(int), st)) != cudaSuccess) return cuda_fail(c, e, "wallok");
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(c, e, "sync");
     restart(c);
     return IDG_OK;
@@ -1597,6 +1617,7 @@ idg_status idg_batch_create(idg_batch **out, idg_ctx *const *ctxs, int n)
         if (ctxs[i]->flags & IDG_NUM_EXPLICIT) return IDG_ERR_ARG;  // batches run IDUGKS iterations
         if (ctxs[i]->relax_sweeps != ctxs[0]->relax_sweeps) return IDG_ERR_ARG;  // one predictor per batch
         if (ctxs[i]->unstr) return IDG_ERR_ARG;  // batches hold structured blocks
+        if (ctxs[i]->implicit_wall) return IDG_ERR_ARG;  // batches keep zero ghost increments
         for (int j = 0; j < i; ++j)
             if (ctxs[j] == ctxs[i]) return IDG_ERR_ARG;
     }
@@ -1800,6 +1821,7 @@ idg_status idg_adjoint(idg_ctx *c, int objective, int side_mask, const int *para
     if (c->flags) return fail(c, IDG_ERR_ARG, "the adjoint does not support numerics flags 0x%x", c->flags);
     if (c->relax_sweeps) return fail(c, IDG_ERR_ARG, "the adjoint transposes the LU-SGS predictor only");
     if (c->unstr) return fail(c, IDG_ERR_ARG, "the adjoint runs on structured blocks only");
+    if (c->implicit_wall) return fail(c, IDG_ERR_ARG, "the adjoint transposes sweeps with zero ghost increments only");
     if (max_iter < 1 || max_iter > idg::kMaxHist) return fail(c, IDG_ERR_ARG, "max_iter out of [1, %d]", idg::kMaxHist);
     if (!workspace) return fail(c, IDG_ERR_ARG, "null adjoint workspace");
     if (((uintptr_t)workspace) & 255) return fail(c, IDG_ERR_ARG, "adjoint workspace must be 256-byte aligned");

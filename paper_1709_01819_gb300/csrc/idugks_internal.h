@@ -89,6 +89,14 @@ struct KParams {
     // depend on none of each other
     const int *sched, *sptr;
     int nsteps_f, nsteps_b;
+    // linearised diffuse wall of the micro sweeps (Eq. 33-35), implicit_wall
+    // = 1: per face, wallS the inner cell's outgoing sum sum_out w (xi.n_out)
+    // G~ of the last iteration, walldrg the ghost density increment drho_g
+    // (wall faces only; else null); wallok 0 after a restart (no last
+    // increment), 1 once an iteration has stored wallS
+    int implicit_wall;
+    double *wallS, *walldrg;
+    int *wallok;
 };
 
 // kernels of one iteration, in launch order

@@ -30,11 +30,13 @@
 //   k_face_moments   warp per face: characteristic reconstruction of fb at the
 //                    half step (Eq. 11, 13) with the gradient (computed in
 //                    place when the limiter is off), wall density (Eq. 35),
-//                    raw moments of fb                                 [a2-a3]
+//                    raw moments of fb; with the linearised wall the ghost
+//                    density increment of Eq. (35)                     [a2-a3]
 //   k_face_params    thread per face: face state, tau, q, equilibrium, and
 //                    the weights of Eq. (18)                              [a4]
 //   k_face_flux      warp per face: f at the face (Eq. 18), flux (Eq. 19),
-//                    flux moments
+//                    flux moments; with the linearised wall the ghost term
+//                    of Eq. (34) on the incoming velocities of wall faces
 //   k_face_phi       thread per face: Phi_f = sum_k w psi F_k (Eq. 27)
 //   k_macro_pre, k_macro_sweep, k_macro_post: macroscopic LU-SGS          [a5]
 //                    (k_macro_sweep_sched on an unstructured mesh; with the
@@ -904,6 +906,35 @@ __device__ __forceinline__ typename V2<T>::t face_fbar(const KParams &p, const F
     return fb;
 }
 
+// Linearised wall (Eq. 33-35), at a wall face f: the outgoing sum
+// S = sum_out w (xi.n_out) G~ of the inner cell's stored state (products in
+// the storage type, compensated sum across lanes: float64 stays exact to
+// round-off, float32 rounds each product as the fluxes themselves are
+// rounded) and the ghost density increment of Eq. (35),
+//   drho_g = (S^n - S^{n-1}) / sum_in w |xi.n_out| G_w,
+// zero in the first iteration after a restart.  The M_ref part of f~
+// cancels in the difference.  Out of line: the wall faces' extra work keeps
+// out of the register allocation of the kernel's hot path.
+template <class T>
+__device__ __noinline__ void wall_ghost_density(const KParams &p, int f, int lane, int c, T on, T nx, T ny,
+                                                double in_sum)
+{
+    using T2 = typename V2<T>::t;
+    const T2 *fc0 = (const T2 *)p.f + (size_t)c * p.Nv;
+    Acc<T> a[1];
+    a[0].zero();
+    vel_loop<1, T>(p.Nv, lane, a, [&](int k, T(&q)[1]) {
+        const T so = on * xi_dot_n<T>(vx<T>(p, k), vy<T>(p, k), nx, ny);
+        if (so > (T)0) q[0] += vw<T>(p, k) * so * fc0[k].x;
+    });
+    a[0].warp_sum();
+    const double sn = __shfl_sync(0xffffffffu, a[0].value(), 0);
+    if (lane == 0) {
+        p.walldrg[f] = *p.wallok ? (sn - p.wallS[f]) / in_sum : 0.0;
+        p.wallS[f] = sn;
+    }
+}
+
 // raw moments of fb - M_ref at every face (plus the wall density, Eq. 35).
 // float32: the kernel is bound by the latency of its stencil loads, so
 // occupancy decides: four 256-thread blocks per SM (64 registers, the lanes'
@@ -941,6 +972,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 1) k_face_moments(La
         rw = (bc[0] + o) / bc[1];
         rhow = (T)rw;
         rwm1 = (T)((bc[0] - bc[1] + o) / bc[1]);
+        if (p.implicit_wall) wall_ghost_density<T>(p, f, lane, fc.rec[0].c, fc.on, fc.nx, fc.ny, bc[1]);
     }
     // fb - M_ref is kept in the face-flux buffer for k_face_flux
     T2 *Fo = (T2 *)p.F + (size_t)f * p.Nv;
@@ -1077,6 +1109,29 @@ __global__ void __launch_bounds__(256) k_face_flux(Launch L)
     if (lane == 0)
 #pragma unroll
         for (int q = 0; q < 4; ++q) acc[q].store(p.phiraw, (size_t)f * 4 + q);
+    if (p.implicit_wall && p.fbc[f] == 1) {
+        // linearised wall (Eq. 33-35): the ghost increment drho_g M_w of the
+        // incoming velocities enters the micro sweeps as the upwind term
+        // |xi.n| S Delta_ghost, i.e. as an extra flux s S drho_g M_w on the
+        // stored F (after Phi is summed: R_W and Phi exclude it)
+        __syncwarp();
+        const double drg = p.walldrg[f];
+        if (drg != 0.0) {
+            const T on = p.fL[f] >= 0 ? (T)1 : (T)-1, SD = S * (T)drg;
+            const T *bG = (const T *)p.bdevG + (size_t)p.fside[f] * p.Nv;
+            const T *bH = (const T *)p.bdevH + (size_t)p.fside[f] * p.Nv;
+            for (int k = lane; k < p.Nv; k += 32) {
+                const T sn = xi_dot_n<T>(vx<T>(p, k), vy<T>(p, k), nx, ny);
+                if (on * sn < (T)0) {
+                    const T a = sn * SD, gr = vgref<T>(p, k);
+                    T2 v = Fo[k];
+                    v.x += a * (bG[k] + gr);
+                    v.y += a * (bH[k] + kRTr * gr);
+                    Fo[k] = v;
+                }
+            }
+        }
+    }
 }
 
 // Phi_f = sum_k w psi F_k (Eq. 27): deviation part plus the flux of M_ref;
@@ -1092,6 +1147,8 @@ __global__ void __launch_bounds__(256) k_face_phi(Launch L)
         p.phi[4 * f + q] = acc_load<T>(p.phiraw, (size_t)f * 4 + q) +
                            g[2] * (g[0] * p.mref_flux[q][0] + g[1] * p.mref_flux[q][1]);
     if (p.fbc[f] == 1) p.phi[4 * f] = 0.0;
+    // the wall sums of this iteration are stored: the next one has a last increment
+    if (f == 0 && p.implicit_wall) *p.wallok = 1;
 }
 
 // ---------------------------------------------------------------------------

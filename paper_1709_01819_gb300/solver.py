@@ -31,6 +31,8 @@ def configure(ctx, prob: Problem, explicit: bool = False):
                        B.IDG_NUM_EXPLICIT if explicit else 0)
     if prob.relax_sweeps:
         B.idg_set_predictor(ctx, prob.relax_sweeps)
+    if getattr(prob, "implicit_wall", 0):
+        B.idg_set_implicit_wall(ctx, 1)
 
 
 class Solver:
