@@ -294,11 +294,15 @@ static void build_geometry(orc_state *s)
     for (int c = 0; c < s->N; ++c) s->nslot[c] = 4;
     const int per_i = s->p.bc_kind[ORC_IMIN] == ORC_BC_PERIODIC;
     const int per_j = s->p.bc_kind[ORC_JMIN] == ORC_BC_PERIODIC;
-    /* cells: area by the polygon (shoelace) formula, centroid of the polygon */
+    /* cells: area by the polygon (shoelace) formula, centroid of the polygon,
+     * in coordinates relative to the cell's first node (the formulas are
+     * translation invariant; in absolute coordinates a small cell far from
+     * the origin would lose ~eps |x|^2 / area to cancellation) */
     for (int j = 0; j < nj; ++j)
         for (int i = 0; i < ni; ++i) {
-            double px[4] = {NX(s, i, j), NX(s, i + 1, j), NX(s, i + 1, j + 1), NX(s, i, j + 1)};
-            double py[4] = {NY(s, i, j), NY(s, i + 1, j), NY(s, i + 1, j + 1), NY(s, i, j + 1)};
+            const double ox = NX(s, i, j), oy = NY(s, i, j);
+            double px[4] = {0.0, NX(s, i + 1, j) - ox, NX(s, i + 1, j + 1) - ox, NX(s, i, j + 1) - ox};
+            double py[4] = {0.0, NY(s, i + 1, j) - oy, NY(s, i + 1, j + 1) - oy, NY(s, i, j + 1) - oy};
             double a = 0, gx = 0, gy = 0;
             for (int m = 0; m < 4; ++m) {
                 int n2 = (m + 1) % 4;
@@ -309,8 +313,8 @@ static void build_geometry(orc_state *s)
             }
             int c = j * ni + i;
             s->area[c] = a;
-            s->cx[c] = gx / (6.0 * a);
-            s->cy[c] = gy / (6.0 * a);
+            s->cx[c] = ox + gx / (6.0 * a);
+            s->cy[c] = oy + gy / (6.0 * a);
         }
     /* faces */
     int f = 0;
@@ -415,19 +419,25 @@ static int build_geometry_unstructured(orc_state *s)
     for (int c = 0; c < N; ++c) {
         int k = p->ucell_nodes[4 * c + 3] < 0 ? 3 : 4;
         s->nslot[c] = k;
+        /* shoelace area and polygon centroid relative to the first node */
+        const int o0 = p->ucell_nodes[4 * c];
+        if (o0 < 0 || o0 >= p->n_unodes) return -1;
+        const double ox = s->nodes_x[o0], oy = s->nodes_y[o0];
         double a = 0, gx = 0, gy = 0;
         for (int m = 0; m < k; ++m) {
             int n0 = p->ucell_nodes[4 * c + m], n1 = p->ucell_nodes[4 * c + (m + 1) % k];
             if (n0 < 0 || n1 < 0 || n0 >= p->n_unodes || n1 >= p->n_unodes || n0 == n1) return -1;
-            double cr = s->nodes_x[n0] * s->nodes_y[n1] - s->nodes_x[n1] * s->nodes_y[n0];
+            double x0 = s->nodes_x[n0] - ox, y0 = s->nodes_y[n0] - oy;
+            double x1 = s->nodes_x[n1] - ox, y1 = s->nodes_y[n1] - oy;
+            double cr = x0 * y1 - x1 * y0;
             a += 0.5 * cr;
-            gx += (s->nodes_x[n0] + s->nodes_x[n1]) * cr;
-            gy += (s->nodes_y[n0] + s->nodes_y[n1]) * cr;
+            gx += (x0 + x1) * cr;
+            gy += (y0 + y1) * cr;
         }
         if (!(a > 0)) return -1;
         s->area[c] = a;
-        s->cx[c] = gx / (6.0 * a);
-        s->cy[c] = gy / (6.0 * a);
+        s->cx[c] = ox + gx / (6.0 * a);
+        s->cy[c] = oy + gy / (6.0 * a);
         ne += k;
     }
     orc_edge *E = (orc_edge *)malloc(sizeof(orc_edge) * (size_t)ne);

@@ -272,6 +272,28 @@ def test_geometry_of_ogrid_is_closed_and_positive():
     assert abs(area.sum() - ring) < 1e-9 * ring
 
 
+@pytest.mark.parametrize("unstructured", [False, True])
+def test_small_cells_far_from_the_origin_have_exact_rectangle_geometry(unstructured):
+    """Cells of 1e-3 x 5e-4 at (1000, 2000): the polygon area and centroid
+    (shoelace) are translation invariant, so they must equal the rectangle's
+    dx dy and midpoint to round-off of the cell size (in absolute
+    coordinates the shoelace terms are ~1e6 and cancel to ~1e-10 of the
+    ~5e-7 area)."""
+    dx, dy, x0, y0 = 1e-3, 5e-4, 1000.0, 2000.0
+    X, Y = I.uniform_nodes(6, 4, x0, x0 + 6 * dx, y0, y0 + 4 * dy)
+    p = I.cavity(6, nv=4)
+    p.nodes_x, p.nodes_y = X, Y
+    if unstructured:
+        p = I.as_unstructured(p)
+    cx, cy, area = O.Oracle(p).geometry()
+    xs = x0 + dx * (np.arange(6) + 0.5)
+    ys = y0 + dy * (np.arange(4) + 0.5)
+    ex, ey = np.meshgrid(xs, ys)
+    assert np.abs(area - dx * dy).max() <= 1e-9 * dx * dy
+    assert np.abs(cx - ex.ravel()).max() <= 1e-9 * dx
+    assert np.abs(cy - ey.ravel()).max() <= 1e-9 * dy
+
+
 # ---------------------------------------------------------------------------
 # whole-iteration pins
 # ---------------------------------------------------------------------------
