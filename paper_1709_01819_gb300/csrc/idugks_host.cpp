@@ -234,19 +234,22 @@ idg_status build_unstructured(idg_ctx *c, double &hmin)
     for (int q = 0; q < N; ++q) {
         const int *cn = &c->ucell[4 * (size_t)q];
         ns[q] = cn[3] < 0 ? 3 : 4;
+        // shoelace area and polygon centroid relative to the first node
+        const double ox = X[cn[0]], oy = Y[cn[0]];
         double a2 = 0, sx = 0, sy = 0;
         for (int m = 0; m < ns[q]; ++m) {
             const int a = cn[m], b = cn[(m + 1) % ns[q]];
             if (a == b) return fail(c, IDG_ERR_ARG, "cell %d repeats node %d", q, a);
-            const double cr = X[a] * Y[b] - X[b] * Y[a];
+            const double xa = X[a] - ox, ya = Y[a] - oy, xb = X[b] - ox, yb = Y[b] - oy;
+            const double cr = xa * yb - xb * ya;
             a2 += cr;
-            sx += (X[a] + X[b]) * cr;
-            sy += (Y[a] + Y[b]) * cr;
+            sx += (xa + xb) * cr;
+            sy += (ya + yb) * cr;
         }
         if (!(a2 > 0)) return fail(c, IDG_ERR_ARG, "cell %d has non-positive area (nodes must run counter-clockwise)", q);
         c->area[q] = 0.5 * a2;
-        c->cxc[q] = sx / (3.0 * a2);
-        c->cyc[q] = sy / (3.0 * a2);
+        c->cxc[q] = ox + sx / (3.0 * a2);
+        c->cyc[q] = oy + sy / (3.0 * a2);
     }
     // match the two slots of every interior edge by its sorted node pair
     struct Edge {
@@ -428,14 +431,17 @@ idg_status build(idg_ctx *c)
     } else {
     auto X = [&](int i, int j) { return c->nodes_x[(size_t)j * (ni + 1) + i]; };
     auto Y = [&](int i, int j) { return c->nodes_y[(size_t)j * (ni + 1) + i]; };
-    // cells: shoelace area and polygon centroid
+    // cells: shoelace area and polygon centroid, relative to the cell's first
+    // node (translation invariant; absolute coordinates would cancel to
+    // ~eps |x|^2 / area in a small cell far from the origin)
     c->area.assign(c->N, 0);
     c->cxc.assign(c->N, 0);
     c->cyc.assign(c->N, 0);
     for (int j = 0; j < nj; ++j)
         for (int i = 0; i < ni; ++i) {
-            double px[4] = {X(i, j), X(i + 1, j), X(i + 1, j + 1), X(i, j + 1)};
-            double py[4] = {Y(i, j), Y(i + 1, j), Y(i + 1, j + 1), Y(i, j + 1)};
+            const double ox = X(i, j), oy = Y(i, j);
+            double px[4] = {0.0, X(i + 1, j) - ox, X(i + 1, j + 1) - ox, X(i, j + 1) - ox};
+            double py[4] = {0.0, Y(i + 1, j) - oy, Y(i + 1, j + 1) - oy, Y(i, j + 1) - oy};
             double a2 = 0, sx = 0, sy = 0;
             for (int m = 0; m < 4; ++m) {
                 int n2 = (m + 1) & 3;
@@ -447,8 +453,8 @@ idg_status build(idg_ctx *c)
             int cc = j * ni + i;
             if (!(a2 > 0)) return fail(c, IDG_ERR_ARG, "cell (%d,%d) has non-positive area", i, j);
             c->area[cc] = 0.5 * a2;
-            c->cxc[cc] = sx / (3.0 * a2);
-            c->cyc[cc] = sy / (3.0 * a2);
+            c->cxc[cc] = ox + sx / (3.0 * a2);
+            c->cyc[cc] = oy + sy / (3.0 * a2);
         }
     // faces: i-faces row by row, then j-faces row by row
     const int nfi_row = per_i ? ni : ni + 1;
@@ -1351,7 +1357,7 @@ idg_status idg_set_tuning(idg_ctx *c, int key, int value)
         if (value != 4 && value != 8) return fail(c, IDG_ERR_ARG, "sweep stages must be 4 or 8");
         k.sweep_stages = value;
     } else if (key == IDG_TUNE_MACRO_STAGES) {
-        if (value != 4 && value != 8) return fail(c, IDG_ERR_ARG, "macro stages must be 4 or 8");
+        if (value != 2 && value != 4 && value != 8) return fail(c, IDG_ERR_ARG, "macro stages must be 2, 4 or 8");
         k.macro_stages = value;
     } else {
         return fail(c, IDG_ERR_ARG, "unknown tuning key %d", key);
