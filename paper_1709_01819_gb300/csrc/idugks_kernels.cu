@@ -2152,7 +2152,9 @@ int plan_shapes(const KParams *hp, int n, bool fp64, Plan &pl)
         if (hp[i].sweep_vpt != pl.sweep_vpt) return (int)cudaErrorInvalidValue;
     }
     if (!pl.sched || pl.sched_smem > 200 * 1024) pl.sched_smem = 0;
-    for (int stages : {std::min(hp[0].macro_stages, 8), 4}) {
+    // a 2-stage prefetch is the fallback that fits a 256-cell hyperplane of
+    // float64 records
+    for (int stages : {std::min(hp[0].macro_stages, 8), 4, 2}) {
         size_t m = 0;
         for (int i = 0; i < n; ++i)
             m = std::max(m, fp64 ? macro_smem_bytes<double>(hp[i], pl.macro_threads, stages)
@@ -2277,8 +2279,10 @@ static int iteration_t(const Plan &pl, cudaStream_t st, void **events)
             k_macro_sweep_sched<T, false><<<nb[KT_MACRO_SWEEP], 256, 0, st>>>(L(KT_MACRO_SWEEP));
     } else if (pl.macro_stages == 8)
         k_macro_sweep<T, 8><<<nb[KT_MACRO_SWEEP], pl.macro_threads, pl.macro_smem, st>>>(L(KT_MACRO_SWEEP));
-    else
+    else if (pl.macro_stages == 4)
         k_macro_sweep<T, 4><<<nb[KT_MACRO_SWEEP], pl.macro_threads, pl.macro_smem, st>>>(L(KT_MACRO_SWEEP));
+    else
+        k_macro_sweep<T, 2><<<nb[KT_MACRO_SWEEP], pl.macro_threads, pl.macro_smem, st>>>(L(KT_MACRO_SWEEP));
     k_macro_post<T><<<nb[KT_MACRO_POST], 32, 0, st>>>(L(KT_MACRO_POST));
     mark(4);
     k_micro_residual<T><<<nb[KT_MICRO_RES], 128, 0, st>>>(L(KT_MICRO_RES));
@@ -2300,6 +2304,7 @@ template <class T> static int configure_t()
     opt((const void *)k_macro_sweep_sched<T, true>);
     opt((const void *)k_macro_sweep<T, 8>);
     opt((const void *)k_macro_sweep<T, 4>);
+    opt((const void *)k_macro_sweep<T, 2>);
     opt((const void *)k_sweep<T, true, 4, 1, true>);
     opt((const void *)k_sweep<T, false, 4, 1, true>);
     opt((const void *)k_sweep<T, true, 4, 2, true>);

@@ -112,8 +112,8 @@ class Solver:
         cur = self.tuning()
         # shrink shared-memory use first so that every intermediate shape fits
         if any(k in kw for k in ("sweep_tv", "sweep_vpt", "sweep_stages", "macro_stages")):
-            for k in ("sweep_stages", "macro_stages"):
-                B.idg_set_tuning(self.ctx, keys[k], 4)
+            B.idg_set_tuning(self.ctx, keys["sweep_stages"], 4)
+            B.idg_set_tuning(self.ctx, keys["macro_stages"], 2)
             B.idg_set_tuning(self.ctx, keys["sweep_vpt"], 1)
             B.idg_set_tuning(self.ctx, keys["sweep_tv"], 1)
         for k in ("graph", "sweep_tv", "sweep_vpt", "sweep_stages", "macro_stages"):
@@ -300,7 +300,10 @@ class Autotuner:
             try:
                 solver.set_tuning(**cand)
             except B.IdgError:
-                continue
+                try:  # the macroscopic records may only fit a shallower prefetch
+                    solver.set_tuning(**dict(cand, macro_stages=2))
+                except B.IdgError:
+                    continue
             solver.iterate_profiled()  # warm-up
             t = min(float(np.sum(solver.iterate_profiled())) for _ in range(self.repeats))
             if t < best_t:
