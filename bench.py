@@ -152,6 +152,22 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(ms: float, dist=None, device="cpu") -> float:
+    """The slowest rank's timed milliseconds: the whole job ends with it
+    (every rank runs its own replica; the collective only reduces timings)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_step: int, steps: int, world_size: int, max_ms: float) -> float:
+    """Whole-job rate: the units all ranks processed over the slowest rank's time."""
+    return units_per_step * steps * world_size / (max_ms * 1e-3)
+
+
 def run_reference(args, prob):
     """The FP64 oracle on the host cores: each step is one IDUGKS iteration of
     the same cavity."""
@@ -348,12 +364,8 @@ def main():
         if dist:
             dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
-    total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], device=f"cuda:{local}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    ups = prob.ncells * prob.nvel * args.steps * ws / (total_ms * 1e-3)
+    total_ms = max_over_ranks(sum(step_ms), dist, f"cuda:{local}")
+    ups = job_throughput(prob.ncells * prob.nvel, args.steps, ws, total_ms)
 
     # per-kernel device time (events between launches) for the roofline
     kms = np.zeros(6)
