@@ -50,8 +50,10 @@ typedef enum {
     IDG_ERR_STATE = 2,         /* call not allowed in the context's current state      */
     IDG_ERR_CUDA = 3,          /* a CUDA runtime call failed                           */
     IDG_ERR_OOM = 4,           /* workspace smaller than idg_workspace_size            */
-    IDG_ERR_NONFINITE = 5,     /* the residual became NaN or Inf                       */
-    IDG_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up                   */
+    IDG_ERR_NONFINITE = 5,     /* the residual became NaN or Inf (sticky until the     */
+                               /* next idg_init_uniform or idg_set_state)              */
+    IDG_ERR_TIMEOUT = 6,       /* reserved: no kernel of this library waits on another */
+                               /* thread block, so none is returned                    */
     IDG_ERR_NOT_CONVERGED = 7  /* idg_iterate reached max_iter above tol               */
 } idg_status;
 

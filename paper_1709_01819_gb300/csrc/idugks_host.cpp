@@ -1219,6 +1219,8 @@ idg_status idg_set_state(idg_ctx *c, const double *G, const double *H, const dou
     int rc = idg::launch_to_dev(c->kp, c->precision == IDG_FP64, dG, dH, c->Nvu, st);
     if (rc) return cuda_fail(c, (cudaError_t)rc, "to_dev");
     if ((e = cudaMemsetAsync(c->kp.wallok, 0, sizeof(int), st)) != cudaSuccess) return cuda_fail(c, e, "wallok");
+    // a new state clears a divergence recorded by an earlier run
+    if ((e = cudaMemsetAsync(c->kp.status, 0, sizeof(int), st)) != cudaSuccess) return cuda_fail(c, e, "status");
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(c, e, "sync");
     restart(c);
     return IDG_OK;
