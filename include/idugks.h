@@ -194,6 +194,22 @@ idg_status idg_set_state(idg_ctx *ctx, const double *G, const double *H, const d
                          void *stream);
 idg_status idg_get_state(idg_ctx *ctx, double *G, double *H, double *W, void *stream);
 
+/* Checkpoint to / restart from a file (host I/O, synchronous on stream).
+ * idg_save writes a 48-byte header -- the 8 bytes "IDGCKPT1", int32 format
+ * version 1, int32 precision, int64 ncell, int64 nvel, int64 iterations
+ * since the last restart, int64 0 -- then, all float64 little-endian: G, H
+ * [ncell][nvel] and W [ncell][4] (the idg_get_state view); the reference
+ * Maxwellian (rho, u, v, T) the storage is taken relative to; and the stored
+ * deviations f~ - M_ref of G and H [ncell][nvel].  idg_load checks the header
+ * against the context (same cell and velocity counts), restores that
+ * reference Maxwellian and the deviations and W as stored, and restarts the
+ * residual history as idg_set_state does: a context of the saving precision
+ * resumes bitwise (the other precision converts the deviations).  Both need
+ * a bound context (IDG_ERR_STATE); a null path, an unopenable, short, foreign
+ * or mismatched file gives IDG_ERR_ARG. */
+idg_status idg_save(idg_ctx *ctx, const char *path, void *stream);
+idg_status idg_load(idg_ctx *ctx, const char *path, void *stream);
+
 /* Run IDUGKS iterations (Section 2.2) until the residual ||R_W/Omega||_2
  * (explicit DUGKS: ||(W^{n+1} - W^n)/dt||_2, see IDG_NUM_EXPLICIT)
  * divided by that of the first iteration after the last (re)start is <= tol,

@@ -47,6 +47,8 @@ SIGNATURES = [
     ("idg_set_numerics", _i, [_vp, _d, _d, _i, _d, _i]),
     ("idg_set_predictor", _i, [_vp, _i]),
     ("idg_set_implicit_wall", _i, [_vp, _i]),
+    ("idg_save", _i, [_vp, C.c_char_p, _vp]),
+    ("idg_load", _i, [_vp, C.c_char_p, _vp]),
     ("idg_set_mesh_unstructured", _i, [_vp, _i, _P(_d), _P(_d), _i, _P(_i), _P(_i)]),
     ("idg_workspace_size", _i, [_vp, _P(_sz)]),
     ("idg_bind_workspace", _i, [_vp, _vp, _sz]),
@@ -157,6 +159,14 @@ def idg_set_predictor(ctx, relax_sweeps):
 
 def idg_set_implicit_wall(ctx, on):
     return check(ctx, lib().idg_set_implicit_wall(ctx, on))
+
+
+def idg_save(ctx, path, stream=None):
+    return check(ctx, lib().idg_save(ctx, str(path).encode(), stream))
+
+
+def idg_load(ctx, path, stream=None):
+    return check(ctx, lib().idg_load(ctx, str(path).encode(), stream))
 
 
 def idg_set_mesh_unstructured(ctx, x, y, cell_nodes, edge_side):

@@ -12,6 +12,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <cstdint>
 #include <string>
 #include <vector>
 
@@ -1244,6 +1245,108 @@ idg_status idg_get_state(idg_ctx *c, double *G, double *H, double *W, void *stre
     if (W && (e = cudaMemcpyAsync(W, c->kp.W, (size_t)c->N * 32, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
         return cuda_fail(c, e, "D2H W");
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(c, e, "sync");
+    return IDG_OK;
+}
+
+// Checkpoint file: a 48-byte header (8-byte magic "IDGCKPT1", int32 format
+// version 1, int32 precision, int64 cells, int64 velocities, int64 iterations
+// since the last restart, int64 reserved 0); G, H [cells][velocities] and W
+// [cells][4] (the idg_get_state view); the reference Maxwellian (rho, u, v,
+// T) the storage is taken relative to; and the stored deviations f~ - M_ref
+// of G and H.  All float64, little-endian.
+namespace {
+struct CkptHeader {
+    char magic[8];
+    int32_t version, precision;
+    int64_t ncell, nvel, iters, reserved;
+};
+static_assert(sizeof(CkptHeader) == 48, "checkpoint header layout");
+const char kCkptMagic[8] = {'I', 'D', 'G', 'C', 'K', 'P', 'T', '1'};
+
+bool write_all(FILE *fp, const std::vector<double> &v) { return std::fwrite(v.data(), 8, v.size(), fp) == v.size(); }
+bool read_all(FILE *fp, std::vector<double> &v) { return std::fread(v.data(), 8, v.size(), fp) == v.size(); }
+}  // namespace
+
+idg_status idg_save(idg_ctx *c, const char *path, void *stream)
+{
+    idg_status s = check_ready(c);
+    if (s) return s;
+    if (!path) return fail(c, IDG_ERR_ARG, "null path");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t n = (size_t)c->N * c->Nvu;
+    std::vector<double> G(n), H(n), W((size_t)4 * c->N), dG(n), dH(n);
+    if ((s = idg_get_state(c, G.data(), H.data(), W.data(), stream))) return s;
+    // the deviations as stored (exact in float64 for either storage type)
+    double *sG = c->stage, *sH = c->stage + n;
+    int rc = idg::launch_from_dev(c->kp, c->precision == IDG_FP64, sG, sH, c->Nvu, st, true);
+    if (rc) return cuda_fail(c, (cudaError_t)rc, "from_dev");
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(dG.data(), sG, n * 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(dH.data(), sH, n * 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return cuda_fail(c, e, "D2H deviations");
+    CkptHeader h{};
+    std::memcpy(h.magic, kCkptMagic, 8);
+    h.version = 1;
+    h.precision = c->precision;
+    h.ncell = c->N;
+    h.nvel = c->Nvu;
+    h.iters = c->host_iter - c->start_iter;
+    const std::vector<double> ref = {c->ref_rho, c->ref_u, c->ref_v, c->ref_T};
+    FILE *fp = std::fopen(path, "wb");
+    if (!fp) return fail(c, IDG_ERR_ARG, "cannot open %s for writing", path);
+    bool ok = std::fwrite(&h, sizeof h, 1, fp) == 1 && write_all(fp, G) && write_all(fp, H) && write_all(fp, W) &&
+              write_all(fp, ref) && write_all(fp, dG) && write_all(fp, dH);
+    ok = (std::fclose(fp) == 0) && ok;
+    if (!ok) return fail(c, IDG_ERR_ARG, "short write to %s", path);
+    return IDG_OK;
+}
+
+idg_status idg_load(idg_ctx *c, const char *path, void *stream)
+{
+    idg_status s = check_ready(c);
+    if (s) return s;
+    if (!path) return fail(c, IDG_ERR_ARG, "null path");
+    FILE *fp = std::fopen(path, "rb");
+    if (!fp) return fail(c, IDG_ERR_ARG, "cannot open %s", path);
+    CkptHeader h{};
+    if (std::fread(&h, sizeof h, 1, fp) != 1 || std::memcmp(h.magic, kCkptMagic, 8) != 0 || h.version != 1) {
+        std::fclose(fp);
+        return fail(c, IDG_ERR_ARG, "%s is not a version-1 checkpoint", path);
+    }
+    if (h.ncell != c->N || h.nvel != c->Nvu) {
+        std::fclose(fp);
+        return fail(c, IDG_ERR_ARG, "checkpoint of %lld cells x %lld velocities, context has %d x %d",
+                    (long long)h.ncell, (long long)h.nvel, c->N, c->Nvu);
+    }
+    const size_t n = (size_t)c->N * c->Nvu;
+    std::vector<double> G(n), H(n), W((size_t)4 * c->N), ref(4), dG(n), dH(n);
+    bool ok = read_all(fp, G) && read_all(fp, H) && read_all(fp, W) && read_all(fp, ref) && read_all(fp, dG) &&
+              read_all(fp, dH);
+    std::fclose(fp);
+    if (!ok) return fail(c, IDG_ERR_ARG, "%s is truncated", path);
+    if (!(ref[0] > 0) || !(ref[3] > 0) || !std::isfinite(ref[1]) || !std::isfinite(ref[2]))
+        return fail(c, IDG_ERR_ARG, "%s holds an invalid reference Maxwellian", path);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "sync");
+    // the storage's reference Maxwellian, then the deviations as stored
+    c->ref_rho = ref[0]; c->ref_u = ref[1]; c->ref_v = ref[2]; c->ref_T = ref[3];
+    if ((s = upload_reference(c))) return s;
+    if ((s = refresh_plan(c))) return s;
+    double *sG = c->stage, *sH = c->stage + n;
+    if (2 * n * sizeof(double) > c->stage_bytes) return fail(c, IDG_ERR_STATE, "staging buffer too small");
+    if ((e = cudaMemcpyAsync(sG, dG.data(), n * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(sH, dH.data(), n * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(c->kp.W, W.data(), W.size() * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return cuda_fail(c, e, "H2D checkpoint");
+    int rc = idg::launch_to_dev(c->kp, c->precision == IDG_FP64, sG, sH, c->Nvu, st, true);
+    if (rc) return cuda_fail(c, (cudaError_t)rc, "to_dev");
+    if ((e = cudaMemsetAsync(c->kp.wallok, 0, sizeof(int), st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(c->kp.status, 0, sizeof(int), st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return cuda_fail(c, e, "restart");
+    restart(c);
     return IDG_OK;
 }
 

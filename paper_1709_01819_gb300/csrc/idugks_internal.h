@@ -137,7 +137,10 @@ int launch_explicit_prologue(const Plan &plan, bool fp64, void *stream);
 int launch_cell_moments_noalloc(const KParams &p, bool fp64, int device, double *out6_dev, void *stream);
 // absolute float64 G, H of [N][nvu] (the first nvu stored velocities of each
 // cell) to / from the storage; to_dev sets the ghost velocities beyond nvu to M_ref
-int launch_to_dev(const KParams &p, bool fp64, const double *G, const double *H, int nvu, void *stream);
-int launch_from_dev(const KParams &p, bool fp64, double *G, double *H, int nvu, void *stream);
+// float64 (G, H) [N][nvu] <-> the storage; deviation: the arrays hold f~ - M_ref
+int launch_to_dev(const KParams &p, bool fp64, const double *G, const double *H, int nvu, void *stream,
+                  bool deviation = false);
+int launch_from_dev(const KParams &p, bool fp64, double *G, double *H, int nvu, void *stream,
+                    bool deviation = false);
 
 }  // namespace idg

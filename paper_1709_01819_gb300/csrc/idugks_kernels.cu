@@ -2026,10 +2026,12 @@ __global__ void __launch_bounds__(512) k_sweep(Launch L)
 // state conversion and diagnostics
 // ---------------------------------------------------------------------------
 template <class T>
-__global__ void k_to_dev(KParams p, const double *G, const double *H, int nvu)
+__global__ void k_to_dev(KParams p, const double *G, const double *H, int nvu, int deviation)
 {
     using T2 = typename V2<T>::t;
     size_t n = (size_t)p.N * p.Nv;
+    // deviation: G, H already hold f~ - M_ref (a checkpoint's stored form)
+    const double ref = deviation ? 0.0 : 1.0;
     double kRTr = p.K * p.RT_r;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
          i += (size_t)gridDim.x * blockDim.x) {
@@ -2040,18 +2042,19 @@ __global__ void k_to_dev(KParams p, const double *G, const double *H, int nvu)
         o.y = (T)0;
         if (k < nvu) {
             const size_t j = c * nvu + k;
-            o.x = (T)(G[j] - p.gref[k]);
-            o.y = (T)(H[j] - kRTr * p.gref[k]);
+            o.x = (T)(G[j] - ref * p.gref[k]);
+            o.y = (T)(H[j] - ref * kRTr * p.gref[k]);
         }
         ((T2 *)p.f)[i] = o;
     }
 }
 
 template <class T>
-__global__ void k_from_dev(KParams p, double *G, double *H, int nvu)
+__global__ void k_from_dev(KParams p, double *G, double *H, int nvu, int deviation)
 {
     using T2 = typename V2<T>::t;
     size_t n = (size_t)p.N * p.Nv;
+    const double ref = deviation ? 0.0 : 1.0;
     double kRTr = p.K * p.RT_r;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
          i += (size_t)gridDim.x * blockDim.x) {
@@ -2060,8 +2063,8 @@ __global__ void k_from_dev(KParams p, double *G, double *H, int nvu)
         if (k >= nvu) continue;
         const size_t j = c * nvu + k;
         T2 v = ((const T2 *)p.f)[i];
-        G[j] = p.gref[k] + (double)v.x;
-        H[j] = kRTr * p.gref[k] + (double)v.y;
+        G[j] = ref * p.gref[k] + (double)v.x;
+        H[j] = ref * kRTr * p.gref[k] + (double)v.y;
     }
 }
 
@@ -2430,19 +2433,20 @@ int launch_batch_gather(const KParams *dparams, int n, int last, double *dres, i
     return (int)cudaGetLastError();
 }
 
-int launch_to_dev(const KParams &p, bool fp64, const double *G, const double *H, int nvu, void *stream)
+int launch_to_dev(const KParams &p, bool fp64, const double *G, const double *H, int nvu, void *stream,
+                  bool deviation)
 {
     cudaStream_t st = (cudaStream_t)stream;
-    if (fp64) k_to_dev<double><<<1024, 256, 0, st>>>(p, G, H, nvu);
-    else k_to_dev<float><<<1024, 256, 0, st>>>(p, G, H, nvu);
+    if (fp64) k_to_dev<double><<<1024, 256, 0, st>>>(p, G, H, nvu, deviation ? 1 : 0);
+    else k_to_dev<float><<<1024, 256, 0, st>>>(p, G, H, nvu, deviation ? 1 : 0);
     return (int)cudaGetLastError();
 }
 
-int launch_from_dev(const KParams &p, bool fp64, double *G, double *H, int nvu, void *stream)
+int launch_from_dev(const KParams &p, bool fp64, double *G, double *H, int nvu, void *stream, bool deviation)
 {
     cudaStream_t st = (cudaStream_t)stream;
-    if (fp64) k_from_dev<double><<<1024, 256, 0, st>>>(p, G, H, nvu);
-    else k_from_dev<float><<<1024, 256, 0, st>>>(p, G, H, nvu);
+    if (fp64) k_from_dev<double><<<1024, 256, 0, st>>>(p, G, H, nvu, deviation ? 1 : 0);
+    else k_from_dev<float><<<1024, 256, 0, st>>>(p, G, H, nvu, deviation ? 1 : 0);
     return (int)cudaGetLastError();
 }
 

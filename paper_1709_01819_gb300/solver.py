@@ -94,6 +94,14 @@ class Solver:
     def get_state(self):
         return B.idg_get_state(self.ctx, self.N, self.Nv, self.stream)
 
+    def save(self, path):
+        """Checkpoint the state to a file (idg_save)."""
+        B.idg_save(self.ctx, path, self.stream)
+
+    def load(self, path):
+        """Restart from a checkpoint file (idg_load)."""
+        B.idg_load(self.ctx, path, self.stream)
+
     def iterate(self, max_iter: int, tol: float = 0.0):
         """Returns (converged, iterations, relative residual)."""
         st, n, r = B.idg_iterate(self.ctx, max_iter, tol, self.stream)

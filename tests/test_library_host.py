@@ -80,6 +80,11 @@ def test_argument_validation_returns_status_codes():
     with pytest.raises(B.IdgError) as e:
         B.idg_workspace_size(ctx2)
     assert e.value.status == B.IDG_ERR_ARG
+    # checkpoints need a bound context
+    for fn in (B.idg_save, B.idg_load):
+        with pytest.raises(B.IdgError) as e:
+            fn(ctx, "/nonexistent/ckpt.bin")
+        assert e.value.status == B.IDG_ERR_STATE
     B.idg_destroy(ctx)
     B.idg_destroy(ctx2)
 
