@@ -195,6 +195,22 @@ def run_reference(args, prob):
         "e2e": {"value": ups, "unit": "cell-velocity updates/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
+    # the oracle's own time to the residual 1e-6 from the uniform start, on the
+    # workloads it converges in seconds (C1, C2); the larger ones would take
+    # hours on the host cores
+    if not args.no_ttr and args.workload in ("cavity64", "couette64"):
+        o2 = O.Oracle(prob)
+        o2.init_uniform()
+        t0, hist = time.perf_counter(), []
+        while len(hist) < 20000:
+            hist.extend(o2.iterate(1))
+            if hist[-1] <= 1e-6 * hist[0]:
+                break
+        n = len(hist)
+        line["time_to_residual_1e-6"] = {
+            "fp64_oracle": {"seconds": time.perf_counter() - t0, "iterations": n,
+                            "residual": hist[-1] / hist[0], "converged": hist[-1] <= 1e-6 * hist[0],
+                            "cores": cores}}
     print(json.dumps(line), flush=True)
 
 
