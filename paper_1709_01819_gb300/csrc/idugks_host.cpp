@@ -1370,6 +1370,18 @@ idg_status idg_iterate(idg_ctx *c, int max_iter, double tol, void *stream, int *
     bool converged = false;
     while (done < max_iter) {
         int n = std::min(chunk, max_iter - done);
+        // near the tolerance, step one iteration at a time so the run stops at
+        // the crossing: the remaining iterations are predicted from the
+        // geometric rate of the last (up to) 16 residuals
+        if (tol > 0 && n > 1 && c->hist.size() >= 2) {
+            const size_t h = c->hist.size(), m = std::min<size_t>(h - 1, 16);
+            const double r1 = c->hist.front(), rl = c->hist.back(), r0 = c->hist[h - 1 - m];
+            if (r1 > 0 && rl > 0 && r0 > 0 && rl < r0) {
+                const double rate = std::pow(rl / r0, 1.0 / (double)m);
+                const double need = std::log(tol * r1 / rl) / std::log(rate);
+                if (need < (double)chunk) n = 1;
+            }
+        }
         long long it0 = c->host_iter;
         if ((n == kGraphChunk || n == 1) && c->use_graph) {
             if ((s = launch_chunk_graph(c, st, n))) return s;
