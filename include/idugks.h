@@ -72,7 +72,8 @@ void idg_destroy(idg_ctx *ctx);
 const char *idg_last_error(const idg_ctx *ctx);
 
 /* Structured quadrilateral block of ni x nj cells (Fig. 1 and Section 2.3),
- * min(ni, nj) <= 256.
+ * min(ni, nj) <= 256 (a larger block is refused with IDG_ERR_ARG by
+ * idg_workspace_size and idg_bind_workspace).
  * nodes_x/nodes_y: (ni+1)*(nj+1) host float64, node (i,j) at j*(ni+1)+i, cells
  * counter-clockwise (positive area).  A periodic direction is declared with
  * idg_set_boundary(kind = IDG_BC_PERIODIC) on both of its sides; the last node

@@ -403,6 +403,10 @@ idg_status build(idg_ctx *c)
     const bool per_j = !c->unstr && c->bc_kind[IDG_JMIN] == IDG_BC_PERIODIC;
     if (!c->unstr && (per_i != (c->bc_kind[IDG_IMAX] == IDG_BC_PERIODIC) || per_j != (c->bc_kind[IDG_JMAX] == IDG_BC_PERIODIC)))
         return fail(c, IDG_ERR_ARG, "a periodic direction needs IDG_BC_PERIODIC on both sides");
+    // the wavefront kernels hold one hyperplane (up to min(ni, nj) cells) in
+    // one thread block: refused here, before any workspace is sized
+    if (!c->unstr && std::min(c->ni, c->nj) > 256)
+        return fail(c, IDG_ERR_ARG, "min(ni, nj) = %d exceeds 256", std::min(c->ni, c->nj));
     const int ni = c->ni, nj = c->nj;
     c->N = ni * nj;
     // velocities

@@ -170,3 +170,33 @@ def test_unstructured_mesh_host_checks_and_sizes():
     bad[0, 1] = 10_000
     with pytest.raises(B.IdgError):
         sizes(dataclasses.replace(prob, cell_nodes=bad))
+
+
+@pytest.mark.parametrize("precision", [B.IDG_FP64, B.IDG_MIXED])
+def test_size_limits_and_empty_inputs(precision):
+    """The documented limits, at and just past the edge, and empty sizes,
+    checked on the host (no device work): a block with min(ni, nj) = 256 plans
+    in either precision (float64 with the 2-hyperplane prefetch of the
+    macroscopic sweep), 257 is refused; 16384 velocities are accepted, 16512
+    refused; zero cells or velocities are refused."""
+    ctx = B.idg_create(precision, 0)
+    X, Y = I.uniform_nodes(1, 1)
+    for ni, nj in ((0, 1), (1, 0)):  # through the C entry: the binding sizes from the arrays
+        assert B.lib().idg_set_mesh_structured(ctx, ni, nj, B.dptr(X), B.dptr(Y)) == B.IDG_ERR_ARG
+    for nx, ny in ((0, 8), (8, 0), (129, 128)):
+        with pytest.raises(B.IdgError) as e:
+            B.idg_set_velocity_grid(ctx, B.IDG_NC_TRAP, nx, ny, -4, 4, -4, 4)
+        assert e.value.status == B.IDG_ERR_ARG
+    B.idg_set_velocity_grid(ctx, B.IDG_NC_TRAP, 128, 128, -4, 4, -4, 4)
+    B.idg_destroy(ctx)
+    for n, ok in ((256, True), (257, False)):
+        p = I.cavity(n, nv=4)
+        p.nodes_x, p.nodes_y = I.uniform_nodes(n, n + 3)
+        ctx = _ctx(p, precision)
+        if ok:
+            assert B.idg_workspace_size(ctx) > 0
+        else:
+            with pytest.raises(B.IdgError) as e:
+                B.idg_workspace_size(ctx)
+            assert e.value.status == B.IDG_ERR_ARG and "256" in B.idg_last_error(ctx)
+        B.idg_destroy(ctx)
