@@ -41,6 +41,35 @@ def test_library_exports_every_declared_symbol():
     assert set(names) <= bound, f"binding lacks {set(names) - bound}"
 
 
+def test_header_is_c99_and_links_from_c(tmp_path):
+    """include/idugks.h is a C header: a strict C99 translation unit that takes
+    the address of every declared entry point compiles without warnings and
+    links against the built library (C linkage, no C++ in the interface)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    names = declared_symbols()
+    src = tmp_path / "abi.c"
+    body = "\n".join(f"    (void *)&{n}," for n in names)
+    src.write_text('#include "idugks.h"\n#include <stdio.h>\n'
+                   "static void *const entry[] = {\n" + body + "\n};\n"
+                   'int main(void) { printf("%u\\n", (unsigned)(sizeof entry / sizeof entry[0])); return 0; }\n')
+    libdir = os.path.dirname(BUILD.LIB)
+    libname = os.path.basename(BUILD.LIB)
+    out = tmp_path / "abi"
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-Wno-pedantic", "-I",
+                        os.path.join(ROOT, "include"), str(src), "-o", str(out), "-L", libdir,
+                        "-l:" + libname, "-Wl,--unresolved-symbols=report-all"],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([cc, "-std=c99", "-pedantic", "-Werror", "-fsyntax-only", "-I",
+                        os.path.join(ROOT, "include"), "-x", "c", "-"],
+                       input='#include "idugks.h"\nint main(void) { return 0; }\n', capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+
+
 def test_nm_lists_every_symbol():
     import subprocess
     out = subprocess.run(["nm", "-D", "--defined-only", BUILD.LIB], capture_output=True, text=True).stdout
