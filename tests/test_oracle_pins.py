@@ -733,6 +733,40 @@ def test_implicit_wall_ghost_increment_is_the_diffuse_reflection_of_the_outgoing
         assert np.abs(dH[c, inc] - prob.K * RTw * dG[c, inc]).max() <= 1e-13 * np.abs(dG[c, inc]).max()
 
 
+def test_implicit_wall_ghost_term_on_a_curved_wall():
+    """The same facts on the cylinder's curved wall (a resting wall at T_w,
+    every wall cell with one wall face of its own normal): the term touches
+    only the incoming velocities of the wall cells, is |xi.n| S drho M_w
+    there with M_w the closed-form resting Maxwellian at T_w and H = K RT_w G,
+    and carries back the mass flux of the last outgoing increments."""
+    prob = I.cylinder(ntheta=16, nr=6, nv=12, vmax=6.0, Ma=0.5, Kn=0.5, limiter=0, cfl_imp=100.0)
+    a, b, dprev, (RGa, RHa), (RGb, RHb) = _wall_pair(prob)
+    ux, uy, w = a.velocity_grid()
+    dG, dH = RGa - RGb, RHa - RHb
+    fc = a.faces()
+    walls = [f for f in range(a.nf) if fc["bc"][f] == I.BC_WALL]
+    cells = set()
+    RTw = prob.bc[[k[0] for k in prob.bc].index(I.BC_WALL)][4] * prob.RT_ref
+    Mw = np.exp(-(ux ** 2 + uy ** 2) / (2 * RTw)) / (2 * np.pi * RTw)
+    for f in walls:
+        c = fc["L"][f] if fc["L"][f] >= 0 else fc["R"][f]
+        on = 1.0 if fc["L"][f] >= 0 else -1.0
+        assert c not in cells
+        cells.add(c)
+        so = on * (ux * fc["nx"][f] + uy * fc["ny"][f])
+        inc, out = so < 0, so > 0
+        assert np.all(dG[c, ~inc] == 0) and np.all(dH[c, ~inc] == 0)
+        ghost = dG[c, inc] / (-so[inc] * fc["S"][f])
+        drho = ghost / Mw[inc]
+        assert np.abs(drho - drho.mean()).max() <= 1e-10 * abs(drho.mean()) and abs(drho.mean()) > 1e-10
+        back = np.sum(w[inc] * -so[inc] * ghost)
+        sent = np.sum(w[out] * so[out] * dprev[c, out])
+        assert abs(back - sent) <= 1e-9 * abs(sent)
+        assert np.abs(dH[c, inc] - prob.K * RTw * dG[c, inc]).max() <= 1e-12 * np.abs(dG[c, inc]).max()
+    others = np.array([c for c in range(a.N) if c not in cells])
+    assert np.all(dG[others] == 0) and np.all(dH[others] == 0)
+
+
 def test_implicit_wall_term_is_zero_after_a_restart():
     """A restart has no last increment (the sweeps start from zero ghost
     increments, end of Section 2.3): the first right-hand side after
