@@ -7,7 +7,15 @@ iteration: cell prep, interior and boundary faces, macroscopic LU-SGS
 predictor, micro LU-SGS forward and backward sweeps.  The f state (33.6 MB)
 fits in L2, so L2 is flushed (a 256 MB write) between timed steps.
 
-Prints one JSON line (metric: cell-velocity updates per second).
+The same run also times, per iteration, the workloads whose state lives in
+HBM (--extra-workloads, default the 128^2 stretched cavity with 28^2
+Gauss-Hermite velocities and the 121 x 81 Ma 5 cylinder with 89^2
+velocities), each with its own roofline.
+
+Prints one JSON line (metric: cell-velocity updates per second).  The
+roofline divides the method's compulsory bytes (algorithmic_bytes) by the
+measured device time of the dominant launch group, and of the whole
+iteration, against the measured HBM copy bandwidth.
 --impl reference times the FP64 CPU oracle on the host cores instead.
 Under torchrun (N > 1) every rank solves its own copy of the cavity (the
 method has no data-parallel exchange: replicas only) and rank 0 reports the
@@ -69,26 +77,86 @@ def workload(name: str) -> I.Problem:
     raise SystemExit(f"unknown workload {name}")
 
 
-def algorithmic_bytes(prob: I.Problem, s: int, nf: int):
-    """Compulsory bytes of each launch group (s = bytes per scalar of f; every
-    per-velocity array holds a G and an H scalar):
-    cell_prep: read f~ twice (moments, fb+), write fb+        6s per cell-velocity
-    face_moments: read fb+, write fb at the faces             2s per cell-velocity + 2s per face-velocity
-                  (limiter on: the gradient kernel also reads fb+ and writes the limited gradients,
-                  which the reconstruction reads back: +10s per cell-velocity)
-    face_flux: read fb, write the face flux                   4s per face-velocity
-    k_sweep_fwd: micro residual (read the fluxes and f~, write R), then the
-                 forward sweep (read R, write Delta*)         2s per face-velocity + 8s per cell-velocity
-    k_sweep_bwd: read Delta* and f~, write f~                 6s per cell-velocity
-                 (Delta itself is kept only across a periodic seam)"""
+def algorithmic_bytes(prob: I.Problem, s: int):
+    """Compulsory bytes of one IDUGKS iteration per launch group (s = bytes per
+    scalar of f; every per-velocity array holds a G and an H scalar).  These
+    are the method's own data movements, not this implementation's arrays:
+    the per-(cell, velocity) state f~ must be read once before the
+    macroscopic predictor (its moments and the face reconstructions), read
+    again after it (the micro residual needs W^{n+1}), the forward sweep's
+    increments Delta* written and read back, and f~ written by the update:
+      cell_prep      read f~ (moments, fb+, face reconstructions)   2s per cell-velocity
+      face_moments   face states from the moments                  O(faces)
+      face_flux      flux moments Phi                              O(faces)
+      macro          R_W, W read and written (float64)             64 B per cell
+      k_sweep_fwd    read f~, write Delta*                         4s per cell-velocity
+      k_sweep_bwd    read Delta* and f~, write f~                  6s per cell-velocity
+    The face groups' per-face side data (a few float64 per face) is counted
+    as 64 B per cell like the predictor's.  The whole iteration's lower bound
+    is 10s per cell-velocity (ITER_SCALARS): the two reads of f~ by the
+    residual and by the update can be one."""
     N, Nv = prob.ncells, prob.nvel
+    cv = N * Nv
     return {
-        "cell_prep": 6 * s * N * Nv,
-        "face_moments": (12 if prob.limiter else 2) * s * N * Nv + 2 * s * nf * Nv,
-        "face_flux": 4 * s * nf * Nv,
-        "k_sweep_fwd": 2 * s * nf * Nv + 8 * s * N * Nv,
-        "k_sweep_bwd": 6 * s * N * Nv,
+        "cell_prep": 2 * s * cv,
+        "face_moments": 64 * N,
+        "face_flux": 64 * N,
+        "macro": 64 * N,
+        "k_sweep_fwd": 4 * s * cv,
+        "k_sweep_bwd": 6 * s * cv,
     }
+
+
+# scalars of f per cell-velocity that one iteration must move at least
+ITER_SCALARS = 10
+
+
+def roofline(prob: I.Problem, s: int, kms, ms_iter: float, peak: float, traffic_of=None):
+    """The dominant launch group (largest device time, every group a
+    candidate) against the HBM copy peak, with its compulsory bytes; the
+    whole iteration's compulsory bytes (ITER_SCALARS per cell-velocity)
+    against the iteration's time beside it."""
+    alg = algorithmic_bytes(prob, s)
+    dom = max(KERNELS, key=lambda k: kms[KERNELS.index(k)])
+    dom_ms = float(kms[KERNELS.index(dom)])
+    achieved = alg[dom] / (dom_ms * 1e-3) / 1e9
+    it_bytes = ITER_SCALARS * s * prob.ncells * prob.nvel
+    it_ach = it_bytes / (ms_iter * 1e-3) / 1e9
+    groups = {k: {"ms": float(kms[i]), "algorithmic_bytes": alg[k],
+                  "achieved_gbs": alg[k] / (float(kms[i]) * 1e-3) / 1e9 if kms[i] > 0 else None}
+              for i, k in enumerate(KERNELS)}
+    for g in groups.values():
+        g["frac"] = g["achieved_gbs"] / peak if g["achieved_gbs"] is not None else None
+    return {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": traffic_of(dom) if traffic_of else None,
+            "algorithmic_bytes": alg[dom], "kernel_ms": dom_ms,
+            "iteration": {"algorithmic_bytes": it_bytes, "ms": ms_iter, "achieved": it_ach,
+                          "frac": it_ach / peak, "scalars_per_cell_velocity": ITER_SCALARS},
+            "groups": groups}
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the machine type)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
+def host_cores() -> int:
+    """Threads the oracle's OpenMP loops use (OMP_NUM_THREADS, else every core)."""
+    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
 
 
 class ClockSampler:
@@ -182,7 +250,7 @@ def run_reference(args, prob):
     o.iterate(args.steps)
     dt = time.perf_counter() - t0
     ups = prob.ncells * prob.nvel * args.steps / dt
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    cores = host_cores()
     line = {
         "impl": "reference", "metric": "cell-velocity updates/s", "value": ups,
         "unit": "cell-velocity updates/s", "n_gpus": args.gpus, "steps": args.steps,
@@ -191,6 +259,7 @@ def run_reference(args, prob):
         "config": {"workload": prob.name, "cells": prob.ncells, "velocities": prob.nvel,
                    "precision": "fp64-oracle"},
         "cpu_baseline": {"value": ups, "unit": "cell-velocity updates/s", "cores": cores, "kind": "oracle",
+                         "cpu_model": cpu_model(), "nproc": os.cpu_count(),
                          "sample": f"{args.steps} full IDUGKS iterations of {prob.name} after {args.warmup} warm-up"},
         "e2e": {"value": ups, "unit": "cell-velocity updates/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
@@ -208,8 +277,8 @@ def run_reference(args, prob):
                 break
         n = len(hist)
         line["time_to_residual_1e-6"] = {
-            "fp64_oracle": {"seconds": time.perf_counter() - t0, "iterations": n,
-                            "residual": hist[-1] / hist[0], "converged": hist[-1] <= 1e-6 * hist[0],
+            "fp64_oracle": {"seconds": time.perf_counter() - t0, "iterations": int(n),
+                            "residual": float(hist[-1] / hist[0]), "converged": bool(hist[-1] <= 1e-6 * hist[0]),
                             "cores": cores}}
     print(json.dumps(line), flush=True)
 
@@ -242,7 +311,7 @@ def _cpu_worker(name, budget_s, q):
         n += 1
     dt = time.perf_counter() - t0
     q.put({"value": prob.ncells * prob.nvel * n / dt, "unit": "cell-velocity updates/s",
-           "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)), "kind": "oracle",
+           "cores": host_cores(), "kind": "oracle", "cpu_model": cpu_model(), "nproc": os.cpu_count(),
            "sample": f"{n} full FP64 IDUGKS iterations of {name} ({dt:.1f} s)"})
 
 
@@ -295,6 +364,70 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+def profiled_group_ms(s, flush, nprof: int = 10):
+    """Mean device ms of the six launch groups over nprof profiled iterations
+    (CUDA events between the launches, L2 flushed before each)."""
+    kms = np.zeros(6)
+    for _ in range(nprof):
+        flush.fill_(1)
+        kms += s.iterate_profiled()
+    return kms / nprof
+
+
+def time_workload(prob, precision, local, flush, peak, tune="auto", steps=10, warmup=3):
+    """ms per iteration (CUDA events around each, L2 flushed between), the
+    update rate, the group times and the roofline of one workload from its
+    uniform start after warm-up iterations."""
+    import torch
+    from paper_1709_01819_gb300.solver import Autotuner, Solver
+    s = Solver(prob, precision, device=local)
+    s.init_uniform()
+    if tune == "auto":
+        Autotuner().tune(s)
+    for _ in range(warmup):
+        s.iterate(1)
+    stream = torch.cuda.current_stream()
+    a = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    b = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        for q in range(steps):
+            flush.fill_(q & 0xff)
+            a[q].record(stream)
+            s.iterate(1)
+            b[q].record(stream)
+        torch.cuda.synchronize()
+    ms = sum(x.elapsed_time(y) for x, y in zip(a, b)) / steps
+    kms = profiled_group_ms(s, flush)
+    sb = 8 if precision == "fp64" else 4
+    out = {"workload": prob.name, "cells": prob.ncells, "velocities": prob.nvel, "precision": precision,
+           "ms_per_step": ms, "value": prob.ncells * prob.nvel / (ms * 1e-3), "unit": "cell-velocity updates/s",
+           "steps": steps, "tuning": s.tuning(), "roofline": roofline(prob, sb, kms, ms, peak),
+           "clocks": clk.summary()}
+    del s
+    torch.cuda.empty_cache()
+    return out
+
+
+def ttr_runs(prob, local, precisions=("mixed", "fp64"), max_iter=20000):
+    """Wall-clock time from the uniform start to the relative residual 1e-6
+    (idg_iterate stops at the crossing), per precision."""
+    import torch
+    from paper_1709_01819_gb300.solver import Solver
+    out = {}
+    for prec in precisions:
+        s2 = Solver(prob, prec, device=local)
+        s2.init_uniform()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ok, n, r = s2.iterate(max_iter, 1e-6)
+        torch.cuda.synchronize()
+        out[prec] = {"seconds": time.perf_counter() - t0, "iterations": n, "residual": r, "converged": ok}
+        del s2
+        torch.cuda.empty_cache()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -311,6 +444,11 @@ def main():
                     help="timed solver with the linearised diffuse wall in the micro sweeps (Eq. 33-35)")
     ap.add_argument("--explicit-ttr", action="store_true",
                     help="also time explicit DUGKS (Eq. 21, same precision) to the residual 1e-6 (tens of seconds)")
+    ap.add_argument("--extra-workloads", default="cavity128,cylinder",
+                    help="comma-separated workloads timed per iteration after the main one (rank 0, N=1); "
+                         "empty to skip")
+    ap.add_argument("--ttr-extra", action="store_true",
+                    help="also time the extra workloads to the residual 1e-6, mixed and FP64 (minutes)")
     ap.add_argument("--tune", default="auto",
                     help="auto: pick the sweep tiles and prefetch depths with the autotuner before timing; "
                          "default: the library's default shape; or an explicit shape such as "
@@ -384,26 +522,17 @@ def main():
     ups = job_throughput(prob.ncells * prob.nvel, args.steps, ws, total_ms)
 
     # per-kernel device time (events between launches) for the roofline
-    kms = np.zeros(6)
-    nprof = 10
-    for _ in range(nprof):
-        flush.fill_(1)
-        kms += s.iterate_profiled()
-    kms /= nprof
+    kms = profiled_group_ms(s, flush)
     sbytes = 8 if args.precision == "fp64" else 4
-    alg = algorithmic_bytes(prob, sbytes, s.nf)
-    dom = max((k for k in alg), key=lambda k: kms[KERNELS.index(k)])
-    dom_ms = kms[KERNELS.index(dom)]
     peaks = {}
     if os.path.exists(PEAKS_FILE):
         peaks = json.load(open(PEAKS_FILE))
     peak = peaks.get("hbm_gbs", 6800.0)
-    achieved = alg[dom] / (dom_ms * 1e-3) / 1e9
-    traffic = None
     tfile = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tfile):
-        tr = json.load(open(tfile)).get(f"{args.workload}:{args.precision}:{dom}")
-        traffic = tr
+    tr = json.load(open(tfile)) if os.path.exists(tfile) else {}
+    roof = roofline(prob, sbytes, kms, sum(step_ms) / args.steps, peak,
+                    lambda g: tr.get(f"{args.workload}:{args.precision}:{g}"))
+    roof["peak_source"] = "measured" if peaks else "fallback"
 
     # end to end through the C ABI with host buffers: per step upload the state
     # from pinned host memory (set_state), iterate once, read the moments back
@@ -478,6 +607,19 @@ def main():
                                                  "residual": r, "converged": ok}
             del s2
 
+    # the HBM-resident workloads (state above or near L2), per iteration, in
+    # the same run: their roofline is the one the HBM bound speaks to
+    extra = {}
+    if rank == 0 and ws == 1 and args.extra_workloads:
+        del s
+        torch.cuda.empty_cache()
+        for name in args.extra_workloads.split(","):
+            extra[name] = time_workload(workload(name), args.precision, local, flush, peak, args.tune,
+                                        steps=10, warmup=3)
+            extra[name]["roofline"]["peak_source"] = roof["peak_source"]
+            if args.ttr_extra:
+                extra[name]["time_to_residual_1e-6"] = ttr_runs(workload(name), local, max_iter=40000)
+
     if rank == 0:
         line = {
             "metric": "cell-velocity updates/s", "value": ups, "unit": "cell-velocity updates/s",
@@ -491,14 +633,12 @@ def main():
                                       else "zero ghost increments"),
                        "precision": args.precision, "l2": "flushed between timed steps (256 MB write)",
                        "parallelism": "replicas" if ws > 1 else "single", "tuning": tuning},
-            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic,
-                         "peak_source": "measured" if peaks else "fallback",
-                         "algorithmic_bytes": alg[dom], "kernel_ms": dom_ms},
+            "roofline": roof,
             "kernel_ms": {k: float(v) for k, v in zip(KERNELS, kms)},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "time_to_residual_1e-6": ttr,
+            "hbm_workloads": extra,
             "clocks": clk.summary(),
             # per iteration: cell moments, cell params, fb+, [limited gradients],
             # face moments, face params, face flux, Phi, macro pre / sweep /

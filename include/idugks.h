@@ -225,10 +225,10 @@ idg_status idg_iterate(idg_ctx *ctx, int max_iter, double tol, void *stream, int
 idg_status idg_get_moments(idg_ctx *ctx, double *out6, void *stream);
 
 /* Same output as idg_get_moments, written to device memory, for callers that
- * must not allocate device memory for it: code running while a CUDA stream
- * capture is open (cudaMalloc is not capturable), real-time loops whose memory
- * is fixed up front, or plug-ins living inside another framework's memory
- * pool.  The call allocates nothing: its per-cell scratch (raw moments) is a
+ * must not allocate device memory for it: real-time loops whose device memory
+ * is fixed up front (an allocation there can stall or fail mid-run), or
+ * plug-ins living inside another framework's memory pool (which owns every
+ * allocation on the device and does not expect a library to make its own).  The call allocates nothing: its per-cell scratch (raw moments) is a
  * static device array of the library, 1.375 MiB on every GPU that loads
  * libidugks, kept until the process exits.  The paper has no counterpart; this
  * is a service of the library.
@@ -236,7 +236,10 @@ idg_status idg_get_moments(idg_ctx *ctx, double *out6, void *stream);
  *    (rho, u, v, T/T_ref, qx, qy); the call is asynchronous on `stream`.
  *  - Meshes of more than 16384 cells are rejected with IDG_ERR_ARG.
  *  - The first call on a device looks up the scratch address (a host-side
- *    runtime query); make that first call before any stream capture begins.
+ *    runtime query, done once per device under a lock); make that first call
+ *    before any stream capture begins.  A cudaDeviceReset of the device
+ *    invalidates the looked-up address: do not call this entry point again in
+ *    a process that has reset the device.
  *  - All calls share the one scratch array: calls whose GPU work overlaps
  *    (different streams, contexts or threads without ordering) race on it.
  *    Every entry a call reads is written by that same call first, so nothing

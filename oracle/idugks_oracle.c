@@ -9,7 +9,7 @@
  * independent faces/cells), every sum runs serially in a fixed order, so the
  * result does not depend on the thread count.
  *
- * Readings of the paper taken here (each one is listed in the design doc):
+ * Readings of the paper taken here (the GPU library takes the same ones):
  *  - reduced distributions G = int f dxi, H = int xi^2 f dxi (Eq. 5), K internal dof;
  *  - Shakhov reduced equilibria derived from the full Shakhov model for
  *    D = 2 + K degrees of freedom (Eq. 20 prints a garbled H line):

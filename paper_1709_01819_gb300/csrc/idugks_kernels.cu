@@ -55,6 +55,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <mutex>
 #include <type_traits>
 
 namespace idg {
@@ -2375,14 +2376,19 @@ static __device__ __align__(256) unsigned char g_noalloc_raw[(size_t)kNoAllocMax
 
 // Device address of the scratch, resolved once per device with that device
 // current (a host-side use of the symbol's name is not a device address).
+// The cache is guarded by a mutex: first calls from several host threads at
+// once resolve it once.  It is keyed by device ordinal, so a cudaDeviceReset
+// of that device (which unloads the module) leaves a stale address behind.
 static void *noalloc_scratch(int device, int *err)
 {
+    static std::mutex mu;
     static void *addr[64] = {nullptr};
     *err = 0;
     if (device < 0 || device >= 64) {
         *err = (int)cudaErrorInvalidDevice;
         return nullptr;
     }
+    std::lock_guard<std::mutex> lock(mu);
     if (!addr[device]) {
         void *ptr = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_raw);

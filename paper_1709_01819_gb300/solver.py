@@ -195,13 +195,32 @@ class SteadySolve:
         return cls._fn.apply(theta, spec)
 
 
+class NotConvergedError(RuntimeError):
+    """A steady solve or its adjoint stopped at max_iter above its tolerance."""
+
+
 class SteadySpec:
+    """What SteadySolve solves.  strict (default True): a forward solve that
+    does not reach tol, or an adjoint that does not reach adj_tol, raises
+    NotConvergedError instead of returning J or a gradient of an unconverged
+    state; with strict=False it warns and spec.last records the flags."""
+
     def __init__(self, problem: Problem, params, objective=B.IDG_OBJ_FORCE_X, side_mask=1 << B.IDG_JMAX,
-                 precision="fp64", max_iter=20000, tol=1e-12, adj_max_iter=20000, adj_tol=1e-10):
+                 precision="fp64", max_iter=20000, tol=1e-12, adj_max_iter=20000, adj_tol=1e-10,
+                 strict=True):
         self.problem, self.params = problem, list(params)
         self.objective, self.side_mask, self.precision = objective, side_mask, precision
         self.max_iter, self.tol, self.adj_max_iter, self.adj_tol = max_iter, tol, adj_max_iter, adj_tol
+        self.strict = strict
         self.last = None  # (solver, forward info, adjoint info) of the last call
+
+
+def _not_converged(spec: SteadySpec, what: str, n: int, r: float, tol: float):
+    msg = f"{what} stopped after {n} iterations at relative residual {r:.3g} > tol {tol:.3g}"
+    if spec.strict:
+        raise NotConvergedError(msg)
+    import warnings
+    warnings.warn(msg, RuntimeWarning, stacklevel=3)
 
 
 def _make_steady_fn():
@@ -214,10 +233,12 @@ def _make_steady_fn():
             solver = Solver(apply_params(spec.problem, spec.params, vals), spec.precision)
             solver.init_uniform()
             ok, n, r = solver.iterate(spec.max_iter, spec.tol)
+            spec.last = {"solver": solver, "converged": ok, "iterations": n, "residual": r}
+            if not ok:
+                _not_converged(spec, "steady solve", n, r, spec.tol)
             force = solver.wall_force(spec.side_mask)
             J = float(force[0 if spec.objective == B.IDG_OBJ_FORCE_X else 1])
             ctx.solver, ctx.spec = solver, spec
-            spec.last = {"solver": solver, "converged": ok, "iterations": n, "residual": r}
             return torch.tensor(J, dtype=torch.float64, device=theta.device)
 
         @staticmethod
@@ -226,6 +247,8 @@ def _make_steady_fn():
             ok, J, g, n, r = ctx.solver.adjoint(spec.objective, spec.side_mask, spec.params,
                                                 spec.adj_max_iter, spec.adj_tol)
             spec.last.update({"adj_converged": ok, "adj_J": J, "adj_iterations": n, "adj_residual": r})
+            if not ok:
+                _not_converged(spec, "adjoint", n, r, spec.adj_tol)
             grad = torch.as_tensor(np.asarray(g), dtype=torch.float64, device=gJ.device)
             return gJ * grad, None
 

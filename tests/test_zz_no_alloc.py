@@ -1,8 +1,9 @@
 """idg_get_moments_noalloc: the moments entry point that allocates nothing.
 
-It serves callers that must not allocate device memory for a query (while a
-stream capture is open, or inside a fixed memory budget): its scratch is a
-static device array of the library instead of the caller's workspace.  This
+It serves callers that must not allocate device memory for a query (a
+real-time loop whose memory is fixed up front, a plug-in inside another
+framework's memory pool): its scratch is a static device array of the library
+instead of the caller's workspace.  This
 checks, through the C ABI, that two calls in a row give the same moments as
 idg_get_moments, and that meshes above the documented 16384-cell limit are
 refused.  The file is named to be collected last.
