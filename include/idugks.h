@@ -283,9 +283,14 @@ idg_status idg_iterate_profiled(idg_ctx *ctx, void *stream, double *kernel_ms);
  * IDG_TUNE_GRAPH (1 default, 0 off): idg_iterate replays chunks of 16
  * iterations (and single iterations) as captured CUDA graphs on a
  * library-owned stream that is ordered after, and before, the caller's
- * stream by events. */
+ * stream by events.  IDG_TUNE_MACRO_KIND: the macroscopic LU-SGS sweeps of a
+ * structured block (Eq. 30) with one thread per line of cells of the shorter
+ * axis (1, default for IDG_MIXED) or with two threads per cell of each i+j
+ * hyperplane (0, default for IDG_FP64);
+ * the same lexicographic dependency order, results equal up to the rounding
+ * order of a cell's neighbour sum; all instances of a batch must agree. */
 enum { IDG_TUNE_SWEEP_TV = 1, IDG_TUNE_SWEEP_STAGES = 2, IDG_TUNE_MACRO_STAGES = 3, IDG_TUNE_GRAPH = 4,
-       IDG_TUNE_SWEEP_VPT = 5 };
+       IDG_TUNE_SWEEP_VPT = 5, IDG_TUNE_MACRO_KIND = 6 };
 idg_status idg_set_tuning(idg_ctx *ctx, int key, int value);
 idg_status idg_get_tuning(const idg_ctx *ctx, int key, int *value);
 

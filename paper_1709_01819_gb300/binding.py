@@ -20,6 +20,7 @@ IDG_NC_TRAP, IDG_NC_SIMPSON, IDG_GAUSS_HERMITE = 0, 1, 2
 IDG_IMIN, IDG_IMAX, IDG_JMIN, IDG_JMAX = 0, 1, 2, 3
 IDG_BGK, IDG_SHAKHOV = 0, 1
 IDG_TUNE_SWEEP_TV, IDG_TUNE_SWEEP_STAGES, IDG_TUNE_MACRO_STAGES, IDG_TUNE_GRAPH, IDG_TUNE_SWEEP_VPT = 1, 2, 3, 4, 5
+IDG_TUNE_MACRO_KIND = 6
 IDG_OBJ_FORCE_X, IDG_OBJ_FORCE_Y = 0, 1
 IDG_PAR_KN, IDG_PAR_WALL_T, IDG_PAR_WALL_U, IDG_PAR_WALL_V = 0, 1, 2, 3
 IDG_NUM_EXPLICIT = 1

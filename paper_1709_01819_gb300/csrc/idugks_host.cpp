@@ -1112,6 +1112,9 @@ idg_status idg_bind_workspace(idg_ctx *c, void *dev_ptr, size_t bytes)
     // falls back to 4)
     k.macro_stages = 8;
     k.sweep_stages = 8;
+    // float64: the hyperplane-slot kernel (two threads per cell halve each
+    // step's float64 chain); float32 storage: one thread per line of cells
+    k.macro_kind = c->precision == IDG_FP64 ? 0 : 1;
     // uploads
     std::vector<float> uxf(c->ux.begin(), c->ux.end()), uyf(c->uy.begin(), c->uy.end()),
         wf(c->w.begin(), c->w.end());
@@ -1480,6 +1483,9 @@ idg_status idg_set_tuning(idg_ctx *c, int key, int value)
     } else if (key == IDG_TUNE_MACRO_STAGES) {
         if (value != 2 && value != 4 && value != 8) return fail(c, IDG_ERR_ARG, "macro stages must be 2, 4 or 8");
         k.macro_stages = value;
+    } else if (key == IDG_TUNE_MACRO_KIND) {
+        if (value != 0 && value != 1) return fail(c, IDG_ERR_ARG, "macro kind must be 0 or 1");
+        k.macro_kind = value;
     } else {
         return fail(c, IDG_ERR_ARG, "unknown tuning key %d", key);
     }
@@ -1506,6 +1512,7 @@ idg_status idg_get_tuning(const idg_ctx *c, int key, int *value)
     else if (key == IDG_TUNE_SWEEP_VPT) *value = c->kp.sweep_vpt;
     else if (key == IDG_TUNE_SWEEP_STAGES) *value = c->plan.sweep_stages;
     else if (key == IDG_TUNE_MACRO_STAGES) *value = c->plan.macro_stages;
+    else if (key == IDG_TUNE_MACRO_KIND) *value = c->kp.macro_kind;
     else return IDG_ERR_ARG;
     return IDG_OK;
 }

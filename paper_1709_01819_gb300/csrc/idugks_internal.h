@@ -81,6 +81,8 @@ struct KParams {
     // slots of the micro sweeps, prefetch depths (hyperplanes; 4 or 8)
     int sweep_tv, sweep_pc, sweep_stages, macro_stages;
     int sweep_vpt;  // consecutive velocities per thread in the micro sweeps (1, 2, 4)
+    int macro_kind; // macroscopic LU-SGS on a structured block: 0 hyperplane slots (k_macro_sweep),
+                    // 1 one thread per line of cells (k_macro_lines)
     int relax_sweeps;  // macroscopic predictor: 0 LU-SGS, n >= 1 n point-relaxation sweeps
     // unstructured meshes: the sweeps' schedule (null on a structured block,
     // whose sweeps walk the i+j hyperplanes): sched [2][N] cells in processing
@@ -118,6 +120,7 @@ struct Plan {
     int macro_threads, sweep_threads;
     size_t macro_smem, fwd_smem, bwd_smem;
     int macro_stages, sweep_stages, limiter_any, sweep_vpt;
+    int macro_kind;      // KParams::macro_kind of every instance
     int explicit_dugks;  // 1: launch_iteration runs one explicit DUGKS step (Eq. 21)
     int relax_sweeps;    // macroscopic predictor of every instance (KParams::relax_sweeps)
     int sched;           // 1: the instances are unstructured (scheduled sweeps)

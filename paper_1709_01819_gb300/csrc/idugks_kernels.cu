@@ -71,6 +71,10 @@ __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, 
 __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+// correctly rounded reciprocals: the same value as 1 / x in IEEE division,
+// without the general division routine
+__device__ __forceinline__ float rcp_rn(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp_rn(double x) { return __drcp_rn(x); }
 __device__ __forceinline__ float t_expm1(float x) { return expm1f(x); }
 __device__ __forceinline__ double t_expm1(double x) { return expm1(x); }
 __device__ __forceinline__ float t_exp(float x) { return expf(x); }
@@ -1325,7 +1329,7 @@ template <class T>
 __device__ __forceinline__ void euler_dflux(T gm1, const T *b, const T *dW, T nx, T ny, T *dF)
 {
     T rho = b[0], mx = b[1], my = b[2], u = b[3], v = b[4], H = b[5];
-    T ir1 = (T)1 / (rho + dW[0]);
+    T ir1 = rcp_rn(rho + dW[0]);
     T du = (dW[1] - u * dW[0]) * ir1, dv = (dW[2] - v * dW[0]) * ir1;
     T vn = u * nx + v * ny, dvn = du * nx + dv * ny, vn1 = vn + dvn;
     T dmu = dW[1] * (u + du) + dW[2] * (v + dv) + mx * du + my * dv;
@@ -1467,6 +1471,209 @@ __global__ void __launch_bounds__(512) k_macro_sweep(Launch L)
         __syncthreads();
     }
     if (tid == 0) *p.iter += 1;
+}
+
+// The same sweeps with one thread per line of cells.  The lines run along
+// the longer axis (w), one thread per line of the shorter axis (t: columns,
+// t = i, when ni <= nj, else rows, t = j), so at step d thread t owns cell
+// (t, w = d - t) of the i+j hyperplane d -- the lexicographic dependency order
+// as above.  Of a cell's lower neighbours (forward; upper ones backward) the
+// one on the same line is the thread's own result of the previous step, kept
+// in registers; the one on the adjacent line is the neighbouring lane's result
+// of the previous step, taken by a warp shuffle (across a warp boundary from a
+// two-slot shared-memory exchange behind the step's barrier).  Across a
+// periodic seam along the lines the neighbour is the thread's own first cell
+// (registers); across a seam between the last and the first line it is kept
+// in shared memory by the line that computed it.  Each thread prefetches its
+// cell records (and, backward, its dW*) kStages-1 steps ahead with cp.async
+// into its own stage slots.  One thread owns all four components of its
+// cell: no pair shuffle, no hyperplane ring.
+constexpr int kLRec = kMRec + 4;  // stage entry: the record, then dW* (backward)
+
+template <class T> struct LineNb {
+    T dw[4], b[6];
+};
+
+template <class T>
+__device__ __forceinline__ void line_shfl(LineNb<T> &o, const LineNb<T> &v, bool up)
+{
+#pragma unroll
+    for (int q = 0; q < 4; ++q) o.dw[q] = up ? __shfl_up_sync(0xffffffffu, v.dw[q], 1) : __shfl_down_sync(0xffffffffu, v.dw[q], 1);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) o.b[q] = up ? __shfl_up_sync(0xffffffffu, v.b[q], 1) : __shfl_down_sync(0xffffffffu, v.b[q], 1);
+}
+
+// acc += 1/2 (dF S - omega Lambda dW_nb) of one neighbour through slot m
+template <class T>
+__device__ __forceinline__ void line_term(T gm1, const T *rec, int m, const LineNb<T> &nb, T (&acc)[4])
+{
+    const T *cf = rec + 12 + 3 * m;
+    T dF[4];
+    euler_dflux<T>(gm1, nb.b, nb.dw, cf[0], cf[1], dF);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] += dF[q] - cf[2] * nb.dw[q];
+}
+
+// the same for a neighbour that may not exist (use false): evaluated on a
+// unit base state in that case and discarded by selects, no branch
+template <class T>
+__device__ __forceinline__ void line_term_sel(T gm1, const T *rec, int m, const LineNb<T> &nb0, bool use, T (&acc)[4])
+{
+    LineNb<T> nb;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) nb.dw[q] = use ? nb0.dw[q] : (T)0;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) nb.b[q] = use ? nb0.b[q] : (q == 0 ? (T)1 : (T)0);
+    const T *cf = rec + 12 + 3 * m;
+    T dF[4];
+    euler_dflux<T>(gm1, nb.b, nb.dw, cf[0], cf[1], dF);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] += use ? dF[q] - cf[2] * nb.dw[q] : (T)0;
+}
+
+template <class T> static size_t macro_lines_smem_bytes(int nthr, int stages, int nw, bool seam)
+{
+    return ((size_t)stages * nthr * kLRec + 2 * 32 * 10 + (seam ? (size_t)nw * 10 : 0)) * sizeof(T);
+}
+
+template <class T, int kStages>
+__global__ void __launch_bounds__(256) k_macro_lines(Launch L)
+{
+    IDG_LOCATE();
+    (void)blk;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int ni = p.ni, nj = p.nj, nthr = blockDim.x;
+    const bool cols = ni <= nj;
+    const int nt = cols ? ni : nj, nw = cols ? nj : ni, nh = nt + nw - 1;
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const bool line = t < nt;
+    // periodic between the last and the first line / along the lines; a
+    // direction one cell wide wraps onto the cell itself (no term)
+    const bool per_t = (cols ? p.per_i : p.per_j) && nt > 1;
+    const bool per_w = (cols ? p.per_j : p.per_i) && nw > 1;
+    // slots (west 0, east 1, south 2, north 3) towards line t-1 / t+1 and
+    // towards w-1 / w+1
+    const int s_tm = cols ? 0 : 2, s_tp = cols ? 1 : 3, s_wm = cols ? 2 : 0, s_wp = cols ? 3 : 1;
+    T *stage = (T *)smraw;                               // [kStages][nthr][kLRec]
+    T *xb = stage + (size_t)kStages * nthr * kLRec;      // [2][32 warps][10] lane 31 -> next warp's lane 0 (fwd)
+    T *seam = xb + 2 * 32 * 10;                          // [nw][10] the seam line's cells (per_t)
+    if (t == 0) record_residual(p);
+    const T gm1 = (T)(p.gam - 1.0);
+    T *dWg = (T *)p.mdW;
+    const T *mrec = (const T *)p.mrec;
+    constexpr int RC = kMRec * sizeof(T) / 16, DC = 4 * sizeof(T) / 16;
+    auto cell_of = [&](int w) { return cols ? w * ni + t : t * ni + w; };
+    for (int dir = 1; dir >= -1; dir -= 2) {
+        auto step_d = [&](int s) { return dir > 0 ? s : nh - 1 - s; };
+        auto issue = [&](int s) {
+            if (s < nh && line) {
+                const int w = step_d(s) - t;
+                if (w >= 0 && w < nw) {
+                    const int c = cell_of(w);
+                    T *dst = stage + ((size_t)(s & (kStages - 1)) * nthr + t) * kLRec;
+#pragma unroll
+                    for (int q = 0; q < RC; ++q)
+                        cp_async16((char *)dst + 16 * q, (const char *)(mrec + (size_t)kMRec * c) + 16 * q);
+                    if (dir < 0)
+#pragma unroll
+                        for (int q = 0; q < DC; ++q)
+                            cp_async16((char *)(dst + kMRec) + 16 * q, (const char *)(dWg + 4 * (size_t)c) + 16 * q);
+                }
+            }
+            cp_commit();
+        };
+        for (int s = 0; s < kStages - 1; ++s) issue(s);
+        LineNb<T> prev, first;  // this line's result of the previous step / of its first cell
+#pragma unroll
+        for (int q = 0; q < 4; ++q) prev.dw[q] = first.dw[q] = (T)0;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) prev.b[q] = first.b[q] = (T)0;
+        for (int s = 0; s < nh; ++s) {
+            cp_wait<kStages - 2>();
+            __syncthreads();  // the exchange slots of the previous step are written
+            issue(s + kStages - 1);
+            const int d = step_d(s), w = d - t;
+            // the adjacent line's result of the previous step (forward: line
+            // t - 1, backward: line t + 1), at this thread's w
+            LineNb<T> adj;
+            line_shfl<T>(adj, prev, dir > 0);
+            const bool edge = dir > 0 ? lane == 0 : (lane == 31 || t == nthr - 1);
+            if (edge) {
+                const int ow = dir > 0 ? wid - 1 : wid + 1;
+                if (ow >= 0 && ow < (nthr >> 5)) {
+                    const T *x = xb + ((size_t)((s + 1) & 1) * 32 + ow) * 10;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) adj.dw[q] = x[q];
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) adj.b[q] = x[4 + q];
+                }
+            }
+            const bool active = line && w >= 0 && w < nw;
+            LineNb<T> out = prev;
+            if (active) {
+                const T *rec = stage + ((size_t)(s & (kStages - 1)) * nthr + t) * kLRec;
+                T acc[4] = {0, 0, 0, 0};
+                if (dir > 0) {
+                    line_term_sel<T>(gm1, rec, s_tm, adj, t >= 1, acc);
+                    line_term_sel<T>(gm1, rec, s_wm, prev, w >= 1, acc);
+                    if (per_t && t == nt - 1) {
+                        LineNb<T> sn;
+                        const T *x = seam + (size_t)w * 10;
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) sn.dw[q] = x[q];
+#pragma unroll
+                        for (int q = 0; q < 6; ++q) sn.b[q] = x[4 + q];
+                        line_term<T>(gm1, rec, s_tp, sn, acc);
+                    }
+                    if (per_w && w == nw - 1) line_term<T>(gm1, rec, s_wp, first, acc);
+                } else {
+                    line_term_sel<T>(gm1, rec, s_tp, adj, t + 1 < nt, acc);
+                    line_term_sel<T>(gm1, rec, s_wp, prev, w + 1 < nw, acc);
+                    if (per_t && t == 0) {
+                        LineNb<T> sn;
+                        const T *x = seam + (size_t)w * 10;
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) sn.dw[q] = x[q];
+#pragma unroll
+                        for (int q = 0; q < 6; ++q) sn.b[q] = x[4 + q];
+                        line_term<T>(gm1, rec, s_tm, sn, acc);
+                    }
+                    if (per_w && w == 0) line_term<T>(gm1, rec, s_wm, first, acc);
+                }
+                // forward: dW*_c = (R_c - sum_lower) / D_c;  backward: dW_c = dW*_c - sum_upper / D_c
+                const T iD = rec[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) out.dw[q] = dir > 0 ? (rec[q] - acc[q]) * iD : rec[kMRec + q] - acc[q] * iD;
+#pragma unroll
+                for (int q = 0; q < 6; ++q) out.b[q] = rec[6 + q];
+                const int c = cell_of(w);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) dWg[4 * (size_t)c + q] = out.dw[q];
+                // the cell a later cell of this line meets across the seam along the line
+                if (per_w && w == (dir > 0 ? 0 : nw - 1)) first = out;
+                // the seam line's cells for the line across the seam between lines
+                if (per_t && t == (dir > 0 ? 0 : nt - 1)) {
+                    T *x = seam + (size_t)w * 10;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) x[q] = out.dw[q];
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) x[4 + q] = out.b[q];
+                }
+                // the warp-boundary lane's result for the next warp's edge lane
+                if (dir > 0 ? lane == 31 : lane == 0) {
+                    T *x = xb + ((size_t)(s & 1) * 32 + wid) * 10;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) x[q] = out.dw[q];
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) x[4 + q] = out.b[q];
+                }
+            }
+            prev = out;
+        }
+        cp_wait<0>();
+        __syncthreads();
+    }
+    if (t == 0) *p.iter += 1;
 }
 
 // The macroscopic LU-SGS sweeps on an unstructured mesh: one CTA walks the
@@ -1998,7 +2205,7 @@ __global__ void __launch_bounds__(512) k_sweep(Launch L)
                     ah -= aS[m] * dn[m].y;
                 }
                 const T2 r = sm.R[rbase + v];
-                const T iD = (T)1 / D;
+                const T iD = rcp_rn(D);
                 T2 o;
                 if (FWD) {
                     o.x = (r.x + ag) * iD;
@@ -2156,6 +2363,29 @@ int plan_shapes(const KParams *hp, int n, bool fp64, Plan &pl)
         if (hp[i].sweep_vpt != pl.sweep_vpt) return (int)cudaErrorInvalidValue;
     }
     if (!pl.sched || pl.sched_smem > 200 * 1024) pl.sched_smem = 0;
+    pl.macro_kind = hp[0].macro_kind;
+    for (int i = 0; i < n; ++i)
+        if (hp[i].macro_kind != pl.macro_kind) return (int)cudaErrorInvalidValue;
+    if (pl.macro_kind == 1 && !pl.sched) {
+        // one thread per line of the shorter axis; the seam array holds the
+        // walk axis' cells when the lines wrap around (a periodic shorter axis)
+        pl.macro_threads = 0;
+        for (int i = 0; i < n; ++i)
+            pl.macro_threads = std::max(pl.macro_threads, ((std::min(hp[i].ni, hp[i].nj) + 31) / 32) * 32);
+        for (int stages : {std::min(hp[0].macro_stages, 8), 4, 2}) {
+            size_t m = 0;
+            for (int i = 0; i < n; ++i) {
+                const bool cols = hp[i].ni <= hp[i].nj;
+                const bool seam = cols ? hp[i].per_i : hp[i].per_j;
+                const int nw = std::max(hp[i].ni, hp[i].nj);
+                m = std::max(m, fp64 ? macro_lines_smem_bytes<double>(pl.macro_threads, stages, nw, seam)
+                                     : macro_lines_smem_bytes<float>(pl.macro_threads, stages, nw, seam));
+            }
+            pl.macro_stages = stages;
+            pl.macro_smem = m;
+            if (m <= lim) break;
+        }
+    } else {
     // a 2-stage prefetch is the fallback that fits a 256-cell hyperplane of
     // float64 records
     for (int stages : {std::min(hp[0].macro_stages, 8), 4, 2}) {
@@ -2166,6 +2396,7 @@ int plan_shapes(const KParams *hp, int n, bool fp64, Plan &pl)
         pl.macro_stages = stages;
         pl.macro_smem = m;
         if (m <= lim) break;
+    }
     }
     for (int stages : {pl.sched ? 4 : std::min(hp[0].sweep_stages, 8), 4}) {
         size_t f = 0, b = 0;
@@ -2281,6 +2512,13 @@ static int iteration_t(const Plan &pl, cudaStream_t st, void **events)
             k_macro_sweep_sched<T, true><<<nb[KT_MACRO_SWEEP], 256, pl.sched_smem, st>>>(L(KT_MACRO_SWEEP));
         else
             k_macro_sweep_sched<T, false><<<nb[KT_MACRO_SWEEP], 256, 0, st>>>(L(KT_MACRO_SWEEP));
+    } else if (pl.macro_kind == 1) {
+        if (pl.macro_stages == 8)
+            k_macro_lines<T, 8><<<nb[KT_MACRO_SWEEP], pl.macro_threads, pl.macro_smem, st>>>(L(KT_MACRO_SWEEP));
+        else if (pl.macro_stages == 4)
+            k_macro_lines<T, 4><<<nb[KT_MACRO_SWEEP], pl.macro_threads, pl.macro_smem, st>>>(L(KT_MACRO_SWEEP));
+        else
+            k_macro_lines<T, 2><<<nb[KT_MACRO_SWEEP], pl.macro_threads, pl.macro_smem, st>>>(L(KT_MACRO_SWEEP));
     } else if (pl.macro_stages == 8)
         k_macro_sweep<T, 8><<<nb[KT_MACRO_SWEEP], pl.macro_threads, pl.macro_smem, st>>>(L(KT_MACRO_SWEEP));
     else if (pl.macro_stages == 4)
@@ -2306,6 +2544,9 @@ template <class T> static int configure_t()
         if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     };
     opt((const void *)k_macro_sweep_sched<T, true>);
+    opt((const void *)k_macro_lines<T, 8>);
+    opt((const void *)k_macro_lines<T, 4>);
+    opt((const void *)k_macro_lines<T, 2>);
     opt((const void *)k_macro_sweep<T, 8>);
     opt((const void *)k_macro_sweep<T, 4>);
     opt((const void *)k_macro_sweep<T, 2>);

@@ -113,18 +113,19 @@ class Solver:
         return B.idg_iterate_profiled(self.ctx, self.stream)
 
     def set_tuning(self, **kw):
-        """sweep_tv=, sweep_vpt=, sweep_stages=, macro_stages=, graph= (launch shapes only)."""
+        """sweep_tv=, sweep_vpt=, sweep_stages=, macro_stages=, macro_kind=, graph=
+        (launch shapes only)."""
         keys = {"sweep_tv": B.IDG_TUNE_SWEEP_TV, "sweep_stages": B.IDG_TUNE_SWEEP_STAGES,
                 "macro_stages": B.IDG_TUNE_MACRO_STAGES, "graph": B.IDG_TUNE_GRAPH,
-                "sweep_vpt": B.IDG_TUNE_SWEEP_VPT}
+                "sweep_vpt": B.IDG_TUNE_SWEEP_VPT, "macro_kind": B.IDG_TUNE_MACRO_KIND}
         cur = self.tuning()
         # shrink shared-memory use first so that every intermediate shape fits
-        if any(k in kw for k in ("sweep_tv", "sweep_vpt", "sweep_stages", "macro_stages")):
+        if any(k in kw for k in ("sweep_tv", "sweep_vpt", "sweep_stages", "macro_stages", "macro_kind")):
             B.idg_set_tuning(self.ctx, keys["sweep_stages"], 4)
             B.idg_set_tuning(self.ctx, keys["macro_stages"], 2)
             B.idg_set_tuning(self.ctx, keys["sweep_vpt"], 1)
             B.idg_set_tuning(self.ctx, keys["sweep_tv"], 1)
-        for k in ("graph", "sweep_tv", "sweep_vpt", "sweep_stages", "macro_stages"):
+        for k in ("graph", "macro_kind", "sweep_tv", "sweep_vpt", "sweep_stages", "macro_stages"):
             v = kw.get(k, cur[k])
             B.idg_set_tuning(self.ctx, keys[k], int(v))
 
@@ -133,7 +134,8 @@ class Solver:
                 "sweep_stages": B.idg_get_tuning(self.ctx, B.IDG_TUNE_SWEEP_STAGES),
                 "macro_stages": B.idg_get_tuning(self.ctx, B.IDG_TUNE_MACRO_STAGES),
                 "graph": B.idg_get_tuning(self.ctx, B.IDG_TUNE_GRAPH),
-                "sweep_vpt": B.idg_get_tuning(self.ctx, B.IDG_TUNE_SWEEP_VPT)}
+                "sweep_vpt": B.idg_get_tuning(self.ctx, B.IDG_TUNE_SWEEP_VPT),
+                "macro_kind": B.idg_get_tuning(self.ctx, B.IDG_TUNE_MACRO_KIND)}
 
     def moments(self) -> np.ndarray:
         return B.idg_get_moments(self.ctx, self.N, self.stream)
