@@ -261,6 +261,28 @@ idg_status idg_get_face_flux_moments(idg_ctx *ctx, double *phi4, void *stream);
  * into the wall (the objective of idg_adjoint).  force2: host, 2 doubles. */
 idg_status idg_get_wall_force(idg_ctx *ctx, int side_mask, double *force2, void *stream);
 
+/* Wall quantities of the last iteration on the faces of one wall side, in
+ * face order (the face numbering of idg_get_face_flux_moments restricted to
+ * that side): the surface pressure, shear stress and heat flux the paper
+ * plots along the cylinder wall (Section 3).  With n the unit normal from the
+ * gas into the wall, t = (-n_y, n_x), S the face length, (P_x, P_y) = the
+ * momentum components of Phi (Eq. 27) oriented along n, over S (the momentum
+ * flux into the wall per unit length, Pi n, which is the stress on the wall
+ * since the mass flux through it is zero) and E the energy component oriented
+ * along n, over S, each face gives five float64:
+ *   x, y   the face midpoint,
+ *   p      = n . (Pi n)                  normal stress (pressure),
+ *   tau_w  = t . (Pi n)                  shear stress,
+ *   q_n    = E - U_w . (Pi n)            heat flux into the wall: the energy
+ *                                        flux in the frame of the wall,
+ *                                        whose velocity U_w is the side's
+ *                                        boundary velocity (idg_set_boundary).
+ * Nondimensional like every output (rho_ref = 1, velocity unit sqrt(2 RT_ref)).
+ * out5: host, room for cap faces (cap 0 and out5 NULL: count only);
+ * *nfaces receives the side's face count (rows beyond cap are not written).
+ * IDG_ERR_ARG if the side is not a wall. */
+idg_status idg_get_wall(idg_ctx *ctx, int side, double *out5, int cap, int *nfaces, void *stream);
+
 /* One iteration with a CUDA event recorded between its kernel launches on
  * the caller's stream (synchronises it).  kernel_ms[0..5] receives the
  * device time of: cell prep, interior faces, boundary faces, macroscopic

@@ -74,6 +74,7 @@ SIGNATURES = [
     ("idg_batch_bind_workspace", _i, [_vp, _vp, _sz]),
     ("idg_batch_iterate", _i, [_vp, _i, _d, _vp, _P(_i), _P(_d), _P(_i)]),
     ("idg_get_wall_force", _i, [_vp, _i, _P(_d), _vp]),
+    ("idg_get_wall", _i, [_vp, _i, _P(_d), _i, _P(_i), _vp]),
     ("idg_adjoint_workspace_size", _i, [_vp, _P(_sz)]),
     ("idg_adjoint_state", _i, [_vp, _vp, _i, _P(_d), _P(_d), _P(_d), _vp]),
     ("idg_adjoint", _i, [_vp, _i, _i, _P(_i), _i, _vp, _sz, _i, _d, _vp, _P(_d), _P(_d), _P(_i), _P(_d)]),
@@ -260,6 +261,15 @@ def idg_get_wall_force(ctx, side_mask, stream=None):
     out = np.zeros(2)
     check(ctx, lib().idg_get_wall_force(ctx, side_mask, dptr(out), stream))
     return out
+
+
+def idg_get_wall(ctx, side, stream=None):
+    """Per face of wall side `side`: x, y (midpoint), p, tau_w, q_n ([nface][5])."""
+    n = C.c_int()
+    check(ctx, lib().idg_get_wall(ctx, side, None, 0, C.byref(n), stream))
+    out = np.zeros((max(n.value, 1), 5))
+    check(ctx, lib().idg_get_wall(ctx, side, dptr(out), n.value, C.byref(n), stream))
+    return out[: n.value]
 
 
 def idg_adjoint_workspace_size(ctx) -> int:

@@ -1593,6 +1593,40 @@ idg_status idg_get_wall_force(idg_ctx *c, int side_mask, double *force2, void *s
     return IDG_OK;
 }
 
+idg_status idg_get_wall(idg_ctx *c, int side, double *out5, int cap, int *nfaces, void *stream)
+{
+    idg_status s = check_ready(c);
+    if (s) return s;
+    if (side < 0 || side > 3 || cap < 0 || (cap > 0 && !out5) || !nfaces)
+        return fail(c, IDG_ERR_ARG, "invalid wall arguments");
+    if (c->bc_kind[side] != IDG_BC_WALL) return fail(c, IDG_ERR_ARG, "side %d is not a wall", side);
+    std::vector<double> phi((size_t)4 * c->nf);
+    if ((s = idg_get_face_flux_moments(c, phi.data(), stream))) return s;
+    const double Uw = c->bc_u[side], Vw = c->bc_v[side];
+    int n = 0;
+    for (int f = 0; f < c->nf; ++f) {
+        if (c->fbc[f] != IDG_BC_WALL || c->fside[f] != side) continue;
+        if (n < cap) {
+            const double *g = &c->fgeo[(size_t)7 * f];
+            const double on = c->fL[f] >= 0 ? 1.0 : -1.0;  // from the gas into the wall
+            const int in = c->fL[f] >= 0 ? c->fL[f] : c->fR[f];
+            const double nx = on * g[0], ny = on * g[1], S = g[2];
+            // momentum flux into the wall per unit length, Pi n
+            const double px = on * phi[(size_t)4 * f + 1] / S, py = on * phi[(size_t)4 * f + 2] / S;
+            const double en = on * phi[(size_t)4 * f + 3] / S;
+            double *o = out5 + (size_t)5 * n;
+            o[0] = c->cxc[in] + (c->fL[f] >= 0 ? g[3] : g[5]);
+            o[1] = c->cyc[in] + (c->fL[f] >= 0 ? g[4] : g[6]);
+            o[2] = px * nx + py * ny;
+            o[3] = -px * ny + py * nx;
+            o[4] = en - (Uw * px + Vw * py);
+        }
+        ++n;
+    }
+    *nfaces = n;
+    return IDG_OK;
+}
+
 }  // extern "C"
 
 // ===========================================================================

@@ -151,6 +151,11 @@ class Solver:
         face fluxes of the last iteration."""
         return B.idg_get_wall_force(self.ctx, side_mask, self.stream)
 
+    def wall(self, side: int) -> np.ndarray:
+        """Per face of a wall side, from the last iteration: midpoint x, y, pressure
+        p, shear stress tau_w and heat flux into the wall q_n ([nface][5])."""
+        return B.idg_get_wall(self.ctx, side, self.stream)
+
     def adjoint(self, objective: int, side_mask: int, params, max_iter: int = 20000, tol: float = 1e-10,
                 keep_state: bool = False):
         """Discrete adjoint at the current state (idg_adjoint).  Returns
