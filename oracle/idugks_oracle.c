@@ -1171,20 +1171,16 @@ static void wall_ghost_terms(orc_state *s)
     free(gw); free(hw);
 }
 
-static double idugks_iteration(orc_state *s)
+/* LU-SGS sweeps of the micro equations (Eq. 26) for (RG, RH) with the
+ * diagonal Dm: (D - L) D^-1 (D - U) Delta = R, L and U the upwind couplings
+ * |xi.n| S of the lower and upper neighbours in the cell numbering (Eq. 25);
+ * each velocity independent; the ghost increments are zero here (their wall
+ * part, if any, is on the right-hand side).  Forward: Delta* = (R + sum over
+ * lower inflow neighbours of |xi.n| S Delta*_nb) / D; backward: Delta =
+ * Delta* + sum over upper inflow neighbours of |xi.n| S Delta_nb / D. */
+static void micro_sweeps(orc_state *s)
 {
     const int N = s->N, Nv = s->Nv;
-    /* DUGKS flux at the half step from f~^n and W^n */
-    cell_prep(s);
-    gradients(s);
-    face_fluxes(s);
-    double res = macro_residual(s);
-    /* macroscopic predictor -> W^{n+1} */
-    macro_predictor(s);
-    micro_residual(s);
-    if (s->p.implicit_wall) wall_ghost_terms(s);
-    /* LU-SGS sweeps for f~, each velocity independent; the ghost increments
-     * are zero here (their wall part, if any, is on the right-hand side) */
 #pragma omp parallel for schedule(static)
     for (int k = 0; k < Nv; ++k) {
         for (int c = 0; c < N; ++c) {
@@ -1224,6 +1220,21 @@ static double idugks_iteration(orc_state *s)
             s->dH[ck] += ah / s->Dm[ck];
         }
     }
+}
+
+static double idugks_iteration(orc_state *s)
+{
+    const int N = s->N, Nv = s->Nv;
+    /* DUGKS flux at the half step from f~^n and W^n */
+    cell_prep(s);
+    gradients(s);
+    face_fluxes(s);
+    double res = macro_residual(s);
+    /* macroscopic predictor -> W^{n+1} */
+    macro_predictor(s);
+    micro_residual(s);
+    if (s->p.implicit_wall) wall_ghost_terms(s);
+    micro_sweeps(s);
     /* simultaneous update, Eq. (32) */
     size_t NNv = (size_t)N * Nv;
     for (size_t i = 0; i < NNv; ++i) { s->G[i] += s->dG[i]; s->H[i] += s->dH[i]; }
@@ -1302,6 +1313,35 @@ void orc_debug_micro_residual(orc_state *s, double *RG, double *RH)
     if (s->p.implicit_wall) wall_ghost_terms(s);
     memcpy(RG, s->RG, NNv * sizeof(double));
     memcpy(RH, s->RH, NNv * sizeof(double));
+}
+
+/* the micro LU-SGS sweeps (Eq. 26) of the current state applied to a given
+ * right-hand side (RG, RH): the diagonal D of the state's iteration and the
+ * increments Delta the sweeps return; the state and its last increments are
+ * left as they were */
+void orc_debug_micro_sweeps(orc_state *s, const double *RG, const double *RH, double *dG, double *dH,
+                            double *D)
+{
+    size_t NNv = (size_t)s->N * s->Nv;
+    double *kg = dalloc(NNv), *kh = dalloc(NNv);
+    memcpy(kg, s->dG, NNv * sizeof(double));
+    memcpy(kh, s->dH, NNv * sizeof(double));
+    cell_prep(s);
+    gradients(s);
+    face_fluxes(s);
+    macro_residual(s);
+    macro_predictor(s);
+    micro_residual(s);
+    memcpy(s->RG, RG, NNv * sizeof(double));
+    memcpy(s->RH, RH, NNv * sizeof(double));
+    micro_sweeps(s);
+    memcpy(dG, s->dG, NNv * sizeof(double));
+    memcpy(dH, s->dH, NNv * sizeof(double));
+    memcpy(D, s->Dm, NNv * sizeof(double));
+    memcpy(s->dG, kg, NNv * sizeof(double));
+    memcpy(s->dH, kh, NNv * sizeof(double));
+    free(kg);
+    free(kh);
 }
 
 void orc_debug_cell_prep(orc_state *s, double *fbG, double *fbH, double *q, double *tau)

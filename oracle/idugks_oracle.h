@@ -99,6 +99,11 @@ void orc_ls_gradient(const orc_state *s, const double *phi, double *grad2);
 /* Venkatakrishnan limiter value (Eq. 16-17) of a cell scalar field [N]. */
 void orc_limiter(const orc_state *s, const double *phi, double *lim);
 double orc_venkat_theta(double x);
+/* the micro LU-SGS sweeps (Eq. 26) of the current state applied to the
+ * right-hand side (RG, RH) [N][Nv]: increments (dG, dH) and the diagonal D
+ * [N][Nv] of the state's iteration; the state is not advanced */
+void orc_debug_micro_sweeps(orc_state *s, const double *RG, const double *RH, double *dG, double *dH,
+                            double *D);
 /* runs the cell-prep step (Eq. 10, 12) on the stored state and copies out
  * fb+ [N][Nv] (G and H), the cell heat flux q [N][2] and tau [N] */
 void orc_debug_cell_prep(orc_state *s, double *fbG, double *fbH, double *q, double *tau);

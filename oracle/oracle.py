@@ -89,6 +89,7 @@ def lib():
         _lib.orc_debug_cell_prep.argtypes = [vp, P(d), P(d), P(d), P(d)]
         _lib.orc_debug_predictor.argtypes = [vp, P(d), P(d)]
         _lib.orc_debug_micro_residual.argtypes = [vp, P(d), P(d)]
+        _lib.orc_debug_micro_sweeps.argtypes = [vp, P(d), P(d), P(d), P(d), P(d)]
     return _lib
 
 
@@ -197,6 +198,16 @@ class Oracle:
         RG, RH = np.zeros((self.N, self.Nv)), np.zeros((self.N, self.Nv))
         lib().orc_debug_micro_residual(self._h, _dp(RG), _dp(RH))
         return RG, RH
+
+    def debug_micro_sweeps(self, RG: np.ndarray, RH: np.ndarray):
+        """The micro LU-SGS sweeps of the current state's iteration applied to
+        the right-hand side (RG, RH) [N][Nv]: (dG, dH, D); the state is not
+        advanced."""
+        RG = np.ascontiguousarray(RG, dtype=np.float64)
+        RH = np.ascontiguousarray(RH, dtype=np.float64)
+        dG, dH, D = (np.zeros((self.N, self.Nv)) for _ in range(3))
+        lib().orc_debug_micro_sweeps(self._h, _dp(RG), _dp(RH), _dp(dG), _dp(dH), _dp(D))
+        return dG, dH, D
 
     def moments(self) -> np.ndarray:
         out = np.zeros((self.N, 6))

@@ -826,3 +826,61 @@ def test_implicit_wall_closed_box_differs_only_in_its_mass(case):
     (W0, m0), (W1, m1) = out
     dm = abs(m1 - m0) / m0
     assert np.abs(W1 - W0).max() <= 1.5 * dm * np.abs(W0).max() + 1e-13
+
+
+@pytest.mark.parametrize("case", ["cavity", "ogrid_seam", "triangles"])
+def test_micro_sweeps_invert_the_lu_sgs_factorisation(case):
+    """The oracle's micro sweeps solve the LU-SGS form of Eq. (26),
+    (D - L) D^-1 (D - U) Delta = R, for a random right-hand side.  L and U are
+    assembled here, per velocity, from the exported face list and the upwind
+    rule of Eq. (25): a cell's equation takes |xi.n_out| S times the
+    increment of each neighbour the velocity comes from (xi.n_out < 0), the
+    lower-numbered ones in L, the higher-numbered ones in U; faces of a cell
+    with itself (a periodic direction one cell wide) and ghosts take none.
+    The diagonal's geometric part is checked too: D - sum_out (xi.n_out)^+ S
+    is the same for every velocity of a cell and positive.  On the O-grid the
+    periodic seam couples the last and the first cell of every ring."""
+    if case == "cavity":
+        p = I.cavity(6, Kn=0.075, U=0.15, nv=6, vmax=4.0)
+        p.nodes_x, p.nodes_y = I.uniform_nodes(6, 5, 0, 1, 0, 0.8)
+    elif case == "ogrid_seam":
+        p = I.cylinder(ntheta=9, nr=5, nv=7, vmax=8.0, Ma=2.0, Kn=0.5, cfl_imp=10.0)
+    else:
+        p = I.tri_cavity(4, Kn=0.075, U=0.15, nv=6, vmax=4.0, cfl_imp=10.0)
+    o = O.Oracle(p)
+    o.init_uniform()
+    o.iterate(2)
+    rng = np.random.default_rng(3)
+    RG, RH = rng.standard_normal((o.N, o.Nv)), rng.standard_normal((o.N, o.Nv))
+    dG, dH, D = o.debug_micro_sweeps(RG, RH)
+    f = o.faces()
+    ux, uy, _ = o.velocity_grid()
+    N = o.N
+    seam = 0
+    for k in range(o.Nv):
+        Lm, Um = np.zeros((N, N)), np.zeros((N, N))
+        out = np.zeros(N)
+        for fi in range(o.nf):
+            a, b = f["L"][fi], f["R"][fi]
+            sn = ux[k] * f["nx"][fi] + uy[k] * f["ny"][fi]
+            S = f["S"][fi]
+            for c, nb, so in ((a, b, sn), (b, a, -sn)):
+                if c < 0:
+                    continue
+                if so > 0 and c != nb:
+                    out[c] += so * S
+                if nb < 0 or nb == c or so >= 0:
+                    continue
+                (Lm if nb < c else Um)[c, nb] += -so * S
+                if abs(nb - c) > 1 and abs(nb - c) != getattr(p, "ni", 0):
+                    seam += 1
+        Dk = D[:, k]
+        A = (np.diag(Dk) - Lm) @ np.diag(1.0 / Dk) @ (np.diag(Dk) - Um)
+        for R, d in ((RG[:, k], dG[:, k]), (RH[:, k], dH[:, k])):
+            assert np.abs(A @ d - R).max() <= 1e-12 * np.abs(R).max(), (case, k)
+        if k == 0:
+            base = Dk - out
+        assert np.allclose(Dk - out, base, rtol=1e-13, atol=0), (case, k)
+    assert np.all(base > 0)
+    if case == "ogrid_seam":
+        assert seam > 0
