@@ -197,17 +197,22 @@ idg_status idg_get_state(idg_ctx *ctx, double *G, double *H, double *W, void *st
 
 /* Checkpoint to / restart from a file (host I/O, synchronous on stream).
  * idg_save writes a 48-byte header -- the 8 bytes "IDGCKPT1", int32 format
- * version 1, int32 precision, int64 ncell, int64 nvel, int64 iterations
- * since the last restart, int64 0 -- then, all float64 little-endian: G, H
- * [ncell][nvel] and W [ncell][4] (the idg_get_state view); the reference
- * Maxwellian (rho, u, v, T) the storage is taken relative to; and the stored
- * deviations f~ - M_ref of G and H [ncell][nvel].  idg_load checks the header
- * against the context (same cell and velocity counts), restores that
- * reference Maxwellian and the deviations and W as stored, and restarts the
- * residual history as idg_set_state does: a context of the saving precision
- * resumes bitwise (the other precision converts the deviations).  Both need
- * a bound context (IDG_ERR_STATE); a null path, an unopenable, short, foreign
- * or mismatched file gives IDG_ERR_ARG. */
+ * version 2, int32 precision, int64 ncell, int64 nvel, int64 iterations
+ * since the last restart, int64 hash of the discretisation (64-bit FNV-1a
+ * of the mesh nodes and cell lists, the discrete velocities and weights and
+ * K, top bit cleared) -- then, all float64 little-endian: G, H [ncell][nvel]
+ * and W [ncell][4] (the idg_get_state view); the reference Maxwellian (rho,
+ * u, v, T) the storage is taken relative to; and the stored deviations
+ * f~ - M_ref of G and H [ncell][nvel].  idg_load checks the header against
+ * the context (same cell and velocity counts and, for version 2, the same
+ * discretisation hash; gas, boundaries and numerics may differ, e.g. to
+ * continue a converged state at another Kn), restores that reference
+ * Maxwellian and the deviations and W as stored, and restarts the residual
+ * history as idg_set_state does: a context of the saving precision resumes
+ * bitwise, one of the other precision converts the deviations to its
+ * storage (the header's precision says which saved it).  Both need a bound
+ * context (IDG_ERR_STATE); a null path, an unopenable, short, foreign or
+ * mismatched file gives IDG_ERR_ARG. */
 idg_status idg_save(idg_ctx *ctx, const char *path, void *stream);
 idg_status idg_load(idg_ctx *ctx, const char *path, void *stream);
 

@@ -1270,6 +1270,37 @@ struct CkptHeader {
 static_assert(sizeof(CkptHeader) == 48, "checkpoint header layout");
 const char kCkptMagic[8] = {'I', 'D', 'G', 'C', 'K', 'P', 'T', '1'};
 
+// 64-bit FNV-1a over the bytes of the discretisation the state lives on:
+// the mesh (node coordinates, unstructured cell lists), the discrete
+// velocities and weights, and the internal degrees of freedom K (the
+// meaning of H).  Gas, boundary and numerical settings are not part of it:
+// a checkpoint may start a run at another Kn or wall state (continuation).
+struct Fnv {
+    uint64_t h = 1469598103934665603ull;
+    void bytes(const void *p, size_t n)
+    {
+        const unsigned char *b = (const unsigned char *)p;
+        for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;
+    }
+    void vec(const std::vector<double> &v) { bytes(v.data(), v.size() * sizeof(double)); }
+    void vec(const std::vector<int> &v) { bytes(v.data(), v.size() * sizeof(int)); }
+};
+
+int64_t discretisation_hash(const idg_ctx *c)
+{
+    Fnv f;
+    const int32_t dims[5] = {c->ni, c->nj, c->unstr ? 1 : 0, c->K, c->Nvu};
+    f.bytes(dims, sizeof dims);
+    f.vec(c->nodes_x);
+    f.vec(c->nodes_y);
+    f.vec(c->ucell);
+    f.vec(c->uside);
+    f.bytes(c->ux.data(), (size_t)c->Nvu * 8);
+    f.bytes(c->uy.data(), (size_t)c->Nvu * 8);
+    f.bytes(c->w.data(), (size_t)c->Nvu * 8);
+    return (int64_t)(f.h & 0x7fffffffffffffffull);
+}
+
 bool write_all(FILE *fp, const std::vector<double> &v) { return std::fwrite(v.data(), 8, v.size(), fp) == v.size(); }
 bool read_all(FILE *fp, std::vector<double> &v) { return std::fread(v.data(), 8, v.size(), fp) == v.size(); }
 }  // namespace
@@ -1294,8 +1325,9 @@ idg_status idg_save(idg_ctx *c, const char *path, void *stream)
         return cuda_fail(c, e, "D2H deviations");
     CkptHeader h{};
     std::memcpy(h.magic, kCkptMagic, 8);
-    h.version = 1;
+    h.version = 2;
     h.precision = c->precision;
+    h.reserved = discretisation_hash(c);
     h.ncell = c->N;
     h.nvel = c->Nvu;
     h.iters = c->host_iter - c->start_iter;
@@ -1317,9 +1349,14 @@ idg_status idg_load(idg_ctx *c, const char *path, void *stream)
     FILE *fp = std::fopen(path, "rb");
     if (!fp) return fail(c, IDG_ERR_ARG, "cannot open %s", path);
     CkptHeader h{};
-    if (std::fread(&h, sizeof h, 1, fp) != 1 || std::memcmp(h.magic, kCkptMagic, 8) != 0 || h.version != 1) {
+    if (std::fread(&h, sizeof h, 1, fp) != 1 || std::memcmp(h.magic, kCkptMagic, 8) != 0 ||
+        (h.version != 1 && h.version != 2)) {
         std::fclose(fp);
-        return fail(c, IDG_ERR_ARG, "%s is not a version-1 checkpoint", path);
+        return fail(c, IDG_ERR_ARG, "%s is not a version-1 or -2 checkpoint", path);
+    }
+    if (h.version == 2 && h.reserved != discretisation_hash(c)) {
+        std::fclose(fp);
+        return fail(c, IDG_ERR_ARG, "%s was saved on another mesh, velocity grid or K", path);
     }
     if (h.ncell != c->N || h.nvel != c->Nvu) {
         std::fclose(fp);

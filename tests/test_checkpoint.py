@@ -36,8 +36,8 @@ def test_restart_from_a_checkpoint_continues_the_run(prec, tmp_path):
     a.save(path)
     G0, H0, W0 = a.get_state()
     raw = path.read_bytes()
-    magic, ver, precision, ncell, nvel, iters, _ = struct.unpack("<8siiqqqq", raw[:48])
-    assert magic == b"IDGCKPT1" and ver == 1 and (ncell, nvel) == (a.N, a.Nv) and iters == 7
+    magic, ver, precision, ncell, nvel, iters, hsh = struct.unpack("<8siiqqqq", raw[:48])
+    assert magic == b"IDGCKPT1" and ver == 2 and (ncell, nvel) == (a.N, a.Nv) and iters == 7 and hsh > 0
     assert len(raw) == 48 + 8 * (4 * a.N * a.Nv + 4 * a.N + 4)
     assert np.array_equal(np.frombuffer(raw, "<f8", a.N * a.Nv, 48).reshape(a.N, a.Nv), G0)
     b = Solver(_prob(), prec)
@@ -65,7 +65,21 @@ def test_mismatched_or_foreign_files_are_refused(tmp_path):
     junk.write_bytes(b"not a checkpoint" * 8)
     short = tmp_path / "short.ckpt"
     short.write_bytes(path.read_bytes()[:1000])
-    for ctx, f in ((other.ctx, path), (a.ctx, junk), (a.ctx, short), (a.ctx, tmp_path / "missing")):
+    # same cell and velocity counts, another mesh (a stretched O-grid) or
+    # another velocity range: refused by the discretisation hash
+    import dataclasses
+    q = _prob()
+    q.nodes_x, q.nodes_y = I.ogrid_nodes(20, 8, q=1.1)
+    moved = Solver(q, "fp64")
+    moved.init_uniform()
+    wider = Solver(dataclasses.replace(_prob(), vrange=(-9.0, 9.0, -9.0, 9.0)), "fp64")
+    wider.init_uniform()
+    # a different Kn is a continuation: accepted
+    kn = Solver(dataclasses.replace(_prob(), Kn=0.7), "fp64")
+    kn.init_uniform()
+    B.idg_load(kn.ctx, path)
+    for ctx, f in ((other.ctx, path), (moved.ctx, path), (wider.ctx, path), (a.ctx, junk), (a.ctx, short),
+                   (a.ctx, tmp_path / "missing")):
         with pytest.raises(B.IdgError) as e:
             B.idg_load(ctx, f)
         assert e.value.status == B.IDG_ERR_ARG

@@ -1,5 +1,5 @@
 """The macroscopic LU-SGS sweeps with one thread per line of cells
-(IDG_TUNE_MACRO_KIND 1, the default) against the FP64 oracle per iteration,
+(IDG_TUNE_MACRO_KIND 1) against the FP64 oracle per iteration,
 and against the hyperplane-slot kernel (kind 0), on the shapes that exercise
 each of its neighbour paths: lines along j (columns) and along i (rows), a
 periodic seam between the last and the first line (O-grids with fewer
@@ -43,6 +43,7 @@ _p.nodes_x, _p.nodes_y = I.uniform_nodes(40, 36, 0, 1, 0, 0.9)
 
 @pytest.mark.parametrize("name", sorted(CASES))
 def test_line_sweeps_match_oracle_and_hyperplane_kernel(name):
+    kind = 1
     from paper_1709_01819_gb300.solver import Solver
     prob = CASES[name]
     o = O.Oracle(prob)
@@ -50,7 +51,7 @@ def test_line_sweeps_match_oracle_and_hyperplane_kernel(name):
     s1 = Solver(prob, "fp64")
     s0 = Solver(prob, "fp64")
     assert s0.tuning()["macro_kind"] == 0  # the float64 default
-    s1.set_tuning(macro_kind=1)
+    s1.set_tuning(macro_kind=kind)
     for s in (s0, s1):
         s.init_uniform()
     for n in (1, 3):
@@ -68,11 +69,12 @@ def test_line_sweeps_match_oracle_and_hyperplane_kernel(name):
 
 
 def test_line_sweeps_mixed_precision_agree_with_hyperplane_kernel():
+    kind = 1
     from paper_1709_01819_gb300.solver import Solver
     prob = CASES["ogrid_34x40_cols_seam_2warps"]
     s1 = Solver(prob, "mixed")
     s0 = Solver(prob, "mixed")
-    assert s1.tuning()["macro_kind"] == 1  # the float32-storage default
+    s1.set_tuning(macro_kind=kind)
     s0.set_tuning(macro_kind=0)
     for s in (s0, s1):
         s.init_uniform()
