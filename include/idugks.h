@@ -298,9 +298,11 @@ idg_status idg_iterate_profiled(idg_ctx *ctx, void *stream, double *kernel_ms);
  * no effect on results).  IDG_TUNE_SWEEP_TV: discrete velocities per thread
  * block of the micro LU-SGS sweeps (power of two, 1..32, times min(ni, nj)
  * at most 512).  IDG_TUNE_SWEEP_STAGES / IDG_TUNE_MACRO_STAGES: hyperplanes
- * prefetched ahead by the micro / macroscopic sweeps (4 or 8; the
- * macroscopic sweep also 2, the depth a float64 block with min(ni, nj) above
- * 213 gets by default, its records filling shared memory).  Returns
+ * prefetched ahead by the micro / macroscopic sweeps (2, 4 or 8; 2 halves the
+ * micro sweeps' shared memory, so more velocity tiles are resident at once
+ * on a large velocity grid; the macroscopic sweep takes 2 by default for a
+ * float64 block with min(ni, nj) above 213, its records filling shared
+ * memory).  Returns
  * IDG_ERR_ARG for a value that is invalid or does not fit in shared memory.
  * IDG_TUNE_SWEEP_VPT: consecutive velocities per thread of the micro sweeps
  * (1, 2 or 4; all instances of a batch must agree).  Any velocity count takes

@@ -1515,7 +1515,7 @@ idg_status idg_set_tuning(idg_ctx *c, int key, int value)
             return fail(c, IDG_ERR_ARG, "velocities per thread %d must be 1, 2 or 4 and divide %d", value, k.Nv);
         k.sweep_vpt = value;
     } else if (key == IDG_TUNE_SWEEP_STAGES) {
-        if (value != 4 && value != 8) return fail(c, IDG_ERR_ARG, "sweep stages must be 4 or 8");
+        if (value != 2 && value != 4 && value != 8) return fail(c, IDG_ERR_ARG, "sweep stages must be 2, 4 or 8");
         k.sweep_stages = value;
     } else if (key == IDG_TUNE_MACRO_STAGES) {
         if (value != 2 && value != 4 && value != 8) return fail(c, IDG_ERR_ARG, "macro stages must be 2, 4 or 8");

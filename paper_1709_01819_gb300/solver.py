@@ -332,8 +332,11 @@ class Autotuner:
             return self.cache[key]
         G, H, W = solver.get_state()
         best, best_t = None, float("inf")
-        cands = [dict(sweep_tv=tv, sweep_vpt=vpt, sweep_stages=st, macro_stages=st)
-                 for tv in self.candidates_tv for vpt in self.candidates_vpt for st in (4, 8)]
+        # the micro sweeps' prefetch depth also decides how many velocity
+        # tiles fit on the GPU at once (shared memory per block); the
+        # macroscopic sweep keeps the deepest prefetch that fits
+        cands = [dict(sweep_tv=tv, sweep_vpt=vpt, sweep_stages=st, macro_stages=8)
+                 for tv in self.candidates_tv for vpt in self.candidates_vpt for st in (2, 4, 8)]
         for cand in cands:
             try:
                 solver.set_tuning(**cand)
