@@ -404,6 +404,23 @@ idg_status idg_adjoint_workspace_size(idg_ctx *ctx, size_t *bytes);
 idg_status idg_adjoint(idg_ctx *ctx, int objective, int side_mask, const int *params, int nparam,
                        void *workspace, size_t bytes, int max_iter, double tol, void *stream, double *J,
                        double *grad, int *iters_done, double *residual);
+/* Solver of idg_adjoint's linear system (I - M^T) lambda = dJ/du (the
+ * paper has no adjoint; a service of the library).  IDG_ADJ_FIXED_POINT
+ * (default): the transposed fixed-point iteration lambda <- dJ/du + M^T
+ * lambda, which converges at the rate of the forward iteration when the
+ * spectral radius of M^T is below one.  IDG_ADJ_GMRES: restarted GMRES(restart)
+ * on the same system with one transposed pass per Krylov vector; it needs no
+ * bound on the spectral radius (the linearisation, with the limiter frozen
+ * at its active branch, can have modes just outside the unit circle where the
+ * nonlinear forward iteration still converges), only a domain with a far
+ * field (one right-hand side; a closed domain returns IDG_ERR_ARG at
+ * idg_adjoint).  restart in [2, 64]; idg_adjoint_workspace_size grows by
+ * (restart + 4) float64 vectors of 2 ncell nvel + 4 ncell.  In GMRES mode
+ * max_iter counts transposed passes and tol bounds the relative residual
+ * ||dJ/du - (I - M^T) lambda|| / ||dJ/du||.  Takes effect at the next
+ * idg_adjoint_workspace_size / idg_adjoint. */
+enum { IDG_ADJ_FIXED_POINT = 0, IDG_ADJ_GMRES = 1 };
+idg_status idg_set_adjoint_solver(idg_ctx *ctx, int method, int restart);
 /* The adjoint variables lambda = (lambda_G, lambda_H [ncell][nvel], lambda_W
  * [ncell][4]) left in the workspace by the last idg_adjoint call of this
  * context.  which = 0: the adjoint of the returned gradient (for a closed

@@ -76,6 +76,7 @@ SIGNATURES = [
     ("idg_get_wall_force", _i, [_vp, _i, _P(_d), _vp]),
     ("idg_get_wall", _i, [_vp, _i, _P(_d), _i, _P(_i), _vp]),
     ("idg_adjoint_workspace_size", _i, [_vp, _P(_sz)]),
+    ("idg_set_adjoint_solver", _i, [_vp, _i, _i]),
     ("idg_adjoint_state", _i, [_vp, _vp, _i, _P(_d), _P(_d), _P(_d), _vp]),
     ("idg_adjoint", _i, [_vp, _i, _i, _P(_i), _i, _vp, _sz, _i, _d, _vp, _P(_d), _P(_d), _P(_i), _P(_d)]),
 ]
@@ -270,6 +271,13 @@ def idg_get_wall(ctx, side, stream=None):
     out = np.zeros((max(n.value, 1), 5))
     check(ctx, lib().idg_get_wall(ctx, side, dptr(out), n.value, C.byref(n), stream))
     return out[: n.value]
+
+
+IDG_ADJ_FIXED_POINT, IDG_ADJ_GMRES = 0, 1
+
+
+def idg_set_adjoint_solver(ctx, method, restart=20):
+    return check(ctx, lib().idg_set_adjoint_solver(ctx, method, restart))
 
 
 def idg_adjoint_workspace_size(ctx) -> int:

@@ -845,6 +845,49 @@ int launch_adjoint_zero(const AParams &a, void *stream)
     return (int)cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// vector operations of the Krylov solve (float64, deterministic: fixed grid,
+// per-block partial sums summed by the host in block order)
+// ---------------------------------------------------------------------------
+constexpr int kVecBlocks = 1024, kVecThreads = 256;
+
+__global__ void __launch_bounds__(kVecThreads) k_vec_dot(const double *x, const double *y, size_t n, double *part)
+{
+    __shared__ double sm[kVecThreads / 32];
+    double s = 0.0;
+    for (size_t i = blockIdx.x * (size_t)kVecThreads + threadIdx.x; i < n; i += (size_t)kVecBlocks * kVecThreads)
+        s += x[i] * y[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kVecThreads / 32; ++w) t += sm[w];
+        part[blockIdx.x] = t;
+    }
+}
+
+// y = a x + b y
+__global__ void k_vec_axpby(double a, const double *x, double b, double *y, size_t n)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        y[i] = a * x[i] + b * y[i];
+}
+
+int launch_vec_dot(const double *x, const double *y, size_t n, double *dpart, void *stream)
+{
+    k_vec_dot<<<kVecBlocks, kVecThreads, 0, (cudaStream_t)stream>>>(x, y, n, dpart);
+    return (int)cudaGetLastError();
+}
+
+int launch_vec_axpby(double a, const double *x, double b, double *y, size_t n, void *stream)
+{
+    k_vec_axpby<<<kVecBlocks, kVecThreads, 0, (cudaStream_t)stream>>>(a, x, b, y, n);
+    return (int)cudaGetLastError();
+}
+
+int vec_dot_blocks() { return kVecBlocks; }
+
 int launch_adjoint_iteration(const AParams &a, int it, void *stream)
 {
     cudaStream_t st = (cudaStream_t)stream;

@@ -73,5 +73,10 @@ size_t adjoint_layout(const AParams &shape, int nrhs, char *base, AParams *out);
 int launch_adjoint_setup(const AParams &a, void *stream);  // linearisation
 int launch_adjoint_zero(const AParams &a, void *stream);   // lambda = 0 of one solve
 int launch_adjoint_iteration(const AParams &a, int it, void *stream);
+// float64 vectors of the Krylov solve: per-block partials of x.y (vec_dot_blocks()
+// of them, summed on the host in order) and y = a x + b y
+int launch_vec_dot(const double *x, const double *y, size_t n, double *dpart, void *stream);
+int launch_vec_axpby(double a, const double *x, double b, double *y, size_t n, void *stream);
+int vec_dot_blocks();
 
 }  // namespace idg

@@ -76,6 +76,8 @@ struct idg_ctx {
     long long host_iter = 0;   // iterations launched since bind
     long long start_iter = 0;  // iteration index of the last (re)start
     std::vector<double> hist;  // absolute residuals since the last (re)start
+    // adjoint solver: IDG_ADJ_FIXED_POINT or IDG_ADJ_GMRES with restart adj_restart
+    int adj_method = 0, adj_restart = 20;
     // last idg_adjoint: number of right-hand sides and the mass multiplier
     int adj_nrhs = 0;
     double adj_beta = 0.0;
@@ -1985,6 +1987,17 @@ int adjoint_rhs(const idg_ctx *c)
     return 2;
 }
 
+// float64 length of the packed adjoint vector (lambda_G, lambda_H, lambda_W)
+size_t krylov_n(const idg_ctx *c) { return (size_t)2 * c->N * c->Nv + (size_t)4 * c->N; }
+
+// the Krylov solve's vectors after the adjoint workspace proper: the basis
+// (restart + 1 vectors), x, b, w, and the dot-product partials
+size_t krylov_bytes(const idg_ctx *c)
+{
+    if (c->adj_method != IDG_ADJ_GMRES) return 0;
+    return ((size_t)(c->adj_restart + 4) * krylov_n(c) + idg::vec_dot_blocks()) * sizeof(double) + 512;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1994,7 +2007,19 @@ idg_status idg_adjoint_workspace_size(idg_ctx *c, size_t *bytes)
     if (!c || !bytes) return IDG_ERR_ARG;
     idg_status s = build(c);
     if (s) return s;
-    *bytes = idg::adjoint_layout(adjoint_shape(c), adjoint_rhs(c), nullptr, nullptr);
+    *bytes = idg::adjoint_layout(adjoint_shape(c), adjoint_rhs(c), nullptr, nullptr) + krylov_bytes(c);
+    return IDG_OK;
+}
+
+idg_status idg_set_adjoint_solver(idg_ctx *c, int method, int restart)
+{
+    if (!c) return IDG_ERR_ARG;
+    if (method != IDG_ADJ_FIXED_POINT && method != IDG_ADJ_GMRES)
+        return fail(c, IDG_ERR_ARG, "unknown adjoint solver %d", method);
+    if (method == IDG_ADJ_GMRES && (restart < 2 || restart > 64))
+        return fail(c, IDG_ERR_ARG, "GMRES restart %d out of [2, 64]", restart);
+    c->adj_method = method;
+    if (method == IDG_ADJ_GMRES) c->adj_restart = restart;
     return IDG_OK;
 }
 
@@ -2031,7 +2056,10 @@ idg_status idg_adjoint(idg_ctx *c, int objective, int side_mask, const int *para
     if (!workspace) return fail(c, IDG_ERR_ARG, "null adjoint workspace");
     if (((uintptr_t)workspace) & 255) return fail(c, IDG_ERR_ARG, "adjoint workspace must be 256-byte aligned");
     const int nrhs = adjoint_rhs(c);
-    const size_t need = idg::adjoint_layout(adjoint_shape(c), nrhs, nullptr, nullptr);
+    if (c->adj_method == IDG_ADJ_GMRES && nrhs != 1)
+        return fail(c, IDG_ERR_ARG, "the GMRES adjoint solves one right-hand side: a domain with a far field");
+    const size_t base_need = idg::adjoint_layout(adjoint_shape(c), nrhs, nullptr, nullptr);
+    const size_t need = base_need + krylov_bytes(c);
     if (bytes < need) return fail(c, IDG_ERR_OOM, "adjoint workspace of %zu bytes, need %zu", bytes, need);
 
     idg::AParams base = adjoint_shape(c);
@@ -2065,17 +2093,134 @@ idg_status idg_adjoint(idg_ctx *c, int objective, int side_mask, const int *para
     for (int r = 0; r < nrhs && !rc; ++r) rc = idg::launch_adjoint_zero(A[r], st);
     if (rc) return cuda_fail(c, (cudaError_t)rc, "adjoint setup");
 
-    // Transposed fixed-point iterations, checked every chunk.  With two
-    // right-hand sides both lambdas grow linearly along the neutral mode
-    // (whose lambda_f part is zero); the multiplier beta = -<dW_J, dW_m> /
-    // <dW_m, dW_m> of the lambda_W increments cancels the growth, and
-    // lambda_J + beta lambda_m is the fixed-mass adjoint.
     const int chunk = 32;
     const size_t N4 = (size_t)4 * c->N;
     std::vector<double> buf[2], dW[2];
     double first = -1.0, rel = NAN, beta = 0.0;
     int done = 0;
     bool converged = false;
+    if (c->adj_method == IDG_ADJ_GMRES) {
+        // Restarted GMRES on (I - M^T) lambda = dJ/du.  One pass of the
+        // transposed iteration maps lambda to F(lambda) = dJ/du + M^T lambda,
+        // so A v = v - F(v) + F(0) and b = F(0); A does not need the spectral
+        // radius of M^T below one, as the fixed-point iteration does.  The
+        // vectors pack (lambda_G, lambda_H, lambda_W); dot products are summed
+        // in a fixed order.  The last pass runs at the solution, leaving the
+        // gradient's intermediates as the fixed-point iteration's last pass does.
+        const size_t n = krylov_n(c), NNv = (size_t)c->N * c->Nv;
+        const int m = c->adj_restart;
+        double *kv = (double *)(((uintptr_t)workspace + base_need + 255) & ~(uintptr_t)255);
+        double *V = kv, *xv = V + (size_t)(m + 1) * n, *bv = xv + n, *wv = bv + n, *dpart = wv + n;
+        const int nblk = idg::vec_dot_blocks();
+        std::vector<double> part(nblk);
+        auto cpy = [&](double *dst, const double *src, size_t cnt) {
+            return cudaMemcpyAsync(dst, src, cnt * 8, cudaMemcpyDeviceToDevice, st);
+        };
+        auto pack = [&](double *v) {
+            cudaError_t x = cpy(v, A[0].lamG, NNv);
+            if (x == cudaSuccess) x = cpy(v + NNv, A[0].lamH, NNv);
+            if (x == cudaSuccess) x = cpy(v + 2 * NNv, A[0].lamW, N4);
+            return x;
+        };
+        auto unpack = [&](const double *v) {
+            cudaError_t x = cpy(A[0].lamG, v, NNv);
+            if (x == cudaSuccess) x = cpy(A[0].lamH, v + NNv, NNv);
+            if (x == cudaSuccess) x = cpy(A[0].lamW, v + 2 * NNv, N4);
+            return x;
+        };
+        int err = 0;
+        auto pass = [&]() {
+            if (!err) err = idg::launch_adjoint_iteration(A[0], done % idg::kMaxHist, st);
+            ++done;
+        };
+        auto F = [&](const double *in, double *out) {  // out = F(in)
+            if (!err) err = (int)unpack(in);
+            pass();
+            if (!err) err = (int)pack(out);
+        };
+        auto axpby = [&](double a, const double *x, double b, double *y) {
+            if (!err) err = idg::launch_vec_axpby(a, x, b, y, n, st);
+        };
+        auto dot = [&](const double *x, const double *y) {
+            if (!err) err = idg::launch_vec_dot(x, y, n, dpart, st);
+            if (!err) err = (int)cudaMemcpyAsync(part.data(), dpart, nblk * 8, cudaMemcpyDeviceToHost, st);
+            if (!err) err = (int)cudaStreamSynchronize(st);
+            double t = 0.0;
+            for (int q = 0; q < nblk; ++q) t += part[q];
+            return err ? NAN : t;
+        };
+        // b = F(0) (lambda is zero after launch_adjoint_zero); x = 0
+        pass();
+        if (!err) err = (int)pack(bv);
+        if (!err) err = (int)cudaMemsetAsync(xv, 0, n * 8, st);
+        const double bnorm = std::sqrt(dot(bv, bv));
+        std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
+        rel = 1.0;
+        while (!err && done < max_iter) {
+            // r = b - A x = F(x) - x
+            F(xv, wv);
+            axpby(-1.0, xv, 1.0, wv);
+            const double r0 = std::sqrt(dot(wv, wv));
+            rel = bnorm > 0 ? r0 / bnorm : 0.0;
+            if (!std::isfinite(rel)) break;
+            if ((tol > 0 && rel <= tol) || r0 == 0.0) break;
+            axpby(1.0 / r0, wv, 0.0, V);
+            std::fill(g.begin(), g.end(), 0.0);
+            g[0] = r0;
+            int k = 0;
+            for (int j = 0; j < m && done < max_iter && !err; ++j) {
+                double *vj = V + (size_t)j * n, *w = V + (size_t)(j + 1) * n;
+                F(vj, w);                  // w = F(v_j)
+                axpby(1.0, vj, -1.0, w);   // w = v_j - F(v_j)
+                axpby(1.0, bv, 1.0, w);    // w = A v_j
+                for (int i = 0; i <= j; ++i) {  // modified Gram-Schmidt
+                    const double hij = dot(w, V + (size_t)i * n);
+                    H[(size_t)i * m + j] = hij;
+                    axpby(-hij, V + (size_t)i * n, 1.0, w);
+                }
+                const double hn = std::sqrt(dot(w, w));
+                H[(size_t)(j + 1) * m + j] = hn;
+                if (hn > 0) axpby(1.0 / hn, w, 0.0, w);
+                for (int i = 0; i < j; ++i) {  // earlier rotations on column j
+                    const double a0 = H[(size_t)i * m + j], a1 = H[(size_t)(i + 1) * m + j];
+                    H[(size_t)i * m + j] = cs[i] * a0 + sn[i] * a1;
+                    H[(size_t)(i + 1) * m + j] = -sn[i] * a0 + cs[i] * a1;
+                }
+                const double a0 = H[(size_t)j * m + j], a1 = H[(size_t)(j + 1) * m + j];
+                const double rr = std::hypot(a0, a1);
+                cs[j] = rr > 0 ? a0 / rr : 1.0;
+                sn[j] = rr > 0 ? a1 / rr : 0.0;
+                H[(size_t)j * m + j] = rr;
+                H[(size_t)(j + 1) * m + j] = 0.0;
+                g[j + 1] = -sn[j] * g[j];
+                g[j] = cs[j] * g[j];
+                k = j + 1;
+                rel = bnorm > 0 ? std::fabs(g[j + 1]) / bnorm : 0.0;
+                if (!std::isfinite(rel) || (tol > 0 && rel <= tol) || hn == 0.0) break;
+            }
+            for (int i = k - 1; i >= 0; --i) {  // H y = g, upper triangular
+                double t = g[i];
+                for (int q = i + 1; q < k; ++q) t -= H[(size_t)i * m + q] * y[q];
+                y[i] = t / H[(size_t)i * m + i];
+            }
+            for (int i = 0; i < k; ++i) axpby(y[i], V + (size_t)i * n, 1.0, xv);
+        }
+        if (err) return cuda_fail(c, (cudaError_t)err, "adjoint GMRES");
+        if (!std::isfinite(rel)) {
+            if (iters_done) *iters_done = done;
+            return fail(c, IDG_ERR_NONFINITE, "adjoint GMRES residual became non-finite");
+        }
+        converged = tol > 0 && rel <= tol;
+        // the last pass at the solution: the gradient's intermediates
+        if ((e = unpack(xv)) != cudaSuccess) return cuda_fail(c, e, "adjoint GMRES");
+        pass();
+        if (err) return cuda_fail(c, (cudaError_t)err, "adjoint GMRES");
+    } else {
+    // Transposed fixed-point iterations, checked every chunk.  With two
+    // right-hand sides both lambdas grow linearly along the neutral mode
+    // (whose lambda_f part is zero); the multiplier beta = -<dW_J, dW_m> /
+    // <dW_m, dW_m> of the lambda_W increments cancels the growth, and
+    // lambda_J + beta lambda_m is the fixed-mass adjoint.
     while (done < max_iter) {
         int n = std::min(chunk, max_iter - done);
         for (int q = 0; q < n; ++q)
@@ -2111,6 +2256,7 @@ idg_status idg_adjoint(idg_ctx *c, int objective, int side_mask, const int *para
         if (first < 0) first = buf[0][0] > 0 ? buf[0][0] : 1.0;
         rel = upd / first;
         if (tol > 0 && rel <= tol) { converged = true; break; }
+    }
     }
 
     // objective at the linearisation state and the parameter gradients of

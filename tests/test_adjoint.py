@@ -141,6 +141,29 @@ def test_adjoint_drag_gradient_cylinder():
     assert np.all(rel <= 1e-4), rel
 
 
+def test_gmres_adjoint_matches_fixed_point_and_differences():
+    """The restarted GMRES solve of (I - M^T) lambda = dJ/du gives the gradient
+    of the fixed-point iteration and of the oracle's central differences on
+    the reduced Ma 5 cylinder; a closed domain (two right-hand sides) is
+    refused."""
+    from paper_1709_01819_gb300 import binding as B
+
+    s = converged(CYL)
+    ok, J, g, n, r = s.adjoint(B.IDG_OBJ_FORCE_X, WALL, CYL_PARAMS, 40000, 1e-11)
+    assert ok, (n, r)
+    okg, Jg, gg, ng, rg = s.adjoint(B.IDG_OBJ_FORCE_X, WALL, CYL_PARAMS, 2000, 1e-11, solver="gmres", restart=20)
+    assert okg, (ng, rg)
+    assert Jg == J
+    assert np.all(np.abs(gg - g) <= 1e-8 * np.abs(g)), (gg, g)
+    _, gfd = oracle_fd(CYL, CYL_PARAMS, WALL, rel_step=1e-5)
+    assert np.all(np.abs(gg - gfd) <= 1e-4 * np.abs(gfd)), (gg, gfd)
+    print("fixed point", n, "passes; GMRES", ng, "passes")
+    cav = converged(CAV)
+    with pytest.raises(B.IdgError) as e:
+        cav.adjoint(B.IDG_OBJ_FORCE_X, LID, CAV_PARAMS, 100, 1e-10, solver="gmres")
+    assert e.value.status == B.IDG_ERR_ARG
+
+
 def test_steady_solve_autograd():
     import torch
 
