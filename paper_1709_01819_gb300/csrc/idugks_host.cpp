@@ -1525,11 +1525,15 @@ idg_status idg_set_tuning(idg_ctx *c, int key, int value)
     } else if (key == IDG_TUNE_MACRO_KIND) {
         if (value != 0 && value != 1) return fail(c, IDG_ERR_ARG, "macro kind must be 0 or 1");
         k.macro_kind = value;
+        // the prefetch depth is re-derived for the other kernel's records
+        k.macro_stages = 8;
     } else {
         return fail(c, IDG_ERR_ARG, "unknown tuning key %d", key);
     }
     idg::Plan trial{};
     idg::blocks_per_instance(k, trial.nblocks);
+    if (key == IDG_TUNE_MACRO_KIND && !idg::plan_shapes(&k, 1, c->precision == IDG_FP64, trial))
+        k.macro_stages = trial.macro_stages;
     if (idg::plan_shapes(&k, 1, c->precision == IDG_FP64, trial) ||
         trial.sweep_stages != k.sweep_stages || trial.macro_stages != k.macro_stages)
         return fail(c, IDG_ERR_ARG, "launch shape does not fit in shared memory");

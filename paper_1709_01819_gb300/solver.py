@@ -126,6 +126,8 @@ class Solver:
             B.idg_set_tuning(self.ctx, keys["sweep_vpt"], 1)
             B.idg_set_tuning(self.ctx, keys["sweep_tv"], 1)
         for k in ("graph", "macro_kind", "sweep_tv", "sweep_vpt", "sweep_stages", "macro_stages"):
+            if k == "macro_stages" and "macro_kind" in kw and k not in kw:
+                continue  # the library re-derives the depth for the chosen kernel
             v = kw.get(k, cur[k])
             B.idg_set_tuning(self.ctx, keys[k], int(v))
 

@@ -4,7 +4,9 @@ and against the hyperplane-slot kernel (kind 0), on the shapes that exercise
 each of its neighbour paths: lines along j (columns) and along i (rows), a
 periodic seam between the last and the first line (O-grids with fewer
 circumferential than radial cells), a periodic seam along the lines, and
-line counts that cross warp boundaries at ragged positions (Eq. 30)."""
+line counts that cross one to four warp boundaries at ragged positions, the
+float64 line kernel's records filling shared memory at 140 and 150 lines
+(Eq. 30)."""
 import numpy as np
 import pytest
 
@@ -34,11 +36,21 @@ CASES = {
     "ogrid_34x40_cols_seam_2warps": I.cylinder(ntheta=34, nr=40, nv=11, vmax=8.0, Ma=2.0, Kn=0.5, cfl_imp=10.0),
     # rows (ni > nj) over two warps (33 lines), periodic along the lines
     "ogrid_40x33_rows_2warps": I.cylinder(ntheta=40, nr=33, nv=11, vmax=8.0, Ma=2.0, Kn=0.5, cfl_imp=10.0),
+    # 70 columns over three warps, the last one ragged
+    "ogrid_70x74_cols_seam_3warps": I.cylinder(ntheta=70, nr=74, nv=11, vmax=8.0, Ma=2.0, Kn=0.5, cfl_imp=10.0),
+    # 150 columns over five warps: the seam between line 149 (warp 4) and
+    # line 0 (warp 0)
+    "ogrid_150x156_cols_seam_5warps": I.cylinder(ntheta=150, nr=156, nv=11, vmax=8.0, Ma=2.0, Kn=0.5,
+                                                  cfl_imp=10.0),
     # a closed box whose lines cross a warp boundary at 36
     "cavity_40x36_rows": I.cavity(40, Kn=0.075, U=0.15, nv=8, vmax=4.0),
+    # 140 rows over five warps, the last one ragged
+    "cavity_150x140_rows_5warps": I.cavity(150, Kn=0.075, U=0.15, nv=6, vmax=4.0),
 }
 _p = CASES["cavity_40x36_rows"]
 _p.nodes_x, _p.nodes_y = I.uniform_nodes(40, 36, 0, 1, 0, 0.9)
+_p = CASES["cavity_150x140_rows_5warps"]
+_p.nodes_x, _p.nodes_y = I.uniform_nodes(150, 140, 0, 1, 0, 140 / 150)
 
 
 @pytest.mark.parametrize("name", sorted(CASES))
@@ -71,7 +83,7 @@ def test_line_sweeps_match_oracle_and_hyperplane_kernel(name):
 def test_line_sweeps_mixed_precision_agree_with_hyperplane_kernel():
     kind = 1
     from paper_1709_01819_gb300.solver import Solver
-    prob = CASES["ogrid_34x40_cols_seam_2warps"]
+    prob = CASES["ogrid_150x156_cols_seam_5warps"]
     s1 = Solver(prob, "mixed")
     s0 = Solver(prob, "mixed")
     s1.set_tuning(macro_kind=kind)
