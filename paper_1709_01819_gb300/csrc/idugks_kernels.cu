@@ -1494,20 +1494,9 @@ template <class T> struct LineNb {
     T dw[4], b[6];
 };
 
-// acc += 1/2 (dF S - omega Lambda dW_nb) of one neighbour through slot m
-template <class T>
-__device__ __forceinline__ void line_term(T gm1, const T *rec, int m, const LineNb<T> &nb, T (&acc)[4])
+template <class T> static size_t macro_lines_smem_bytes(int nlines, int stages, int nw, bool seam)
 {
-    const T *cf = rec + 12 + 3 * m;
-    T dF[4];
-    euler_dflux<T>(gm1, nb.b, nb.dw, cf[0], cf[1], dF);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) acc[q] += dF[q] - cf[2] * nb.dw[q];
-}
-
-template <class T> static size_t macro_lines_smem_bytes(int nthr, int stages, int nw, bool seam)
-{
-    return ((size_t)stages * nthr * kLRec + 2 * 32 * 10 + (seam ? (size_t)nw * 10 : 0)) * sizeof(T);
+    return ((size_t)stages * nlines * kLRec + 2 * 32 * 12 + (seam ? (size_t)nw * 10 : 0)) * sizeof(T);
 }
 
 // what every step of k_macro_lines reads that does not change
@@ -1520,29 +1509,89 @@ template <class T> struct LineCtx {
     __device__ __forceinline__ int cell_of(int w) const { return cols ? w * ni + t : t * ni + w; }
 };
 
+// 16-byte cp.async that copies nothing and zero-fills its destination when
+// !valid (the source must still be a valid address)
+__device__ __forceinline__ void cp_async16_zfill(void *s, const void *g, bool valid)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_addr(s)), "l"(g), "r"(valid ? 16 : 0)
+                 : "memory");
+}
+
+// the record's first 12 entries (R[4], 1/D, pad, base state[6]) by 16-byte
+// shared-memory loads (the stage slots are 16-byte aligned)
+__device__ __forceinline__ void ld_rec12(const float *rec, float (&o)[12])
+{
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const float4 v = reinterpret_cast<const float4 *>(rec)[q];
+        o[4 * q] = v.x, o[4 * q + 1] = v.y, o[4 * q + 2] = v.z, o[4 * q + 3] = v.w;
+    }
+}
+__device__ __forceinline__ void ld_rec12(const double *rec, double (&o)[12])
+{
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        const double2 v = reinterpret_cast<const double2 *>(rec)[q];
+        o[2 * q] = v.x, o[2 * q + 1] = v.y;
+    }
+}
+
+// 1/x for the line sweep's flux increments: one approximate reciprocal in
+// float32 (the predictor's increments set the convergence path, not the
+// fixed point), correctly rounded in float64 (FP64 parity with the oracle)
+__device__ __forceinline__ float rcp_line(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ double rcp_line(double x) { return __drcp_rn(x); }
+
+// acc += 1/2 (dF S - omega Lambda dW_nb) of one neighbour through the slot
+// whose coefficients start at cf (euler_dflux with rcp_line)
+template <class T>
+__device__ __forceinline__ void line_term2(T gm1, const T *cf, const LineNb<T> &nb, T (&acc)[4])
+{
+    const T nx = cf[0], ny = cf[1], ol = cf[2];
+    const T *b = nb.b, *dW = nb.dw;
+    T rho = b[0], mx = b[1], my = b[2], u = b[3], v = b[4], H = b[5];
+    T ir1 = rcp_line(rho + dW[0]);
+    T du = (dW[1] - u * dW[0]) * ir1, dv = (dW[2] - v * dW[0]) * ir1;
+    T vn = u * nx + v * ny, dvn = du * nx + dv * ny, vn1 = vn + dvn;
+    T dmu = dW[1] * (u + du) + dW[2] * (v + dv) + mx * du + my * dv;
+    T dp = gm1 * (dW[3] - (T)0.5 * dmu);
+    acc[0] += dW[0] * vn1 + rho * dvn - ol * dW[0];
+    acc[1] += dW[1] * vn1 + mx * dvn + dp * nx - ol * dW[1];
+    acc[2] += dW[2] * vn1 + my * dvn + dp * ny - ol * dW[2];
+    acc[3] += (dW[3] + dp) * vn1 + H * dvn - ol * dW[3];
+}
+
 // one direction of k_macro_lines (the direction a template parameter: one
-// shuffle direction, one set of slots).  A neighbour that does not exist
-// enters with a zero increment on a unit-density base state: its flux
-// increment (euler_dflux) is then exactly zero, so no term needs a branch.
-template <class T, int kStages, bool FWD> __device__ __forceinline__ void line_sweep(const LineCtx<T> &x)
+// shuffle direction, one set of slots; SEAM: the block has a periodic seam).
+// The step is written without branches on the common path so that the
+// compiler can interleave the prefetch, the record loads and the stores with
+// the dependent flux arithmetic: every thread issues its copies each step
+// (zero-filling the slot where its line has no cell at that step), evaluates
+// the step on whatever the slot holds, and keeps the result only where the
+// line has a cell.  A neighbour that does not exist enters with a zero
+// increment on a unit-density base state: its flux increment is exactly
+// zero, so no term needs a branch.
+template <class T, int kStages, bool FWD, bool SEAM> __device__ __forceinline__ void line_sweep(const LineCtx<T> &x)
 {
     constexpr int RC = kMRec * sizeof(T) / 16, DC = 4 * sizeof(T) / 16;
     auto step_d = [&](int s) { return FWD ? s : x.nh - 1 - s; };
     auto issue = [&](int s) {
-        if (s < x.nh && x.line) {
-            const int w = step_d(s) - x.t;
-            if (w >= 0 && w < x.nw) {
-                const int c = x.cell_of(w);
-                T *dst = x.stage + ((size_t)(s & (kStages - 1)) * x.nthr + x.t) * kLRec;
+        const int w = step_d(s) - x.t;
+        const bool valid = s < x.nh && x.line && (unsigned)w < (unsigned)x.nw;
+        const int c = valid ? x.cell_of(w) : 0;
+        T *dst = x.stage + ((size_t)(s & (kStages - 1)) * x.nthr + x.t) * kLRec;
 #pragma unroll
-                for (int q = 0; q < RC; ++q)
-                    cp_async16((char *)dst + 16 * q, (const char *)(x.mrec + (size_t)kMRec * c) + 16 * q);
-                if (!FWD)
+        for (int q = 0; q < RC; ++q)
+            cp_async16_zfill((char *)dst + 16 * q, (const char *)(x.mrec + (size_t)kMRec * c) + 16 * q, valid);
+        if (!FWD)
 #pragma unroll
-                    for (int q = 0; q < DC; ++q)
-                        cp_async16((char *)(dst + kMRec) + 16 * q, (const char *)(x.dWg + 4 * (size_t)c) + 16 * q);
-            }
-        }
+            for (int q = 0; q < DC; ++q)
+                cp_async16_zfill((char *)(dst + kMRec) + 16 * q, (const char *)(x.dWg + 4 * (size_t)c) + 16 * q, valid);
         cp_commit();
     };
     for (int s = 0; s < kStages - 1; ++s) issue(s);
@@ -1554,39 +1603,40 @@ template <class T, int kStages, bool FWD> __device__ __forceinline__ void line_s
     const int s_adj = FWD ? x.s_tm : x.s_tp, s_own = FWD ? x.s_wm : x.s_wp;
     const int s_seam_t = FWD ? x.s_tp : x.s_tm, s_seam_w = FWD ? x.s_wp : x.s_wm;
     const bool has_adj = FWD ? x.t >= 1 : x.t + 1 < x.nt;
-    const bool seam_t_reader = x.per_t && x.t == (FWD ? x.nt - 1 : 0);
-    const bool seam_t_writer = x.per_t && x.t == (FWD ? 0 : x.nt - 1);
+    const bool seam_t_reader = SEAM && x.per_t && x.t == (FWD ? x.nt - 1 : 0);
+    const bool seam_t_writer = SEAM && x.per_t && x.t == (FWD ? 0 : x.nt - 1);
     const bool edge_reader = FWD ? (x.lane == 0 && x.wid > 0) : (x.lane == 31 && x.wid + 1 < x.nwarp);
     const bool edge_writer = FWD ? x.lane == 31 : x.lane == 0;
-    const int edge_src = FWD ? x.wid - 1 : x.wid + 1;
+    // the exchange entry this thread may read (a valid one for every thread)
+    const int edge_src = edge_reader ? (FWD ? x.wid - 1 : x.wid + 1) : 0;
     for (int s = 0; s < x.nh; ++s) {
         cp_wait<kStages - 2>();
-        __syncthreads();  // the exchange slots of the previous step are written
+        __syncthreads();  // the step's records and the exchange entries of the previous step are written
         issue(s + kStages - 1);
         const int w = step_d(s) - x.t;
+        const bool on = x.line && (unsigned)w < (unsigned)x.nw;
+        const T *rec = x.stage + ((size_t)(s & (kStages - 1)) * x.nthr + x.t) * kLRec;
+        T r12[12];
+        ld_rec12(rec, r12);
         // the adjacent line's result of the previous step, at this thread's w
+        T ev[12];
+        ld_rec12(x.xb + ((size_t)((s + 1) & 1) * 32 + edge_src) * 12, ev);
         LineNb<T> adj;
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-            adj.dw[q] = FWD ? __shfl_up_sync(0xffffffffu, prev.dw[q], 1) : __shfl_down_sync(0xffffffffu, prev.dw[q], 1);
-#pragma unroll
-        for (int q = 0; q < 6; ++q)
-            adj.b[q] = FWD ? __shfl_up_sync(0xffffffffu, prev.b[q], 1) : __shfl_down_sync(0xffffffffu, prev.b[q], 1);
-        if (edge_reader) {
-            const T *e = x.xb + ((size_t)((s + 1) & 1) * 32 + edge_src) * 10;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) adj.dw[q] = e[q];
-#pragma unroll
-            for (int q = 0; q < 6; ++q) adj.b[q] = e[4 + q];
+        for (int q = 0; q < 4; ++q) {
+            const T sh = FWD ? __shfl_up_sync(0xffffffffu, prev.dw[q], 1) : __shfl_down_sync(0xffffffffu, prev.dw[q], 1);
+            adj.dw[q] = has_adj ? (edge_reader ? ev[q] : sh) : (T)0;
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) adj.dw[q] = has_adj ? adj.dw[q] : (T)0;
-        if (x.line && w >= 0 && w < x.nw) {
-            const T *rec = x.stage + ((size_t)(s & (kStages - 1)) * x.nthr + x.t) * kLRec;
-            T acc[4] = {0, 0, 0, 0};
-            line_term<T>(x.gm1, rec, s_adj, adj, acc);
-            // prev is the zero-increment initial state at the line's first cell
-            line_term<T>(x.gm1, rec, s_own, prev, acc);
+        for (int q = 0; q < 6; ++q) {
+            const T sh = FWD ? __shfl_up_sync(0xffffffffu, prev.b[q], 1) : __shfl_down_sync(0xffffffffu, prev.b[q], 1);
+            adj.b[q] = edge_reader ? ev[4 + q] : sh;
+        }
+        T acc[4] = {0, 0, 0, 0};
+        line_term2<T>(x.gm1, rec + 12 + 3 * s_adj, adj, acc);
+        // prev is the zero-increment initial state at the line's first cell
+        line_term2<T>(x.gm1, rec + 12 + 3 * s_own, prev, acc);
+        if (SEAM && on) {
             if (seam_t_reader) {
                 LineNb<T> sn;
                 const T *e = x.seam + (size_t)w * 10;
@@ -1594,44 +1644,71 @@ template <class T, int kStages, bool FWD> __device__ __forceinline__ void line_s
                 for (int q = 0; q < 4; ++q) sn.dw[q] = e[q];
 #pragma unroll
                 for (int q = 0; q < 6; ++q) sn.b[q] = e[4 + q];
-                line_term<T>(x.gm1, rec, s_seam_t, sn, acc);
+                line_term2<T>(x.gm1, rec + 12 + 3 * s_seam_t, sn, acc);
             }
-            if (x.per_w && w == (FWD ? x.nw - 1 : 0)) line_term<T>(x.gm1, rec, s_seam_w, first, acc);
-            // forward: dW*_c = (R_c - sum_lower) / D_c;  backward: dW_c = dW*_c - sum_upper / D_c
-            const T iD = rec[4];
+            if (x.per_w && w == (FWD ? x.nw - 1 : 0)) line_term2<T>(x.gm1, rec + 12 + 3 * s_seam_w, first, acc);
+        }
+        // forward: dW*_c = (R_c - sum_lower) / D_c;  backward: dW_c = dW*_c - sum_upper / D_c
+        const T iD = r12[4];
+        LineNb<T> out;
+        if (FWD) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) prev.dw[q] = FWD ? (rec[q] - acc[q]) * iD : rec[kMRec + q] - acc[q] * iD;
+            for (int q = 0; q < 4; ++q) out.dw[q] = (r12[q] - acc[q]) * iD;
+        } else {
+            T ds[4];
+            if (sizeof(T) == 4) {
+                const float4 v = *reinterpret_cast<const float4 *>(rec + kMRec);
+                ds[0] = v.x, ds[1] = v.y, ds[2] = v.z, ds[3] = v.w;
+            } else {
 #pragma unroll
-            for (int q = 0; q < 6; ++q) prev.b[q] = rec[6 + q];
-            const int c = x.cell_of(w);
+                for (int q = 0; q < 4; ++q) ds[q] = rec[kMRec + q];
+            }
 #pragma unroll
-            for (int q = 0; q < 4; ++q) x.dWg[4 * (size_t)c + q] = prev.dw[q];
+            for (int q = 0; q < 4; ++q) out.dw[q] = ds[q] - acc[q] * iD;
+        }
+#pragma unroll
+        for (int q = 0; q < 6; ++q) out.b[q] = r12[6 + q];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) prev.dw[q] = on ? out.dw[q] : prev.dw[q];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) prev.b[q] = on ? out.b[q] : prev.b[q];
+        if (on) {
+            T *g = x.dWg + 4 * (size_t)x.cell_of(w);
+            if (sizeof(T) == 4) {
+                *reinterpret_cast<float4 *>(g) = make_float4(out.dw[0], out.dw[1], out.dw[2], out.dw[3]);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) g[q] = out.dw[q];
+            }
+        }
+        if (SEAM && on) {
             // the cell a later cell of this line meets across the seam along the line
-            if (x.per_w && w == (FWD ? 0 : x.nw - 1)) first = prev;
+            if (x.per_w && w == (FWD ? 0 : x.nw - 1)) first = out;
             // the seam line's cells for the line across the seam between lines
             if (seam_t_writer) {
                 T *e = x.seam + (size_t)w * 10;
 #pragma unroll
-                for (int q = 0; q < 4; ++q) e[q] = prev.dw[q];
+                for (int q = 0; q < 4; ++q) e[q] = out.dw[q];
 #pragma unroll
-                for (int q = 0; q < 6; ++q) e[4 + q] = prev.b[q];
+                for (int q = 0; q < 6; ++q) e[4 + q] = out.b[q];
             }
-            // the warp-boundary lane's result for the next warp's edge lane
-            if (edge_writer) {
-                T *e = x.xb + ((size_t)(s & 1) * 32 + x.wid) * 10;
+        }
+        // the warp-boundary lane's result for the next warp's edge lane
+        // (its line's current state; a line without a cell leaves it as it was)
+        if (edge_writer) {
+            T *e = x.xb + ((size_t)(s & 1) * 32 + x.wid) * 12;
 #pragma unroll
-                for (int q = 0; q < 4; ++q) e[q] = prev.dw[q];
+            for (int q = 0; q < 4; ++q) e[q] = prev.dw[q];
 #pragma unroll
-                for (int q = 0; q < 6; ++q) e[4 + q] = prev.b[q];
-            }
+            for (int q = 0; q < 6; ++q) e[4 + q] = prev.b[q];
         }
     }
     cp_wait<0>();
     __syncthreads();
 }
 
-template <class T, int kStages>
-__global__ void __launch_bounds__(256) k_macro_lines(Launch L)
+template <class T, int kStages, bool SEAM>
+__global__ void __launch_bounds__(256, 1) k_macro_lines(Launch L)
 {
     IDG_LOCATE();
     (void)blk;
@@ -1659,18 +1736,18 @@ __global__ void __launch_bounds__(256) k_macro_lines(Launch L)
     x.s_wm = x.cols ? 2 : 0;
     x.s_wp = x.cols ? 3 : 1;
     x.stage = (T *)smraw;                                     // [kStages][nthr][kLRec]
-    x.xb = x.stage + (size_t)kStages * x.nthr * kLRec;        // [2][32 warps][10] warp-boundary exchange
-    x.seam = x.xb + 2 * 32 * 10;                              // [nw][10] the seam line's cells (per_t)
+    x.xb = x.stage + (size_t)kStages * x.nthr * kLRec;        // [2][32 warps][12] warp-boundary exchange
+    x.seam = x.xb + 2 * 32 * 12;                              // [nw][10] the seam line's cells (per_t)
     x.dWg = (T *)p.mdW;
     x.mrec = (const T *)p.mrec;
     x.gm1 = (T)(p.gam - 1.0);
-    // exchange slots never written read as benign neighbours (zero increment,
-    // unit density); they are masked out anyway
-    for (int q = x.t; q < 2 * 32 * 10; q += x.nthr) x.xb[q] = (q % 10 == 4) ? (T)1 : (T)0;
+    // exchange entries never written read as benign neighbours (zero
+    // increment, unit density)
+    for (int q = x.t; q < 2 * 32 * 12; q += x.nthr) x.xb[q] = (q % 12 == 4) ? (T)1 : (T)0;
     if (x.t == 0) record_residual(p);
     __syncthreads();
-    line_sweep<T, kStages, true>(x);
-    line_sweep<T, kStages, false>(x);
+    line_sweep<T, kStages, true, SEAM>(x);
+    line_sweep<T, kStages, false, SEAM>(x);
     if (x.t == 0) *p.iter += 1;
 }
 
@@ -2368,17 +2445,22 @@ int plan_shapes(const KParams *hp, int n, bool fp64, Plan &pl)
     if (pl.macro_kind == 1 && !pl.sched) {
         // one thread per line of the shorter axis; the seam array holds the
         // walk axis' cells when the lines wrap around (a periodic shorter axis)
-        pl.macro_threads = 0;
-        for (int i = 0; i < n; ++i)
-            pl.macro_threads = std::max(pl.macro_threads, ((std::min(hp[i].ni, hp[i].nj) + 31) / 32) * 32);
+        int ntmax = 0;
+        pl.macro_seam = 0;
+        for (int i = 0; i < n; ++i) {
+            ntmax = std::max(ntmax, std::min(hp[i].ni, hp[i].nj));
+            pl.macro_seam |= hp[i].per_i | hp[i].per_j;
+        }
+        pl.macro_threads = ((ntmax + 31) / 32) * 32;
+        const int nlines = pl.macro_threads;
         for (int stages : {std::min(hp[0].macro_stages, 8), 4, 2}) {
             size_t m = 0;
             for (int i = 0; i < n; ++i) {
                 const bool cols = hp[i].ni <= hp[i].nj;
                 const bool seam = cols ? hp[i].per_i : hp[i].per_j;
                 const int nw = std::max(hp[i].ni, hp[i].nj);
-                m = std::max(m, fp64 ? macro_lines_smem_bytes<double>(pl.macro_threads, stages, nw, seam)
-                                     : macro_lines_smem_bytes<float>(pl.macro_threads, stages, nw, seam));
+                m = std::max(m, fp64 ? macro_lines_smem_bytes<double>(nlines, stages, nw, seam)
+                                     : macro_lines_smem_bytes<float>(nlines, stages, nw, seam));
             }
             pl.macro_stages = stages;
             pl.macro_smem = m;
@@ -2513,12 +2595,18 @@ static int iteration_t(const Plan &pl, cudaStream_t st, void **events)
         else
             k_macro_sweep_sched<T, false><<<nb[KT_MACRO_SWEEP], 256, 0, st>>>(L(KT_MACRO_SWEEP));
     } else if (pl.macro_kind == 1) {
-        if (pl.macro_stages == 8)
-            k_macro_lines<T, 8><<<nb[KT_MACRO_SWEEP], pl.macro_threads, pl.macro_smem, st>>>(L(KT_MACRO_SWEEP));
-        else if (pl.macro_stages == 4)
-            k_macro_lines<T, 4><<<nb[KT_MACRO_SWEEP], pl.macro_threads, pl.macro_smem, st>>>(L(KT_MACRO_SWEEP));
-        else
-            k_macro_lines<T, 2><<<nb[KT_MACRO_SWEEP], pl.macro_threads, pl.macro_smem, st>>>(L(KT_MACRO_SWEEP));
+        const int nb1 = nb[KT_MACRO_SWEEP], nt1 = pl.macro_threads;
+        const size_t sm1 = pl.macro_smem;
+        const Launch L1 = L(KT_MACRO_SWEEP);
+        if (pl.macro_seam) {
+            if (pl.macro_stages == 8) k_macro_lines<T, 8, true><<<nb1, nt1, sm1, st>>>(L1);
+            else if (pl.macro_stages == 4) k_macro_lines<T, 4, true><<<nb1, nt1, sm1, st>>>(L1);
+            else k_macro_lines<T, 2, true><<<nb1, nt1, sm1, st>>>(L1);
+        } else {
+            if (pl.macro_stages == 8) k_macro_lines<T, 8, false><<<nb1, nt1, sm1, st>>>(L1);
+            else if (pl.macro_stages == 4) k_macro_lines<T, 4, false><<<nb1, nt1, sm1, st>>>(L1);
+            else k_macro_lines<T, 2, false><<<nb1, nt1, sm1, st>>>(L1);
+        }
     } else if (pl.macro_stages == 8)
         k_macro_sweep<T, 8><<<nb[KT_MACRO_SWEEP], pl.macro_threads, pl.macro_smem, st>>>(L(KT_MACRO_SWEEP));
     else if (pl.macro_stages == 4)
@@ -2544,9 +2632,12 @@ template <class T> static int configure_t()
         if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     };
     opt((const void *)k_macro_sweep_sched<T, true>);
-    opt((const void *)k_macro_lines<T, 8>);
-    opt((const void *)k_macro_lines<T, 4>);
-    opt((const void *)k_macro_lines<T, 2>);
+    opt((const void *)k_macro_lines<T, 8, false>);
+    opt((const void *)k_macro_lines<T, 4, false>);
+    opt((const void *)k_macro_lines<T, 2, false>);
+    opt((const void *)k_macro_lines<T, 8, true>);
+    opt((const void *)k_macro_lines<T, 4, true>);
+    opt((const void *)k_macro_lines<T, 2, true>);
     opt((const void *)k_macro_sweep<T, 8>);
     opt((const void *)k_macro_sweep<T, 4>);
     opt((const void *)k_macro_sweep<T, 2>);

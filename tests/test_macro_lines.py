@@ -6,7 +6,9 @@ periodic seam between the last and the first line (O-grids with fewer
 circumferential than radial cells), a periodic seam along the lines, and
 line counts that cross one to four warp boundaries at ragged positions, the
 float64 line kernel's records filling shared memory at 140 and 150 lines
-(Eq. 30)."""
+(Eq. 30).  The cavities run the kernel's seam-free instantiation, the O-grids
+the one with seam terms; in mixed precision both are held to the slot kernel
+(whose reciprocals are correctly rounded)."""
 import numpy as np
 import pytest
 
@@ -80,10 +82,11 @@ def test_line_sweeps_match_oracle_and_hyperplane_kernel(name):
         assert _rel(G1, G0) < 1e-13
 
 
-def test_line_sweeps_mixed_precision_agree_with_hyperplane_kernel():
+@pytest.mark.parametrize("name", ["ogrid_150x156_cols_seam_5warps", "cavity_150x140_rows_5warps"])
+def test_line_sweeps_mixed_precision_agree_with_hyperplane_kernel(name):
     kind = 1
     from paper_1709_01819_gb300.solver import Solver
-    prob = CASES["ogrid_150x156_cols_seam_5warps"]
+    prob = CASES[name]
     s1 = Solver(prob, "mixed")
     s0 = Solver(prob, "mixed")
     s1.set_tuning(macro_kind=kind)
