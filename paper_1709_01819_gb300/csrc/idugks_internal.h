@@ -121,7 +121,7 @@ struct Plan {
     size_t macro_smem, fwd_smem, bwd_smem;
     int macro_stages, sweep_stages, limiter_any, sweep_vpt;
     int macro_kind;      // KParams::macro_kind of every instance
-    int macro_seam;      // 1: an instance has a periodic direction (k_macro_lines' seam terms)
+    int any_seam;        // 1: an instance has a periodic direction (k_macro_lines' seam terms)
     int explicit_dugks;  // 1: launch_iteration runs one explicit DUGKS step (Eq. 21)
     int relax_sweeps;    // macroscopic predictor of every instance (KParams::relax_sweeps)
     int sched;           // 1: the instances are unstructured (scheduled sweeps)

@@ -75,6 +75,17 @@ __device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(
 // without the general division routine
 __device__ __forceinline__ float rcp_rn(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double rcp_rn(double x) { return __drcp_rn(x); }
+// 1/x in the line macroscopic sweep's flux increments: one approximate
+// reciprocal in float32 -- the predictor's increments set the convergence
+// path, not the fixed point, which the residual alone fixes -- and correctly
+// rounded in float64 (FP64 parity with the oracle)
+__device__ __forceinline__ float rcp_line(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ double rcp_line(double x) { return __drcp_rn(x); }
 __device__ __forceinline__ float t_expm1(float x) { return expm1f(x); }
 __device__ __forceinline__ double t_expm1(double x) { return expm1(x); }
 __device__ __forceinline__ float t_exp(float x) { return expf(x); }
@@ -1536,16 +1547,6 @@ __device__ __forceinline__ void ld_rec12(const double *rec, double (&o)[12])
     }
 }
 
-// 1/x for the line sweep's flux increments: one approximate reciprocal in
-// float32 (the predictor's increments set the convergence path, not the
-// fixed point), correctly rounded in float64 (FP64 parity with the oracle)
-__device__ __forceinline__ float rcp_line(float x)
-{
-    float r;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
-__device__ __forceinline__ double rcp_line(double x) { return __drcp_rn(x); }
 
 // acc += 1/2 (dF S - omega Lambda dW_nb) of one neighbour through the slot
 // whose coefficients start at cf (euler_dflux with rcp_line)
@@ -2439,6 +2440,8 @@ int plan_shapes(const KParams *hp, int n, bool fp64, Plan &pl)
         if (hp[i].sweep_vpt != pl.sweep_vpt) return (int)cudaErrorInvalidValue;
     }
     if (!pl.sched || pl.sched_smem > 200 * 1024) pl.sched_smem = 0;
+    pl.any_seam = 0;
+    for (int i = 0; i < n; ++i) pl.any_seam |= hp[i].per_i | hp[i].per_j;
     pl.macro_kind = hp[0].macro_kind;
     for (int i = 0; i < n; ++i)
         if (hp[i].macro_kind != pl.macro_kind) return (int)cudaErrorInvalidValue;
@@ -2446,11 +2449,7 @@ int plan_shapes(const KParams *hp, int n, bool fp64, Plan &pl)
         // one thread per line of the shorter axis; the seam array holds the
         // walk axis' cells when the lines wrap around (a periodic shorter axis)
         int ntmax = 0;
-        pl.macro_seam = 0;
-        for (int i = 0; i < n; ++i) {
-            ntmax = std::max(ntmax, std::min(hp[i].ni, hp[i].nj));
-            pl.macro_seam |= hp[i].per_i | hp[i].per_j;
-        }
+        for (int i = 0; i < n; ++i) ntmax = std::max(ntmax, std::min(hp[i].ni, hp[i].nj));
         pl.macro_threads = ((ntmax + 31) / 32) * 32;
         const int nlines = pl.macro_threads;
         for (int stages : {std::min(hp[0].macro_stages, 8), 4, 2}) {
@@ -2598,7 +2597,7 @@ static int iteration_t(const Plan &pl, cudaStream_t st, void **events)
         const int nb1 = nb[KT_MACRO_SWEEP], nt1 = pl.macro_threads;
         const size_t sm1 = pl.macro_smem;
         const Launch L1 = L(KT_MACRO_SWEEP);
-        if (pl.macro_seam) {
+        if (pl.any_seam) {
             if (pl.macro_stages == 8) k_macro_lines<T, 8, true><<<nb1, nt1, sm1, st>>>(L1);
             else if (pl.macro_stages == 4) k_macro_lines<T, 4, true><<<nb1, nt1, sm1, st>>>(L1);
             else k_macro_lines<T, 2, true><<<nb1, nt1, sm1, st>>>(L1);
