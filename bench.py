@@ -374,10 +374,11 @@ def profiled_group_ms(s, flush, nprof: int = 10):
     return kms / nprof
 
 
-def time_workload(prob, precision, local, flush, peak, tune="auto", steps=10, warmup=3):
+def time_workload(prob, precision, local, flush, peak, tune="auto", steps=10, warmup=3, traffic_of=None):
     """ms per iteration (CUDA events around each, L2 flushed between), the
     update rate, the group times and the roofline of one workload from its
-    uniform start after warm-up iterations."""
+    uniform start after warm-up iterations; traffic_of(group) gives the
+    group's DRAM bytes per launch from an ncu capture (or None)."""
     import torch
     from paper_1709_01819_gb300.solver import Autotuner, Solver
     s = Solver(prob, precision, device=local)
@@ -402,7 +403,7 @@ def time_workload(prob, precision, local, flush, peak, tune="auto", steps=10, wa
     sb = 8 if precision == "fp64" else 4
     out = {"workload": prob.name, "cells": prob.ncells, "velocities": prob.nvel, "precision": precision,
            "ms_per_step": ms, "value": prob.ncells * prob.nvel / (ms * 1e-3), "unit": "cell-velocity updates/s",
-           "steps": steps, "tuning": s.tuning(), "roofline": roofline(prob, sb, kms, ms, peak),
+           "steps": steps, "tuning": s.tuning(), "roofline": roofline(prob, sb, kms, ms, peak, traffic_of),
            "clocks": clk.summary()}
     del s
     torch.cuda.empty_cache()
@@ -615,7 +616,8 @@ def main():
         torch.cuda.empty_cache()
         for name in args.extra_workloads.split(","):
             extra[name] = time_workload(workload(name), args.precision, local, flush, peak, args.tune,
-                                        steps=10, warmup=3)
+                                        steps=10, warmup=3,
+                                        traffic_of=lambda g, n=name: tr.get(f"{n}:{args.precision}:{g}"))
             extra[name]["roofline"]["peak_source"] = roof["peak_source"]
             if args.ttr_extra:
                 extra[name]["time_to_residual_1e-6"] = ttr_runs(workload(name), local, max_iter=40000)
