@@ -103,7 +103,10 @@ def test_adjoint_first_two_passes_match_forward_differences():
 
 
 def test_adjoint_mixed_precision_state():
-    """The adjoint (float64) linearised at a float32 state converged to 1e-6."""
+    """The adjoint (float64) linearised at a float32 state converged to 1e-6,
+    held to the same 1e-4 as the FP64 state (measured on a GB300: 1.5e-8 to
+    3.4e-8 relative against the oracle's central differences; the float32
+    state's objective is within 1e-7 of the oracle's)."""
     from paper_1709_01819_gb300 import binding as B
 
     s = converged(CAV, "mixed", tol=1e-6)
@@ -112,7 +115,7 @@ def test_adjoint_mixed_precision_state():
     _, gfd = oracle_fd(CAV, CAV_PARAMS, LID)
     rel = np.abs(g - gfd) / np.abs(gfd)
     print("mixed-precision state: adjoint", g, "fd", gfd, "rel", rel)
-    assert np.all(rel <= 1e-3), rel
+    assert np.all(rel <= 1e-4), rel
 
 
 # reduced hypersonic cylinder: Ma 5, Shakhov, VHS 0.81, limiter, far field
