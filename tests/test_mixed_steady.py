@@ -42,7 +42,11 @@ def test_mixed_steady_field_within_1e5_of_fp64(name):
     stops near 3e-7); float64 continued from that state until its own
     residual has fallen by at least 1e5 more; the two fields compared.  At
     full size (the 128^2 cavity, the 121 x 81 cylinder) the same measurement
-    gives rel. L2 8.5e-8 / 1.7e-6 on u and 5.9e-9 / 5.6e-6 on T."""
+    gives rel. L2 8.5e-8 / 1.7e-6 on u and 5.9e-9 / 5.6e-6 on T.  The
+    float32 path's vacuum limit of Eq. 18 (faces below 1e-6 of the reference
+    density) acts only in the impulsive start's transient: at the converged
+    field every cell's density is far above it, and the float64 path, which
+    has no such limit, keeps the field."""
     from paper_1709_01819_gb300.solver import Solver
     prob = CASES[name]
     m = Solver(prob, "mixed")
@@ -62,5 +66,6 @@ def test_mixed_steady_field_within_1e5_of_fp64(name):
     rel = lambda a, b: np.linalg.norm(a - b) / np.linalg.norm(b)
     eu = rel(mm[:, 1:3], mf[:, 1:3])
     eT = rel(mm[:, 3], mf[:, 3])
-    print(f"{name}: rel. L2 u {eu:.3g}, T {eT:.3g}")
+    print(f"{name}: rel. L2 u {eu:.3g}, T {eT:.3g}, min density {mm[:, 0].min():.3g}")
     assert eu <= 1e-5 and eT <= 1e-5, (eu, eT)
+    assert mm[:, 0].min() > 1e-3 * prob.init[0], mm[:, 0].min()
