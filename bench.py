@@ -327,14 +327,18 @@ def run_batch(args):
     """64 seeded cavities (Kn log-uniform in [1e-3, 10], lid speed in [0.05, 0.3],
     n in {32, 48, 64, 96}, 32 x 32 velocities), mixed precision, autotuned sweep
     tiles, one launch per kernel over all instances, graph-replayed.  A step is
-    one iteration of every instance; the 2.2 GB state exceeds L2."""
+    one iteration of every instance; the 2.2 GB state exceeds L2.  --tune
+    default / an explicit shape replace the autotuner as for one instance."""
     import torch
     from paper_1709_01819_gb300 import build
     from paper_1709_01819_gb300.solver import BatchSolver
     build.build()
     probs = I.batch_c4()
     t0 = time.perf_counter()
-    bs = BatchSolver(probs, args.precision, autotune=True)
+    fixed = None
+    if args.tune not in ("auto", "default"):
+        fixed = {k: int(v) for k, v in (kv.split("=") for kv in args.tune.split(","))}
+    bs = BatchSolver(probs, args.precision, autotune=args.tune == "auto", tuning=fixed)
     setup_s = time.perf_counter() - t0
     bs.iterate(args.warmup)
     torch.cuda.synchronize()
@@ -347,6 +351,11 @@ def run_batch(args):
         torch.cuda.synchronize()
     ms = a.elapsed_time(e)
     cv = bs.cell_velocities
+    peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
+    peak = peaks.get("hbm_gbs", 6800.0)
+    sb = 8 if args.precision == "fp64" else 4
+    ib = ITER_SCALARS * sb * cv  # the whole iteration's algorithmic bytes, all instances
+    ach = ib / (ms / args.steps * 1e-3) / 1e9
     tiles = {}
     for s in bs.solvers:
         t = s.tuning()
@@ -358,7 +367,11 @@ def run_batch(args):
         "dtype": "f32" if args.precision == "mixed" else "f64", "data": "synthetic",
         "config": {"workload": "batch of 64 cavities (seed 170901819)", "instances": len(probs),
                    "cell_velocities": cv, "precision": args.precision, "l2": "state larger than L2",
-                   "autotuned_sweep_tv": tiles, "setup_and_tuning_s": setup_s},
+                   "sweep_tv": tiles, "tuning": args.tune, "setup_and_tuning_s": setup_s},
+        "roofline": {"bound": "hbm", "kernel": "whole iteration, all instances", "achieved": ach, "peak": peak,
+                     "unit": "GB/s", "frac": ach / peak, "traffic": None, "algorithmic_bytes": ib,
+                     "scalars_per_cell_velocity": ITER_SCALARS,
+                     "peak_source": "measured" if peaks else "fallback"},
         "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)

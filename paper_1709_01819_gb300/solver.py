@@ -273,7 +273,10 @@ class BatchSolver:
     once over all instances (idg_batch_*).  Instances may differ in size, gas,
     boundaries and tuning; all use one precision on one device."""
 
-    def __init__(self, problems, precision: str = "mixed", device: int = 0, autotune: bool = False):
+    def __init__(self, problems, precision: str = "mixed", device: int = 0, autotune: bool = False,
+                 tuning: dict = None):
+        """tuning: launch-shape keys of Solver.set_tuning applied to every
+        instance (instead of autotune)."""
         import torch
 
         self.torch = torch
@@ -281,6 +284,8 @@ class BatchSolver:
         self.solvers = [Solver(p, precision, device) for p in problems]
         for s in self.solvers:
             s.init_uniform()
+            if tuning:
+                s.set_tuning(**tuning)
         if autotune:
             # one batch shares the velocities-per-thread of its sweeps: tune
             # the largest instance first and keep its choice for the rest
