@@ -295,6 +295,43 @@ class BatchSolver:
             for s in order[1:]:
                 tuner.tune(s)
         self._make_batch()
+        if autotune and len(self.solvers) > 1:
+            self._tune_sweep_stages()
+
+    def _tune_sweep_stages(self, candidates=(8, 4, 2), iters: int = 4):
+        """The micro sweeps' prefetch depth of the whole batch, timed on the
+        batch itself: one instance alone runs fewer sweep blocks than the SMs
+        hold, where a deeper prefetch pays; a batch runs many waves of them,
+        where the shared memory a shallower one frees buys resident blocks.
+        The instances are back at their uniform start afterwards."""
+        torch = self.torch
+        best = None
+        for st in candidates:
+            try:
+                for s in self.solvers:
+                    s.set_tuning(sweep_stages=st)
+            except B.IdgError:
+                continue
+            self._remake()
+            self.iterate(2)
+            a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            stream = torch.cuda.current_stream(self.device)
+            a.record(stream)
+            self.iterate(iters)
+            e.record(stream)
+            torch.cuda.synchronize(self.device)
+            ms = a.elapsed_time(e)
+            if best is None or ms < best[0]:
+                best = (ms, st)
+        for s in self.solvers:
+            s.set_tuning(sweep_stages=best[1])
+            s.init_uniform()
+        self._remake()
+
+    def _remake(self):
+        B.idg_batch_destroy(self.handle)
+        self.handle = None
+        self._make_batch()
 
     def _make_batch(self):
         self.handle = B.idg_batch_create([s.ctx for s in self.solvers])
