@@ -422,6 +422,19 @@ idg_status idg_adjoint(idg_ctx *ctx, int objective, int side_mask, const int *pa
  * idg_adjoint_workspace_size / idg_adjoint. */
 enum { IDG_ADJ_FIXED_POINT = 0, IDG_ADJ_GMRES = 1 };
 idg_status idg_set_adjoint_solver(idg_ctx *ctx, int method, int restart);
+/* How idg_adjoint linearises the Venkatakrishnan limiter (Eq. 16-17).
+ * IDG_ADJ_LIMITER_EXACT (default): the factor phi of each (cell, velocity,
+ * component) is differentiated with its binding face and extreme neighbour
+ * fixed -- the exact derivative of the iteration where it is smooth.  Near a
+ * local extremum of a velocity's fb+ field, phi's derivative grows like
+ * 1/d (d the extrapolated increment to the binding face), and the exact
+ * linearisation can be unstable where the forward iteration is not.
+ * IDG_ADJ_LIMITER_FROZEN: phi is held at its value at the linearisation
+ * point (its derivative dropped): the gradient of the scheme with phi fixed,
+ * an approximation of the exact one.  Takes effect at the next idg_adjoint;
+ * IDG_ERR_ARG for another mode. */
+enum { IDG_ADJ_LIMITER_EXACT = 0, IDG_ADJ_LIMITER_FROZEN = 1 };
+idg_status idg_set_adjoint_limiter(idg_ctx *ctx, int mode);
 /* The adjoint variables lambda = (lambda_G, lambda_H [ncell][nvel], lambda_W
  * [ncell][4]) left in the workspace by the last idg_adjoint call of this
  * context.  which = 0: the adjoint of the returned gradient (for a closed

@@ -77,6 +77,7 @@ SIGNATURES = [
     ("idg_get_wall", _i, [_vp, _i, _P(_d), _i, _P(_i), _vp]),
     ("idg_adjoint_workspace_size", _i, [_vp, _P(_sz)]),
     ("idg_set_adjoint_solver", _i, [_vp, _i, _i]),
+    ("idg_set_adjoint_limiter", _i, [_vp, _i]),
     ("idg_adjoint_state", _i, [_vp, _vp, _i, _P(_d), _P(_d), _P(_d), _vp]),
     ("idg_adjoint", _i, [_vp, _i, _i, _P(_i), _i, _vp, _sz, _i, _d, _vp, _P(_d), _P(_d), _P(_i), _P(_d)]),
 ]
@@ -278,6 +279,13 @@ IDG_ADJ_FIXED_POINT, IDG_ADJ_GMRES = 0, 1
 
 def idg_set_adjoint_solver(ctx, method, restart=20):
     return check(ctx, lib().idg_set_adjoint_solver(ctx, method, restart))
+
+
+IDG_ADJ_LIMITER_EXACT, IDG_ADJ_LIMITER_FROZEN = 0, 1
+
+
+def idg_set_adjoint_limiter(ctx, mode):
+    return check(ctx, lib().idg_set_adjoint_limiter(ctx, mode))
 
 
 def idg_adjoint_workspace_size(ctx) -> int:

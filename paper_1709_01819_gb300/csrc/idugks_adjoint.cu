@@ -183,7 +183,7 @@ __global__ void k_adj_grad_lin(AParams a)
                 phi = th;
                 ms = m;
                 es = e;
-                A = adj::venkat_d(x) / d;
+                A = a.lim_frozen ? 0.0 : adj::venkat_d(x) / d;
                 B = -x * A;
             }
         }

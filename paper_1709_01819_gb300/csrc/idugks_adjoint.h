@@ -26,6 +26,7 @@ enum { FP_RHO, FP_U, FP_V, FP_RT, FP_TAU, FP_QBX, FP_QBY, FP_QX, FP_QY, FP_A, FP
 struct AParams {
     // sizes and model
     int N, Nv, nf, ni, nj, K, shakhov, limiter;
+    int lim_frozen;    // 1: the limiter factor is held at its linearisation value (no derivative)
     double dt, h, mu_ref, RT_ref, omega, Pr, gam, lusgs_omega, kappa;
     // geometry of the forward context (device, float64 / int)
     const double *area, *dtimp, *fgeo, *ux, *uy, *w;

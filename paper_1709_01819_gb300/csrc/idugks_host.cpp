@@ -78,6 +78,7 @@ struct idg_ctx {
     std::vector<double> hist;  // absolute residuals since the last (re)start
     // adjoint solver: IDG_ADJ_FIXED_POINT or IDG_ADJ_GMRES with restart adj_restart
     int adj_method = 0, adj_restart = 20;
+    int adj_lim_frozen = 0;  // idg_set_adjoint_limiter: 1 holds the limiter factor at the linearisation
     // last idg_adjoint: number of right-hand sides and the mass multiplier
     int adj_nrhs = 0;
     double adj_beta = 0.0;
@@ -2027,6 +2028,15 @@ idg_status idg_set_adjoint_solver(idg_ctx *c, int method, int restart)
     return IDG_OK;
 }
 
+idg_status idg_set_adjoint_limiter(idg_ctx *c, int mode)
+{
+    if (!c) return IDG_ERR_ARG;
+    if (mode != IDG_ADJ_LIMITER_EXACT && mode != IDG_ADJ_LIMITER_FROZEN)
+        return fail(c, IDG_ERR_ARG, "unknown adjoint limiter mode %d", mode);
+    c->adj_lim_frozen = mode == IDG_ADJ_LIMITER_FROZEN;
+    return IDG_OK;
+}
+
 idg_status idg_adjoint(idg_ctx *c, int objective, int side_mask, const int *params, int nparam,
                        void *workspace, size_t bytes, int max_iter, double tol, void *stream, double *J,
                        double *grad, int *iters_done, double *residual)
@@ -2069,6 +2079,7 @@ idg_status idg_adjoint(idg_ctx *c, int objective, int side_mask, const int *para
     idg::AParams base = adjoint_shape(c);
     const KParams &k = c->kp;
     base.K = c->K; base.shakhov = c->model == IDG_SHAKHOV; base.limiter = c->limiter;
+    base.lim_frozen = c->adj_lim_frozen;
     base.dt = k.dt; base.h = k.h; base.mu_ref = k.mu_ref; base.RT_ref = k.RT_ref; base.omega = k.omega;
     base.Pr = k.Pr; base.gam = k.gam; base.lusgs_omega = k.lusgs_omega;
     base.kappa = base.shakhov ? (1.0 - c->Pr) / (c->K + 4) : 0.0;

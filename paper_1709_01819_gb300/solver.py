@@ -159,14 +159,19 @@ class Solver:
         return B.idg_get_wall(self.ctx, side, self.stream)
 
     def adjoint(self, objective: int, side_mask: int, params, max_iter: int = 20000, tol: float = 1e-10,
-                keep_state: bool = False, solver: str = "fixed_point", restart: int = 20):
+                keep_state: bool = False, solver: str = "fixed_point", restart: int = 20,
+                limiter: str = "exact"):
         """Discrete adjoint at the current state (idg_adjoint).  Returns
         (converged, J, dJ/dparams, iterations, relative update); with
         keep_state the adjoint variables stay readable by adjoint_state().
         solver: "fixed_point" (the transposed iteration) or "gmres" (restarted
-        GMRES on the same linear system, domains with a far field)."""
+        GMRES on the same linear system, domains with a far field).
+        limiter: "exact" (the limiter factor differentiated) or "frozen" (held
+        at the converged state: an approximate gradient, idg_set_adjoint_limiter)."""
         B.idg_set_adjoint_solver(self.ctx, B.IDG_ADJ_GMRES if solver == "gmres" else B.IDG_ADJ_FIXED_POINT,
                                  restart)
+        B.idg_set_adjoint_limiter(self.ctx, B.IDG_ADJ_LIMITER_FROZEN if limiter == "frozen"
+                                  else B.IDG_ADJ_LIMITER_EXACT)
         nbytes = B.idg_adjoint_workspace_size(self.ctx)
         ws = self.torch.empty(nbytes + 256, dtype=self.torch.uint8, device=f"cuda:{self.device}")
         aligned = (ws.data_ptr() + 255) & ~255
