@@ -744,7 +744,12 @@ void orc_ls_gradient(const orc_state *s, const double *phi, double *grad2)
 /* Venkatakrishnan limiter of one scalar in one cell, Eq. (16)-(17): the face
  * value is the unlimited extrapolation to each face midpoint; the max and min
  * run over the least-squares neighbours and the cell itself; phi is the
- * minimum over the faces. */
+ * minimum over the faces.  With a smoothing constant K > 0 (the form of the
+ * limiter's source, Venkatakrishnan's steady-convergence paper, that the
+ * paper cites for it) each face's factor is, with D the extrapolated
+ * increment and P the increment to the neighbourhood's max (D > 0) or min
+ * (D < 0), (P^2 + eps^2 + 2 D P) / (P^2 + 2 D^2 + P D + eps^2), eps^2 =
+ * (K h)^3, h = sqrt(area); eps = 0 gives theta(P / D) of Eq. (17). */
 static double limiter_cell(const orc_state *s, int c, const double *val, size_t stride, size_t off,
                            double gx, double gy)
 {
@@ -758,14 +763,19 @@ static double limiter_cell(const orc_state *s, int c, const double *val, size_t 
         if (v < vmin) vmin = v;
     }
     double phi = 1.0;
+    const double Kh = s->p.venkat_k * sqrt(s->area[c]);
+    const double e2 = Kh * Kh * Kh;
     for (int m = 0; m < s->nslot[c]; ++m) {
         const orc_face *F = &s->face[s->cell_face[4 * c + m]];
         int sg = s->cell_sign[4 * c + m];
         double rx = sg > 0 ? F->rLx : F->rRx, ry = sg > 0 ? F->rLy : F->rRy;
         double d = gx * rx + gy * ry;
         double t = 1.0;
-        if (d > 0) t = orc_venkat_theta((vmax - v0) / d);
-        else if (d < 0) t = orc_venkat_theta((vmin - v0) / d);
+        if (d != 0) {
+            double P = d > 0 ? vmax - v0 : vmin - v0;
+            if (e2 > 0) t = (P * P + e2 + 2.0 * d * P) / (P * P + 2.0 * d * d + P * d + e2);
+            else t = orc_venkat_theta(P / d);
+        }
         if (t < phi) phi = t;
     }
     return phi;

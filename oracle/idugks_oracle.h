@@ -53,6 +53,9 @@ typedef struct {
                                 /* linearised diffuse-reflection increment of Eq.     */
                                 /* (34)-(35) from the inner cell's last increment;    */
                                 /* 0: ghost increments are zero (end of Section 2.3)  */
+    double venkat_k;            /* 0: the limiter of Eq. (16)-(17) as printed; K > 0: */
+                                /* Venkatakrishnan's smoothing constant, eps^2 =      */
+                                /* (K h)^3 with h = sqrt(cell area), in the ratio      */
 } orc_problem;
 
 typedef struct orc_state orc_state;

@@ -48,6 +48,7 @@ class _Problem(C.Structure):
         ("n_ucells", C.c_int), ("n_unodes", C.c_int),
         ("ucell_nodes", C.POINTER(C.c_int)), ("uedge_side", C.POINTER(C.c_int)),
         ("implicit_wall", C.c_int),
+        ("venkat_k", C.c_double),
     ]
 
 
@@ -137,6 +138,7 @@ class Oracle:
         p.limiter, p.flags, p.lusgs_omega = prob.limiter, prob.flags, prob.lusgs_omega
         p.relax_sweeps = prob.relax_sweeps
         p.implicit_wall = int(getattr(prob, "implicit_wall", 0))
+        p.venkat_k = float(getattr(prob, "venkat_k", 0.0))
         if getattr(prob, "cell_nodes", None) is not None:
             self._cn = np.ascontiguousarray(prob.cell_nodes, dtype=np.int32)
             self._es = np.ascontiguousarray(prob.edge_side, dtype=np.int32)

@@ -59,6 +59,7 @@ class Problem:
     lusgs_omega: float = 2.0
     relax_sweeps: int = 0          # macroscopic predictor: 0 LU-SGS, n >= 1 n point-relaxation sweeps
     implicit_wall: int = 0         # 1: linearised diffuse-wall ghost increments in the micro sweeps (Eq. 34-35)
+    venkat_k: float = 0.0          # limiter smoothing constant K (eps^2 = (K sqrt(area))^3); 0: Eq. 16-17 as printed
     # unstructured mesh (triangles and quadrilaterals): nodes_x, nodes_y are
     # then flat node arrays, cell_nodes [ncells][4] int (counter-clockwise, -1
     # as the 4th node of a triangle), edge_side [ncells][4] int: boundary group

@@ -261,6 +261,56 @@ def test_limiter_zero_at_a_strict_local_maximum():
     assert lim[c] == 0.0
 
 
+def _uniform_block_k(K, n=12):
+    import dataclasses
+    p = dataclasses.replace(I.cavity(n, nv=4), venkat_k=K)
+    o = O.Oracle(p)
+    cx, cy, _ = o.geometry()
+    interior = np.array([(0 < c % n < n - 1) and (0 < c // n < n - 1) for c in range(n * n)])
+    return o, cx, cy, interior
+
+
+def test_smoothed_limiter_keeps_linear_fields_unlimited():
+    """The smoothing constant (the limiter's source form, eps^2 = (K h)^3)
+    keeps the property of Eq. (17) that a linear field's binding ratio 2
+    gives exactly 1: numerator and denominator both become 8 D^2 + eps^2."""
+    for K in (0.3, 3.0):
+        o, cx, cy, inner = _uniform_block_k(K)
+        for b, c in ((1.3, 0.4), (-0.7, 2.1)):
+            lim = o.limiter(0.2 + b * cx + c * cy)
+            assert np.all(np.abs(lim[inner] - 1.0) < 1e-12), (K, b, c)
+
+
+def test_smoothed_limiter_limits_of_the_constant():
+    """K -> 0 recovers Eq. (16)-(17); K -> infinity switches limiting off;
+    where limiting is active (ratio <= 2) phi does not decrease with K."""
+    v = np.random.default_rng(11).normal(size=144)
+    base = _uniform_block()[0].limiter(v)
+    tiny = _uniform_block_k(1e-7)[0].limiter(v)
+    assert np.allclose(tiny, base, rtol=0, atol=1e-12)
+    huge = _uniform_block_k(1e6)[0].limiter(v)
+    assert np.all(np.abs(huge - 1.0) < 1e-12)
+    prev = base
+    for K in (0.5, 1.0, 2.0, 4.0):
+        cur = _uniform_block_k(K)[0].limiter(v)
+        assert np.all(cur >= prev - 1e-15), K
+        prev = cur
+
+
+def test_smoothed_limiter_at_a_strict_local_maximum_scales_with_k_cubed():
+    """Where Eq. (17) clips to 0 (the cell is its neighbourhood's maximum),
+    the smoothed factor is eps^2 / (2 D^2 + eps^2) ~ (K h)^3 / (2 D^2): it
+    grows as the cube of K for small K."""
+    rng = np.random.default_rng(7)
+    v = rng.uniform(0.0, 0.3, 144)
+    c = 5 * 12 + 6
+    v[c] = 1.0
+    v[c + 1], v[c - 1] = 0.6, 0.1
+    phi = [_uniform_block_k(K)[0].limiter(v)[c] for K in (1e-3, 2e-3)]
+    assert 0.0 < phi[0] < 1e-6
+    assert abs(phi[1] / phi[0] - 8.0) < 1e-5, phi
+
+
 def test_limiter_is_invariant_under_affine_maps():
     o, cx, cy, _ = _uniform_block()
     v = np.random.default_rng(3).normal(size=cx.size)
