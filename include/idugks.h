@@ -142,6 +142,21 @@ enum { IDG_NUM_EXPLICIT = 1 };
 idg_status idg_set_numerics(idg_ctx *ctx, double cfl_imp, double cfl_phys, int limiter,
                             double lusgs_omega, int flags);
 
+/* Smoothing constant K of the Venkatakrishnan limiter (Eq. 16-17, limiter
+ * 1 of idg_set_numerics).  K = 0 (default): the limiter as the paper prints
+ * it, whose factor drops to 0 wherever a cell value is its neighbourhood's
+ * extremum.  K > 0: the form of the limiter's source (Venkatakrishnan's
+ * steady-convergence paper, which the paper cites), each face's factor
+ *     (P^2 + eps^2 + 2 D P) / (P^2 + 2 D^2 + P D + eps^2),
+ * D the unlimited extrapolated increment to the face, P the increment to the
+ * neighbourhood's max (D > 0) or min (D < 0), eps^2 = (K h)^3 with h the
+ * square root of the cell's area; eps = 0 is Eq. 17's theta(P / D).  It
+ * removes the limiter's switching at extrema, which can hold a steady
+ * iteration in a limit cycle (and makes the limiter's derivative bounded for
+ * idg_adjoint); too large a K under-limits shocks.  K >= 0, finite; before
+ * idg_bind_workspace. */
+idg_status idg_set_limiter_smoothing(idg_ctx *ctx, double K);
+
 /* Macroscopic predictor of the implicit iteration (Eq. 28-31).  relax_sweeps
  * 0 (default): the LU-SGS forward and backward sweeps of Eq. (30).
  * relax_sweeps n in 1..64: point relaxation of the same predictor equations,

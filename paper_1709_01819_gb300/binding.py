@@ -78,6 +78,7 @@ SIGNATURES = [
     ("idg_adjoint_workspace_size", _i, [_vp, _P(_sz)]),
     ("idg_set_adjoint_solver", _i, [_vp, _i, _i]),
     ("idg_set_adjoint_limiter", _i, [_vp, _i]),
+    ("idg_set_limiter_smoothing", _i, [_vp, _d]),
     ("idg_adjoint_state", _i, [_vp, _vp, _i, _P(_d), _P(_d), _P(_d), _vp]),
     ("idg_adjoint", _i, [_vp, _i, _i, _P(_i), _i, _vp, _sz, _i, _d, _vp, _P(_d), _P(_d), _P(_i), _P(_d)]),
 ]
@@ -279,6 +280,10 @@ IDG_ADJ_FIXED_POINT, IDG_ADJ_GMRES = 0, 1
 
 def idg_set_adjoint_solver(ctx, method, restart=20):
     return check(ctx, lib().idg_set_adjoint_solver(ctx, method, restart))
+
+
+def idg_set_limiter_smoothing(ctx, K):
+    return check(ctx, lib().idg_set_limiter_smoothing(ctx, float(K)))
 
 
 IDG_ADJ_LIMITER_EXACT, IDG_ADJ_LIMITER_FROZEN = 0, 1

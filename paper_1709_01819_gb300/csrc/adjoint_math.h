@@ -144,6 +144,21 @@ IDG_AD double venkat_d(double x)
     return (-x * x + 4.0 * x + 4.0) / (d * d);
 }
 
+// The limiter's factor at one face with the smoothing constant e2 = eps^2 >
+// 0, phi = N / M with N = P^2 + e2 + 2 D P, M = P^2 + 2 D^2 + P D + e2 (P the
+// increment to the neighbourhood's extremum, D the extrapolated one), and its
+// partial derivatives in P and D
+IDG_AD double venkat_eps(double P, double D, double e2)
+{
+    return (P * P + e2 + 2.0 * D * P) / (P * P + 2.0 * D * D + P * D + e2);
+}
+IDG_AD void venkat_eps_d(double P, double D, double e2, double &dP, double &dD)
+{
+    const double N = P * P + e2 + 2.0 * D * P, M = P * P + 2.0 * D * D + P * D + e2, iM2 = 1.0 / (M * M);
+    dP = ((2.0 * P + 2.0 * D) * M - N * (2.0 * P + D)) * iM2;
+    dD = (2.0 * P * M - N * (4.0 * D + P)) * iM2;
+}
+
 // Euler flux F(W).n and the transposed Jacobian product (dF.n/dW)^T y
 IDG_AD void euler_flux(const double *W, double gam, double nx, double ny, double *F)
 {

@@ -173,18 +173,31 @@ __global__ void k_adj_grad_lin(AParams a)
     double phi = 1.0, A = 0.0, B = 0.0;
     int ms = -1, es = -1;
     if (a.limiter) {
+        // the smoothing constant's eps^2 = (K h)^3, h = sqrt(area) (0: Eq. 16-17)
+        const double e2 = a.venkat_k3 > 0.0 ? a.venkat_k3 * a.area[c] * sqrt(a.area[c]) : 0.0;
         for (int m = 0; m < 4; ++m) {
             const double d = gx * a.crv[8 * c + 2 * m] + gy * a.crv[8 * c + 2 * m + 1];
-            double x = 0.0, th = 1.0;
+            double x = 0.0, th = 1.0, P = 0.0;
             int e = -1;
-            if (d > 0) { x = (vmax - v0) / d; th = adj::venkat(x); e = emax; }
-            else if (d < 0) { x = (vmin - v0) / d; th = adj::venkat(x); e = emin; }
+            if (d > 0) { P = vmax - v0; e = emax; }
+            else if (d < 0) { P = vmin - v0; e = emin; }
+            if (d != 0) {
+                x = P / d;
+                th = e2 > 0 ? adj::venkat_eps(P, d, e2) : adj::venkat(x);
+            }
             if (th < phi) {
                 phi = th;
                 ms = m;
                 es = e;
-                A = a.lim_frozen ? 0.0 : adj::venkat_d(x) / d;
-                B = -x * A;
+                // A = dphi / dP, B = dphi / dD at the binding face
+                if (a.lim_frozen) {
+                    A = B = 0.0;
+                } else if (e2 > 0) {
+                    adj::venkat_eps_d(P, d, e2, A, B);
+                } else {
+                    A = adj::venkat_d(x) / d;
+                    B = -x * A;
+                }
             }
         }
     }

@@ -27,6 +27,7 @@ struct AParams {
     // sizes and model
     int N, Nv, nf, ni, nj, K, shakhov, limiter;
     int lim_frozen;    // 1: the limiter factor is held at its linearisation value (no derivative)
+    double venkat_k3;  // cube of the limiter's smoothing constant (0: Eq. 16-17)
     double dt, h, mu_ref, RT_ref, omega, Pr, gam, lusgs_omega, kappa;
     // geometry of the forward context (device, float64 / int)
     const double *area, *dtimp, *fgeo, *ux, *uy, *w;

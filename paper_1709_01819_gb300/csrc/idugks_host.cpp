@@ -79,6 +79,7 @@ struct idg_ctx {
     // adjoint solver: IDG_ADJ_FIXED_POINT or IDG_ADJ_GMRES with restart adj_restart
     int adj_method = 0, adj_restart = 20;
     int adj_lim_frozen = 0;  // idg_set_adjoint_limiter: 1 holds the limiter factor at the linearisation
+    double venkat_k = 0.0;   // idg_set_limiter_smoothing
     // last idg_adjoint: number of right-hand sides and the mass multiplier
     int adj_nrhs = 0;
     double adj_beta = 0.0;
@@ -1002,6 +1003,16 @@ idg_status idg_set_numerics(idg_ctx *c, double cfl_imp, double cfl_phys, int lim
     return IDG_OK;
 }
 
+idg_status idg_set_limiter_smoothing(idg_ctx *c, double K)
+{
+    if (!c) return IDG_ERR_ARG;
+    if (c->bound) return fail(c, IDG_ERR_STATE, "setters are closed after idg_bind_workspace");
+    if (!(K >= 0.0) || !std::isfinite(K)) return fail(c, IDG_ERR_ARG, "limiter smoothing constant %g", K);
+    c->venkat_k = K;
+    c->built = false;
+    return IDG_OK;
+}
+
 idg_status idg_set_predictor(idg_ctx *c, int relax_sweeps)
 {
     if (!c) return IDG_ERR_ARG;
@@ -1089,6 +1100,7 @@ idg_status idg_bind_workspace(idg_ctx *c, void *dev_ptr, size_t bytes)
     layout(c, c->ws, &k);
     k.N = c->N; k.Nv = c->Nv; k.nf = c->nf; k.ni = c->ni; k.nj = c->nj; k.nvx = c->nvx;
     k.K = c->K; k.shakhov = c->model == IDG_SHAKHOV; k.limiter = c->limiter;
+    k.venkat_k3 = c->venkat_k * c->venkat_k * c->venkat_k;
     k.per_i = c->bc_kind[IDG_IMIN] == IDG_BC_PERIODIC;
     k.per_j = c->bc_kind[IDG_JMIN] == IDG_BC_PERIODIC;
     k.dt = c->dt; k.h = 0.5 * c->dt; k.mu_ref = c->mu_ref; k.RT_ref = c->RT_ref; k.omega = c->omega;
@@ -2080,6 +2092,7 @@ idg_status idg_adjoint(idg_ctx *c, int objective, int side_mask, const int *para
     const KParams &k = c->kp;
     base.K = c->K; base.shakhov = c->model == IDG_SHAKHOV; base.limiter = c->limiter;
     base.lim_frozen = c->adj_lim_frozen;
+    base.venkat_k3 = c->venkat_k * c->venkat_k * c->venkat_k;
     base.dt = k.dt; base.h = k.h; base.mu_ref = k.mu_ref; base.RT_ref = k.RT_ref; base.omega = k.omega;
     base.Pr = k.Pr; base.gam = k.gam; base.lusgs_omega = k.lusgs_omega;
     base.kappa = base.shakhov ? (1.0 - c->Pr) / (c->K + 4) : 0.0;

@@ -47,6 +47,7 @@ struct KParams {
     const void *bdevG, *bdevH;   // [4][Nv] T: boundary Maxwellian minus M_ref (wall: unit density)
     // gas and numerics
     double dt, h, mu_ref, RT_ref, omega, Pr, gam, lusgs_omega;
+    double venkat_k3;  // cube of the limiter's smoothing constant: eps^2 = venkat_k3 * area^(3/2)
     // reference Maxwellian parameters and its discrete moments
     double rho_r, U_r, V_r, RT_r;
     double mref_raw[kRaw];     // raw moments: G: 1,x,y,xx,xy,yy,x|xi|^2,y|xi|^2; H: 1,x,y

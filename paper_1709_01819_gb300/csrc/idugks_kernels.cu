@@ -711,9 +711,25 @@ template <> __device__ __forceinline__ void load4<double>(const double *s, doubl
 // phi = theta(min(2, min_m x_m)): one evaluation of theta instead of four.
 // Selects instead of branches: the sign of d differs between neighbouring
 // velocities.
+// With the smoothing constant (e2 = eps^2 > 0) each face's factor is
+// (P^2 + e2 + 2 D P) / (P^2 + 2 D^2 + P D + e2), P the increment to the
+// neighbourhood's max or min, D the extrapolated one, and the minimum is
+// taken over the four faces (the factor is no function of P / D alone).
 template <class T>
-__device__ __forceinline__ T limit_scalar_sel(const T (&frx)[4], const T (&fry)[4], T v0, T vmax, T vmin, T sx, T sy)
+__device__ __forceinline__ T limit_scalar_sel(const T (&frx)[4], const T (&fry)[4], T v0, T vmax, T vmin, T sx, T sy,
+                                              T e2)
 {
+    if (e2 > (T)0) {
+        T phi = (T)1;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const T d = sx * frx[m] + sy * fry[m];
+            const T P = (d > (T)0 ? vmax : vmin) - v0;
+            const T t = lim_div(P * P + e2 + (T)2 * d * P, P * P + (T)2 * d * d + P * d + e2);
+            phi = (d != (T)0 && t < phi) ? t : phi;
+        }
+        return phi;
+    }
     T xm = (T)2;
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
@@ -769,10 +785,16 @@ __global__ void __launch_bounds__(128) k_cell_grad(Launch L)
         }
     }
     T *gout = (T *)p.grad + 4 * ((size_t)c * p.Nv + k);
+    // the smoothing constant's eps^2 = (K h)^3, h = sqrt(area) (0: Eq. 16-17)
+    T e2 = (T)0;
+    if (p.venkat_k3 > 0.0) {
+        const double a = p.area[c];
+        e2 = (T)(p.venkat_k3 * a * sqrt(a));
+    }
 #pragma unroll
     for (int v = 0; v < 2; ++v) {
-        const T pg = limit_scalar_sel<T>(frx, fry, g0[v], gmax[v], gmin[v], sgx[v], sgy[v]);
-        const T ph = limit_scalar_sel<T>(frx, fry, h0[v], hmax[v], hmin[v], shx[v], shy[v]);
+        const T pg = limit_scalar_sel<T>(frx, fry, g0[v], gmax[v], gmin[v], sgx[v], sgy[v], e2);
+        const T ph = limit_scalar_sel<T>(frx, fry, h0[v], hmax[v], hmin[v], shx[v], shy[v], e2);
         store4<T>(gout + 4 * v, pg * sgx[v], pg * sgy[v], ph * shx[v], ph * shy[v]);
     }
 }

@@ -33,6 +33,8 @@ def configure(ctx, prob: Problem, explicit: bool = False):
         B.idg_set_predictor(ctx, prob.relax_sweeps)
     if getattr(prob, "implicit_wall", 0):
         B.idg_set_implicit_wall(ctx, 1)
+    if getattr(prob, "venkat_k", 0.0):
+        B.idg_set_limiter_smoothing(ctx, prob.venkat_k)
 
 
 class Solver:

@@ -127,6 +127,15 @@ int main()
         worst = std::max(worst, rel((venkat(x + eps) - venkat(x - eps)) / (2 * eps), venkat_d(x)));
     }
     printf("venkat_d %.3e\n", worst);
+    // the smoothed factor's partial derivatives
+    worst = 0;
+    for (int t = 0; t < 200; ++t) {
+        double P = U(-2, 2), D = U(0.05, 2) * (t & 1 ? 1 : -1), e2 = U(1e-4, 1), dP, dD;
+        venkat_eps_d(P, D, e2, dP, dD);
+        worst = std::max({worst, rel((venkat_eps(P + eps, D, e2) - venkat_eps(P - eps, D, e2)) / (2 * eps), dP),
+                          rel((venkat_eps(P, D + eps, e2) - venkat_eps(P, D - eps, e2)) / (2 * eps), dD)});
+    }
+    printf("venkat_eps_d %.3e\n", worst);
     // Euler flux Jacobian, transposed
     worst = 0;
     for (int t = 0; t < 200; ++t) {

@@ -18,7 +18,7 @@ def test_local_vjps_match_central_differences():
         out = subprocess.check_output([exe], text=True)
     errs = {line.split()[0]: float(line.split()[1]) for line in out.strip().splitlines()}
     assert set(errs) == {"prim_vjp", "tau_vjp", "eq_vjp_bgk", "eq_vjp_shakhov", "bnd_vjp", "heat_uv_vjp",
-                         "venkat_d", "euler_jacT"}
+                         "venkat_d", "venkat_eps_d", "euler_jacT"}
     for name, e in errs.items():
         # central differences with step 1e-6 on O(1) inputs: ~1e-9 truncation + rounding
         assert e < 1e-6, (name, e)
