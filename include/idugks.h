@@ -330,10 +330,11 @@ idg_status idg_iterate_profiled(idg_ctx *ctx, void *stream, double *kernel_ms);
  * stream by events.  IDG_TUNE_MACRO_KIND: the macroscopic LU-SGS sweeps of a
  * structured block (Eq. 30) with one thread per line of cells of the shorter
  * axis (1, default for IDG_MIXED) or with two threads per cell of each i+j
- * hyperplane (0, default for IDG_FP64); setting it re-derives the macroscopic prefetch depth (8
- * where the records fit in shared memory, else 4, else 2);
- * the same lexicographic dependency order, results equal up to the rounding
- * order of a cell's neighbour sum; all instances of a batch must agree. */
+ * hyperplane (0, default for IDG_FP64); setting it re-derives the
+ * macroscopic prefetch depth (8 where the records fit in shared memory, else
+ * 4, else 2); the same lexicographic dependency order, results equal up to
+ * the rounding order of a cell's neighbour sum; all instances of a batch
+ * must agree. */
 enum { IDG_TUNE_SWEEP_TV = 1, IDG_TUNE_SWEEP_STAGES = 2, IDG_TUNE_MACRO_STAGES = 3, IDG_TUNE_GRAPH = 4,
        IDG_TUNE_SWEEP_VPT = 5, IDG_TUNE_MACRO_KIND = 6 };
 idg_status idg_set_tuning(idg_ctx *ctx, int key, int value);

@@ -331,7 +331,8 @@ class BatchSolver:
             if best is None or ms < best[0]:
                 best = (ms, st)
         for s in self.solvers:
-            s.set_tuning(sweep_stages=best[1])
+            if best is not None:
+                s.set_tuning(sweep_stages=best[1])
             s.init_uniform()
         self._remake()
 
