@@ -342,7 +342,13 @@ class BatchSolver:
         self._make_batch()
 
     def _make_batch(self):
-        self.handle = B.idg_batch_create([s.ctx for s in self.solvers])
+        # largest wavefront first: every batched kernel lays its blocks out in
+        # the batch's instance order and the hardware dispatches them in
+        # block order, so the micro sweeps' longest tiles (ni + nj - 1 steps)
+        # start first and the shortest fill the last wave
+        self._order = sorted(range(len(self.solvers)),
+                             key=lambda i: -(self.solvers[i].prob.ni + self.solvers[i].prob.nj))
+        self.handle = B.idg_batch_create([self.solvers[i].ctx for i in self._order])
         nbytes = B.idg_batch_workspace_size(self.handle)
         self.workspace = self.torch.empty(nbytes + 256, dtype=self.torch.uint8, device=f"cuda:{self.device}")
         aligned = (self.workspace.data_ptr() + 255) & ~255
@@ -359,7 +365,10 @@ class BatchSolver:
     def iterate(self, max_iter: int, tol: float = 0.0):
         """Returns (all converged, iterations launched, largest relative residual, per-instance flags)."""
         st, n, r, conv = B.idg_batch_iterate(self.handle, len(self.solvers), max_iter, tol, self.stream)
-        return st == B.IDG_OK, n, r, conv
+        flags = [False] * len(conv)
+        for j, i in enumerate(self._order):
+            flags[i] = conv[j]
+        return st == B.IDG_OK, n, r, flags
 
     def __del__(self):
         h = getattr(self, "handle", None)
