@@ -205,7 +205,10 @@ idg_status idg_init_uniform(idg_ctx *ctx, double rho, double u, double v, double
 
 /* Replace / read the state.  G, H: host [ncell][nvel] float64 of f~ (Eq. 10),
  * W: host [ncell][4] float64 conservative variables (Eq. 4).  Any pointer may
- * be NULL in idg_get_state. */
+ * be NULL in idg_get_state.  idg_set_state reads page-locked host arrays that
+ * the CUDA runtime maps into the device's address space (cudaHostAlloc,
+ * cudaHostRegister) in place, from its conversion kernel; other host memory
+ * is first copied to a device staging buffer.  The result is the same. */
 idg_status idg_set_state(idg_ctx *ctx, const double *G, const double *H, const double *W,
                          void *stream);
 idg_status idg_get_state(idg_ctx *ctx, double *G, double *H, double *W, void *stream);

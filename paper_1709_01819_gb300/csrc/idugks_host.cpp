@@ -1232,14 +1232,28 @@ idg_status idg_set_state(idg_ctx *c, const double *G, const double *H, const dou
     cudaStream_t st = (cudaStream_t)stream;
     size_t n = (size_t)c->N * c->Nvu;
     cudaError_t e;
-    // stage G and H as float64 in the face-flux buffer (large enough: nf >= 2N)
-    double *dG = c->stage, *dH = c->stage + n;
-    if (2 * n * sizeof(double) > c->stage_bytes) return fail(c, IDG_ERR_STATE, "staging buffer too small");
-    if ((e = cudaMemcpyAsync(dG, G, n * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess) return cuda_fail(c, e, "H2D G");
-    if ((e = cudaMemcpyAsync(dH, H, n * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess) return cuda_fail(c, e, "H2D H");
+    // page-locked host arrays that the runtime maps into the device's address
+    // space are read in place by the conversion kernel over the host link;
+    // other host memory is staged as float64 in the face-flux buffer (large
+    // enough: nf >= 2N)
+    const double *gG = nullptr, *gH = nullptr;
+    cudaPointerAttributes aG{}, aH{};
+    if (cudaPointerGetAttributes(&aG, G) == cudaSuccess && aG.type == cudaMemoryTypeHost && aG.devicePointer &&
+        cudaPointerGetAttributes(&aH, H) == cudaSuccess && aH.type == cudaMemoryTypeHost && aH.devicePointer) {
+        gG = (const double *)aG.devicePointer;
+        gH = (const double *)aH.devicePointer;
+    } else {
+        (void)cudaGetLastError();  // a query of plain host memory leaves no error behind
+        double *dG = c->stage, *dH = c->stage + n;
+        if (2 * n * sizeof(double) > c->stage_bytes) return fail(c, IDG_ERR_STATE, "staging buffer too small");
+        if ((e = cudaMemcpyAsync(dG, G, n * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess) return cuda_fail(c, e, "H2D G");
+        if ((e = cudaMemcpyAsync(dH, H, n * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess) return cuda_fail(c, e, "H2D H");
+        gG = dG;
+        gH = dH;
+    }
     if ((e = cudaMemcpyAsync(c->kp.W, W, (size_t)c->N * 32, cudaMemcpyHostToDevice, st)) != cudaSuccess)
         return cuda_fail(c, e, "H2D W");
-    int rc = idg::launch_to_dev(c->kp, c->precision == IDG_FP64, dG, dH, c->Nvu, st);
+    int rc = idg::launch_to_dev(c->kp, c->precision == IDG_FP64, gG, gH, c->Nvu, st);
     if (rc) return cuda_fail(c, (cudaError_t)rc, "to_dev");
     if ((e = cudaMemsetAsync(c->kp.wallok, 0, sizeof(int), st)) != cudaSuccess) return cuda_fail(c, e, "wallok");
     // a new state clears a divergence recorded by an earlier run
